@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark: CG iterations/s of a full 512x512 regularized spiral
+reconstruction on GB300 (one JSON line on stdout).
+
+One step = the whole hot path on one synthetic acquisition, through the C ABI
+with inputs already resident in HBM:
+    set_trajectory_dev  (fixed-point trajectory, G build, kernel spectrum)
+    set_data_dev        (||s||^2, D = H^H s)
+    solve_dev           (50 Polak-Ribiere CG iterations on the Toeplitz form)
+value = 50 * steps / (sum of per-step device times); the L2 cache is flushed
+(256 MB write) before every timed step.  e2e repeats the step through the
+host-pointer API (pinned host buffers, copies inside the timed region).
+
+Workload (512x512, the metric's configuration): ellipses x smooth complex
+phase + 40 bars + texture, Archimedean spiral 32 x 4096 (L = 131072), 30 dB
+noise, Huber phi alpha 0.05, lambda 0.05, M = 1024, 50 iterations, seed 3.
+
+--impl reference times the FP64 CPU oracle (direct NUDFT form of the same
+minimiser) on a bounded sample of the same workload, on the host cores.
+Under torchrun every rank runs its own reconstructions (replicas; the
+reconstructions are independent), value = all ranks' iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG iters/s at 512^2 (mixed-prec vs FP32 plain, <=1e-3 err); p50/p99 latency"
+UNIT = "iters/s"
+ITERS = 50
+
+
+def workload(seed=3):
+    from paper_0908_3252_gb300 import synth
+    N, I, S = 512, 32, 4096
+    g = synth.rng(seed)
+    f_true = synth.phantom(N, "edges_texture", g)
+    kx, ky = synth.spiral(N, I, S, "archimedean")
+    return dict(N=N, M=1024, kx=kx, ky=ky, f_true=f_true, g=g, snr=30.0,
+                lambda1=0.05, alpha1=0.05, lambda0=0.0, alpha0=0.05, phi=0,
+                name=f"512x512 edges+texture phantom, Archimedean spiral {I}x{S} (L={I * S}), "
+                     f"30 dB, Huber a=0.05 l=0.05, M=1024, {ITERS} CG iters")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def clocks_start():
+    try:
+        f = open(os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else os.devnull, "w")
+    except OSError:
+        f = open(os.devnull, "w")
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return None, f
+    return proc, f
+
+
+def clocks_stop(proc, f, gpu_index):
+    if proc is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    proc.terminate()
+    try:
+        out, _ = proc.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out, _ = proc.communicate()
+    f.write(out)
+    f.close()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            if int(parts[0]) != gpu_index:
+                continue
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+def oracle_sample(w, budget_s=12.0):
+    """Times the FP64 oracle's NUDFTs on a bounded sample of the workload and
+    extrapolates its CG iterations/s: the oracle minimiser does, per
+    iteration, two forward products (H d, H f) and one adjoint (the gradient),
+    each N^2 L phase terms; plus one forward and one adjoint to start."""
+    from oracle import oracle as O
+    N, L = w["N"], w["kx"].shape[0]
+    f = w["f_true"]
+    rs = np.random.default_rng(0)
+    r = (rs.standard_normal(L) + 1j * rs.standard_normal(L))
+
+    def t_forward(ls):
+        idx = np.linspace(0, L - 1, ls).astype(np.int64)
+        t0 = time.perf_counter()
+        O.forward(w["kx"][idx], w["ky"][idx], f)
+        return (time.perf_counter() - t0) * L / ls
+
+    def t_adjoint(ps):
+        pix = rs.integers(0, N * N, ps)
+        t0 = time.perf_counter()
+        O.adjoint_at(w["kx"], w["ky"], r, N, (pix // N).astype(np.int32), (pix % N).astype(np.int32))
+        return (time.perf_counter() - t0) * (N * N) / ps
+
+    cores = O.num_threads()
+    # calibrate on a tiny sample, then size each leg to ~budget/2
+    tf = t_forward(cores)
+    ta = t_adjoint(cores)
+    ls = int(max(cores, min(L, (budget_s / 2) / max(tf / L, 1e-12))))
+    ps = int(max(cores, min(N * N, (budget_s / 2) / max(ta / (N * N), 1e-12))))
+    TF = t_forward(ls)
+    TA = t_adjoint(ps)
+    total = ITERS * (2 * TF + TA) + (TF + TA)
+    return dict(value=ITERS / total, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"oracle FP64 direct NUDFT: forward on {ls} of {L} samples and adjoint on "
+                       f"{ps} of {N * N} pixels, extrapolated to {ITERS} iterations "
+                       f"(2 forward + 1 adjoint per iteration, +1 of each to start): "
+                       f"{total:.3e} s per reconstruction")
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    w = workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, budget_s=3.0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * ITERS / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU leg
+
+def run_ours(args):
+    import torch
+    from paper_0908_3252_gb300 import build, spirec, synth
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    spirec.load()
+
+    prec = {"fp32": spirec.SPIREC_FP32, "fp16x3": spirec.SPIREC_MIXED_FP16X3,
+            "bf16x3": spirec.SPIREC_MIXED_BF16X3}[args.precision]
+    w = workload(seed=3 + rank)
+    N, M = w["N"], w["M"]
+    L = w["kx"].shape[0]
+    stream = torch.cuda.Stream(device=dev)
+    h = spirec.spirec_plan_create(N, L, M, prec, stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        kx_d = torch.from_numpy(w["kx"]).to(dev)
+        ky_d = torch.from_numpy(w["ky"]).to(dev)
+        # simulate the data with the exact forward model on the GPU
+        spirec.spirec_set_trajectory_dev(h, kx_d, ky_d)
+        f_d = torch.from_numpy(w["f_true"].astype(np.complex64)).to(dev)
+        y_d = torch.zeros(L, dtype=torch.complex64, device=dev)
+        spirec.spirec_forward_dev(h, f_d, y_d)
+        y = y_d.cpu().numpy().astype(np.complex128)
+        s = synth.add_noise(y, w["snr"], w["g"]).astype(np.complex64)
+        s_d = torch.from_numpy(s).to(dev)
+        spirec.spirec_set_reg(h, w["lambda1"], w["alpha1"], w["lambda0"], w["alpha0"], w["phi"])
+        x_d = torch.zeros((N, N), dtype=torch.complex64, device=dev)
+        J_d = torch.zeros(ITERS + 1, dtype=torch.float64, device=dev)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+        def step():
+            spirec.spirec_set_trajectory_dev(h, kx_d, ky_d)
+            spirec.spirec_set_data_dev(h, s_d)
+            spirec.spirec_solve_dev(h, None, ITERS, x_d, J_d)
+
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        spirec.spirec_timing(h, 1)
+        l0 = spirec.spirec_launch_count(h)
+        proc, cf = clocks_start()
+        evs = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        clocks = clocks_stop(proc, cf, torch.cuda.current_device())
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = spirec.spirec_launch_count(h) - l0
+        stages = spirec.spirec_timing_read(h)
+        spirec.spirec_timing(h, 0)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        J = J_d.cpu().numpy()
+        x_gpu = x_d.cpu().numpy()
+
+    t_s = ms / 1000.0
+    if ws > 1:
+        tt = torch.tensor([t_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_s = float(tt.item())
+    value = ws * ITERS * args.steps / t_s
+
+    # ---- end to end through the host-pointer API (pinned buffers)
+    kx_h = torch.from_numpy(w["kx"]).pin_memory().numpy()
+    ky_h = torch.from_numpy(w["ky"]).pin_memory().numpy()
+    s_h = torch.from_numpy(s).pin_memory().numpy()
+    xo = torch.zeros((N, N), dtype=torch.complex64).pin_memory().numpy()
+    Jo = torch.zeros(ITERS + 1, dtype=torch.float64).pin_memory().numpy()
+    lib = spirec.load()
+    import ctypes
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        spirec._check(lib.spirec_set_trajectory(h, ctypes.c_void_p(kx_h.ctypes.data),
+                                                ctypes.c_void_p(ky_h.ctypes.data)))
+        spirec._check(lib.spirec_set_data(h, ctypes.c_void_p(s_h.ctypes.data)))
+        spirec._check(lib.spirec_solve(h, None, ITERS, ctypes.c_void_p(xo.ctypes.data),
+                                       ctypes.c_void_p(Jo.ctypes.data)))
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_t = sum(e2e_times)
+    if ws > 1:
+        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_t = float(tt.item())
+    e2e_value = ws * ITERS * args.steps / e2e_t
+    spirec.spirec_plan_destroy(h)
+
+    # ---- FP32 plain path on the same workload (the metric's comparison)
+    extra = {}
+    if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
+        h2 = spirec.spirec_plan_create(N, L, M, spirec.SPIREC_FP32, stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            spirec.spirec_set_reg(h2, w["lambda1"], w["alpha1"], w["lambda0"], w["alpha0"], w["phi"])
+            x2 = torch.zeros_like(x_d)
+            J2 = torch.zeros_like(J_d)
+            tt = []
+            for i in range(2):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                spirec.spirec_set_trajectory_dev(h2, kx_d, ky_d)
+                spirec.spirec_set_data_dev(h2, s_d)
+                spirec.spirec_solve_dev(h2, None, ITERS, x2, J2)
+                e1.record(stream)
+                tt.append((e0, e1))
+            torch.cuda.synchronize()
+            t2 = tt[1][0].elapsed_time(tt[1][1]) / 1000.0
+            xf = x2.cpu().numpy()
+        spirec.spirec_plan_destroy(h2)
+        extra["fp32_plain_value"] = ITERS / t2
+        extra["mixed_vs_fp32_rel_l2"] = float(np.linalg.norm(x_gpu - xf) / np.linalg.norm(xf))
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant stage
+    pk = peaks()
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms, dom_n = stages[dom]
+    avg_ms = dom_ms / max(dom_n, 1)
+    if dom == "gram":
+        flops = 8.0 * N * (2 * N - 1) * L
+        achieved = flops / (avg_ms / 1000.0) / 1e12
+        if prec == spirec.SPIREC_FP32:
+            sm_max = (pk or {}).get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "gram (FP32 CUDA cores)",
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        else:
+            peak = (pk or {}).get("bf16_tflops", 1900.0)
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "gram (tcgen05 FP16x3)",
+                    "peak_source": "measured bf16 burst (fp16 dense rate equal)" if pk else "fallback"}
+    elif dom == "iterations":
+        bytes_ = 160.0 * N * N * ITERS
+        achieved = bytes_ / (avg_ms / 1000.0) / 1e9
+        peak = (pk or {}).get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "CG iteration loop",
+                "peak_source": "measured" if pk else "fallback"}
+    else:
+        flops = 8.0 * N * N * L
+        achieved = flops / (avg_ms / 1000.0) / 1e12
+        peak = (pk or {}).get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom}
+    roof["stage_ms_per_step"] = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
+
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        cpu = oracle_sample(w, budget_s=args.cpu_budget)
+
+    dtype = {spirec.SPIREC_FP32: "f32", spirec.SPIREC_MIXED_FP16X3: "fp16x3+f32",
+             spirec.SPIREC_MIXED_BF16X3: "bf16x3+f32"}[prec]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": w["name"], "precision": args.precision, "iters_per_step": ITERS,
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{ws}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(16 * L + 8 * L),
+                "d2h_bytes_per_step": int(8 * N * N + 8 * (ITERS + 1) + 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "J_first_last": [float(J[0]), float(J[-1])],
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("SPIREC_BENCH_PRECISION", "fp16x3"),
+                    choices=["fp32", "fp16x3", "bf16x3"])
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

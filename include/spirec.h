@@ -1,0 +1,196 @@
+/*
+ * spirec.h -- C ABI of the GB300 regularized spiral-MRI reconstruction library
+ * (libspirec.so).
+ *
+ * The library minimises the criterion of section 3.3 of Boubertakh et al.,
+ * "Regularized Reconstruction of MR Images from Spiral Acquisitions":
+ *
+ *     J(f) = ||s - H f||^2 + lambda1 Omega1(f) + lambda0 Omega0(f)
+ *
+ * with the exact, interpolation-free Fourier operator of Eq. ModDirect,
+ *
+ *     (H f)_l = (1/N) sum_{n,m=0}^{N-1} f[n][m] exp(+i 2 pi (kx_l m + ky_l n)),
+ *
+ * through the rewriting of section 3.4 (Eq. NewCritLS): the data enter once as
+ * D = H^H s (Eq. AnnMatGD), the trajectory once as G (Eq. AnnMatG), and every
+ * iteration of the Polak-Ribiere conjugate gradient runs in the image domain,
+ * with H^H H applied as a zero-padded M x M FFT convolution by conj(G).
+ *
+ * Conventions (every entry point):
+ *   - Images f[n][m] are N x N, row-major (f[n*N + m]); n is the row index and
+ *     pairs with ky, m the column index and pairs with kx (Eq. ModDirect).
+ *   - Complex arrays are interleaved (re, im) float32: an image is 2*N*N floats,
+ *     a data vector 2*L floats.
+ *   - Trajectories are float64 arrays kx[L], ky[L] in cycles/pixel, every value
+ *     in [-0.5, 0.5] (section 2).
+ *   - Gradients are dJ/dRe f + i dJ/dIm f, so the data-term gradient is
+ *     2 (T f - D) with T = H^H H (section 3.4, Appendix B).
+ *   - Every function returns a spirec_status; none aborts or traps the GPU.
+ *     On failure spirec_last_error() gives a message (thread-local).
+ *   - Functions without the _dev suffix take HOST pointers: the library copies
+ *     inputs in and results out and returns after the copy-out finished.
+ *     Functions with the _dev suffix take DEVICE pointers (current device),
+ *     enqueue their work on the plan's stream and return without waiting; the
+ *     caller keeps those buffers alive until spirec_sync() or a later
+ *     stream-ordered use.
+ *   - The caller owns every array it passes; the plan owns all device state it
+ *     allocates (trajectory, G, the kernel spectrum, D, iterates, scratch) until
+ *     spirec_plan_destroy().  A plan is not thread-safe: one host thread at a
+ *     time.
+ */
+#ifndef SPIREC_H
+#define SPIREC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spirec_plan_s* spirec_plan;
+
+typedef enum {
+    SPIREC_OK = 0,
+    SPIREC_EINVAL = -1,      /* bad argument: size, |k| > 0.5, NaN, unknown enum   */
+    SPIREC_ENOMEM = -2,      /* device or host allocation failed                   */
+    SPIREC_ECUDA = -3,       /* a CUDA runtime call failed                         */
+    SPIREC_ESTATE = -4,      /* call out of order, e.g. solve before set_data      */
+    SPIREC_EBUSY = -5,       /* resource budget exceeded                           */
+    SPIREC_ETIMEOUT = -6,    /* a bounded device wait ran out                      */
+    SPIREC_ENUMERIC = -7,    /* NaN or Inf met in the criterion                    */
+    SPIREC_EUNSUPPORTED = -8 /* size or mode this build does not handle            */
+} spirec_status;
+
+/* Arithmetic of the trajectory contractions (G, D and H f).  The Toeplitz FFT,
+ * the penalty and the CG vectors are FP32 in every mode; CG scalars are FP64.
+ *   SPIREC_FP32         plain FP32 CUDA-core contraction.
+ *   SPIREC_MIXED_FP16X3 tcgen05 tensor cores, each phase split into FP16 hi+lo,
+ *                       products hi*hi + hi*lo + lo*hi, FP32 accumulation.
+ *   SPIREC_MIXED_BF16X3 the same with BF16 hi+lo. */
+typedef enum {
+    SPIREC_FP32 = 0,
+    SPIREC_MIXED_FP16X3 = 1,
+    SPIREC_MIXED_BF16X3 = 2
+} spirec_precision;
+
+/* Penalty phi_alpha(r), r = |z| the modulus of a complex difference or pixel.
+ *   HUBER       r^2 if r <= alpha, else 2 alpha r - alpha^2   (section 3.3)
+ *   HYPERBOLIC  2 alpha (sqrt(alpha^2 + r^2) - alpha)         (not in the paper)
+ *   QUADRATIC   r^2 (Hunt's phi, section 3.3)                              */
+typedef enum {
+    SPIREC_PHI_HUBER = 0,
+    SPIREC_PHI_HYPERBOLIC = 1,
+    SPIREC_PHI_QUADRATIC = 2
+} spirec_phi;
+
+/* Create a plan for an N x N image and L k-space samples.
+ *   M          Toeplitz embedding grid side; 0 selects the smallest supported
+ *              M >= 2N-1 (M = 2N for the usual sizes).  M must be >= 2N-1 and
+ *              factor into 2, 3 and 5.  Sections 3.4 and Appendix B: the
+ *              convolution by conj(G) is linear, so the FFT grid must hold the
+ *              (2N-1)^2 lags without wrap-around.
+ *   precision  spirec_precision.
+ *   stream     cudaStream_t the plan orders its work after and before (NULL:
+ *              the legacy default stream).  Internally the plan works on its
+ *              own stream, joined to this one with events.
+ *   kx, ky     optional HOST trajectory (L values each); NULL defers it to
+ *              spirec_set_trajectory().
+ * Allocates all device memory the plan needs; SPIREC_ENOMEM if that fails.
+ * Valid sizes: 2 <= N <= 2048, 1 <= L <= 2^31. */
+int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_t precision,
+                       void* stream, const double* kx, const double* ky);
+
+/* Release every device resource of the plan.  NULL is accepted. */
+int spirec_plan_destroy(spirec_plan plan);
+
+/* Load a trajectory (L points) and build, once per trajectory:
+ *   G_{u,v} = (1/N^2) sum_l exp(+i2pi(kx_l u + ky_l v)) for u in [0, N-1],
+ *   v in [1-N, N-1] (Eq. AnnMatG; the other half is G_{-u,-v} = conj G_{u,v}),
+ *   and the real spectrum of the M x M circulant that holds conj(G).
+ * Each k is reduced exactly: it is stored as a 64-bit fixed-point fraction of a
+ * cycle, so k * index mod 1 is exact before the trig call.
+ * SPIREC_EINVAL if any |k| > 0.5 or a value is not finite.  Invalidates D. */
+int spirec_set_trajectory(spirec_plan plan, const double* kx, const double* ky);
+int spirec_set_trajectory_dev(spirec_plan plan, const double* kx, const double* ky);
+
+/* Load data s (2L floats) and compute, once per data set,
+ *   D[n][m] = (1/N) sum_l s_l exp(-i2pi(kx_l m + ky_l n))   (Eq. AnnMatGD)
+ * and ||s||^2 in FP64.  SPIREC_ESTATE without a trajectory. */
+int spirec_set_data(spirec_plan plan, const float* s);
+int spirec_set_data_dev(spirec_plan plan, const float* s);
+
+/* Set R(f) = lambda1 Omega1(f) + lambda0 Omega0(f) (section 3.3):
+ *   Omega1 = sum phi_alpha1(|f[n+1][m]-f[n][m]|) + sum phi_alpha1(|f[n][m+1]-f[n][m]|)
+ *            (free boundary: N(N-1) differences per direction),
+ *   Omega0 = sum phi_alpha0(|f[n][m]|).
+ * lambdas >= 0, alphas > 0 (alphas are unused by the quadratic phi). */
+int spirec_set_reg(spirec_plan plan, double lambda1, double alpha1, double lambda0,
+                   double alpha0, int32_t phi);
+
+/* Run `iters` iterations of the pseudo-conjugate gradient with the
+ * Polak-Ribiere correction (section 3.3) from x0:
+ *   d0 = -grad J(x0); per iteration three majorize-minimize steps on
+ *   h(t) = J(f + t d) from t = 0, f += t d, beta = max(0, Re<g',g'-g>/<g,g>),
+ *   d = -g' + beta d, and d = -g' when Re<g', d> >= 0.
+ * x0: 2N^2 floats or NULL (zeros).  x_out: 2N^2 floats.  J_hist: iters+1
+ * doubles (J(x0), then J after each iteration) or NULL.  iters >= 0.
+ * SPIREC_ESTATE before set_data and set_reg; SPIREC_ENUMERIC if J is not
+ * finite at the end. */
+int spirec_solve(spirec_plan plan, const float* x0, int32_t iters, float* x_out, double* J_hist);
+/* Device-pointer variant; J_hist is a DEVICE array here.  The numeric check
+ * is left to the caller (J_hist). */
+int spirec_solve_dev(spirec_plan plan, const float* x0, int32_t iters, float* x_out,
+                     double* J_hist);
+
+/* ---- operator access (device pointers, enqueued on the plan's stream) ---- */
+
+/* y = H x (Eq. ModDirect): x 2N^2 floats, y 2L floats.  Needs a trajectory. */
+int spirec_forward_dev(spirec_plan plan, const float* x, float* y);
+/* x = H^H y: y 2L floats, x 2N^2 floats (Eq. AnnMatGD with s = y). */
+int spirec_adjoint_dev(spirec_plan plan, const float* y, float* x);
+/* Copy G's half: 2 * N * (2N-1) floats, entry (u, v) at [u*(2N-1) + v+N-1]. */
+int spirec_gram_dev(spirec_plan plan, float* G);
+/* Copy the real kernel spectrum, M*M floats, [ky*M + kx] (unnormalised DFT of
+ * the circulant c[v mod M][u mod M] = conj G_{u,v}, divided by M^2). */
+int spirec_kernel_spectrum_dev(spirec_plan plan, float* C);
+/* Copy D (2N^2 floats).  Needs set_data. */
+int spirec_data_adjoint_dev(spirec_plan plan, float* D);
+/* Tx = H^H H x by the M x M zero-padded FFT (section 3.4): 2N^2 floats each. */
+int spirec_toeplitz_dev(spirec_plan plan, const float* x, float* Tx);
+/* J(x) through the rewritten form (Eq. NewCritLS plus R) and g = grad J(x)
+ * (g: 2N^2 floats, device).  J is written to *J_host after a stream sync.
+ * Needs set_data and set_reg. */
+int spirec_objective_grad_dev(spirec_plan plan, const float* x, double* J_host, float* g);
+
+/* Wait for all work of the plan. */
+int spirec_sync(spirec_plan plan);
+
+/* Plan facts: any pointer may be NULL. */
+int spirec_plan_info(spirec_plan plan, int32_t* N, int64_t* L, int32_t* M, int32_t* precision,
+                     size_t* device_bytes);
+
+/* Kernel timing with CUDA events recorded on the plan's own stream, for the
+ * benchmark.  enable != 0 starts recording (and zeroes the totals).
+ * spirec_timing_read returns, per stage, the summed milliseconds and launch
+ * counts since enable: out_ms/out_count have SPIREC_NUM_STAGES entries in
+ * the order gram, spectrum, adjoint_d, iterations.  Syncs the plan. */
+#define SPIREC_NUM_STAGES 4
+int spirec_timing(spirec_plan plan, int32_t enable);
+int spirec_timing_read(spirec_plan plan, double* out_ms, int64_t* out_count);
+
+/* Number of CUDA kernels the plan has launched so far (a CUDA-graph replay
+ * counts each of its kernel nodes).  Memory copies and sets are not kernels. */
+int spirec_launch_count(spirec_plan plan, int64_t* count);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* spirec_last_error(void);
+
+/* Library version string. */
+const char* spirec_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIREC_H */

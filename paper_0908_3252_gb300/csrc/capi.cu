@@ -1,0 +1,793 @@
+// capi.cu -- the C ABI of libspirec.so (declared in include/spirec.h): plan
+// lifetime, argument checks, stream joins, the solve driver and its CUDA
+// graph.  Every compute step runs in the kernels of the other .cu files.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.cuh"
+
+namespace spirec {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    if (e == cudaErrorMemoryAllocation) return SPIREC_ENOMEM;
+    return SPIREC_ECUDA;
+}
+
+namespace {
+
+// k * 2^64 mod 2^64 as a signed 64-bit integer; flags |k| > 0.5 or non-finite.
+__global__ void k_traj_fixed(const double* __restrict__ kx, const double* __restrict__ ky,
+                             int64_t L, int64_t* __restrict__ kxq, int64_t* __restrict__ kyq,
+                             int* flag)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L;
+         l += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const double k = c == 0 ? kx[l] : ky[l];
+            int64_t q = 0;
+            if (!(fabs(k) <= 0.5)) {  // also catches NaN
+                atomicOr(flag, 1);
+            } else {
+                double t = k * 18446744073709551616.0;  // exact: power-of-two scaling
+                if (t >= 9223372036854775808.0) t -= 18446744073709551616.0;
+                q = __double2ll_rn(t);
+            }
+            if (c == 0) kxq[l] = q;
+            else kyq[l] = q;
+        }
+    }
+}
+
+// out[ky*M + kx] = Chat[kx*M + ky]
+__global__ void k_transpose_real(const float* __restrict__ in, int M, float* __restrict__ out)
+{
+    const int64_t MM = (int64_t)M * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MM;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ky = e / M, kx = e % M;
+        out[e] = in[kx * M + ky];
+    }
+}
+
+bool smooth235(int m)
+{
+    if (m < 1) return false;
+    for (int f : {2, 3, 5})
+        while (m % f == 0) m /= f;
+    return m == 1;
+}
+
+struct Join {
+    // Orders the plan's stream after the caller's stream on entry, and the
+    // caller's stream after the plan's stream on exit.
+    spirec_plan p;
+    explicit Join(spirec_plan pp) : p(pp)
+    {
+        cudaEventRecord(p->ev_join, p->user_stream);
+        cudaStreamWaitEvent(p->stream, p->ev_join, 0);
+    }
+    ~Join()
+    {
+        cudaEventRecord(p->ev_join, p->stream);
+        cudaStreamWaitEvent(p->user_stream, p->ev_join, 0);
+    }
+};
+
+template <typename T>
+int dalloc(spirec_plan p, T** ptr, size_t count)
+{
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    const size_t bytes = count * sizeof(T);
+    if (getenv("SPIREC_FAIL_ALLOC_AFTER")) {
+        static thread_local long budget = -2;
+        if (budget == -2) budget = atol(getenv("SPIREC_FAIL_ALLOC_AFTER"));
+        if (budget-- <= 0) {
+            set_error("injected allocation failure");
+            return SPIREC_ENOMEM;
+        }
+    }
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        return SPIREC_ENOMEM;
+    }
+    p->device_bytes += bytes;
+    return SPIREC_OK;
+}
+
+void free_plan(spirec_plan p)
+{
+    if (!p) return;
+    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s,
+                    p->f[0], p->f[1], p->d, p->g, p->Tf, p->Td, p->tmp, p->twiddle,
+                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (int i = 0; i < (int)(sizeof(p->tev) / sizeof(p->tev[0])); ++i)
+        if (p->tev_made[i]) cudaEventDestroy(p->tev[i]);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+int check_plan(spirec_plan p)
+{
+    if (!p) {
+        set_error("null plan");
+        return SPIREC_EINVAL;
+    }
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != p->device) {
+        set_error("plan belongs to device %d, current device is %d", p->device, dev);
+        return SPIREC_EINVAL;
+    }
+    return SPIREC_OK;
+}
+
+// --- timing: event pairs per stage on the plan's stream
+int tstart(spirec_plan p, int stage, cudaEvent_t* out)
+{
+    *out = nullptr;
+    if (!p->timing) return SPIREC_OK;
+    if (p->tev_used + 2 > (int)(sizeof(p->tev) / sizeof(p->tev[0]))) {
+        // fold finished pairs into the totals
+        SPIREC_CK(cudaStreamSynchronize(p->stream));
+        for (int i = 0; i < p->tev_used; i += 2) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->tev[i], p->tev[i + 1]);
+            p->t_ms[p->tev_stage[i / 2]] += ms;
+            p->t_cnt[p->tev_stage[i / 2]] += 1;
+        }
+        p->tev_used = 0;
+    }
+    cudaEvent_t* e = &p->tev[p->tev_used];
+    if (!p->tev_made[p->tev_used]) {
+        SPIREC_CK(cudaEventCreate(&e[0]));
+        SPIREC_CK(cudaEventCreate(&e[1]));
+        p->tev_made[p->tev_used] = p->tev_made[p->tev_used + 1] = true;
+    }
+    p->tev_stage[p->tev_used / 2] = stage;
+    SPIREC_CK(cudaEventRecord(e[0], p->stream));
+    *out = e[1];
+    p->tev_used += 2;
+    return SPIREC_OK;
+}
+
+int tstop(spirec_plan p, cudaEvent_t e)
+{
+    if (e) SPIREC_CK(cudaEventRecord(e, p->stream));
+    return SPIREC_OK;
+}
+
+int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev)
+{
+    SPIREC_CK(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+    int blocks = (int)((p->L + 255) / 256);
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    k_traj_fixed<<<blocks, 256, 0, p->stream>>>(kx_dev, ky_dev, p->L, p->kxq, p->kyq, p->dflag);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
+    int flag = 0;
+    SPIREC_CK(cudaMemcpyAsync(&flag, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    if (flag) {
+        p->have_traj = false;
+        set_error("trajectory has a value outside [-0.5, 0.5] or not finite");
+        return SPIREC_EINVAL;
+    }
+    cudaEvent_t e;
+    int rc;
+    if ((rc = tstart(p, 0, &e)) != SPIREC_OK) return rc;
+    if ((rc = launch_gram(p)) != SPIREC_OK) return rc;
+    if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
+    if ((rc = tstart(p, 1, &e)) != SPIREC_OK) return rc;
+    if ((rc = launch_spectrum(p)) != SPIREC_OK) return rc;
+    if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
+    p->have_traj = true;
+    p->have_data = false;
+    return SPIREC_OK;
+}
+
+int build_data(spirec_plan p)
+{
+    int rc;
+    if ((rc = launch_data_norm(p)) != SPIREC_OK) return rc;
+    cudaEvent_t e;
+    if ((rc = tstart(p, 2, &e)) != SPIREC_OK) return rc;
+    if ((rc = launch_adjoint(p, p->s, p->D)) != SPIREC_OK) return rc;
+    if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
+    p->have_data = true;
+    return SPIREC_OK;
+}
+
+int ensure_J(spirec_plan p, int iters)
+{
+    if (p->Jcap >= iters + 1) return SPIREC_OK;
+    if (p->Jdev) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(p->Jdev);
+        p->Jdev = nullptr;
+    }
+    int cap = iters + 1 < 64 ? 64 : iters + 1;
+    int rc = dalloc(p, &p->Jdev, (size_t)cap);
+    if (rc != SPIREC_OK) {
+        p->Jcap = 0;
+        return rc;
+    }
+    p->Jcap = cap;
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    return SPIREC_OK;
+}
+
+// Iteration loop, replayed from a CUDA graph captured once per (plan, iters).
+int run_iterations(spirec_plan p, int iters)
+{
+    if (iters == 0) return SPIREC_OK;
+    if (!p->graph || p->graph_iters != iters) {
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        SPIREC_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = p->launches;
+        int rc = SPIREC_OK;
+        for (int k = 0; k < iters && rc == SPIREC_OK; ++k) rc = cg_iteration(p, k, p->Jdev);
+        cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+        p->graph_kernels = p->launches - l0;  // captured, not yet run
+        p->launches = l0;
+        if (rc != SPIREC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p->graph = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        p->graph_iters = iters;
+    }
+    SPIREC_CK(cudaGraphLaunch(p->graph, p->stream));
+    p->launches += p->graph_kernels;
+    return SPIREC_OK;
+}
+
+int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
+{
+    if (!p->have_traj || !p->have_data) {
+        set_error("solve needs a trajectory and data (spirec_set_trajectory, spirec_set_data)");
+        return SPIREC_ESTATE;
+    }
+    if (!p->have_reg) {
+        set_error("solve needs spirec_set_reg first");
+        return SPIREC_ESTATE;
+    }
+    if (iters < 0) {
+        set_error("iters must be >= 0");
+        return SPIREC_EINVAL;
+    }
+    int rc;
+    if ((rc = ensure_J(p, iters)) != SPIREC_OK) return rc;
+    const size_t img = (size_t)p->N * p->N * sizeof(float2);
+    cudaEvent_t e;
+    if ((rc = tstart(p, 3, &e)) != SPIREC_OK) return rc;
+    if (x0) {
+        SPIREC_CK(cudaMemcpyAsync(p->f[0], x0, img,
+                                  x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+        if ((rc = launch_toeplitz(p, p->f[0], p->Tf, -1)) != SPIREC_OK) return rc;
+    } else {
+        SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
+        SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
+    }
+    if ((rc = launch_update(p, p->f[0], p->f[0], p->Tf, nullptr, p->g, 1, p->Jdev)) != SPIREC_OK) return rc;
+    if ((rc = launch_direction(p, 1)) != SPIREC_OK) return rc;
+    if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
+    return tstop(p, e);
+}
+
+}  // namespace
+}  // namespace spirec
+
+using namespace spirec;
+
+extern "C" {
+
+const char* spirec_last_error(void) { return g_err; }
+
+const char* spirec_version(void) { return "spirec 0.1 (sm_103a)"; }
+
+int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_t precision,
+                       void* stream, const double* kx, const double* ky)
+{
+    g_err[0] = 0;
+    if (!out) {
+        set_error("out is NULL");
+        return SPIREC_EINVAL;
+    }
+    *out = nullptr;
+    if (N < 2 || N > 2048 || L < 1 || L > (int64_t)1 << 31) {
+        set_error("unsupported sizes N=%d L=%lld", N, (long long)L);
+        return SPIREC_EINVAL;
+    }
+    if (precision < SPIREC_FP32 || precision > SPIREC_MIXED_BF16X3) {
+        set_error("unknown precision %d", precision);
+        return SPIREC_EINVAL;
+    }
+    if (M == 0) {
+        M = 2 * N - 1;
+        while (!smooth235(M)) ++M;
+    }
+    if (M < 2 * N - 1 || !smooth235(M) || M > 4096) {
+        set_error("M=%d must be >= 2N-1 = %d, <= 4096 and factor into 2, 3, 5", M, 2 * N - 1);
+        return SPIREC_EINVAL;
+    }
+    spirec_plan p = new (std::nothrow) spirec_plan_s();
+    if (!p) {
+        set_error("host allocation failed");
+        return SPIREC_ENOMEM;
+    }
+    memset((void*)p, 0, sizeof(*p));
+    p->N = N;
+    p->L = L;
+    p->M = M;
+    p->precision = precision;
+    p->user_stream = (cudaStream_t)stream;
+    int rc = SPIREC_OK;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    make_fft_plan(M, &p->fft);
+#define TRY(x)                       \
+    do {                             \
+        if ((rc = (x)) != SPIREC_OK) { \
+            free_plan(p);            \
+            return rc;               \
+        }                            \
+    } while (0)
+#define TRYCUDA(x)                         \
+    do {                                   \
+        cudaError_t e2 = (x);              \
+        if (e2 != cudaSuccess) {           \
+            rc = cuda_fail(e2, #x);        \
+            free_plan(p);                  \
+            return rc;                     \
+        }                                  \
+    } while (0)
+    TRYCUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+    TRYCUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    const size_t NN = (size_t)N * N;
+    TRY(dalloc(p, &p->kxq, (size_t)L));
+    TRY(dalloc(p, &p->kyq, (size_t)L));
+    TRY(dalloc(p, &p->kstage, 2 * (size_t)L));
+    TRY(dalloc(p, &p->dflag, 1));
+    TRY(dalloc(p, &p->G, (size_t)N * (2 * N - 1)));
+    TRY(dalloc(p, &p->Chat, (size_t)M * M));
+    TRY(dalloc(p, &p->cwork, (size_t)M * M));
+    TRY(dalloc(p, &p->X, (size_t)N * M));
+    TRY(dalloc(p, &p->D, NN));
+    TRY(dalloc(p, &p->s, (size_t)L));
+    TRY(dalloc(p, &p->f[0], NN));
+    TRY(dalloc(p, &p->f[1], NN));
+    TRY(dalloc(p, &p->d, NN));
+    TRY(dalloc(p, &p->g, NN));
+    TRY(dalloc(p, &p->Tf, NN));
+    TRY(dalloc(p, &p->Td, NN));
+    TRY(dalloc(p, &p->tmp, NN));
+    TRY(dalloc(p, &p->twiddle, (size_t)M));
+    TRY(dalloc(p, &p->part, (size_t)P_NSLOTS * kMaxParts));
+    TRY(dalloc(p, &p->scal, (size_t)S_NSCAL));
+    TRY(dalloc(p, &p->counters, (size_t)C_N));
+    {
+        size_t a = 8 * (size_t)N * (2 * N - 1) * 2;  // floats: 8 splits of G
+        size_t b = 4 * (size_t)L * 2;                 // forward row-block partials
+        size_t c = kpart_floats_tc(N, L, precision);
+        size_t n = a > b ? a : b;
+        if (c > n) n = c;
+        TRY(dalloc(p, &p->kpart, n));
+        p->kpart_bytes = n * sizeof(float);
+    }
+    TRYCUDA(cudaMemsetAsync(p->counters, 0, C_N * sizeof(unsigned), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->scal, 0, S_NSCAL * sizeof(double), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->d, 0, NN * sizeof(float2), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->g, 0, NN * sizeof(float2), p->stream));
+    {
+        float2* tw = (float2*)malloc(sizeof(float2) * M);
+        if (!tw) {
+            free_plan(p);
+            set_error("host allocation failed");
+            return SPIREC_ENOMEM;
+        }
+        for (int k = 0; k < M; ++k) {
+            const double a = -2.0 * M_PI * (double)k / (double)M;
+            tw[k] = make_float2((float)cos(a), (float)sin(a));
+        }
+        e = cudaMemcpyAsync(p->twiddle, tw, sizeof(float2) * M, cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        free(tw);
+        TRYCUDA(e);
+    }
+    TRY(fft_setup_attributes(M));
+    TRY(tc_setup_attributes());
+    if (kx || ky) {
+        if (!kx || !ky) {
+            free_plan(p);
+            set_error("kx and ky must both be given or both be NULL");
+            return SPIREC_EINVAL;
+        }
+        TRY(spirec_set_trajectory(p, kx, ky));
+    }
+#undef TRY
+#undef TRYCUDA
+    *out = p;
+    return SPIREC_OK;
+}
+
+int spirec_plan_destroy(spirec_plan plan)
+{
+    if (!plan) return SPIREC_OK;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return SPIREC_OK;
+}
+
+int spirec_set_trajectory(spirec_plan p, const double* kx, const double* ky)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!kx || !ky) {
+        set_error("kx, ky must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(p->kstage, kx, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
+    SPIREC_CK(cudaMemcpyAsync(p->kstage + p->L, ky, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
+    return build_trajectory(p, p->kstage, p->kstage + p->L);
+}
+
+int spirec_set_trajectory_dev(spirec_plan p, const double* kx, const double* ky)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!kx || !ky) {
+        set_error("kx, ky must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    Join j(p);
+    return build_trajectory(p, kx, ky);
+}
+
+int spirec_set_data(spirec_plan p, const float* s)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!s) {
+        set_error("s must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("set_data needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(p->s, s, sizeof(float2) * p->L, cudaMemcpyHostToDevice, p->stream));
+    rc = build_data(p);
+    if (rc == SPIREC_OK) SPIREC_CK(cudaStreamSynchronize(p->stream));
+    return rc;
+}
+
+int spirec_set_data_dev(spirec_plan p, const float* s)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!s) {
+        set_error("s must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("set_data needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(p->s, s, sizeof(float2) * p->L, cudaMemcpyDeviceToDevice, p->stream));
+    return build_data(p);
+}
+
+int spirec_set_reg(spirec_plan p, double lambda1, double alpha1, double lambda0, double alpha0,
+                   int32_t phi)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!(lambda1 >= 0.0) || !(lambda0 >= 0.0) || !isfinite(lambda1) || !isfinite(lambda0)) {
+        set_error("lambdas must be finite and >= 0");
+        return SPIREC_EINVAL;
+    }
+    if (phi < SPIREC_PHI_HUBER || phi > SPIREC_PHI_QUADRATIC) {
+        set_error("unknown phi %d", phi);
+        return SPIREC_EINVAL;
+    }
+    if (phi != SPIREC_PHI_QUADRATIC &&
+        (!(alpha1 > 0.0) || !(alpha0 > 0.0) || !isfinite(alpha1) || !isfinite(alpha0))) {
+        set_error("alphas must be finite and > 0");
+        return SPIREC_EINVAL;
+    }
+    p->reg.lambda1 = (float)lambda1;
+    p->reg.alpha1 = (float)alpha1;
+    p->reg.lambda0 = (float)lambda0;
+    p->reg.alpha0 = (float)alpha0;
+    p->reg.kind = phi;
+    p->have_reg = true;
+    if (p->graph) {  // the graph holds the penalty by value
+        cudaStreamSynchronize(p->stream);
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    return SPIREC_OK;
+}
+
+int spirec_solve(spirec_plan p, const float* x0, int32_t iters, float* x_out, double* J_hist)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x_out) {
+        set_error("x_out must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    Join j(p);
+    if ((rc = solve_core(p, x0, false, iters)) != SPIREC_OK) return rc;
+    const size_t img = (size_t)p->N * p->N * sizeof(float2);
+    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[iters & 1], img, cudaMemcpyDeviceToHost, p->stream));
+    double Jlast = 0.0;
+    SPIREC_CK(cudaMemcpyAsync(&Jlast, p->Jdev + iters, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    if (J_hist)
+        SPIREC_CK(cudaMemcpyAsync(J_hist, p->Jdev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost,
+                                  p->stream));
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    if (!isfinite(Jlast)) {
+        set_error("criterion is not finite after %d iterations", iters);
+        return SPIREC_ENUMERIC;
+    }
+    return SPIREC_OK;
+}
+
+int spirec_solve_dev(spirec_plan p, const float* x0, int32_t iters, float* x_out, double* J_hist)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x_out) {
+        set_error("x_out must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    Join j(p);
+    if ((rc = solve_core(p, x0, true, iters)) != SPIREC_OK) return rc;
+    const size_t img = (size_t)p->N * p->N * sizeof(float2);
+    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[iters & 1], img, cudaMemcpyDeviceToDevice, p->stream));
+    if (J_hist)
+        SPIREC_CK(cudaMemcpyAsync(J_hist, p->Jdev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToDevice,
+                                  p->stream));
+    return SPIREC_OK;
+}
+
+int spirec_forward_dev(spirec_plan p, const float* x, float* y)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !y) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("forward needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    return launch_forward(p, (const float2*)x, (float2*)y);
+}
+
+int spirec_adjoint_dev(spirec_plan p, const float* y, float* x)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !y) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("adjoint needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    return launch_adjoint(p, (const float2*)y, (float2*)x);
+}
+
+int spirec_gram_dev(spirec_plan p, float* G)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!G) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("no trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(G, p->G, sizeof(float2) * (size_t)p->N * (2 * p->N - 1),
+                              cudaMemcpyDeviceToDevice, p->stream));
+    return SPIREC_OK;
+}
+
+int spirec_kernel_spectrum_dev(spirec_plan p, float* C)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!C) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("no trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    k_transpose_real<<<4 * 152, 256, 0, p->stream>>>(p->Chat, p->M, C);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
+    return SPIREC_OK;
+}
+
+int spirec_data_adjoint_dev(spirec_plan p, float* D)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!D) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_data) {
+        set_error("no data");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(D, p->D, sizeof(float2) * (size_t)p->N * p->N, cudaMemcpyDeviceToDevice,
+                              p->stream));
+    return SPIREC_OK;
+}
+
+int spirec_toeplitz_dev(spirec_plan p, const float* x, float* Tx)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !Tx) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("no trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    return launch_toeplitz(p, (const float2*)x, (float2*)Tx, -1);
+}
+
+int spirec_objective_grad_dev(spirec_plan p, const float* x, double* J_host, float* g)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !g) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_data || !p->have_reg) {
+        set_error("objective needs data and a penalty");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    if ((rc = launch_toeplitz(p, (const float2*)x, p->tmp, -1)) != SPIREC_OK) return rc;
+    if ((rc = launch_update(p, (const float2*)x, (float2*)x, p->tmp, nullptr, (float2*)g, 1, nullptr)) !=
+        SPIREC_OK)
+        return rc;
+    if (J_host) {
+        SPIREC_CK(cudaMemcpyAsync(J_host, p->scal + S_J, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        SPIREC_CK(cudaStreamSynchronize(p->stream));
+    }
+    return SPIREC_OK;
+}
+
+int spirec_sync(spirec_plan p)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    return SPIREC_OK;
+}
+
+int spirec_plan_info(spirec_plan p, int32_t* N, int64_t* L, int32_t* M, int32_t* precision,
+                     size_t* device_bytes)
+{
+    if (!p) {
+        set_error("null plan");
+        return SPIREC_EINVAL;
+    }
+    if (N) *N = p->N;
+    if (L) *L = p->L;
+    if (M) *M = p->M;
+    if (precision) *precision = p->precision;
+    if (device_bytes) *device_bytes = p->device_bytes;
+    return SPIREC_OK;
+}
+
+int spirec_launch_count(spirec_plan p, int64_t* count)
+{
+    if (!p || !count) {
+        set_error("null argument");
+        return SPIREC_EINVAL;
+    }
+    *count = p->launches;
+    return SPIREC_OK;
+}
+
+int spirec_timing(spirec_plan p, int32_t enable)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    p->timing = enable != 0;
+    p->tev_used = 0;
+    for (int i = 0; i < SPIREC_NUM_STAGES; ++i) {
+        p->t_ms[i] = 0.0;
+        p->t_cnt[i] = 0;
+    }
+    return SPIREC_OK;
+}
+
+int spirec_timing_read(spirec_plan p, double* out_ms, int64_t* out_count)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < p->tev_used; i += 2) {
+        float ms = 0.f;
+        SPIREC_CK(cudaEventElapsedTime(&ms, p->tev[i], p->tev[i + 1]));
+        p->t_ms[p->tev_stage[i / 2]] += ms;
+        p->t_cnt[p->tev_stage[i / 2]] += 1;
+    }
+    p->tev_used = 0;
+    for (int i = 0; i < SPIREC_NUM_STAGES; ++i) {
+        if (out_ms) out_ms[i] = p->t_ms[i];
+        if (out_count) out_count[i] = p->t_cnt[i];
+    }
+    return SPIREC_OK;
+}
+
+}  // extern "C"

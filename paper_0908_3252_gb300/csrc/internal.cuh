@@ -1,0 +1,170 @@
+// internal.cuh -- shared declarations of the CUDA path (plan state, device
+// helpers, kernel launchers).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spirec.h"
+
+namespace spirec {
+
+// ------------------------------------------------------------ error helpers
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SPIREC_CK(call)                                        \
+    do {                                                       \
+        cudaError_t e__ = (call);                              \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #call);  \
+    } while (0)
+
+// ---------------------------------------------------------------- FFT plan
+
+constexpr int kMaxStages = 16;
+struct FftPlan {
+    int M;
+    int nstages;
+    int radix[kMaxStages];
+};
+bool make_fft_plan(int M, FftPlan* p);
+
+// ----------------------------------------------------------- partial sums
+
+// Slots of the partial-sum array (each slot holds kMaxParts doubles, one per
+// block of the kernel that produced them).
+constexpr int kMaxParts = 1024;
+enum PartSlot {
+    P_Q2 = 0,    // Re<d, T d>
+    P_Q1 = 1,    // Re<d, g_ls>
+    P_LS = 2,    // line-search step: num, den (2 slots)
+    P_UPD = 4,   // gradient/update: 6 slots (see k_update)
+    P_MISC = 10, // one-off sums (||s||^2)
+    P_NSLOTS = 12
+};
+
+constexpr int kUpdVals = 6;  // sums of the update kernel
+
+// Arrival counters of the last-block reductions, one per kernel kind.
+enum Counter { C_TOEP = 0, C_LS = 1, C_UPD = 2, C_DIR = 3, C_MISC = 4, C_N = 8 };
+
+// Device scalars (FP64), written by the last block of the kernel that
+// reduces them and read by later kernels in stream order.
+enum Scalar {
+    S_SS = 0,    // ||s||^2
+    S_Q1 = 1,    // Re<d, g_ls>
+    S_Q2 = 2,    // ||H d||^2 = Re<d, T d>
+    S_T1 = 3,    // line-search steps t1, t2, t3 (S_T1 + j)
+    S_T3 = 5,
+    S_GG = 6,    // <g, g> of the current gradient
+    S_BETA = 7,  // Polak-Ribiere beta for the next direction (0 = restart)
+    S_J = 8,     // J of the current iterate
+    S_R = 9,     // R of the current iterate
+    S_TMP = 10,  // result of a one-off dot
+    S_NSCAL = 16
+};
+
+struct Reg {
+    float lambda1, alpha1, lambda0, alpha0;
+    int kind;
+};
+
+// ------------------------------------------------------------------- plan
+
+}  // namespace spirec
+
+struct spirec_plan_s {
+    int N;
+    int64_t L;
+    int M;
+    int precision;
+    int device;
+    cudaStream_t user_stream;
+    cudaStream_t stream;  // own, non-blocking
+    cudaEvent_t ev_join;
+
+    // trajectory, fixed point: k * 2^64 mod 2^64
+    int64_t* kxq;
+    int64_t* kyq;
+    double* kstage;  // 2L: host trajectory staged on the device
+    int* dflag;  // device error flag
+
+    float2* G;     // N x (2N-1)
+    float* Chat;   // M x M real, transposed: Chat[kx*M + ky]
+    float2* cwork; // M x M complex (spectrum build)
+    float2* X;     // N x M complex (Toeplitz rows)
+    float2* D;     // N x N
+    float2* s;     // L
+    float2* f[2];
+    float2* d;
+    float2* g;
+    float2* Tf;
+    float2* Td;
+    float2* tmp;   // N x N scratch for operator calls
+    float2* twiddle;  // M entries, exp(-2 pi i k / M)
+    double* part;  // P_NSLOTS x kMaxParts
+    double* scal;  // S_NSCAL
+    unsigned* counters;  // C_N
+    double* Jdev;  // J history (device), capacity Jcap
+    int Jcap;
+    float* kpart;  // split-K partial sums of the contractions
+    size_t kpart_bytes;
+    size_t device_bytes;
+
+    spirec::FftPlan fft;
+    spirec::Reg reg;
+    bool have_traj, have_data, have_reg;
+
+    // kernels launched (graph replays count every kernel node)
+    int64_t launches;
+    int64_t graph_kernels;
+
+    // CUDA graph of the iteration loop
+    cudaGraphExec_t graph;
+    int graph_iters;
+    int graph_parity_out;
+
+    // timing
+    bool timing;
+    cudaEvent_t tev[2 * 64];
+    bool tev_made[2 * 64];
+    int tev_stage[64];
+    int tev_used;
+    double t_ms[SPIREC_NUM_STAGES];
+    int64_t t_cnt[SPIREC_NUM_STAGES];
+};
+
+namespace spirec {
+
+// -------------------------------------------------------------- launchers
+// All launchers enqueue on p->stream and return a spirec_status.
+
+int launch_gram(spirec_plan p);            // G from the trajectory
+int launch_spectrum(spirec_plan p);        // Chat from G
+int launch_adjoint(spirec_plan p, const float2* y, float2* x);  // x = H^H y
+int launch_forward(spirec_plan p, const float2* x, float2* y);  // y = H x
+
+// Toeplitz T x -> Tx; with dot_scalar >= 0 also scal[dot_scalar] = Re<x, Tx>.
+int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar);
+int fft_setup_attributes(int maxM);
+
+// CG pieces (cg.cu).  Iterate k reads f[k & 1] and writes f[(k + 1) & 1].
+int launch_data_norm(spirec_plan p);
+// gradient at f (Tf given): g, J -> Jout, <g,g>; first = no step taken
+int launch_update(spirec_plan p, const float2* f_in, float2* f_out, float2* Tf, const float2* Td,
+                  float2* g, int first, double* Jout);
+int launch_direction(spirec_plan p, int first);
+int launch_line_search(spirec_plan p, const float2* f, int step);
+int cg_iteration(spirec_plan p, int k, double* Jdev);
+
+// tensor-core contractions (FP16x3 / BF16x3)
+int launch_gram_tc(spirec_plan p);
+int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x);
+size_t kpart_floats_tc(int N, int64_t L, int precision);  // split-K buffer need
+int tc_setup_attributes();
+
+int vec_blocks(int N);
+constexpr int kVecThreads = 256;
+
+}  // namespace spirec

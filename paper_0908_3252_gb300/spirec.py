@@ -1,0 +1,270 @@
+"""Python binding of libspirec.so (argument marshalling only).
+
+Every function named ``spirec_*`` here calls the C entry point of the same
+name in ``include/spirec.h`` through ctypes; no step of the reconstruction
+runs in Python.  Host-pointer entry points take numpy arrays (``complex64`` for
+complex data, ``float64`` for trajectories); ``*_dev`` entry points take CUDA
+tensors (torch is used only to own device memory and streams).
+
+The library must have been built (``paper_0908_3252_gb300.build.build()``);
+importing this module without it raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspirec.so")
+
+SPIREC_OK = 0
+SPIREC_EINVAL = -1
+SPIREC_ENOMEM = -2
+SPIREC_ECUDA = -3
+SPIREC_ESTATE = -4
+SPIREC_EBUSY = -5
+SPIREC_ETIMEOUT = -6
+SPIREC_ENUMERIC = -7
+SPIREC_EUNSUPPORTED = -8
+
+SPIREC_FP32 = 0
+SPIREC_MIXED_FP16X3 = 1
+SPIREC_MIXED_BF16X3 = 2
+
+SPIREC_PHI_HUBER = 0
+SPIREC_PHI_HYPERBOLIC = 1
+SPIREC_PHI_QUADRATIC = 2
+
+SPIREC_NUM_STAGES = 4
+STAGES = ("gram", "spectrum", "adjoint_d", "iterations")
+
+# name -> (restype, argtypes) for every symbol declared in include/spirec.h
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+SIGNATURES = {
+    "spirec_plan_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _I64, _I32, _I32, _P, _P, _P]),
+    "spirec_plan_destroy": (ctypes.c_int, [_P]),
+    "spirec_set_trajectory": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_set_trajectory_dev": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_set_data": (ctypes.c_int, [_P, _P]),
+    "spirec_set_data_dev": (ctypes.c_int, [_P, _P]),
+    "spirec_set_reg": (ctypes.c_int, [_P, _D, _D, _D, _D, _I32]),
+    "spirec_solve": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "spirec_solve_dev": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
+    "spirec_forward_dev": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_adjoint_dev": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_gram_dev": (ctypes.c_int, [_P, _P]),
+    "spirec_kernel_spectrum_dev": (ctypes.c_int, [_P, _P]),
+    "spirec_data_adjoint_dev": (ctypes.c_int, [_P, _P]),
+    "spirec_toeplitz_dev": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_objective_grad_dev": (ctypes.c_int, [_P, _P, _P, _P]),
+    "spirec_sync": (ctypes.c_int, [_P]),
+    "spirec_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "spirec_launch_count": (ctypes.c_int, [_P, _P]),
+    "spirec_timing": (ctypes.c_int, [_P, _I32]),
+    "spirec_timing_read": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_last_error": (ctypes.c_char_p, []),
+    "spirec_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class SpirecError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"spirec status {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load libspirec.so and declare its signatures.  Raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"{path} is not built; run paper_0908_3252_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != SPIREC_OK:
+        raise SpirecError(rc, load().spirec_last_error().decode())
+    return rc
+
+
+def _host_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device entry points take contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _c64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.complex64)
+    if n is not None:
+        assert a.size == n
+    return a
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---- thin wrappers with the C names (status checked, pointers marshalled)
+
+def spirec_last_error() -> str:
+    return load().spirec_last_error().decode()
+
+
+def spirec_version() -> str:
+    return load().spirec_version().decode()
+
+
+def spirec_plan_create(N, L, M=0, precision=SPIREC_FP32, stream=None, kx=None, ky=None):
+    plan = ctypes.c_void_p()
+    kx = _f64(kx) if kx is not None else None
+    ky = _f64(ky) if ky is not None else None
+    _check(load().spirec_plan_create(ctypes.byref(plan), int(N), int(L), int(M), int(precision),
+                                     ctypes.c_void_p(stream) if stream else None,
+                                     _host_ptr(kx), _host_ptr(ky)))
+    return plan
+
+
+def spirec_plan_destroy(plan):
+    return _check(load().spirec_plan_destroy(plan))
+
+
+def spirec_set_trajectory(plan, kx, ky):
+    kx, ky = _f64(kx), _f64(ky)
+    return _check(load().spirec_set_trajectory(plan, _host_ptr(kx), _host_ptr(ky)))
+
+
+def spirec_set_trajectory_dev(plan, kx, ky):
+    return _check(load().spirec_set_trajectory_dev(plan, _dev_ptr(kx), _dev_ptr(ky)))
+
+
+def spirec_set_data(plan, s):
+    s = _c64(s)
+    return _check(load().spirec_set_data(plan, _host_ptr(s)))
+
+
+def spirec_set_data_dev(plan, s):
+    return _check(load().spirec_set_data_dev(plan, _dev_ptr(s)))
+
+
+def spirec_set_reg(plan, lambda1, alpha1, lambda0, alpha0, phi):
+    return _check(load().spirec_set_reg(plan, float(lambda1), float(alpha1), float(lambda0),
+                                        float(alpha0), int(phi)))
+
+
+def spirec_solve(plan, x0, iters, N):
+    """Host variant: returns (x (N,N) complex64, J_hist (iters+1,) float64)."""
+    x0 = _c64(x0, N * N) if x0 is not None else None
+    x = np.zeros((N, N), np.complex64)
+    J = np.zeros(iters + 1, np.float64)
+    _check(load().spirec_solve(plan, _host_ptr(x0), int(iters), _host_ptr(x), _host_ptr(J)))
+    return x, J
+
+
+def spirec_solve_dev(plan, x0, iters, x_out, J_hist=None):
+    return _check(load().spirec_solve_dev(plan, _dev_ptr(x0), int(iters), _dev_ptr(x_out), _dev_ptr(J_hist)))
+
+
+def spirec_forward_dev(plan, x, y):
+    return _check(load().spirec_forward_dev(plan, _dev_ptr(x), _dev_ptr(y)))
+
+
+def spirec_adjoint_dev(plan, y, x):
+    return _check(load().spirec_adjoint_dev(plan, _dev_ptr(y), _dev_ptr(x)))
+
+
+def spirec_gram_dev(plan, G):
+    return _check(load().spirec_gram_dev(plan, _dev_ptr(G)))
+
+
+def spirec_kernel_spectrum_dev(plan, C):
+    return _check(load().spirec_kernel_spectrum_dev(plan, _dev_ptr(C)))
+
+
+def spirec_data_adjoint_dev(plan, D):
+    return _check(load().spirec_data_adjoint_dev(plan, _dev_ptr(D)))
+
+
+def spirec_toeplitz_dev(plan, x, Tx):
+    return _check(load().spirec_toeplitz_dev(plan, _dev_ptr(x), _dev_ptr(Tx)))
+
+
+def spirec_objective_grad_dev(plan, x, g):
+    J = ctypes.c_double(0.0)
+    _check(load().spirec_objective_grad_dev(plan, _dev_ptr(x), ctypes.byref(J), _dev_ptr(g)))
+    return J.value
+
+
+def spirec_sync(plan):
+    return _check(load().spirec_sync(plan))
+
+
+def spirec_plan_info(plan):
+    N, L, M, prec, nbytes = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
+    _check(load().spirec_plan_info(plan, ctypes.byref(N), ctypes.byref(L), ctypes.byref(M),
+                                   ctypes.byref(prec), ctypes.byref(nbytes)))
+    return dict(N=N.value, L=L.value, M=M.value, precision=prec.value, device_bytes=nbytes.value)
+
+
+def spirec_launch_count(plan):
+    c = ctypes.c_int64()
+    _check(load().spirec_launch_count(plan, ctypes.byref(c)))
+    return c.value
+
+
+def spirec_timing(plan, enable):
+    return _check(load().spirec_timing(plan, int(enable)))
+
+
+def spirec_timing_read(plan):
+    ms = (ctypes.c_double * SPIREC_NUM_STAGES)()
+    cnt = (ctypes.c_int64 * SPIREC_NUM_STAGES)()
+    _check(load().spirec_timing_read(plan, ms, cnt))
+    return {STAGES[i]: (ms[i], cnt[i]) for i in range(SPIREC_NUM_STAGES)}
+
+
+# ---- small convenience owner used by the tests and the benchmark
+
+class Plan:
+    """Owns a spirec_plan handle; every method is one C-ABI call."""
+
+    def __init__(self, N, L, M=0, precision=SPIREC_FP32, stream=None, kx=None, ky=None):
+        self.N, self.L = int(N), int(L)
+        self.h = spirec_plan_create(N, L, M, precision, stream, kx, ky)
+        self.info = spirec_plan_info(self.h)
+        self.M = self.info["M"]
+
+    def close(self):
+        if self.h is not None:
+            spirec_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

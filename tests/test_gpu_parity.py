@@ -1,0 +1,222 @@
+"""GPU parity: every operator of the CUDA path against the FP64 oracle, called
+through the C ABI (libspirec.so).
+
+Tolerances (relative L2 against the FP64 oracle, same inputs on both sides):
+  FP32 path            1e-5   (the FP32 tolerance of the reconstruction target)
+  FP16x3 / BF16x3 path 1e-3   (mixed-precision contraction target)
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_0908_3252_gb300 import synth
+from tests.helpers import c64, empty_c64, from_dev, rel, to_dev, workload_c1, workload_ragged
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-5, 1: 1e-3, 2: 1e-3}
+PRECISIONS = [0]
+
+
+@pytest.fixture(scope="module")
+def sp():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0908_3252_gb300 import build, spirec
+    build.build()
+    spirec.load()
+    return spirec
+
+
+def _plan(sp, w, prec, M=0):
+    import torch
+    L = w["kx"].shape[0]
+    p = sp.Plan(w["N"], L, M, prec, torch.cuda.current_stream().cuda_stream, w["kx"], w["ky"])
+    return p
+
+
+def _half(Gfull, N):
+    # oracle G indexed [v+N-1, u+N-1] -> plan layout [u][v+N-1] for u >= 0
+    return Gfull[:, N - 1:].T
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("wname", ["c1", "ragged"])
+def test_gram(sp, prec, wname):
+    w = workload_c1() if wname == "c1" else workload_ragged()
+    N = w["N"]
+    with _plan(sp, w, prec) as p:
+        G = empty_c64((N, 2 * N - 1))
+        sp.spirec_gram_dev(p.h, G)
+        got = from_dev(G)
+    want = _half(O.gram(w["kx"], w["ky"], N), N)
+    assert rel(got, want) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("wname", ["c1", "ragged"])
+def test_adjoint_D(sp, prec, wname):
+    w = workload_c1() if wname == "c1" else workload_ragged()
+    N = w["N"]
+    with _plan(sp, w, prec) as p:
+        sp.spirec_set_data(p.h, w["s"])
+        D = empty_c64((N, N))
+        sp.spirec_data_adjoint_dev(p.h, D)
+        got = from_dev(D)
+    want = O.adjoint(w["kx"], w["ky"], w["s"], N)
+    assert rel(got, want) < TOL[prec]
+
+
+@pytest.mark.parametrize("wname", ["c1", "ragged"])
+def test_forward(sp, wname):
+    w = workload_c1() if wname == "c1" else workload_ragged()
+    N = w["N"]
+    x = c64(w["f_true"])
+    with _plan(sp, w, 0) as p:
+        xd = to_dev(x)
+        y = empty_c64((w["kx"].shape[0],))
+        sp.spirec_forward_dev(p.h, xd, y)
+        got = from_dev(y)
+    assert rel(got, O.forward(w["kx"], w["ky"], x)) < 1e-5
+
+
+@pytest.mark.parametrize("wname", ["c1", "ragged"])
+def test_toeplitz_equals_normal_operator(sp, wname):
+    """T x by the zero-padded FFT equals the oracle's H^H (H x) (Appendix B)."""
+    w = workload_c1() if wname == "c1" else workload_ragged()
+    N = w["N"]
+    g = synth.rng(5)
+    x = c64(synth.complex_normal((N, N), g))
+    with _plan(sp, w, 0) as p:
+        Tx = empty_c64((N, N))
+        sp.spirec_toeplitz_dev(p.h, to_dev(x), Tx)
+        got = from_dev(Tx)
+    want = O.adjoint(w["kx"], w["ky"], O.forward(w["kx"], w["ky"], x), N)
+    assert rel(got, want) < 1e-5
+
+
+def test_spectrum_is_the_embedded_gram(sp):
+    """Chat = Re FFT2(c) / M^2 with c[v mod M][u mod M] = conj G_{u,v}."""
+    w = workload_ragged(N=20, I=2, S=150)
+    N = w["N"]
+    with _plan(sp, w, 0) as p:
+        M = p.M
+        import torch
+        C = torch.zeros((M, M), dtype=torch.float32, device="cuda:0")
+        sp.spirec_kernel_spectrum_dev(p.h, C)
+        got = from_dev(C)
+    G = O.gram(w["kx"], w["ky"], N)
+    c = np.zeros((M, M), np.complex128)
+    for v in range(-(N - 1), N):
+        for u in range(-(N - 1), N):
+            c[v % M, u % M] = np.conj(G[v + N - 1, u + N - 1])
+    spec = np.fft.fft2(c) / M ** 2
+    assert np.max(np.abs(spec.imag)) < 1e-12 * np.max(np.abs(spec.real)) + 1e-15
+    assert rel(got, spec.real) < 1e-5
+
+
+@pytest.mark.parametrize("kind", [O.PHI_HUBER, O.PHI_HYPERBOLIC, O.PHI_QUADRATIC])
+def test_objective_and_gradient(sp, kind):
+    w = workload_ragged(kind=kind)
+    N, reg = w["N"], w["reg"]
+    g = synth.rng(17)
+    x = c64(w["f_true"] + 0.1 * synth.complex_normal((N, N), g))
+    with _plan(sp, w, 0) as p:
+        sp.spirec_set_data(p.h, w["s"])
+        sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+        gd = empty_c64((N, N))
+        J = sp.spirec_objective_grad_dev(p.h, to_dev(x), gd)
+        got = from_dev(gd)
+    assert rel(got, O.gradient(w["kx"], w["ky"], w["s"], x, reg)) < 1e-5
+    Jo = O.objective(w["kx"], w["ky"], w["s"], x, reg)
+    assert abs(J - Jo) < 1e-5 * Jo
+
+
+def _solve_both(sp, w, prec, x0=None):
+    N, reg, iters = w["N"], w["reg"], w["iters"]
+    with _plan(sp, w, prec) as p:
+        sp.spirec_set_data(p.h, w["s"])
+        sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+        x, J = sp.spirec_solve(p.h, x0, iters, N)
+    xo, Jo, _ = O.solve(w["kx"], w["ky"], w["s"], reg,
+                        np.zeros((N, N)) if x0 is None else c64(x0), iters)
+    return x, J, xo, Jo
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_solve_c1(sp, prec):
+    """32x32 workload, 50 iterations: iterate and J history against the oracle."""
+    w = workload_c1()
+    x, J, xo, Jo = _solve_both(sp, w, prec)
+    assert np.all(np.isfinite(J))
+    assert np.all(np.diff(J) <= 1e-6 * J[0]), "J must not increase"
+    assert rel(J, Jo) < TOL[prec]
+    assert rel(x, xo) < TOL[prec]
+
+
+def test_solve_ragged_with_x0(sp):
+    w = workload_ragged()
+    g = synth.rng(3)
+    x0 = (0.5 * w["f_true"] + 0.05 * synth.complex_normal(w["f_true"].shape, g)).astype(np.complex64)
+    x, J, xo, Jo = _solve_both(sp, w, 0, x0)
+    assert np.all(np.diff(J) <= 1e-6 * J[0])
+    assert rel(J, Jo) < 1e-5
+    assert rel(x, xo) < 1e-5
+
+
+def test_solve_zero_iterations_returns_x0(sp):
+    w = workload_ragged(N=16, I=2, S=100)
+    w["iters"] = 0
+    x0 = w["f_true"].astype(np.complex64)
+    x, J, xo, Jo = _solve_both(sp, w, 0, x0)
+    assert np.array_equal(x, x0)
+    assert abs(J[0] - Jo[0]) < 1e-5 * Jo[0]
+
+
+def test_smallest_sizes(sp):
+    """N = 2, L = 1: every tile is a ragged tail."""
+    N = 2
+    kx, ky = np.array([0.21]), np.array([-0.37])
+    w = dict(N=N, kx=kx, ky=ky, s=c64(np.array([0.3 - 0.2j])),
+             reg=O.Reg(0.1, 0.05, 0.01, 0.05, O.PHI_HUBER), iters=4,
+             f_true=np.zeros((N, N)))
+    x, J, xo, Jo = _solve_both(sp, w, 0)
+    assert rel(x, xo) < 1e-5
+    assert rel(J, Jo) < 1e-5
+
+
+def test_cartesian_grid_inverts_exactly(sp):
+    """Complete Cartesian grid, lambda = 0: one iteration returns H^H s = f."""
+    N = 16
+    kx, ky = synth.cartesian(N)
+    f = synth.phantom(N, "ellipses_phase", synth.rng(8))
+    s = c64(O.forward(kx, ky, f))
+    w = dict(N=N, kx=kx, ky=ky, s=s, reg=O.Reg(0.0, 1.0, 0.0, 1.0, O.PHI_HUBER), iters=1, f_true=f)
+    x, J, xo, Jo = _solve_both(sp, w, 0)
+    assert rel(x, f) < 1e-5
+    assert rel(x, xo) < 1e-5
+
+
+def test_errors(sp):
+    import torch
+    w = workload_ragged(N=8, I=1, S=20)
+    with _plan(sp, w, 0) as p:
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_solve(p.h, None, 3, 8)
+        assert e.value.code == sp.SPIREC_ESTATE
+        bad = w["kx"].copy()
+        bad[3] = 0.51
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_set_trajectory(p.h, bad, w["ky"])
+        assert e.value.code == sp.SPIREC_EINVAL
+        bad[3] = np.nan
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_set_trajectory(p.h, bad, w["ky"])
+        assert e.value.code == sp.SPIREC_EINVAL
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_set_reg(p.h, -1.0, 0.1, 0.0, 0.1, 0)
+        assert e.value.code == sp.SPIREC_EINVAL
+    with pytest.raises(sp.SpirecError) as e:
+        sp.Plan(8, 20, 10, 0, torch.cuda.current_stream().cuda_stream)  # M < 2N-1
+    assert e.value.code == sp.SPIREC_EINVAL
