@@ -127,4 +127,5 @@ def test_solve_properties(sp, traj, plan):
     assert J[-1] < 0.05 * J[0]
     gd = empty_c64((N, N))
     J2 = sp.spirec_objective_grad_dev(p.h, to_dev(xr), gd)
-    assert abs(J2 - J[-1]) < 1e-4 * J[-1]
+    # both are differences of terms of size ||s||^2 = J[0] (x0 = 0)
+    assert abs(J2 - J[-1]) < 1e-5 * J[0]
