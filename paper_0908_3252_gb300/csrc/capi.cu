@@ -120,7 +120,7 @@ void free_plan(spirec_plan p)
 {
     if (!p) return;
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s,
-                    p->f[0], p->f[1], p->d, p->g, p->Tf, p->Td, p->tmp, p->twiddle,
+                    p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -182,22 +182,36 @@ int tstop(spirec_plan p, cudaEvent_t e)
     return SPIREC_OK;
 }
 
+int read_device_flags(spirec_plan p, int* flags)
+{
+    SPIREC_CK(cudaMemcpyAsync(flags, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    return SPIREC_OK;
+}
+
+int flags_status(int flags)
+{
+    if (flags & E_TRAJ) {
+        set_error("trajectory has a value outside [-0.5, 0.5] or not finite");
+        return SPIREC_EINVAL;
+    }
+    if (flags & E_TIMEOUT) {
+        set_error("a tensor-core pipeline wait ran out of time");
+        return SPIREC_ETIMEOUT;
+    }
+    return SPIREC_OK;
+}
+
 int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev)
 {
+    p->have_traj = false;
+    p->have_data = false;
     SPIREC_CK(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
     int blocks = (int)((p->L + 255) / 256);
     if (blocks > 8 * 152) blocks = 8 * 152;
     k_traj_fixed<<<blocks, 256, 0, p->stream>>>(kx_dev, ky_dev, p->L, p->kxq, p->kyq, p->dflag);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
-    int flag = 0;
-    SPIREC_CK(cudaMemcpyAsync(&flag, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    SPIREC_CK(cudaStreamSynchronize(p->stream));
-    if (flag) {
-        p->have_traj = false;
-        set_error("trajectory has a value outside [-0.5, 0.5] or not finite");
-        return SPIREC_EINVAL;
-    }
     cudaEvent_t e;
     int rc;
     if ((rc = tstart(p, 0, &e)) != SPIREC_OK) return rc;
@@ -206,8 +220,10 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev)
     if ((rc = tstart(p, 1, &e)) != SPIREC_OK) return rc;
     if ((rc = launch_spectrum(p)) != SPIREC_OK) return rc;
     if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
+    int flags = 0;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
     p->have_traj = true;
-    p->have_data = false;
     return SPIREC_OK;
 }
 
@@ -307,8 +323,9 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
-    if ((rc = launch_update(p, p->f[0], p->f[0], p->Tf, nullptr, p->g, 1, p->Jdev)) != SPIREC_OK) return rc;
-    if ((rc = launch_direction(p, 1)) != SPIREC_OK) return rc;
+    // gradient at x0, J(x0), beta = 0 (the first direction is -g)
+    if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->Tf, nullptr, p->g, 1, p->Jdev)) != SPIREC_OK)
+        return rc;
     if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
     return tstop(p, e);
 }
@@ -398,7 +415,8 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->s, (size_t)L));
     TRY(dalloc(p, &p->f[0], NN));
     TRY(dalloc(p, &p->f[1], NN));
-    TRY(dalloc(p, &p->d, NN));
+    TRY(dalloc(p, &p->dbuf[0], NN));
+    TRY(dalloc(p, &p->dbuf[1], NN));
     TRY(dalloc(p, &p->g, NN));
     TRY(dalloc(p, &p->Tf, NN));
     TRY(dalloc(p, &p->Td, NN));
@@ -418,7 +436,8 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     }
     TRYCUDA(cudaMemsetAsync(p->counters, 0, C_N * sizeof(unsigned), p->stream));
     TRYCUDA(cudaMemsetAsync(p->scal, 0, S_NSCAL * sizeof(double), p->stream));
-    TRYCUDA(cudaMemsetAsync(p->d, 0, NN * sizeof(float2), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->dbuf[0], 0, NN * sizeof(float2), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->dbuf[1], 0, NN * sizeof(float2), p->stream));
     TRYCUDA(cudaMemsetAsync(p->g, 0, NN * sizeof(float2), p->stream));
     {
         float2* tw = (float2*)malloc(sizeof(float2) * M);
@@ -572,6 +591,9 @@ int spirec_solve(spirec_plan p, const float* x0, int32_t iters, float* x_out, do
         SPIREC_CK(cudaMemcpyAsync(J_hist, p->Jdev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost,
                                   p->stream));
     SPIREC_CK(cudaStreamSynchronize(p->stream));
+    int flags = 0;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
     if (!isfinite(Jlast)) {
         set_error("criterion is not finite after %d iterations", iters);
         return SPIREC_ENUMERIC;
@@ -714,8 +736,8 @@ int spirec_objective_grad_dev(spirec_plan p, const float* x, double* J_host, flo
     }
     Join j(p);
     if ((rc = launch_toeplitz(p, (const float2*)x, p->tmp, -1)) != SPIREC_OK) return rc;
-    if ((rc = launch_update(p, (const float2*)x, (float2*)x, p->tmp, nullptr, (float2*)g, 1, nullptr)) !=
-        SPIREC_OK)
+    if ((rc = launch_update(p, (const float2*)x, (float2*)x, p->dbuf[0], p->tmp, nullptr, (float2*)g, 1,
+                            nullptr)) != SPIREC_OK)
         return rc;
     if (J_host) {
         SPIREC_CK(cudaMemcpyAsync(J_host, p->scal + S_J, sizeof(double), cudaMemcpyDeviceToHost, p->stream));

@@ -1,17 +1,25 @@
-// fft.cu -- shared-memory mixed-radix FFTs for the Toeplitz (Gram) operator
-// and its kernel spectrum.
+// fft.cu -- shared-memory FFTs for the Toeplitz (Gram) operator, its kernel
+// spectrum, and the row passes of the CG iteration that fuse into them.
 //
 // T x = H^H H x is a 2-D linear convolution of x with conj(G) (Appendix B).
-// Embedded in an M x M circulant (M >= 2N-1, section 3.4's "circular
-// convolution" after zero padding) it becomes
+// Embedded in an M x M circulant (M >= 2N-1; the "circular convolution" of
+// section 3.4 holds only after this zero padding) it becomes
 //     T x = crop_N( IFFT2( Chat .* FFT2( pad_M(x) ) ) ),
 // with Chat = FFT2(c) / M^2 real because c[-y][-x] = conj c[y][x] (the point
-// symmetry of G).  The apply runs in three passes over an N x M buffer:
-//   1. N row FFTs of the zero-padded rows (N inputs, M outputs),
-//   2. per column: FFT (N nonzero inputs) -> * Chat -> IFFT, keep rows < N,
-//   3. N row IFFTs, keep columns < N, and the dot Re<x, T x> in FP64.
-// Each FFT is a self-sorting Stockham transform in shared memory with radix
-// 2, 3, 4 or 5 stages and a twiddle table exp(-2 pi i k / M).
+// symmetry of G).  The apply runs in three passes over an N x M buffer X:
+//   rows:    N row FFTs of the zero-padded rows (N inputs, M outputs),
+//   columns: per column FFT (N nonzero inputs) -> * Chat -> IFFT, rows < N,
+//   rows:    N row IFFTs, columns < N kept.
+// Inside the CG iteration the first row pass also forms the new direction
+// d = -g + beta d_old and the first line-search sums, and the last row pass
+// forms q2 = Re<d, T d> and the first line-search step (cg.cu holds the
+// other CG kernels).
+//
+// FFTs are self-sorting Stockham transforms in shared memory.  For
+// power-of-two M (the sizes the plan picks) the transform is compile-time:
+// one radix-4 butterfly per thread per stage (plus one radix-2 stage for odd
+// log2 M), values in registers between a read and a write phase.  Any other
+// M = 2^a 3^b 5^c runs the runtime mixed-radix path with a ping-pong buffer.
 #include <stdint.h>
 
 #include "internal.cuh"
@@ -41,7 +49,9 @@ bool make_fft_plan(int M, FftPlan* p)
 
 namespace {
 
-// Small DFT of size R: X[q] = sum_r v[r] w^(r q), w = exp(-+2 pi i / R).
+// ------------------------------------------------------------ small DFTs
+
+// X[q] = sum_r v[r] w^(r q), w = exp(-+2 pi i / R).
 template <int R, bool INV>
 __device__ __forceinline__ void dft_small(float2* v)
 {
@@ -55,7 +65,7 @@ __device__ __forceinline__ void dft_small(float2* v)
         const float2 s1 = make_float2(a.x - c.x, a.y - c.y);
         const float2 s2 = make_float2(b.x + d.x, b.y + d.y);
         const float2 s3 = make_float2(b.x - d.x, b.y - d.y);
-        // forward: X1 = s1 - i s3, X3 = s1 + i s3; inverse swaps them
+        // forward: X1 = s1 - i s3, X3 = s1 + i s3; the inverse swaps them
         const float2 mis3 = INV ? make_float2(-s3.y, s3.x) : make_float2(s3.y, -s3.x);
         v[0] = make_float2(s0.x + s2.x, s0.y + s2.y);
         v[2] = make_float2(s0.x - s2.x, s0.y - s2.y);
@@ -69,7 +79,6 @@ __device__ __forceinline__ void dft_small(float2* v)
         const float2 u = make_float2(b.x - c.x, b.y - c.y);
         v[0] = make_float2(a.x + t.x, a.y + t.y);
         const float2 m = make_float2(a.x + c1 * t.x, a.y + c1 * t.y);
-        // s1 * i * u = (-s1 u.y, s1 u.x)
         v[1] = make_float2(m.x - s1 * u.y, m.y + s1 * u.x);
         v[2] = make_float2(m.x + s1 * u.y, m.y - s1 * u.x);
     } else {  // R == 5
@@ -84,7 +93,6 @@ __device__ __forceinline__ void dft_small(float2* v)
         v[0] = make_float2(a.x + b1.x + b2.x, a.y + b1.y + b2.y);
         const float2 m1 = make_float2(a.x + c1 * b1.x + c2 * b2.x, a.y + c1 * b1.y + c2 * b2.y);
         const float2 m2 = make_float2(a.x + c2 * b1.x + c1 * b2.x, a.y + c2 * b1.y + c1 * b2.y);
-        // i * (s1 d1 + s2 d2) and i * (s2 d1 - s1 d2)
         const float2 e1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
         const float2 e2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
         v[1] = make_float2(m1.x - e1.y, m1.y + e1.x);
@@ -94,11 +102,19 @@ __device__ __forceinline__ void dft_small(float2* v)
     }
 }
 
-// One Stockham stage of radix R over nseq sequences (stride ld) of length M.
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, bool inv)
+{
+    float2 w = __ldg(tw + e);
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// --------------------------------------------- runtime mixed-radix Stockham
+
 template <int R, bool INV>
-__device__ __forceinline__ void stage(const float2* __restrict__ in, float2* __restrict__ out,
-                                      int M, int Ns, int nseq, int ld,
-                                      const float2* __restrict__ tw)
+__device__ __forceinline__ void stage_rt(const float2* __restrict__ in, float2* __restrict__ out,
+                                         int M, int Ns, int nseq, int ld,
+                                         const float2* __restrict__ tw)
 {
     const int nb = M / R;
     const int tstep = M / (Ns * R);
@@ -111,11 +127,7 @@ __device__ __forceinline__ void stage(const float2* __restrict__ in, float2* __r
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-            float2 w = __ldg(&tw[k * r * tstep]);
-            if (INV) w.y = -w.y;
-            v[r] = cmul(v[r], w);
-        }
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, k * r * tstep, INV));
         dft_small<R, INV>(v);
         const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
@@ -123,20 +135,18 @@ __device__ __forceinline__ void stage(const float2* __restrict__ in, float2* __r
     }
 }
 
-// Full transform; data starts in a, scratch b; returns the buffer holding
-// the result.  Ends with a __syncthreads().
 template <bool INV>
-__device__ float2* fft_smem(float2* a, float2* b, const FftPlan& fp, int nseq, int ld,
-                            const float2* __restrict__ tw)
+__device__ float2* fft_rt(float2* a, float2* b, const FftPlan& fp, int nseq, int ld,
+                          const float2* __restrict__ tw)
 {
     int Ns = 1;
     for (int s = 0; s < fp.nstages; ++s) {
         const int R = fp.radix[s];
         switch (R) {
-        case 4: stage<4, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        case 2: stage<2, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        case 3: stage<3, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        default: stage<5, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
+        case 4: stage_rt<4, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
+        case 2: stage_rt<2, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
+        case 3: stage_rt<3, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
+        default: stage_rt<5, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
         }
         __syncthreads();
         float2* t = a;
@@ -147,57 +157,239 @@ __device__ float2* fft_smem(float2* a, float2* b, const FftPlan& fp, int nseq, i
     return a;
 }
 
-// Row transforms: rows [0, rows) of `in` (stride ld_in, first n_in entries
-// nonzero) -> `out` (stride ld_out, first n_out entries kept).  With dotx,
-// also Re<dotx[row][i], out[row][i]> for i < n_out, reduced per block and
-// finished by the last block into scal[dot_scalar].
-template <bool INV>
-__global__ void k_fft_rows(const float2* in, int ld_in, int n_in, int rows, float2* out,
-                           int ld_out, int n_out, FftPlan fp, const float2* __restrict__ tw,
-                           int rows_per_cta, const float2* __restrict__ dotx, double* part,
-                           unsigned* counter, double* scal, int dot_scalar)
+// --------------------------------------------- compile-time power-of-two
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// In-place transform of nseq sequences (stride ld) of length M; the block has
+// exactly nseq * M / 4 threads, one radix-4 butterfly each per stage.
+template <int M, bool INV>
+__device__ __forceinline__ void fft_pow2(float2* buf, int ld, const float2* __restrict__ tw)
+{
+    constexpr int LOG2M = ilog2(M);
+    constexpr int NB = M / 4;
+    const int q = threadIdx.x / NB, j = threadIdx.x % NB;
+    float2* s = buf + q * ld;
+#pragma unroll
+    for (int lns = 0; lns + 2 <= LOG2M; lns += 2) {
+        const int Ns = 1 << lns;
+        const int k = j & (Ns - 1);
+        float2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = s[j + r * NB];
+        __syncthreads();
+#pragma unroll
+        for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], twiddle(tw, (k * r) << (LOG2M - lns - 2), INV));
+        dft_small<4, INV>(v);
+        const int base = ((j >> lns) << (lns + 2)) + k;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s[base + r * Ns] = v[r];
+        __syncthreads();
+    }
+    if (LOG2M & 1) {  // last stage radix 2, Ns = M/2: butterflies jj and jj + M/2
+        float2 a[2], b[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            a[h] = s[j + h * NB];
+            b[h] = s[j + h * NB + M / 2];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h * NB;
+            float2 v[2] = {a[h], cmul(b[h], twiddle(tw, jj, INV))};
+            dft_small<2, INV>(v);
+            s[jj] = v[0];
+            s[jj + M / 2] = v[1];
+        }
+        __syncthreads();
+    }
+}
+
+// Transform dispatch: MC > 0 compile-time size (in place, nseq*MC/4 threads),
+// MC == 0 runtime plan (ping-pong, any block size).  Returns the buffer with
+// the result; ends with __syncthreads().
+template <int MC, bool INV>
+__device__ __forceinline__ float2* fft_block(float2* a, float2* b, const FftPlan& fp, int nseq,
+                                             int ld, const float2* __restrict__ tw)
+{
+    if constexpr (MC > 0) {
+        fft_pow2<MC, INV>(a, ld, tw);
+        return a;
+    } else {
+        return fft_rt<INV>(a, b, fp, nseq, ld, tw);
+    }
+}
+
+// --------------------------------------------- CG helpers
+
+__device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// d = -g + beta d_old (d = -g on a restart, so a stale d_old never enters).
+__device__ __forceinline__ float2 new_direction(float2 g, float2 dold, float beta, bool restart)
+{
+    return restart ? make_float2(-g.x, -g.y) : make_float2(fmaf(beta, dold.x, -g.x), fmaf(beta, dold.y, -g.y));
+}
+
+// ------------------------------------------------------------- row pass 1
+
+// MODE 0: row FFTs of `in` (rows [0, rows), n_in nonzero inputs per row at
+// stride ld_in) into X (stride M).
+// MODE 1 (CG): the input rows are the new direction d = -g + beta d_old,
+// written to c.d_new; also the block sums of
+//   q1   = Re<d, 2 (Tf - D)>
+//   num0 = sum_e lambda b(|z_e|) Re(conj(z_e) w_e),  den0 = sum_e lambda b(|z_e|) |w_e|^2
+// (first line-search step, t = 0), finished by the last block into scal.
+template <int MC, int MODE>
+__global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, int rows,
+                           float2* __restrict__ X, FftPlan fp, const float2* __restrict__ tw,
+                           int rpc, CgPass c)
 {
     extern __shared__ float2 sm[];
     const int M = fp.M;
     float2* a = sm;
-    float2* b = sm + rows_per_cta * M;
-    const int r0 = blockIdx.x * rows_per_cta;
-    const int nr = min(rows_per_cta, rows - r0);
-    for (int e = threadIdx.x; e < nr * M; e += blockDim.x) {
-        const int q = e / M, i = e - q * M;
-        a[q * M + i] = i < n_in ? in[(int64_t)(r0 + q) * ld_in + i] : make_float2(0.f, 0.f);
+    float2* b = sm + rpc * M;
+    const int r0 = blockIdx.x * rpc;
+    const int nr = min(rpc, rows - r0);
+    const int N = n_in;
+    float beta = 0.f;
+    bool restart = true;
+    if (MODE == 1) {
+        const double bd = c.scal[S_BETA];
+        beta = (float)bd;
+        restart = bd == 0.0;
+    }
+    for (int e = threadIdx.x; e < rpc * M; e += blockDim.x) {
+        const int q = e / M, m = e - q * M;
+        float2 v = make_float2(0.f, 0.f);
+        if (q < nr && m < N) {
+            const int64_t o = (int64_t)(r0 + q) * ld_in + m;
+            if (MODE == 0) {
+                v = in[o];
+            } else {
+                v = new_direction(c.g[o], c.d_old[o], beta, restart);
+                c.d_new[o] = v;
+            }
+        }
+        a[e] = v;
     }
     __syncthreads();
-    float2* res = fft_smem<INV>(a, b, fp, nr, M, tw);
-    float acc = 0.f;
-    for (int e = threadIdx.x; e < nr * n_out; e += blockDim.x) {
-        const int q = e / n_out, i = e - q * n_out;
-        const float2 v = res[q * M + i];
-        const int64_t o = (int64_t)(r0 + q) * ld_out + i;
-        out[o] = v;
-        if (dotx) {
-            const float2 xv = dotx[o];
-            acc = fmaf(xv.x, v.x, fmaf(xv.y, v.y, acc));
+    if (MODE == 1) {
+        const Reg reg = c.reg;
+        float q1 = 0.f, num = 0.f, den = 0.f;
+        for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+            const int q = e / N, m = e - q * N;
+            const int n = r0 + q;
+            const int64_t o = (int64_t)n * N + m;
+            const float2 dn = a[q * M + m];
+            const float2 fp_ = c.f[o];
+            q1 += 2.f * redot(dn, f2sub(c.Tf[o], c.D[o]));
+            if (reg.lambda1 != 0.f) {
+                if (m + 1 < N) {
+                    const float2 w = f2sub(a[q * M + m + 1], dn);
+                    const float2 z = f2sub(c.f[o + 1], fp_);
+                    const float bw = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z));
+                    num = fmaf(bw, redot(z, w), num);
+                    den = fmaf(bw, redot(w, w), den);
+                }
+                if (n + 1 < N) {
+                    const float2 dd = new_direction(c.g[o + N], c.d_old[o + N], beta, restart);
+                    const float2 w = f2sub(dd, dn);
+                    const float2 z = f2sub(c.f[o + N], fp_);
+                    const float bw = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z));
+                    num = fmaf(bw, redot(z, w), num);
+                    den = fmaf(bw, redot(w, w), den);
+                }
+            }
+            if (reg.lambda0 != 0.f) {
+                const float bw = reg.lambda0 * phi_weight(reg.kind, reg.alpha0, redot(fp_, fp_));
+                num = fmaf(bw, redot(fp_, dn), num);
+                den = fmaf(bw, redot(dn, dn), den);
+            }
+        }
+        FF v[3] = {FF{q1, 0.f}, FF{num, 0.f}, FF{den, 0.f}};
+        block_sum_ff<3>(v);
+        store_parts<3>(v, c.parts, kMaxParts);
+        if (last_block(c.counter)) {
+            FF t[3];
+            sum_parts_ff<3>(c.parts, kMaxParts, gridDim.x, t);
+            if (threadIdx.x == 0) {
+                c.scal[S_Q1] = ff_to_double(t[0]);
+                c.scal[S_NUM0] = ff_to_double(t[1]);
+                c.scal[S_DEN0] = ff_to_double(t[2]);
+                *c.counter = 0u;
+            }
         }
     }
+    float2* res = fft_block<MC, false>(a, b, fp, nr, M, tw);
+    for (int e = threadIdx.x; e < nr * M; e += blockDim.x) {
+        const int q = e / M, m = e - q * M;
+        X[(int64_t)(r0 + q) * M + m] = res[e];
+    }
+}
+
+// ------------------------------------------------------------- row pass 3
+
+// Row IFFTs of X (rows [0, rows)), first n_out columns to out (stride n_out).
+// With dotx: s = Re<dotx, out> reduced over the grid; MODE 0 stores it in
+// scal[dot_scalar]; MODE 1 (CG) stores q2 = s and the first line-search step
+//   t1 = -(q1 + num0) / (2 q2 + den0)   (0 when the curvature is not > 0).
+template <int MC, int MODE>
+__global__ void k_rows_inv(const float2* __restrict__ X, int rows, float2* __restrict__ out,
+                           int n_out, FftPlan fp, const float2* __restrict__ tw, int rpc,
+                           const float2* __restrict__ dotx, CgPass c, int dot_scalar)
+{
+    extern __shared__ float2 sm[];
+    const int M = fp.M;
+    float2* a = sm;
+    float2* b = sm + rpc * M;
+    const int r0 = blockIdx.x * rpc;
+    const int nr = min(rpc, rows - r0);
+    for (int e = threadIdx.x; e < rpc * M; e += blockDim.x) {
+        const int q = e / M;
+        a[e] = q < nr ? X[(int64_t)r0 * M + e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2* res = fft_block<MC, true>(a, b, fp, nr, M, tw);
+    float acc = 0.f;
+    for (int e = threadIdx.x; e < nr * n_out; e += blockDim.x) {
+        const int q = e / n_out, m = e - q * n_out;
+        const float2 v = res[q * M + m];
+        const int64_t o = (int64_t)(r0 + q) * n_out + m;
+        out[o] = v;
+        if (dotx) acc += redot(dotx[o], v);
+    }
     if (dotx) {
-        const double tot = block_sum((double)acc);
-        if (threadIdx.x == 0) part[blockIdx.x] = tot;
-        if (last_block(counter)) {
-            const double s = sum_parts(part, gridDim.x);
+        FF v[1] = {FF{acc, 0.f}};
+        block_sum_ff<1>(v);
+        store_parts<1>(v, c.parts, kMaxParts);
+        if (last_block(c.counter)) {
+            FF t[1];
+            sum_parts_ff<1>(c.parts, kMaxParts, gridDim.x, t);
             if (threadIdx.x == 0) {
-                scal[dot_scalar] = s;
-                *counter = 0u;
+                const double s = ff_to_double(t[0]);
+                if (MODE == 0) {
+                    c.scal[dot_scalar] = s;
+                } else {
+                    c.scal[S_Q2] = s;
+                    const double curv = 2.0 * s + c.scal[S_DEN0];
+                    c.scal[S_T1] = curv > 0.0 ? -(c.scal[S_Q1] + c.scal[S_NUM0]) / curv : 0.0;
+                }
+                *c.counter = 0u;
             }
         }
     }
 }
 
-// Column pass of the Toeplitz apply: for columns [x0, x0+cpc) of the N x M
-// buffer X: FFT of the N nonzero rows, multiply by Chat[x][ky], IFFT, keep
-// rows < N.  Sequences sit at stride M+1 in shared memory (bank spread).
-__global__ void k_fft_cols_filter(float2* X, int N, FftPlan fp, const float2* __restrict__ tw,
-                                  const float* __restrict__ Chat, int cpc)
+// ------------------------------------------------------------- column pass
+
+// Columns [x0, x0+cpc) of the N x M buffer X: FFT of the n_in nonzero rows,
+// multiply by Chat[x][ky], IFFT, keep rows < n_out.  Sequences sit at stride
+// M+1 in shared memory (spreads the banks of the transposed loads).
+template <int MC>
+__global__ void k_cols_filter(float2* X, int n_in, int n_out, FftPlan fp, const float2* __restrict__ tw,
+                              const float* __restrict__ Chat, int cpc)
 {
     extern __shared__ float2 sm[];
     const int M = fp.M;
@@ -206,31 +398,32 @@ __global__ void k_fft_cols_filter(float2* X, int N, FftPlan fp, const float2* __
     float2* b = sm + cpc * ld;
     const int x0 = blockIdx.x * cpc;
     const int nc = min(cpc, M - x0);
-    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
-        const int y = e / nc, c = e - y * nc;
-        a[c * ld + y] = y < N ? X[(int64_t)y * M + x0 + c] : make_float2(0.f, 0.f);
+    for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
+        const int y = e / cpc, cc = e - y * cpc;
+        a[cc * ld + y] = (y < n_in && cc < nc) ? X[(int64_t)y * M + x0 + cc] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* res = fft_smem<false>(a, b, fp, nc, ld, tw);
+    float2* res = fft_block<MC, false>(a, b, fp, cpc, ld, tw);
+    for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
+        const int cc = e / M, ky = e - cc * M;
+        const float h = cc < nc ? __ldg(&Chat[(int64_t)(x0 + cc) * M + ky]) : 0.f;
+        const float2 v = res[cc * ld + ky];
+        res[cc * ld + ky] = make_float2(v.x * h, v.y * h);
+    }
+    __syncthreads();
     float2* other = res == a ? b : a;
-    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
-        const int c = e / M, ky = e - c * M;
-        const float h = __ldg(&Chat[(int64_t)(x0 + c) * M + ky]);
-        const float2 v = res[c * ld + ky];
-        res[c * ld + ky] = make_float2(v.x * h, v.y * h);
-    }
-    __syncthreads();
-    float2* res2 = fft_smem<true>(res, other, fp, nc, ld, tw);
-    for (int e = threadIdx.x; e < nc * N; e += blockDim.x) {
-        const int y = e / nc, c = e - y * nc;
-        X[(int64_t)y * M + x0 + c] = res2[c * ld + y];
+    float2* res2 = fft_block<MC, true>(res, other, fp, cpc, ld, tw);
+    for (int e = threadIdx.x; e < cpc * n_out; e += blockDim.x) {
+        const int y = e / cpc, cc = e - y * cpc;
+        if (cc < nc) X[(int64_t)y * M + x0 + cc] = res2[cc * ld + y];
     }
 }
 
 // Column FFTs of the M x M circulant and the real spectrum:
 // Chat[x][ky] = Re(FFT2 c)[ky][x] / M^2.
-__global__ void k_fft_cols_spectrum(const float2* cwork, FftPlan fp, const float2* __restrict__ tw,
-                                    float* Chat, int cpc)
+template <int MC>
+__global__ void k_cols_spectrum(const float2* cwork, FftPlan fp, const float2* __restrict__ tw,
+                                float* Chat, int cpc)
 {
     extern __shared__ float2 sm[];
     const int M = fp.M;
@@ -239,16 +432,16 @@ __global__ void k_fft_cols_spectrum(const float2* cwork, FftPlan fp, const float
     float2* b = sm + cpc * ld;
     const int x0 = blockIdx.x * cpc;
     const int nc = min(cpc, M - x0);
-    for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
-        const int y = e / nc, c = e - y * nc;
-        a[c * ld + y] = cwork[(int64_t)y * M + x0 + c];
+    for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
+        const int y = e / cpc, cc = e - y * cpc;
+        a[cc * ld + y] = cc < nc ? cwork[(int64_t)y * M + x0 + cc] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    float2* res = fft_smem<false>(a, b, fp, nc, ld, tw);
+    float2* res = fft_block<MC, false>(a, b, fp, cpc, ld, tw);
     const float inv = 1.0f / ((float)M * (float)M);
     for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
-        const int c = e / M, ky = e - c * M;
-        Chat[(int64_t)(x0 + c) * M + ky] = res[c * ld + ky].x * inv;
+        const int cc = e / M, ky = e - cc * M;
+        Chat[(int64_t)(x0 + cc) * M + ky] = res[cc * ld + ky].x * inv;
     }
 }
 
@@ -277,71 +470,234 @@ __global__ void k_embed(const float2* __restrict__ G, int N, int M, float2* cwor
     }
 }
 
+// ------------------------------------------------------------- launch shapes
+
 constexpr int kFftSmemCap = 200 * 1024;
 
-int rows_per_cta(int M) { return M >= 1024 ? 1 : 1024 / M; }
-int cols_per_cta(int M)
+struct Shape {
+    int per_cta;  // rows or columns per CTA
+    int threads;
+    size_t smem;
+};
+
+// Compile-time path: nseq * M / 4 threads (<= 1024), single buffer.
+// Runtime path: 256 threads, ping-pong buffers.
+Shape row_shape(int M, bool pow2)
 {
-    int c = M >= 1024 ? 4 : (M >= 512 ? 8 : 16);
-    const int cap = kFftSmemCap / (2 * (M + 1) * (int)sizeof(float2));
-    return c < cap ? c : (cap < 1 ? 1 : cap);
+    if (pow2) {
+        const int nb = M / 4;
+        const int rpc = nb >= 256 ? 1 : 256 / nb;
+        return Shape{rpc, rpc * nb, (size_t)rpc * M * sizeof(float2)};
+    }
+    const int rpc = M >= 1024 ? 1 : 1024 / M;
+    return Shape{rpc, 256, 2 * (size_t)rpc * M * sizeof(float2)};
 }
+
+Shape col_shape(int M, bool pow2)
+{
+    if (pow2) {
+        const int nb = M / 4;
+        int cpc = nb >= 1024 ? 1 : 1024 / nb;
+        while (cpc > 1 && (size_t)cpc * (M + 1) * sizeof(float2) > (size_t)kFftSmemCap) cpc /= 2;
+        return Shape{cpc, cpc * nb, (size_t)cpc * (M + 1) * sizeof(float2)};
+    }
+    int cpc = M >= 1024 ? 4 : (M >= 512 ? 8 : 16);
+    while (cpc > 1 && 2 * (size_t)cpc * (M + 1) * sizeof(float2) > (size_t)kFftSmemCap) --cpc;
+    return Shape{cpc, 256, 2 * (size_t)cpc * (M + 1) * sizeof(float2)};
+}
+
+template <int MC>
+int set_attrs()
+{
+    const int bytes = kFftSmemCap;
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_inv<MC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_inv<MC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_cols_filter<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_cols_spectrum<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return SPIREC_OK;
+}
+
+// Calls f.template operator()<MC>() with the compile-time size for M, or
+// MC = 0 for sizes without a specialisation.
+template <typename F>
+int with_size(int M, F&& f)
+{
+    switch (M) {
+    case 16: return f.template operator()<16>();
+    case 32: return f.template operator()<32>();
+    case 64: return f.template operator()<64>();
+    case 128: return f.template operator()<128>();
+    case 256: return f.template operator()<256>();
+    case 512: return f.template operator()<512>();
+    case 1024: return f.template operator()<1024>();
+    case 2048: return f.template operator()<2048>();
+    case 4096: return f.template operator()<4096>();
+    default: return f.template operator()<0>();
+    }
+}
+
+bool is_pow2_specialised(int M) { return M >= 16 && M <= 4096 && (M & (M - 1)) == 0; }
+
+CgPass plain_pass(spirec_plan p, int slot, unsigned* counter)
+{
+    CgPass c{};
+    c.parts = reinterpret_cast<float2*>(p->part) + (size_t)slot * kMaxParts;
+    c.counter = counter;
+    c.scal = p->scal;
+    c.reg = p->reg;
+    return c;
+}
+
+struct AttrAll {
+    template <int MC>
+    int operator()() { return MC > 0 ? set_attrs<MC>() : SPIREC_OK; }
+};
+
+struct LaunchRowsFwd {
+    spirec_plan p;
+    const float2* in;
+    int ld_in, n_in, rows, mode, blocks;
+    Shape s;
+    CgPass c;
+    template <int MC>
+    int operator()()
+    {
+        if (mode == 0)
+            k_rows_fwd<MC, 0><<<blocks, s.threads, s.smem, p->stream>>>(in, ld_in, n_in, rows, p->X, p->fft,
+                                                                        p->twiddle, s.per_cta, c);
+        else
+            k_rows_fwd<MC, 1><<<blocks, s.threads, s.smem, p->stream>>>(in, ld_in, n_in, rows, p->X, p->fft,
+                                                                        p->twiddle, s.per_cta, c);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 1;
+        return SPIREC_OK;
+    }
+};
+
+struct LaunchCols {
+    spirec_plan p;
+    int n_in, n_out, blocks;
+    Shape s;
+    template <int MC>
+    int operator()()
+    {
+        k_cols_filter<MC><<<blocks, s.threads, s.smem, p->stream>>>(p->X, n_in, n_out, p->fft, p->twiddle,
+                                                                    p->Chat, s.per_cta);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 1;
+        return SPIREC_OK;
+    }
+};
+
+struct LaunchRowsInv {
+    spirec_plan p;
+    float2* out;
+    int mode;
+    const float2* dotx;
+    int dot_scalar, blocks;
+    Shape s;
+    CgPass c;
+    template <int MC>
+    int operator()()
+    {
+        if (mode == 0)
+            k_rows_inv<MC, 0><<<blocks, s.threads, s.smem, p->stream>>>(p->X, p->N, out, p->N, p->fft,
+                                                                        p->twiddle, s.per_cta, dotx, c, dot_scalar);
+        else
+            k_rows_inv<MC, 1><<<blocks, s.threads, s.smem, p->stream>>>(p->X, p->N, out, p->N, p->fft,
+                                                                        p->twiddle, s.per_cta, dotx, c, dot_scalar);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 1;
+        return SPIREC_OK;
+    }
+};
+
+struct LaunchSpectrum {
+    spirec_plan p;
+    Shape rs, cs;
+    template <int MC>
+    int operator()()
+    {
+        const int M = p->M;
+        CgPass c{};
+        // rows of the circulant, in place (each block reads its rows fully first)
+        k_rows_fwd<MC, 0><<<(M + rs.per_cta - 1) / rs.per_cta, rs.threads, rs.smem, p->stream>>>(
+            p->cwork, M, M, M, p->cwork, p->fft, p->twiddle, rs.per_cta, c);
+        SPIREC_CK(cudaGetLastError());
+        k_cols_spectrum<MC><<<(M + cs.per_cta - 1) / cs.per_cta, cs.threads, cs.smem, p->stream>>>(
+            p->cwork, p->fft, p->twiddle, p->Chat, cs.per_cta);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 2;
+        return SPIREC_OK;
+    }
+};
 
 }  // namespace
 
 int fft_setup_attributes(int)
 {
-    // one fixed ceiling for every plan: per-function attributes are global
-    const int bytes = kFftSmemCap;
-    SPIREC_CK(cudaFuncSetAttribute(k_fft_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SPIREC_CK(cudaFuncSetAttribute(k_fft_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SPIREC_CK(cudaFuncSetAttribute(k_fft_cols_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SPIREC_CK(cudaFuncSetAttribute(k_fft_cols_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int rc;
+    if ((rc = set_attrs<0>()) != SPIREC_OK) return rc;
+    for (int M = 16; M <= 4096; M *= 2)
+        if ((rc = with_size(M, AttrAll{})) != SPIREC_OK) return rc;
     return SPIREC_OK;
+}
+
+int launch_rows_fwd(spirec_plan p, const float2* in, int ld_in, int n_in, int rows, int mode,
+                    const CgPass* cg)
+{
+    const int M = p->M;
+    const Shape s = row_shape(M, is_pow2_specialised(M));
+    const int blocks = (rows + s.per_cta - 1) / s.per_cta;
+    if (mode == 1 && blocks > kMaxParts) {
+        set_error("too many row blocks");
+        return SPIREC_EUNSUPPORTED;
+    }
+    const CgPass c = cg ? *cg : plain_pass(p, 0, nullptr);
+    return with_size(M, LaunchRowsFwd{p, in, ld_in, n_in, rows, mode, blocks, s, c});
+}
+
+int launch_cols(spirec_plan p, int n_in, int n_out)
+{
+    const int M = p->M;
+    const Shape s = col_shape(M, is_pow2_specialised(M));
+    const int blocks = (M + s.per_cta - 1) / s.per_cta;
+    return with_size(M, LaunchCols{p, n_in, n_out, blocks, s});
+}
+
+int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, const CgPass* cg,
+                    int dot_scalar)
+{
+    const int M = p->M, N = p->N;
+    const Shape s = row_shape(M, is_pow2_specialised(M));
+    const int blocks = (N + s.per_cta - 1) / s.per_cta;
+    if (dotx && blocks > kMaxParts) {
+        set_error("too many row blocks");
+        return SPIREC_EUNSUPPORTED;
+    }
+    const CgPass c = cg ? *cg : plain_pass(p, P_MISC, p->counters + C_MISC);
+    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c});
 }
 
 int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar)
 {
-    const int N = p->N, M = p->M;
-    const int rpc = rows_per_cta(M);
-    const int cpc = cols_per_cta(M);
-    const size_t rbytes = 2 * (size_t)rpc * M * sizeof(float2);
-    const size_t cbytes = 2 * (size_t)cpc * (M + 1) * sizeof(float2);
-    const int threads = 256;
-    const int rblocks = (N + rpc - 1) / rpc;
-    k_fft_rows<false><<<rblocks, threads, rbytes, p->stream>>>(
-        x, N, N, N, p->X, M, M, p->fft, p->twiddle, rpc, nullptr, nullptr, nullptr, nullptr, 0);
-    SPIREC_CK(cudaGetLastError());
-    k_fft_cols_filter<<<(M + cpc - 1) / cpc, threads, cbytes, p->stream>>>(p->X, N, p->fft, p->twiddle, p->Chat, cpc);
-    SPIREC_CK(cudaGetLastError());
-    const bool dot = dot_scalar >= 0;
-    if (dot && rblocks > kMaxParts) return SPIREC_EUNSUPPORTED;
-    k_fft_rows<true><<<rblocks, threads, rbytes, p->stream>>>(
-        p->X, M, M, N, Tx, N, N, p->fft, p->twiddle, rpc, dot ? x : nullptr,
-        dot ? p->part + (size_t)P_Q2 * kMaxParts : nullptr, dot ? p->counters + C_TOEP : nullptr,
-        p->scal, dot ? dot_scalar : 0);
-    SPIREC_CK(cudaGetLastError());
-    p->launches += 3;
-    return SPIREC_OK;
+    int rc;
+    const int N = p->N;
+    if ((rc = launch_rows_fwd(p, x, N, N, N, 0, nullptr)) != SPIREC_OK) return rc;
+    if ((rc = launch_cols(p, N, N)) != SPIREC_OK) return rc;
+    return launch_rows_inv(p, Tx, 0, dot_scalar >= 0 ? x : nullptr, nullptr, dot_scalar);
 }
 
 int launch_spectrum(spirec_plan p)
 {
     const int N = p->N, M = p->M;
-    const int rpc = rows_per_cta(M);
-    const int cpc = cols_per_cta(M);
-    const size_t rbytes = 2 * (size_t)rpc * M * sizeof(float2);
-    const size_t cbytes = 2 * (size_t)cpc * (M + 1) * sizeof(float2);
     k_embed<<<4 * 152, 256, 0, p->stream>>>(p->G, N, M, p->cwork);
     SPIREC_CK(cudaGetLastError());
-    k_fft_rows<false><<<(M + rpc - 1) / rpc, 256, rbytes, p->stream>>>(
-        p->cwork, M, M, M, p->cwork, M, M, p->fft, p->twiddle, rpc, nullptr, nullptr, nullptr,
-        nullptr, 0);
-    SPIREC_CK(cudaGetLastError());
-    k_fft_cols_spectrum<<<(M + cpc - 1) / cpc, 256, cbytes, p->stream>>>(p->cwork, p->fft, p->twiddle, p->Chat, cpc);
-    SPIREC_CK(cudaGetLastError());
-    p->launches += 3;
-    return SPIREC_OK;
+    p->launches += 1;
+    const bool pow2 = is_pow2_specialised(M);
+    return with_size(M, LaunchSpectrum{p, row_shape(M, pow2), col_shape(M, pow2)});
 }
 
 }  // namespace spirec

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/spirec.h"
+#include "penalty.cuh"
 
 namespace spirec {
 
@@ -32,42 +33,60 @@ bool make_fft_plan(int M, FftPlan* p);
 
 // ----------------------------------------------------------- partial sums
 
-// Slots of the partial-sum array (each slot holds kMaxParts doubles, one per
-// block of the kernel that produced them).
-constexpr int kMaxParts = 1024;
+// Slots of the block-partial array (float-float pairs, kMaxParts per slot,
+// one per block of the kernel that produced them).
+constexpr int kMaxParts = 4096;
 enum PartSlot {
-    P_Q2 = 0,    // Re<d, T d>
-    P_Q1 = 1,    // Re<d, g_ls>
-    P_LS = 2,    // line-search step: num, den (2 slots)
-    P_UPD = 4,   // gradient/update: 6 slots (see k_update)
-    P_MISC = 10, // one-off sums (||s||^2)
-    P_NSLOTS = 12
+    P_ROWA = 0,   // row pass 1 of the CG: q1, num0, den0 (3 slots)
+    P_ROWC = 3,   // row pass 3: q2 (or a plain dot)
+    P_LS = 4,     // line-search step: num, den (2 slots)
+    P_UPD = 6,    // gradient/update: 6 slots (see k_update)
+    P_MISC = 12,  // one-off sums (2 slots)
+    P_NSLOTS = 14
 };
-
 constexpr int kUpdVals = 6;  // sums of the update kernel
 
 // Arrival counters of the last-block reductions, one per kernel kind.
-enum Counter { C_TOEP = 0, C_LS = 1, C_UPD = 2, C_DIR = 3, C_MISC = 4, C_N = 8 };
+enum Counter { C_ROWA = 0, C_ROWC = 1, C_LS = 2, C_UPD = 3, C_MISC = 4, C_AMAX = 5, C_N = 8 };
+
+// Bits of the device error word (plan->dflag).
+enum DeviceError { E_TRAJ = 1, E_TIMEOUT = 2 };
 
 // Device scalars (FP64), written by the last block of the kernel that
 // reduces them and read by later kernels in stream order.
 enum Scalar {
-    S_SS = 0,    // ||s||^2
-    S_Q1 = 1,    // Re<d, g_ls>
-    S_Q2 = 2,    // ||H d||^2 = Re<d, T d>
-    S_T1 = 3,    // line-search steps t1, t2, t3 (S_T1 + j)
+    S_SS = 0,     // ||s||^2
+    S_Q1 = 1,     // Re<d, g_ls>
+    S_Q2 = 2,     // ||H d||^2 = Re<d, T d>
+    S_T1 = 3,     // line-search steps t1, t2, t3 (S_T1 + j)
     S_T3 = 5,
-    S_GG = 6,    // <g, g> of the current gradient
-    S_BETA = 7,  // Polak-Ribiere beta for the next direction (0 = restart)
-    S_J = 8,     // J of the current iterate
-    S_R = 9,     // R of the current iterate
-    S_TMP = 10,  // result of a one-off dot
+    S_GG = 6,     // <g, g> of the current gradient
+    S_BETA = 7,   // Polak-Ribiere beta for the next direction (0 = restart)
+    S_J = 8,      // J of the current iterate
+    S_R = 9,      // R of the current iterate
+    S_TMP = 10,   // result of a one-off dot
+    S_NUM0 = 11,  // penalty part of h'(0)
+    S_DEN0 = 12,  // penalty part of the majorant curvature at t = 0
     S_NSCAL = 16
 };
 
 struct Reg {
     float lambda1, alpha1, lambda0, alpha0;
     int kind;
+};
+
+// Pointers of the fused CG passes (row pass 1 and 3 of the Toeplitz apply).
+struct CgPass {
+    const float2* g;
+    const float2* d_old;
+    float2* d_new;
+    const float2* f;
+    const float2* Tf;
+    const float2* D;
+    Reg reg;
+    float2* parts;
+    unsigned* counter;
+    double* scal;
 };
 
 // ------------------------------------------------------------------- plan
@@ -97,13 +116,13 @@ struct spirec_plan_s {
     float2* D;     // N x N
     float2* s;     // L
     float2* f[2];
-    float2* d;
+    float2* dbuf[2];  // direction of iteration k in dbuf[k & 1]
     float2* g;
     float2* Tf;
     float2* Td;
     float2* tmp;   // N x N scratch for operator calls
     float2* twiddle;  // M entries, exp(-2 pi i k / M)
-    double* part;  // P_NSLOTS x kMaxParts
+    double* part;  // P_NSLOTS x kMaxParts (float-float pairs)
     double* scal;  // S_NSCAL
     unsigned* counters;  // C_N
     double* Jdev;  // J history (device), capacity Jcap
@@ -148,14 +167,19 @@ int launch_forward(spirec_plan p, const float2* x, float2* y);  // y = H x
 // Toeplitz T x -> Tx; with dot_scalar >= 0 also scal[dot_scalar] = Re<x, Tx>.
 int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar);
 int fft_setup_attributes(int maxM);
+// Toeplitz passes; mode 1 = the fused CG forms (see fft.cu).
+int launch_rows_fwd(spirec_plan p, const float2* in, int ld_in, int n_in, int rows, int mode,
+                    const CgPass* cg);
+int launch_cols(spirec_plan p, int n_in, int n_out);
+int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, const CgPass* cg,
+                    int dot_scalar);
 
-// CG pieces (cg.cu).  Iterate k reads f[k & 1] and writes f[(k + 1) & 1].
+// CG pieces (cg.cu).  Iteration k reads f[k & 1] and writes f[(k + 1) & 1].
 int launch_data_norm(spirec_plan p);
 // gradient at f (Tf given): g, J -> Jout, <g,g>; first = no step taken
-int launch_update(spirec_plan p, const float2* f_in, float2* f_out, float2* Tf, const float2* Td,
-                  float2* g, int first, double* Jout);
-int launch_direction(spirec_plan p, int first);
-int launch_line_search(spirec_plan p, const float2* f, int step);
+int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf,
+                  const float2* Td, float2* g, int first, double* Jout);
+int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step);
 int cg_iteration(spirec_plan p, int k, double* Jdev);
 
 // tensor-core contractions (FP16x3 / BF16x3)

@@ -1,22 +1,608 @@
-// nudft_tc.cu -- tensor-core (tcgen05) contractions; placeholder until the
-// split-precision kernels land.
+// nudft_tc.cu -- tensor-core (tcgen05, sm_103a) contractions of the exact
+// NUDFT: G (Eq. AnnMatG) and D = H^H s (Eq. AnnMatGD).
+//
+// Both are complex GEMMs C[i][c] = sum_l A(l,i) B(l,c) of depth K = L whose
+// operands are phases generated on the fly (phase.cuh).  A CTA owns a tile of
+// 128 complex rows x 128 complex columns and runs it as ONE real GEMM
+//      [Ar Ai] (128 x 2K)  x  [[Br Bi]; [-Bi Br]] (2K x 256)
+// so the accumulator (128 lanes x 256 FP32 columns of tensor memory) holds
+// Re C in columns 0..127 and Im C in columns 128..255.
+//
+// Split precision: every operand value x is stored as x_hi = fp16(x) (or
+// bf16) and x_lo = fp16(x - x_hi); three MMAs hi*hi + hi*lo + lo*hi feed the
+// same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for FP16).
+//
+// Pipeline per CTA (288 threads):
+//   warps 0-7  producers: per stage of 32 samples, build the factor tables
+//              exp(i2pi k (base + 16a)) and exp(i2pi k b), multiply them out
+//              into the four operand tiles (A_hi, A_lo, B_hi, B_lo) in the
+//              128-byte-swizzled K-major layout the MMA reads, then arrive on
+//              full[stage];
+//   warp 8     allocates 256 TMEM columns; one lane waits on full[stage],
+//              issues 12 tcgen05.mma (K = 16 each) and commits to empty[stage];
+//   warps 0-7  drain: every SEG stages (512 samples) the finished accumulator
+//              is read with tcgen05.ld and added, in FP32 with round-to-
+//              nearest, to the CTA's split-K partial tile in global memory
+//              (column-major, so each lane row maps to consecutive addresses).
+// The tensor core's FP32 accumulation loses about one unit in the last place
+// per accumulation step (truncation-like, measured: 2.8e-4 relative after
+// 12k steps); draining every 192 steps bounds that error, and the two TMEM
+// accumulators (2 x 256 columns) let the MMA run on while one is drained.
+// Two stages of 96 KB double-buffer generation against the tensor core.
+// Every mbarrier wait is bounded in time; on expiry the kernel records an
+// error bit, lets the other roles run out, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
 #include "internal.cuh"
+#include "phase.cuh"
 
 namespace spirec {
 
-size_t kpart_floats_tc(int, int64_t, int) { return 0; }
-int tc_setup_attributes() { return SPIREC_OK; }
+namespace {
 
-int launch_gram_tc(spirec_plan)
+constexpr int TC_ROWS = 128;        // complex rows per tile (MMA M)
+constexpr int TC_COLS = 128;        // complex columns per tile (MMA N = 256 real)
+constexpr int TC_KS = 32;           // samples per stage (64 real K per operand set)
+constexpr int TC_STAGES = 2;
+constexpr int TC_PRODUCERS = 256;   // 8 warps
+constexpr int TC_THREADS = TC_PRODUCERS + 32;
+constexpr int TC_TAB = 24;          // 8 base + 16 offset phasors per sample
+constexpr int TC_SEG = 16;          // stages per accumulator segment
+constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
+constexpr uint32_t B_BYTES = 2 * TC_COLS * 128;      // 256 rows x 64 halves
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr uint32_t TAB_OFF = TC_STAGES * STAGE_BYTES;
+constexpr uint32_t TAB_BYTES = 2 * TC_KS * TC_TAB * 8;
+constexpr uint32_t BAR_OFF = TAB_OFF + TAB_BYTES;
+constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr int kErrTimeout = E_TIMEOUT;
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    set_error("mixed-precision contraction not built");
-    return SPIREC_EUNSUPPORTED;
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-int launch_adjoint_tc(spirec_plan, const float2*, float2*)
+__device__ __forceinline__ uint64_t globaltimer()
 {
-    set_error("mixed-precision contraction not built");
-    return SPIREC_EUNSUPPORTED;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after kWaitNs without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void producers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), leading offset unused for this layout, version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (64ull << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    // load and wait in one statement: the registers are valid only after the wait
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+// Byte offset of 16-byte chunk `chunk` (0..7) of K-major row `row` in a
+// 128-byte-swizzled tile whose base is 1024-aligned.
+__device__ __forceinline__ uint32_t sw128(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// hi/lo split of 8 values into 4 packed words each.
+template <bool BF16>
+__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float a = x[2 * q], b = x[2 * q + 1];
+        if (BF16) {
+            const __nv_bfloat162 hv = __floats2bfloat162_rn(a, b);
+            const float2 back = __bfloat1622float2(hv);
+            const __nv_bfloat162 lv = __floats2bfloat162_rn(a - back.x, b - back.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        } else {
+            const __half2 hv = __floats2half2_rn(a, b);
+            const float2 back = __half22float2(hv);
+            const __half2 lv = __floats2half2_rn(a - back.x, b - back.y);
+            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
+            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
+        }
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ uint4 neg4(uint4 v)
+{
+    const uint32_t s = 0x80008000u;  // sign bits of both packed halves
+    return make_uint4(v.x ^ s, v.y ^ s, v.z ^ s, v.w ^ s);
+}
+
+// 2^-e with 2^e >= sqrt(amax2): scales the weights into (-1, 1).
+__device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
+{
+    if (!amax2_bits) return 1.f;
+    const float a = sqrtf(__uint_as_float(*amax2_bits));
+    if (!(a > 0.f)) return 1.f;
+    int e;
+    frexpf(a, &e);
+    return ldexpf(1.f, -e);
+}
+
+// Adds (first: stores) one accumulator buffer into the column-major partial
+// tile; warp w reads TMEM lanes 32 (w % 4).. and complex columns
+// [64 (w / 4), 64 (w / 4) + 64) (real part at column c, imaginary at 128 + c).
+__device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, int warp, int lane,
+                                                  bool first)
+{
+    const int lbase = 32 * (warp & 3);
+    const int half = warp >> 2;
+    const int row = lbase + lane;
+#pragma unroll 1
+    for (int cc = 0; cc < 64; cc += 16) {
+        float re[16], im[16];
+        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(64 * half + cc);
+        tmem_ld16(ta, re);
+        tmem_ld16(ta + 128, im);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = 64 * half + cc + j;
+            float* pr = ptile + (size_t)col * TC_ROWS + row;
+            float* pi = ptile + (size_t)(128 + col) * TC_ROWS + row;
+            if (first) {
+                *pr = re[j];
+                *pi = im[j];
+            } else {
+                *pr += re[j];
+                *pi += im[j];
+            }
+        }
+    }
+}
+
+// C partial for split blockIdx.z over samples [ch0*32, ch1*32):
+//   A(l,i) = exp(sa i2pi ka_l (i + oa)),  B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
+template <bool BF16, bool WEIGHTED>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
+                const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L,
+                int R, int C, int oa, int ob, int sa, int sb, int64_t chunks_per_split,
+                float* __restrict__ part, int* err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    float2* tabA = reinterpret_cast<float2*>(smem + TAB_OFF);
+    float2* tabB = tabA + TC_KS * TC_TAB;
+    const uint32_t bar_full = sbase + BAR_OFF;           // 2 x 8 B: stage filled
+    const uint32_t bar_empty = sbase + BAR_OFF + 16;     // 2 x 8 B: stage consumed
+    const uint32_t bar_acc_full = sbase + BAR_OFF + 32;  // 2 x 8 B: segment accumulated
+    const uint32_t bar_acc_empty = sbase + BAR_OFF + 48; // 2 x 8 B: accumulator drained
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + BAR_OFF + 64);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + BAR_OFF + 68);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.y * TC_ROWS, c0 = blockIdx.x * TC_COLS;
+    const int64_t nchunks = (L + TC_KS - 1) / TC_KS;
+    const int64_t ch0 = (int64_t)blockIdx.z * chunks_per_split;
+    int64_t ch1 = ch0 + chunks_per_split;
+    if (ch1 > nchunks) ch1 = nchunks;
+    const int nloc = ch1 > ch0 ? (int)(ch1 - ch0) : 0;
+    const int nseg = (nloc + TC_SEG - 1) / TC_SEG;
+    // partial tile of this split: column-major [256 real columns][128 rows]
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    float* ptile = part + ((int64_t)blockIdx.z * gridDim.x * gridDim.y + tile) * (256 * TC_ROWS);
+
+    if (tid == 0) {
+        mbar_init(bar_full, TC_PRODUCERS);
+        mbar_init(bar_full + 8, TC_PRODUCERS);
+        mbar_init(bar_empty, 1);
+        mbar_init(bar_empty + 8, 1);
+        mbar_init(bar_acc_full, 1);
+        mbar_init(bar_acc_full + 8, 1);
+        mbar_init(bar_acc_empty, TC_PRODUCERS);
+        mbar_init(bar_acc_empty + 8, TC_PRODUCERS);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 8) {
+        // ------------------------------------------------ producers
+        const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
+        for (int it = 0; it < nloc; ++it) {
+            const int s = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            if (tid == 0 && it >= 2 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+                *abort_flag = 1;
+                atomicOr(err, kErrTimeout);
+            }
+            producers_sync();  // stage s is free; the previous tables are no longer read
+            if (*abort_flag) break;
+            const int64_t l0 = (ch0 + it) * TC_KS;
+            // factor tables: [A|B][l][8 base, 16 offset]
+            for (int e = tid; e < 2 * TC_KS * TC_TAB; e += TC_PRODUCERS) {
+                const int which = e / (TC_KS * TC_TAB);
+                const int rem = e - which * TC_KS * TC_TAB;
+                const int l = rem / TC_TAB, idx = rem - l * TC_TAB;
+                const int64_t lg = l0 + l;
+                float2 v = make_float2(0.f, 0.f);
+                if (lg < L) {
+                    if (which == 0) {
+                        const int j = idx < 8 ? i0 + 16 * idx + oa : idx - 8;
+                        v = phasor_q(__ldg(ka + lg), j);
+                        if (sa < 0) v.y = -v.y;
+                    } else {
+                        const int j = idx < 8 ? c0 + 16 * idx + ob : idx - 8;
+                        v = phasor_q(__ldg(kb + lg), j);
+                        if (sb < 0) v.y = -v.y;
+                        if (WEIGHTED && idx < 8) {
+                            float2 ww = __ldg(w + lg);
+                            ww.x *= wmul;
+                            ww.y *= wmul;
+                            v = cmul(v, ww);
+                        }
+                    }
+                }
+                (which == 0 ? tabA : tabB)[l * TC_TAB + idx] = v;
+            }
+            producers_sync();
+            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int u = tid + TC_PRODUCERS * q;
+                const int r = u & 127, g = u >> 7;  // row (A) or column (B), sample group
+                float re[8], im[8];
+                // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int l = 8 * g + e;
+                    const float2 v = cmul(tabA[l * TC_TAB + (r >> 4)], tabA[l * TC_TAB + 8 + (r & 15)]);
+                    re[e] = v.x;
+                    im[e] = v.y;
+                }
+                uint4 rh, rl, ih, il;
+                split8<BF16>(re, rh, rl);
+                split8<BF16>(im, ih, il);
+                st_shared_v4(aH + sw128(r, g), rh);
+                st_shared_v4(aH + sw128(r, 4 + g), ih);
+                st_shared_v4(aL + sw128(r, g), rl);
+                st_shared_v4(aL + sw128(r, 4 + g), il);
+                // B column r: row r = [Br | -Bi], row 128 + r = [Bi | Br]
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int l = 8 * g + e;
+                    const float2 v = cmul(tabB[l * TC_TAB + (r >> 4)], tabB[l * TC_TAB + 8 + (r & 15)]);
+                    re[e] = v.x;
+                    im[e] = v.y;
+                }
+                split8<BF16>(re, rh, rl);
+                split8<BF16>(im, ih, il);
+                st_shared_v4(bH + sw128(r, g), rh);
+                st_shared_v4(bH + sw128(r, 4 + g), neg4(ih));
+                st_shared_v4(bH + sw128(128 + r, g), ih);
+                st_shared_v4(bH + sw128(128 + r, 4 + g), rh);
+                st_shared_v4(bL + sw128(r, g), rl);
+                st_shared_v4(bL + sw128(r, 4 + g), neg4(il));
+                st_shared_v4(bL + sw128(128 + r, g), il);
+                st_shared_v4(bL + sw128(128 + r, 4 + g), rl);
+            }
+            fence_proxy_async();
+            mbar_arrive(bar_full + 8 * s);
+            // the MMA now has this stage queued: drain the previous segment
+            if (it % TC_SEG == 0 && it > 0) {
+                const int j = it / TC_SEG - 1;
+                if (!mbar_wait(bar_acc_full + 8 * (j & 1), (uint32_t)(j >> 1) & 1)) {
+                    atomicOr(err, kErrTimeout);
+                    *abort_flag = 1;
+                }
+                tc_fence_after();
+                drain_accumulator(tmem + 256u * (j & 1), ptile, warp, lane, j == 0);
+                tc_fence_before();
+                mbar_arrive(bar_acc_empty + 8 * (j & 1));
+            }
+        }
+        // last segment (or zeros when this split has no samples)
+        if (nseg == 0) {
+            for (int e = tid; e < 256 * TC_ROWS; e += TC_PRODUCERS) ptile[e] = 0.f;
+        } else if (!*abort_flag) {
+            const int j = nseg - 1;
+            if (!mbar_wait(bar_acc_full + 8 * (j & 1), (uint32_t)(j >> 1) & 1)) {
+                atomicOr(err, kErrTimeout);
+            } else {
+                tc_fence_after();
+                drain_accumulator(tmem + 256u * (j & 1), ptile, warp, lane, j == 0);
+            }
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and 10,
+        // both K-major, N = 256 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
+        const uint32_t fmt = BF16 ? 1u : 0u;
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+        for (int it = 0; it < nloc; ++it) {
+            const int s = it & 1;
+            const uint32_t use = (uint32_t)(it >> 1);
+            const int seg = it / TC_SEG, pos = it - seg * TC_SEG;
+            const uint32_t tacc = tmem + 256u * (seg & 1);
+            if (pos == 0 && seg >= 2 &&
+                !mbar_wait(bar_acc_empty + 8 * (seg & 1), (uint32_t)((seg - 2) >> 1) & 1)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            if (!mbar_wait(bar_full + 8 * s, use & 1)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t off = 32u * kk;  // 16 halves along K
+                mma_f16(tacc, sdesc(aH + off), sdesc(bH + off), idesc, (pos > 0 || kk > 0) ? 1u : 0u);
+                mma_f16(tacc, sdesc(aH + off), sdesc(bL + off), idesc, 1u);
+                mma_f16(tacc, sdesc(aL + off), sdesc(bH + off), idesc, 1u);
+            }
+            mma_commit(bar_empty + 8 * s);
+            if (pos == TC_SEG - 1 || it == nloc - 1) mma_commit(bar_acc_full + 8 * (seg & 1));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// out[i][c] = scale * 2^e * sum_z part[z][tile(i,c)]: the partial tiles are
+// column-major [256 real columns][128 rows]; 2^e undoes the weight scaling.
+__global__ void k_reduce_tc(const float* __restrict__ part, int S, int R, int C, int tilesC,
+                            float scale, const unsigned* __restrict__ amax2, float2* __restrict__ out)
+{
+    float sc = scale;
+    if (amax2) sc = scale / weight_scale_inv(amax2);
+    const int tilesR = (R + TC_ROWS - 1) / TC_ROWS;
+    const int64_t tiles = (int64_t)tilesR * tilesC;
+    const int64_t RC = (int64_t)R * C;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < RC;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        // consecutive threads walk down a column (rows are contiguous in a tile)
+        const int c = (int)(e / R), i = (int)(e - (int64_t)c * R);
+        const int64_t t = (int64_t)(i / TC_ROWS) * tilesC + c / TC_COLS;
+        const int row = i % TC_ROWS, col = c % TC_COLS;
+        float ar = 0.f, ai = 0.f;
+        for (int z = 0; z < S; ++z) {
+            const float* pt = part + ((int64_t)z * tiles + t) * (256 * TC_ROWS);
+            ar += pt[col * TC_ROWS + row];
+            ai += pt[(128 + col) * TC_ROWS + row];
+        }
+        out[(int64_t)i * C + c] = make_float2(ar * sc, ai * sc);
+    }
+}
+
+// amax2 = max_l |y_l|^2 as float bits (non-negative floats order like unsigned).
+__global__ void k_absmax2(const float2* __restrict__ y, int64_t n, unsigned* amax2)
+{
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = y[i];
+        m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && isfinite(m)) atomicMax(amax2, __float_as_uint(m));
+}
+
+constexpr int kSMs = 152;
+
+int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const float2* w, int R,
+                  int C, int oa, int ob, int sa, int sb, float scale, float2* out)
+{
+    const int64_t nchunks = (p->L + TC_KS - 1) / TC_KS;
+    const int tilesR = (R + TC_ROWS - 1) / TC_ROWS, tilesC = (C + TC_COLS - 1) / TC_COLS;
+    const int tiles = tilesR * tilesC;
+    int64_t S = kSMs / tiles;
+    if (S < 1) S = 1;
+    if (S > nchunks) S = nchunks;
+    const int64_t RC = (int64_t)R * C;
+    const size_t tile_bytes = 256 * TC_ROWS * sizeof(float);
+    while (S > 1 && (size_t)(S * tiles) * tile_bytes > p->kpart_bytes) --S;
+    const int64_t cps = (nchunks + S - 1) / S;
+    const int Seff = (int)((nchunks + cps - 1) / cps);
+    unsigned* amax = nullptr;
+    if (w) {
+        amax = p->counters + C_AMAX;
+        SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
+        int blocks = (int)((p->L + 255) / 256);
+        if (blocks > 4 * kSMs) blocks = 4 * kSMs;
+        k_absmax2<<<blocks, 256, 0, p->stream>>>(w, p->L, amax);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 1;
+    }
+    dim3 grid(tilesC, tilesR, Seff);
+    float* part = p->kpart;
+    const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
+    if (bf16 && w)
+        k_tc_phase_gemm<true, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
+            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+    else if (bf16)
+        k_tc_phase_gemm<true, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
+            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+    else if (w)
+        k_tc_phase_gemm<false, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
+            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+    else
+        k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
+            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+    SPIREC_CK(cudaGetLastError());
+    int rblocks = (int)((RC + 255) / 256);
+    if (rblocks > 4 * kSMs) rblocks = 4 * kSMs;
+    k_reduce_tc<<<rblocks, 256, 0, p->stream>>>(part, Seff, R, C, tilesC, scale, amax, out);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 2;
+    return SPIREC_OK;
+}
+
+}  // namespace
+
+size_t kpart_floats_tc(int, int64_t, int precision)
+{
+    if (precision == SPIREC_FP32) return 0;
+    // S * tiles <= 152 and R * C <= tiles * 128 * 128
+    return (size_t)kSMs * TC_ROWS * TC_COLS * 2;
+}
+
+int tc_setup_attributes()
+{
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    return SPIREC_OK;
+}
+
+int launch_gram_tc(spirec_plan p)
+{
+    const int N = p->N;
+    return tc_phase_gemm(p, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
+                         1.0f / ((float)N * (float)N), p->G);
+}
+
+int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
+{
+    const int N = p->N;
+    return tc_phase_gemm(p, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
 }
 
 }  // namespace spirec

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 N, I, S, M = 512, 32, 4096, 1024
 TOL = {0: 1e-5, 1: 1e-3, 2: 1e-3}
-PRECISIONS = [0]
+PRECISIONS = [0, 1, 2]
 
 
 @pytest.fixture(scope="module")

@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1: 1e-3, 2: 1e-3}
 ITER_TOL = 1e-3
-PRECISIONS = [0]
+PRECISIONS = [0, 1, 2]
 
 
 def _terms(w, x, reg):
