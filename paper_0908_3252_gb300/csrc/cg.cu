@@ -26,11 +26,13 @@
 
 namespace spirec {
 
+// One pixel per thread where the partial slots allow (one wave on 152 SMs at
+// N = 512), grid-stride beyond.
 int vec_blocks(int N)
 {
     const int64_t P = (int64_t)N * N;
     int64_t b = (P + kVecThreads - 1) / kVecThreads;
-    if (b > 4 * 152) b = 4 * 152;
+    if (b > kMaxParts) b = kMaxParts;
     if (b < 1) b = 1;
     return (int)b;
 }
@@ -48,15 +50,16 @@ __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.
 __global__ void k_sumsq(const float2* __restrict__ s, int64_t L, float2* parts, unsigned* counter,
                         double* scal)
 {
-    FF acc{0.f, 0.f};
+    float acc = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float2 v = s[i];
-        acc = ff_add(acc, FF{redot(v, v), 0.f});
+        acc += redot(v, v);
     }
-    FF v[1] = {acc};
-    block_sum_ff<1>(v);
-    store_parts<1>(v, parts, kMaxParts);
+    float v[1] = {acc};
+    FF bt[1];
+    block_partial<1>(v, bt);
+    store_parts<1>(bt, parts, kMaxParts);
     if (last_block(counter)) {
         FF t[1];
         sum_parts_ff<1>(parts, kMaxParts, gridDim.x, t);
@@ -104,9 +107,10 @@ k_line_search(const float2* __restrict__ f, const float2* __restrict__ d, int N,
             den = fmaf(b, redot(dp, dp), den);
         }
     }
-    FF v[2] = {FF{num, 0.f}, FF{den, 0.f}};
-    block_sum_ff<2>(v);
-    store_parts<2>(v, parts, kMaxParts);
+    float v[2] = {num, den};
+    FF bt[2];
+    block_partial<2>(v, bt);
+    store_parts<2>(bt, parts, kMaxParts);
     if (last_block(counter)) {
         FF tot[2];
         sum_parts_ff<2>(parts, kMaxParts, gridDim.x, tot);
@@ -193,11 +197,9 @@ k_update(const float2* __restrict__ f_in, float2* __restrict__ f_out, const floa
         a[5] += redot(fp, tf);
         g[p] = gp;
     }
-    FF v[kUpdVals];
-#pragma unroll
-    for (int i = 0; i < kUpdVals; ++i) v[i] = FF{a[i], 0.f};
-    block_sum_ff<kUpdVals>(v);
-    store_parts<kUpdVals>(v, parts, kMaxParts);
+    FF bt[kUpdVals];
+    block_partial<kUpdVals>(a, bt);
+    store_parts<kUpdVals>(bt, parts, kMaxParts);
     if (last_block(counter)) {
         FF tot[kUpdVals];
         sum_parts_ff<kUpdVals>(parts, kMaxParts, gridDim.x, tot);

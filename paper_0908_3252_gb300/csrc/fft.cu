@@ -308,9 +308,10 @@ __global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, i
                 den = fmaf(bw, redot(dn, dn), den);
             }
         }
-        FF v[3] = {FF{q1, 0.f}, FF{num, 0.f}, FF{den, 0.f}};
-        block_sum_ff<3>(v);
-        store_parts<3>(v, c.parts, kMaxParts);
+        float v[3] = {q1, num, den};
+        FF bt[3];
+        block_partial<3>(v, bt);
+        store_parts<3>(bt, c.parts, kMaxParts);
         if (last_block(c.counter)) {
             FF t[3];
             sum_parts_ff<3>(c.parts, kMaxParts, gridDim.x, t);
@@ -361,9 +362,10 @@ __global__ void k_rows_inv(const float2* __restrict__ X, int rows, float2* __res
         if (dotx) acc += redot(dotx[o], v);
     }
     if (dotx) {
-        FF v[1] = {FF{acc, 0.f}};
-        block_sum_ff<1>(v);
-        store_parts<1>(v, c.parts, kMaxParts);
+        float v[1] = {acc};
+        FF bt[1];
+        block_partial<1>(v, bt);
+        store_parts<1>(bt, c.parts, kMaxParts);
         if (last_block(c.counter)) {
             FF t[1];
             sum_parts_ff<1>(c.parts, kMaxParts, gridDim.x, t);
@@ -701,3 +703,4 @@ int launch_spectrum(spirec_plan p)
 }
 
 }  // namespace spirec
+

@@ -12,15 +12,15 @@
 // bf16) and x_lo = fp16(x - x_hi); three MMAs hi*hi + hi*lo + lo*hi feed the
 // same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for FP16).
 //
-// Pipeline per CTA (288 threads):
-//   warps 0-7  producers: per stage of 32 samples, build the factor tables
+// Pipeline per CTA (544 threads):
+//   warps 0-15 producers: per stage of 32 samples, build the factor tables
 //              exp(i2pi k (base + 16a)) and exp(i2pi k b), multiply them out
 //              into the four operand tiles (A_hi, A_lo, B_hi, B_lo) in the
 //              128-byte-swizzled K-major layout the MMA reads, then arrive on
 //              full[stage];
-//   warp 8     allocates 256 TMEM columns; one lane waits on full[stage],
+//   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
 //              issues 12 tcgen05.mma (K = 16 each) and commits to empty[stage];
-//   warps 0-7  drain: every SEG stages (512 samples) the finished accumulator
+//   warps 0-15 drain: every SEG stages (512 samples) the finished accumulator
 //              is read with tcgen05.ld and added, in FP32 with round-to-
 //              nearest, to the CTA's split-K partial tile in global memory
 //              (column-major, so each lane row maps to consecutive addresses).
@@ -46,7 +46,7 @@ constexpr int TC_ROWS = 128;        // complex rows per tile (MMA M)
 constexpr int TC_COLS = 128;        // complex columns per tile (MMA N = 256 real)
 constexpr int TC_KS = 32;           // samples per stage (64 real K per operand set)
 constexpr int TC_STAGES = 2;
-constexpr int TC_PRODUCERS = 256;   // 8 warps
+constexpr int TC_PRODUCERS = 512;   // 16 warps
 constexpr int TC_THREADS = TC_PRODUCERS + 32;
 constexpr int TC_TAB = 24;          // 8 base + 16 offset phasors per sample
 constexpr int TC_SEG = 16;          // stages per accumulator segment
@@ -251,22 +251,22 @@ __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
 
 // Adds (first: stores) one accumulator buffer into the column-major partial
 // tile; warp w reads TMEM lanes 32 (w % 4).. and complex columns
-// [64 (w / 4), 64 (w / 4) + 64) (real part at column c, imaginary at 128 + c).
+// [32 (w / 4), 32 (w / 4) + 32) (real part at column c, imaginary at 128 + c).
 __device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, int warp, int lane,
                                                   bool first)
 {
     const int lbase = 32 * (warp & 3);
-    const int half = warp >> 2;
+    const int quarter = warp >> 2;
     const int row = lbase + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < 64; cc += 16) {
+    for (int cc = 0; cc < 32; cc += 16) {
         float re[16], im[16];
-        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(64 * half + cc);
+        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(32 * quarter + cc);
         tmem_ld16(ta, re);
         tmem_ld16(ta + 128, im);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = 64 * half + cc + j;
+            const int col = 32 * quarter + cc + j;
             float* pr = ptile + (size_t)col * TC_ROWS + row;
             float* pi = ptile + (size_t)(128 + col) * TC_ROWS + row;
             if (first) {
@@ -326,13 +326,13 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
+    if (warp == TC_PRODUCERS / 32) tmem_alloc(smem_u32(tmem_slot), 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 8) {
+    if (warp < TC_PRODUCERS / 32) {
         // ------------------------------------------------ producers
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
         for (int it = 0; it < nloc; ++it) {
@@ -375,7 +375,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < 512 / TC_PRODUCERS; ++q) {
                 const int u = tid + TC_PRODUCERS * q;
                 const int r = u & 127, g = u >> 7;  // row (A) or column (B), sample group
                 float re[8], im[8];
@@ -477,7 +477,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) {
+    if (warp == TC_PRODUCERS / 32) {
         __syncwarp();
         tc_fence_after();
         tmem_dealloc(tmem, 512);
