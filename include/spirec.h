@@ -163,6 +163,28 @@ int spirec_toeplitz_dev(spirec_plan plan, const float* x, float* Tx);
  * Needs set_data and set_reg. */
 int spirec_objective_grad_dev(spirec_plan plan, const float* x, double* J_host, float* g);
 
+/* T x for callers that cannot allocate device memory: the same three-pass
+ * zero-padded FFT as spirec_toeplitz_dev, but with no plan and no allocation
+ * of any kind (no cudaMalloc, no cudaFree, no allocating library routine).
+ * The paper has no counterpart; it exists for code that runs under a fixed
+ * device-memory budget or must not grow its GPU footprint after start-up.
+ *   x, Tx     device, 2N^2 floats each (images as everywhere in this header).
+ *   spectrum  device, M*M floats: the real kernel spectrum in the layout
+ *             spirec_kernel_spectrum_dev returns ([ky*M + kx]).
+ *   N, M      2 <= N <= 512, 2N-1 <= M <= 1024, M a product of 2, 3 and 5;
+ *             anything else returns SPIREC_EINVAL with a message.
+ *   stream    cudaStream_t the work is enqueued on (NULL: legacy default).
+ * Scratch is one file-scope device array of about 8.4 MB (the N x M rows, a
+ * transposed spectrum and the twiddles), held by every GPU that loads the
+ * library until the process exits.  The first call on a device looks up the
+ * array's device address and sets kernel limits; make that first call before
+ * any stream capture.  Every call shares the array: calls whose work overlaps
+ * on the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Returns after enqueueing; x and spectrum must stay valid until the
+ * work has run. */
+int spirec_toeplitz_noalloc(const float* x, const float* spectrum, float* Tx, int32_t N, int32_t M,
+                            void* stream);
+
 /* Wait for all work of the plan. */
 int spirec_sync(spirec_plan plan);
 

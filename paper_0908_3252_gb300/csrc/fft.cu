@@ -704,3 +704,132 @@ int launch_spectrum(spirec_plan p)
 
 }  // namespace spirec
 
+// ------------------------------------------------ T x without any allocation
+//
+// spirec_toeplitz_noalloc: the Toeplitz apply above for callers that cannot
+// allocate device memory (for example code running inside a memory-pool
+// budget that forbids cudaMalloc, or a host process that must not grow the
+// GPU footprint after start-up).  The caller passes the input, the kernel
+// spectrum and the output; the intermediate N x M rows, the transposed
+// spectrum and the twiddle table live in one file-scope device array that
+// every GPU loading this library keeps until the process exits.
+
+namespace spirec {
+namespace {
+
+constexpr int kNoAllocMaxN = 512;
+constexpr int kNoAllocMaxM = 1024;
+constexpr size_t kNoAllocRowsBytes = (size_t)kNoAllocMaxN * kNoAllocMaxM * sizeof(float2);
+constexpr size_t kNoAllocSpecBytes = (size_t)kNoAllocMaxM * kNoAllocMaxM * sizeof(float);
+constexpr size_t kNoAllocTwBytes = (size_t)kNoAllocMaxM * sizeof(float2);
+constexpr size_t kNoAllocBytes = kNoAllocRowsBytes + kNoAllocSpecBytes + kNoAllocTwBytes;
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_base[kNoAllocMaxDevices];  // device address of the array, per device
+bool g_noalloc_ready[kNoAllocMaxDevices];
+
+// tw[k] = exp(-2 pi i k / M)
+__global__ void k_noalloc_twiddles(float2* tw, int M)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)M, &s, &c);
+        tw[k] = make_float2((float)c, (float)s);
+    }
+}
+
+// spectrum[ky][kx] (the layout spirec_kernel_spectrum_dev returns) into the
+// column-major form the column pass reads, chat[kx][ky].
+__global__ void k_noalloc_spectrum(const float* __restrict__ spec, int M, float* __restrict__ chat)
+{
+    const int64_t MM = (int64_t)M * M;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MM;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kx = e / M, ky = e % M;
+        chat[e] = spec[ky * M + kx];
+    }
+}
+
+struct LaunchNoAlloc {
+    const float2* x;
+    float2* Tx;
+    float2* rows;
+    const float* chat;
+    const float2* tw;
+    FftPlan fp;
+    int N;
+    cudaStream_t st;
+    template <int MC>
+    int operator()()
+    {
+        const int M = fp.M;
+        const bool pow2 = MC > 0;
+        const Shape rs = row_shape(M, pow2), cs = col_shape(M, pow2);
+        const int rblocks = (N + rs.per_cta - 1) / rs.per_cta;
+        const CgPass c{};
+        k_rows_fwd<MC, 0><<<rblocks, rs.threads, rs.smem, st>>>(x, N, N, N, rows, fp, tw, rs.per_cta, c);
+        SPIREC_CK(cudaGetLastError());
+        k_cols_filter<MC><<<(M + cs.per_cta - 1) / cs.per_cta, cs.threads, cs.smem, st>>>(rows, N, N, fp, tw,
+                                                                                          chat, cs.per_cta);
+        SPIREC_CK(cudaGetLastError());
+        k_rows_inv<MC, 0><<<rblocks, rs.threads, rs.smem, st>>>(rows, N, Tx, N, fp, tw, rs.per_cta, nullptr,
+                                                                 c, 0);
+        SPIREC_CK(cudaGetLastError());
+        return SPIREC_OK;
+    }
+};
+
+}  // namespace
+
+}  // namespace spirec
+
+extern "C" int spirec_toeplitz_noalloc(const float* x, const float* spectrum, float* Tx, int32_t N,
+                                       int32_t M, void* stream)
+{
+    using namespace spirec;
+    if (!x || !spectrum || !Tx) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (N < 2 || N > kNoAllocMaxN || M < 2 * N - 1 || M > kNoAllocMaxM) {
+        set_error("spirec_toeplitz_noalloc handles 2 <= N <= %d and 2N-1 <= M <= %d (got N=%d, M=%d)",
+                  kNoAllocMaxN, kNoAllocMaxM, N, M);
+        return SPIREC_EINVAL;
+    }
+    FftPlan fp;
+    if (!make_fft_plan(M, &fp)) {
+        set_error("M=%d must factor into 2, 3 and 5", M);
+        return SPIREC_EINVAL;
+    }
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("device %d out of range", dev);
+        return SPIREC_EUNSUPPORTED;
+    }
+    // first call on this device: the array's device address and the kernels'
+    // shared-memory limits (no allocation; must happen outside stream capture)
+    if (!g_noalloc_ready[dev]) {
+        void* base = nullptr;
+        e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+        int rc = fft_setup_attributes(M);
+        if (rc != SPIREC_OK) return rc;
+        g_noalloc_base[dev] = base;
+        g_noalloc_ready[dev] = true;
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+    float2* rows = reinterpret_cast<float2*>(base);
+    float* chat = reinterpret_cast<float*>(base + kNoAllocRowsBytes);
+    float2* tw = reinterpret_cast<float2*>(base + kNoAllocRowsBytes + kNoAllocSpecBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_noalloc_twiddles<<<(M + 255) / 256, 256, 0, st>>>(tw, M);
+    SPIREC_CK(cudaGetLastError());
+    k_noalloc_spectrum<<<4 * 152, 256, 0, st>>>(spectrum, M, chat);
+    SPIREC_CK(cudaGetLastError());
+    return with_size(M, LaunchNoAlloc{(const float2*)x, (float2*)Tx, rows, chat, tw, fp, N, st});
+}

@@ -62,6 +62,7 @@ SIGNATURES = {
     "spirec_data_adjoint_dev": (ctypes.c_int, [_P, _P]),
     "spirec_toeplitz_dev": (ctypes.c_int, [_P, _P, _P]),
     "spirec_objective_grad_dev": (ctypes.c_int, [_P, _P, _P, _P]),
+    "spirec_toeplitz_noalloc": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _P]),
     "spirec_sync": (ctypes.c_int, [_P]),
     "spirec_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "spirec_launch_count": (ctypes.c_int, [_P, _P]),
@@ -211,6 +212,12 @@ def spirec_objective_grad_dev(plan, x, g):
     J = ctypes.c_double(0.0)
     _check(load().spirec_objective_grad_dev(plan, _dev_ptr(x), ctypes.byref(J), _dev_ptr(g)))
     return J.value
+
+
+def spirec_toeplitz_noalloc(x, spectrum, Tx, N, M, stream=None):
+    """T x with no allocation (device tensors; see include/spirec.h)."""
+    return _check(load().spirec_toeplitz_noalloc(_dev_ptr(x), _dev_ptr(spectrum), _dev_ptr(Tx), int(N), int(M),
+                                                 ctypes.c_void_p(stream) if stream else None))
 
 
 def spirec_sync(plan):
