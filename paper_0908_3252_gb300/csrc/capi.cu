@@ -121,7 +121,7 @@ void free_plan(spirec_plan p)
     if (!p) return;
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
-                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage};
+                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -403,8 +403,10 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRYCUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
     TRYCUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
     const size_t NN = (size_t)N * N;
-    TRY(dalloc(p, &p->kxq, (size_t)L));
-    TRY(dalloc(p, &p->kyq, (size_t)L));
+    // sample arrays carry 32 elements of padding: the tensor-core kernel reads
+    // whole 16-byte multiples of a 32-sample chunk by TMA bulk copy
+    TRY(dalloc(p, &p->kxq, (size_t)L + 32));
+    TRY(dalloc(p, &p->kyq, (size_t)L + 32));
     TRY(dalloc(p, &p->kstage, 2 * (size_t)L));
     TRY(dalloc(p, &p->dflag, 1));
     TRY(dalloc(p, &p->G, (size_t)N * (2 * N - 1)));
@@ -412,7 +414,8 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->cwork, (size_t)M * M));
     TRY(dalloc(p, &p->X, (size_t)N * M));
     TRY(dalloc(p, &p->D, NN));
-    TRY(dalloc(p, &p->s, (size_t)L));
+    TRY(dalloc(p, &p->s, (size_t)L + 32));
+    TRY(dalloc(p, &p->ystage, (size_t)L + 32));
     TRY(dalloc(p, &p->f[0], NN));
     TRY(dalloc(p, &p->f[1], NN));
     TRY(dalloc(p, &p->dbuf[0], NN));

@@ -72,7 +72,9 @@ __global__ void k_sumsq(const float2* __restrict__ s, int64_t L, float2* parts, 
 
 // Line-search step `step` (1 or 2) at t = t_step over the right/down edges of
 // every pixel (Omega1) and the pixels (Omega0); the last block forms
-// t_{step+1} = t - (q1 + 2 q2 t + num) / (2 q2 + den).
+// t_{step+1} = t - (q1 + 2 q2 t + num) / (2 q2 + den).  All loads of a pixel
+// are issued before any use (neighbour indices clamped, contributions masked)
+// so a thread waits on memory once, not once per edge.
 __global__ void __launch_bounds__(kVecThreads)
 k_line_search(const float2* __restrict__ f, const float2* __restrict__ d, int N, Reg reg, int step,
               float2* parts, unsigned* counter, double* scal)
@@ -83,19 +85,21 @@ k_line_search(const float2* __restrict__ f, const float2* __restrict__ d, int N,
     float num = 0.f, den = 0.f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const int n = p / N, m = p - n * N;
-        const float2 fp = f[p], dp = d[p];
+        const bool has_r = m + 1 < N, has_d = n + 1 < N;
+        const int pr = has_r ? p + 1 : p, pd = has_d ? p + N : p;
+        const float2 fp = f[p], dp = d[p], fr = f[pr], dr = d[pr], fd = f[pd], dd = d[pd];
         if (reg.lambda1 != 0.f) {
-            if (m + 1 < N) {
-                const float2 w = f2sub(d[p + 1], dp);
-                const float2 x = f2axpy(tf, w, f2sub(f[p + 1], fp));
-                const float b = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x));
+            {
+                const float2 w = f2sub(dr, dp);
+                const float2 x = f2axpy(tf, w, f2sub(fr, fp));
+                const float b = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
                 num = fmaf(b, redot(x, w), num);
                 den = fmaf(b, redot(w, w), den);
             }
-            if (n + 1 < N) {
-                const float2 w = f2sub(d[p + N], dp);
-                const float2 x = f2axpy(tf, w, f2sub(f[p + N], fp));
-                const float b = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x));
+            {
+                const float2 w = f2sub(dd, dp);
+                const float2 x = f2axpy(tf, w, f2sub(fd, fp));
+                const float b = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
                 num = fmaf(b, redot(x, w), num);
                 den = fmaf(b, redot(w, w), den);
             }
@@ -124,77 +128,80 @@ k_line_search(const float2* __restrict__ f, const float2* __restrict__ d, int N,
     }
 }
 
-// Gradient and step.  With first == 0: f_out = f_in + t3 d, Tf += t3 Td.
+// Gradient and step.  Unless FIRST: f_out = f_in + t3 d, Tf += t3 Td.
 // Then g = 2 (Tf - D) + grad R(f_out), and the block sums
 //   0 <g,g>, 1 Re<g, g_old>, 2 Re<g, d>, 3 R(f), 4 Re<f, D>, 5 Re<f, Tf>.
 // The last block forms J = ||s||^2 - 2 Re<f,D> + Re<f,Tf> + R (-> *Jout),
 // beta = max(0, (<g,g> - Re<g,g_old>) / <g_old,g_old>), set to 0 when
 // Re<g, -g + beta d> >= 0 (restart), and <g,g> for the next iteration.
+// Edge of the gradient stencil: an edge from p to q with z = f_q - f_p adds
+// +psi(z) at q and -psi(z) at p, psi(z) = b(|z|) z.
+template <bool FIRST>
 __global__ void __launch_bounds__(kVecThreads)
 k_update(const float2* __restrict__ f_in, float2* __restrict__ f_out, const float2* __restrict__ d,
          float2* __restrict__ Tf, const float2* __restrict__ Td, const float2* __restrict__ D,
-         float2* __restrict__ g, int N, Reg reg, int first, float2* parts, unsigned* counter,
-         double* scal, double* Jout)
+         float2* __restrict__ g, int N, Reg reg, float2* parts, unsigned* counter, double* scal,
+         double* Jout)
 {
-    const float t = first ? 0.f : (float)scal[S_T3];
+    const float t = FIRST ? 0.f : (float)scal[S_T3];
     const int P = N * N;
     float a[kUpdVals];
 #pragma unroll
     for (int i = 0; i < kUpdVals; ++i) a[i] = 0.f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const int n = p / N, m = p - n * N;
-        // f at p and at its four neighbours after the step
-        const float2 fp = first ? f_in[p] : f2axpy(t, d[p], f_in[p]);
+        const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
+        const int pu = has_u ? p - N : p, pl = has_l ? p - 1 : p;
+        const int pd = has_d ? p + N : p, pr = has_r ? p + 1 : p;
+        // every load first
+        float2 fc = f_in[p], fu = f_in[pu], fl = f_in[pl], fdn = f_in[pd], fr = f_in[pr];
         float2 tf = Tf[p];
-        if (!first) {
-            tf = f2axpy(t, Td[p], tf);
-            Tf[p] = tf;
-            f_out[p] = fp;
-        }
         const float2 dv = D[p];
+        float2 dc = make_float2(0.f, 0.f), gold = dc, tdv = dc;
+        if (!FIRST) {
+            dc = d[p];
+            const float2 du = d[pu], dl = d[pl], ddn = d[pd], dr = d[pr];
+            tdv = Td[p];
+            gold = g[p];
+            fc = f2axpy(t, dc, fc);
+            fu = f2axpy(t, du, fu);
+            fl = f2axpy(t, dl, fl);
+            fdn = f2axpy(t, ddn, fdn);
+            fr = f2axpy(t, dr, fr);
+            tf = f2axpy(t, tdv, tf);
+            Tf[p] = tf;
+            f_out[p] = fc;
+        }
         float2 gp = make_float2(2.f * (tf.x - dv.x), 2.f * (tf.y - dv.y));
         float rv = 0.f;
         if (reg.lambda1 != 0.f) {
             const float l1 = reg.lambda1;
-            // edges into p (from up, left): +psi(f_p - f_q); out of p (down, right): -psi(f_q - f_p)
-            if (n > 0) {
-                const float2 fq = first ? f_in[p - N] : f2axpy(t, d[p - N], f_in[p - N]);
-                const float2 z = f2sub(fp, fq);
-                gp = f2axpy(l1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)), z, gp);
-            }
-            if (m > 0) {
-                const float2 fq = first ? f_in[p - 1] : f2axpy(t, d[p - 1], f_in[p - 1]);
-                const float2 z = f2sub(fp, fq);
-                gp = f2axpy(l1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)), z, gp);
-            }
-            if (n + 1 < N) {
-                const float2 fq = first ? f_in[p + N] : f2axpy(t, d[p + N], f_in[p + N]);
-                const float2 z = f2sub(fq, fp);
-                const float r2 = redot(z, z);
-                gp = f2axpy(-l1 * phi_weight(reg.kind, reg.alpha1, r2), z, gp);
-                rv = fmaf(l1, phi_value(reg.kind, reg.alpha1, r2), rv);
-            }
-            if (m + 1 < N) {
-                const float2 fq = first ? f_in[p + 1] : f2axpy(t, d[p + 1], f_in[p + 1]);
-                const float2 z = f2sub(fq, fp);
-                const float r2 = redot(z, z);
-                gp = f2axpy(-l1 * phi_weight(reg.kind, reg.alpha1, r2), z, gp);
-                rv = fmaf(l1, phi_value(reg.kind, reg.alpha1, r2), rv);
-            }
+            const float2 zu = f2sub(fc, fu), zl = f2sub(fc, fl), zd = f2sub(fdn, fc), zr = f2sub(fr, fc);
+            const float ru = redot(zu, zu), rl = redot(zl, zl), rd = redot(zd, zd), rr = redot(zr, zr);
+            const float bu = has_u ? l1 * phi_weight(reg.kind, reg.alpha1, ru) : 0.f;
+            const float bl = has_l ? l1 * phi_weight(reg.kind, reg.alpha1, rl) : 0.f;
+            const float bd = has_d ? l1 * phi_weight(reg.kind, reg.alpha1, rd) : 0.f;
+            const float br = has_r ? l1 * phi_weight(reg.kind, reg.alpha1, rr) : 0.f;
+            gp = f2axpy(bu, zu, gp);
+            gp = f2axpy(bl, zl, gp);
+            gp = f2axpy(-bd, zd, gp);
+            gp = f2axpy(-br, zr, gp);
+            rv = (has_d ? l1 * phi_value(reg.kind, reg.alpha1, rd) : 0.f) +
+                 (has_r ? l1 * phi_value(reg.kind, reg.alpha1, rr) : 0.f);
         }
         if (reg.lambda0 != 0.f) {
-            const float r2 = redot(fp, fp);
-            gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fp, gp);
+            const float r2 = redot(fc, fc);
+            gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fc, gp);
             rv = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), rv);
         }
         a[0] += redot(gp, gp);
-        if (!first) {
-            a[1] += redot(gp, g[p]);
-            a[2] += redot(gp, d[p]);
+        if (!FIRST) {
+            a[1] += redot(gp, gold);
+            a[2] += redot(gp, dc);
         }
         a[3] += rv;
-        a[4] += redot(fp, dv);
-        a[5] += redot(fp, tf);
+        a[4] += redot(fc, dv);
+        a[5] += redot(fc, tf);
         g[p] = gp;
     }
     FF bt[kUpdVals];
@@ -208,7 +215,7 @@ k_update(const float2* __restrict__ f_in, float2* __restrict__ f_out, const floa
             for (int i = 0; i < kUpdVals; ++i) s[i] = ff_to_double(tot[i]);
             const double J = scal[S_SS] - 2.0 * s[4] + s[5] + s[3];
             double beta = 0.0;
-            if (!first) {
+            if (!FIRST) {
                 const double gg_old = scal[S_GG];
                 beta = gg_old > 0.0 ? (s[0] - s[1]) / gg_old : 0.0;
                 if (beta < 0.0) beta = 0.0;
@@ -250,9 +257,12 @@ int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step
 int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf,
                   const float2* Td, float2* g, int first, double* Jout)
 {
-    k_update<<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-        f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, first, slot(p, P_UPD), p->counters + C_UPD,
-        p->scal, Jout);
+    if (first)
+        k_update<true><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
+            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+    else
+        k_update<false><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
+            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     return SPIREC_OK;

@@ -282,22 +282,28 @@ __global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, i
             const int q = e / N, m = e - q * N;
             const int n = r0 + q;
             const int64_t o = (int64_t)n * N + m;
+            const bool has_r = m + 1 < N, has_d = n + 1 < N;
+            const int64_t od = has_d ? o + N : o;
+            // every load first (clamped neighbours, masked contributions)
             const float2 dn = a[q * M + m];
-            const float2 fp_ = c.f[o];
-            q1 += 2.f * redot(dn, f2sub(c.Tf[o], c.D[o]));
+            const float2 dr = a[q * M + (has_r ? m + 1 : m)];
+            const float2 fp_ = c.f[o], fr = c.f[has_r ? o + 1 : o], fd = c.f[od];
+            const float2 gd = c.g[od], dold_d = c.d_old[od];
+            const float2 tfv = c.Tf[o], dv = c.D[o];
+            q1 += 2.f * redot(dn, f2sub(tfv, dv));
             if (reg.lambda1 != 0.f) {
-                if (m + 1 < N) {
-                    const float2 w = f2sub(a[q * M + m + 1], dn);
-                    const float2 z = f2sub(c.f[o + 1], fp_);
-                    const float bw = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z));
+                {
+                    const float2 w = f2sub(dr, dn);
+                    const float2 z = f2sub(fr, fp_);
+                    const float bw = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
                     num = fmaf(bw, redot(z, w), num);
                     den = fmaf(bw, redot(w, w), den);
                 }
-                if (n + 1 < N) {
-                    const float2 dd = new_direction(c.g[o + N], c.d_old[o + N], beta, restart);
+                {
+                    const float2 dd = new_direction(gd, dold_d, beta, restart);
                     const float2 w = f2sub(dd, dn);
-                    const float2 z = f2sub(c.f[o + N], fp_);
-                    const float bw = reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z));
+                    const float2 z = f2sub(fd, fp_);
+                    const float bw = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
                     num = fmaf(bw, redot(z, w), num);
                     den = fmaf(bw, redot(w, w), den);
                 }

@@ -114,7 +114,8 @@ struct spirec_plan_s {
     float2* cwork; // M x M complex (spectrum build)
     float2* X;     // N x M complex (Toeplitz rows)
     float2* D;     // N x N
-    float2* s;     // L
+    float2* s;     // L (+32 padding)
+    float2* ystage;  // L (+32 padding): a caller's y staged for the tensor-core adjoint
     float2* f[2];
     float2* dbuf[2];  // direction of iteration k in dbuf[k & 1]
     float2* g;

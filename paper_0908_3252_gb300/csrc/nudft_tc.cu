@@ -28,7 +28,10 @@
 // per accumulation step (truncation-like, measured: 2.8e-4 relative after
 // 12k steps); draining every 192 steps bounds that error, and the two TMEM
 // accumulators (2 x 256 columns) let the MMA run on while one is drained.
-// Two stages of 96 KB double-buffer generation against the tensor core.
+// Two stages of 96 KB double-buffer generation against the tensor core.  The
+// stage's 32 samples of the trajectory (and of the data, for D) arrive by TMA
+// bulk copy (cp.async.bulk) into a 4-deep shared-memory ring two stages
+// ahead, so the table builders never wait on global memory.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error bit, lets the other roles run out, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -55,7 +58,10 @@ constexpr uint32_t B_BYTES = 2 * TC_COLS * 128;      // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr uint32_t TAB_OFF = TC_STAGES * STAGE_BYTES;
 constexpr uint32_t TAB_BYTES = 2 * TC_KS * TC_TAB * 8;
-constexpr uint32_t BAR_OFF = TAB_OFF + TAB_BYTES;
+constexpr int TRAJ_RING = 4;
+constexpr uint32_t TRAJ_BUF = 3 * TC_KS * 8;                // ka, kb (int64) and w (float2)
+constexpr uint32_t TRAJ_OFF = TAB_OFF + TAB_BYTES;
+constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
@@ -109,6 +115,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             if (mbar_try(bar, parity)) return true;
         if (globaltimer() - t0 > kWaitNs) return false;
     }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on `bar`.
+// dst and src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init()
@@ -298,8 +319,10 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
     const uint32_t bar_empty = sbase + BAR_OFF + 16;     // 2 x 8 B: stage consumed
     const uint32_t bar_acc_full = sbase + BAR_OFF + 32;  // 2 x 8 B: segment accumulated
     const uint32_t bar_acc_empty = sbase + BAR_OFF + 48; // 2 x 8 B: accumulator drained
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + BAR_OFF + 64);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + BAR_OFF + 68);
+    const uint32_t bar_traj = sbase + BAR_OFF + 64;      // 4 x 8 B: trajectory chunk landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + BAR_OFF + 96);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + BAR_OFF + 100);
+    const uint32_t traj_s = sbase + TRAJ_OFF;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -323,6 +346,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
         mbar_init(bar_acc_full + 8, 1);
         mbar_init(bar_acc_empty, TC_PRODUCERS);
         mbar_init(bar_acc_empty + 8, TC_PRODUCERS);
+        for (int r = 0; r < TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -335,6 +359,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
     if (warp < TC_PRODUCERS / 32) {
         // ------------------------------------------------ producers
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
+        // TMA feed of the trajectory (and data) chunk of stage `it` into ring slot it % 4
+        auto issue_traj = [&](int it) {
+            const int64_t l0 = (ch0 + it) * TC_KS;
+            int64_t cnt = L - l0;
+            if (cnt > TC_KS) cnt = TC_KS;
+            const uint32_t bytes = (uint32_t)(((cnt + 1) & ~1) * 8);  // multiple of 16; arrays are padded
+            const uint32_t buf = traj_s + (uint32_t)(it % TRAJ_RING) * TRAJ_BUF;
+            const uint32_t bar = bar_traj + 8 * (it % TRAJ_RING);
+            fence_proxy_async();
+            mbar_expect_tx(bar, (WEIGHTED ? 3u : 2u) * bytes);
+            bulk_g2s(buf, ka + l0, bytes, bar);
+            bulk_g2s(buf + TC_KS * 8, kb + l0, bytes, bar);
+            if (WEIGHTED) bulk_g2s(buf + 2 * TC_KS * 8, w + l0, bytes, bar);
+        };
+        if (tid == 0)
+            for (int it = 0; it < 2 && it < nloc; ++it) issue_traj(it);
         for (int it = 0; it < nloc; ++it) {
             const int s = it & 1;
             const uint32_t use = (uint32_t)(it >> 1);
@@ -344,7 +384,16 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             }
             producers_sync();  // stage s is free; the previous tables are no longer read
             if (*abort_flag) break;
+            if (tid == 0 && it + 2 < nloc) issue_traj(it + 2);
+            if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1)) {
+                *abort_flag = 1;
+                atomicOr(err, kErrTimeout);
+            }
             const int64_t l0 = (ch0 + it) * TC_KS;
+            const uint8_t* tbuf = smem + TRAJ_OFF + (it % TRAJ_RING) * TRAJ_BUF;
+            const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
+            const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
+            const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
             // factor tables: [A|B][l][8 base, 16 offset]
             for (int e = tid; e < 2 * TC_KS * TC_TAB; e += TC_PRODUCERS) {
                 const int which = e / (TC_KS * TC_TAB);
@@ -355,14 +404,14 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
                 if (lg < L) {
                     if (which == 0) {
                         const int j = idx < 8 ? i0 + 16 * idx + oa : idx - 8;
-                        v = phasor_q(__ldg(ka + lg), j);
+                        v = phasor_q(ka_s[l], j);
                         if (sa < 0) v.y = -v.y;
                     } else {
                         const int j = idx < 8 ? c0 + 16 * idx + ob : idx - 8;
-                        v = phasor_q(__ldg(kb + lg), j);
+                        v = phasor_q(kb_s[l], j);
                         if (sb < 0) v.y = -v.y;
                         if (WEIGHTED && idx < 8) {
-                            float2 ww = __ldg(w + lg);
+                            float2 ww = w_s[l];
                             ww.x *= wmul;
                             ww.y *= wmul;
                             v = cmul(v, ww);
@@ -541,6 +590,11 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
     const int64_t cps = (nchunks + S - 1) / S;
     const int Seff = (int)((nchunks + cps - 1) / cps);
     unsigned* amax = nullptr;
+    if (w && w != p->s) {
+        // the kernel reads padded, plan-owned sample arrays
+        SPIREC_CK(cudaMemcpyAsync(p->ystage, w, sizeof(float2) * p->L, cudaMemcpyDeviceToDevice, p->stream));
+        w = p->ystage;
+    }
     if (w) {
         amax = p->counters + C_AMAX;
         SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
