@@ -201,6 +201,15 @@ int spirec_plan_info(spirec_plan plan, int32_t* N, int64_t* L, int32_t* M, int32
 int spirec_timing(spirec_plan plan, int32_t enable);
 int spirec_timing_read(spirec_plan plan, double* out_ms, int64_t* out_count);
 
+/* Copy the plan's FP64 device scalars to the host (diagnostics; syncs the
+ * plan).  out receives min(n, SPIREC_NUM_SCALARS) values in this order:
+ * 0 ||s||^2, 1 q1, 2 q2, 3-5 line-search steps t1..t3, 6 <g,g>, 7 beta,
+ * 8 J, 9 R, 16-27 nanoseconds block 0 of the persistent CG loop spent in each
+ * phase of its last solve (work, then barrier + reduction, for the six
+ * phases). */
+#define SPIREC_NUM_SCALARS 32
+int spirec_plan_scalars(spirec_plan plan, double* out, int32_t n);
+
 /* Number of CUDA kernels the plan has launched so far (a CUDA-graph replay
  * counts each of its kernel nodes).  Memory copies and sets are not kernels. */
 int spirec_launch_count(spirec_plan plan, int64_t* count);

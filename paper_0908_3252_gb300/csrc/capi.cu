@@ -323,10 +323,16 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
-    // gradient at x0, J(x0), beta = 0 (the first direction is -g)
-    if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->Tf, nullptr, p->g, 1, p->Jdev)) != SPIREC_OK)
-        return rc;
-    if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
+    if (loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
+        // first gradient and every iteration in one persistent kernel
+        if ((rc = launch_cg_loop(p, iters)) != SPIREC_OK) return rc;
+    } else {
+        // gradient at x0, J(x0), beta = 0 (the first direction is -g)
+        if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->Tf, nullptr, p->g, 1, p->Jdev)) !=
+            SPIREC_OK)
+            return rc;
+        if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
+    }
     return tstop(p, e);
 }
 
@@ -769,6 +775,20 @@ int spirec_plan_info(spirec_plan p, int32_t* N, int64_t* L, int32_t* M, int32_t*
     if (M) *M = p->M;
     if (precision) *precision = p->precision;
     if (device_bytes) *device_bytes = p->device_bytes;
+    return SPIREC_OK;
+}
+
+int spirec_plan_scalars(spirec_plan p, double* out, int32_t n)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!out || n < 0) {
+        set_error("bad output");
+        return SPIREC_EINVAL;
+    }
+    if (n > S_NSCAL) n = S_NSCAL;
+    SPIREC_CK(cudaMemcpyAsync(out, p->scal, sizeof(double) * n, cudaMemcpyDeviceToHost, p->stream));
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
     return SPIREC_OK;
 }
 

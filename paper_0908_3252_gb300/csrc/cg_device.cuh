@@ -1,0 +1,147 @@
+// cg_device.cuh -- per-pixel bodies of the line search and of the gradient/
+// update step (see cg.cu for the math), shared by the stand-alone kernels and
+// the persistent CG loop.  Iterates are read with ld.global.cg so a
+// persistent kernel never sees a stale L1 line written by another block.
+#pragma once
+
+#include "internal.cuh"
+
+namespace spirec {
+namespace cgd {
+
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2axpy(float t, float2 d, float2 f)
+{
+    return make_float2(fmaf(t, d.x, f.x), fmaf(t, d.y, f.y));
+}
+__device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+
+// Line-search sums at step t for pixel p: its right and down edges (Omega1)
+// and the pixel (Omega0).  num += lambda b(|x|) Re(conj(x) w),
+// den += lambda b(|x|) |w|^2 with x = z + t w.  All loads first.
+__device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const float2* d, const Reg& reg,
+                                         float tf, float& num, float& den)
+{
+    const int n = p / N, m = p - n * N;
+    const bool has_r = m + 1 < N, has_d = n + 1 < N;
+    const int pr = has_r ? p + 1 : p, pd = has_d ? p + N : p;
+    const float2 fp = __ldcg(f + p), dp = __ldcg(d + p), fr = __ldcg(f + pr), dr = __ldcg(d + pr);
+    const float2 fd = __ldcg(f + pd), dd = __ldcg(d + pd);
+    if (reg.lambda1 != 0.f) {
+        {
+            const float2 w = f2sub(dr, dp);
+            const float2 x = f2axpy(tf, w, f2sub(fr, fp));
+            const float b = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
+            num = fmaf(b, redot(x, w), num);
+            den = fmaf(b, redot(w, w), den);
+        }
+        {
+            const float2 w = f2sub(dd, dp);
+            const float2 x = f2axpy(tf, w, f2sub(fd, fp));
+            const float b = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
+            num = fmaf(b, redot(x, w), num);
+            den = fmaf(b, redot(w, w), den);
+        }
+    }
+    if (reg.lambda0 != 0.f) {
+        const float2 x = f2axpy(tf, dp, fp);
+        const float b = reg.lambda0 * phi_weight(reg.kind, reg.alpha0, redot(x, x));
+        num = fmaf(b, redot(x, dp), num);
+        den = fmaf(b, redot(dp, dp), den);
+    }
+}
+
+// t_{j+1} from t_j and the grid sums (majorize-minimize step; t stays when
+// the curvature is not positive).
+__device__ __forceinline__ double ls_next(double t, double q1, double q2, double num, double den)
+{
+    const double h1 = q1 + 2.0 * q2 * t + num;
+    const double c = 2.0 * q2 + den;
+    return c > 0.0 ? t - h1 / c : t;
+}
+
+// Gradient and step at pixel p.  Unless FIRST: f_out = f_in + t d,
+// Tf += t Td.  g = 2 (Tf - D) + grad R(f); per-thread sums
+//   a[0] <g,g>, a[1] Re<g, g_old>, a[2] Re<g, d>, a[3] R(f), a[4] Re<f, D>, a[5] Re<f, Tf>.
+// An edge from p to q with z = f_q - f_p adds +psi(z) at q and -psi(z) at p,
+// psi(z) = b(|z|) z.  All loads first (clamped neighbours, masked terms).
+template <bool FIRST>
+__device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, float2* f_out,
+                                             const float2* d, float2* Tf, const float2* Td,
+                                             const float2* __restrict__ D, float2* g, const Reg& reg,
+                                             float t, float (&a)[kUpdVals])
+{
+    const int n = p / N, m = p - n * N;
+    const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
+    const int pu = has_u ? p - N : p, pl = has_l ? p - 1 : p;
+    const int pd = has_d ? p + N : p, pr = has_r ? p + 1 : p;
+    float2 fc = __ldcg(f_in + p), fu = __ldcg(f_in + pu), fl = __ldcg(f_in + pl);
+    float2 fdn = __ldcg(f_in + pd), fr = __ldcg(f_in + pr);
+    float2 tf = __ldcg(Tf + p);
+    const float2 dv = __ldg(D + p);
+    float2 dc = make_float2(0.f, 0.f), gold = dc;
+    if (!FIRST) {
+        dc = __ldcg(d + p);
+        const float2 du = __ldcg(d + pu), dl = __ldcg(d + pl), ddn = __ldcg(d + pd), dr = __ldcg(d + pr);
+        const float2 tdv = __ldcg(Td + p);
+        gold = __ldcg(g + p);
+        fc = f2axpy(t, dc, fc);
+        fu = f2axpy(t, du, fu);
+        fl = f2axpy(t, dl, fl);
+        fdn = f2axpy(t, ddn, fdn);
+        fr = f2axpy(t, dr, fr);
+        tf = f2axpy(t, tdv, tf);
+        Tf[p] = tf;
+        f_out[p] = fc;
+    }
+    float2 gp = make_float2(2.f * (tf.x - dv.x), 2.f * (tf.y - dv.y));
+    float rv = 0.f;
+    if (reg.lambda1 != 0.f) {
+        const float l1 = reg.lambda1;
+        const float2 zu = f2sub(fc, fu), zl = f2sub(fc, fl), zd = f2sub(fdn, fc), zr = f2sub(fr, fc);
+        const float ru = redot(zu, zu), rl = redot(zl, zl), rd = redot(zd, zd), rr = redot(zr, zr);
+        const float bu = has_u ? l1 * phi_weight(reg.kind, reg.alpha1, ru) : 0.f;
+        const float bl = has_l ? l1 * phi_weight(reg.kind, reg.alpha1, rl) : 0.f;
+        const float bd = has_d ? l1 * phi_weight(reg.kind, reg.alpha1, rd) : 0.f;
+        const float br = has_r ? l1 * phi_weight(reg.kind, reg.alpha1, rr) : 0.f;
+        gp = f2axpy(bu, zu, gp);
+        gp = f2axpy(bl, zl, gp);
+        gp = f2axpy(-bd, zd, gp);
+        gp = f2axpy(-br, zr, gp);
+        rv = (has_d ? l1 * phi_value(reg.kind, reg.alpha1, rd) : 0.f) +
+             (has_r ? l1 * phi_value(reg.kind, reg.alpha1, rr) : 0.f);
+    }
+    if (reg.lambda0 != 0.f) {
+        const float r2 = redot(fc, fc);
+        gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fc, gp);
+        rv = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), rv);
+    }
+    a[0] += redot(gp, gp);
+    if (!FIRST) {
+        a[1] += redot(gp, gold);
+        a[2] += redot(gp, dc);
+    }
+    a[3] += rv;
+    a[4] += redot(fc, dv);
+    a[5] += redot(fc, tf);
+    g[p] = gp;
+}
+
+// Scalars after an update: J = ||s||^2 - 2 Re<f,D> + Re<f,Tf> + R and the
+// Polak-Ribiere beta = max(0, (<g,g> - Re<g,g_old>) / <g_old,g_old>), set to
+// 0 when Re<g, -g + beta d> >= 0 (restart) or on the first gradient.
+__device__ __forceinline__ void update_finish(const double (&s)[kUpdVals], double ss, double gg_old,
+                                              bool first, double* J, double* beta)
+{
+    *J = ss - 2.0 * s[4] + s[5] + s[3];
+    double b = 0.0;
+    if (!first) {
+        b = gg_old > 0.0 ? (s[0] - s[1]) / gg_old : 0.0;
+        if (b < 0.0) b = 0.0;
+        if (-s[0] + b * s[2] >= 0.0) b = 0.0;
+    }
+    *beta = b;
+}
+
+}  // namespace cgd
+}  // namespace spirec

@@ -12,8 +12,9 @@
 //   rows:    N row IFFTs, columns < N kept.
 // Inside the CG iteration the first row pass also forms the new direction
 // d = -g + beta d_old and the first line-search sums, and the last row pass
-// forms q2 = Re<d, T d> and the first line-search step (cg.cu holds the
-// other CG kernels).
+// forms q2 = Re<d, T d> and the first line-search step.  The bodies of the
+// passes live in fft_device.cuh (shared with the persistent loop of
+// cg_loop.cu); this file holds the stand-alone kernels and their launchers.
 //
 // FFTs are self-sorting Stockham transforms in shared memory.  For
 // power-of-two M (the sizes the plan picks) the transform is compile-time:
@@ -22,6 +23,7 @@
 // M = 2^a 3^b 5^c runs the runtime mixed-radix path with a ping-pong buffer.
 #include <stdint.h>
 
+#include "fft_device.cuh"
 #include "internal.cuh"
 #include "phase.cuh"
 #include "reduce.cuh"
@@ -49,210 +51,22 @@ bool make_fft_plan(int M, FftPlan* p)
 
 namespace {
 
-// ------------------------------------------------------------ small DFTs
-
-// X[q] = sum_r v[r] w^(r q), w = exp(-+2 pi i / R).
-template <int R, bool INV>
-__device__ __forceinline__ void dft_small(float2* v)
-{
-    if (R == 2) {
-        const float2 a = v[0], b = v[1];
-        v[0] = make_float2(a.x + b.x, a.y + b.y);
-        v[1] = make_float2(a.x - b.x, a.y - b.y);
-    } else if (R == 4) {
-        const float2 a = v[0], b = v[1], c = v[2], d = v[3];
-        const float2 s0 = make_float2(a.x + c.x, a.y + c.y);
-        const float2 s1 = make_float2(a.x - c.x, a.y - c.y);
-        const float2 s2 = make_float2(b.x + d.x, b.y + d.y);
-        const float2 s3 = make_float2(b.x - d.x, b.y - d.y);
-        // forward: X1 = s1 - i s3, X3 = s1 + i s3; the inverse swaps them
-        const float2 mis3 = INV ? make_float2(-s3.y, s3.x) : make_float2(s3.y, -s3.x);
-        v[0] = make_float2(s0.x + s2.x, s0.y + s2.y);
-        v[2] = make_float2(s0.x - s2.x, s0.y - s2.y);
-        v[1] = make_float2(s1.x + mis3.x, s1.y + mis3.y);
-        v[3] = make_float2(s1.x - mis3.x, s1.y - mis3.y);
-    } else if (R == 3) {
-        const float c1 = -0.5f;
-        const float s1 = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
-        const float2 a = v[0], b = v[1], c = v[2];
-        const float2 t = make_float2(b.x + c.x, b.y + c.y);
-        const float2 u = make_float2(b.x - c.x, b.y - c.y);
-        v[0] = make_float2(a.x + t.x, a.y + t.y);
-        const float2 m = make_float2(a.x + c1 * t.x, a.y + c1 * t.y);
-        v[1] = make_float2(m.x - s1 * u.y, m.y + s1 * u.x);
-        v[2] = make_float2(m.x + s1 * u.y, m.y - s1 * u.x);
-    } else {  // R == 5
-        const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
-        const float sg = INV ? 1.f : -1.f;
-        const float s1 = sg * 0.95105651629515357212f, s2 = sg * 0.58778525229247312917f;
-        const float2 a = v[0];
-        const float2 b1 = make_float2(v[1].x + v[4].x, v[1].y + v[4].y);
-        const float2 d1 = make_float2(v[1].x - v[4].x, v[1].y - v[4].y);
-        const float2 b2 = make_float2(v[2].x + v[3].x, v[2].y + v[3].y);
-        const float2 d2 = make_float2(v[2].x - v[3].x, v[2].y - v[3].y);
-        v[0] = make_float2(a.x + b1.x + b2.x, a.y + b1.y + b2.y);
-        const float2 m1 = make_float2(a.x + c1 * b1.x + c2 * b2.x, a.y + c1 * b1.y + c2 * b2.y);
-        const float2 m2 = make_float2(a.x + c2 * b1.x + c1 * b2.x, a.y + c2 * b1.y + c1 * b2.y);
-        const float2 e1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
-        const float2 e2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
-        v[1] = make_float2(m1.x - e1.y, m1.y + e1.x);
-        v[4] = make_float2(m1.x + e1.y, m1.y - e1.x);
-        v[2] = make_float2(m2.x - e2.y, m2.y + e2.x);
-        v[3] = make_float2(m2.x + e2.y, m2.y - e2.x);
-    }
-}
-
-__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, bool inv)
-{
-    float2 w = __ldg(tw + e);
-    if (inv) w.y = -w.y;
-    return w;
-}
-
-// --------------------------------------------- runtime mixed-radix Stockham
-
-template <int R, bool INV>
-__device__ __forceinline__ void stage_rt(const float2* __restrict__ in, float2* __restrict__ out,
-                                         int M, int Ns, int nseq, int ld,
-                                         const float2* __restrict__ tw)
-{
-    const int nb = M / R;
-    const int tstep = M / (Ns * R);
-    for (int idx = threadIdx.x; idx < nseq * nb; idx += blockDim.x) {
-        const int q = idx / nb, j = idx - q * nb;
-        const float2* src = in + q * ld;
-        float2* dst = out + q * ld;
-        const int k = j % Ns;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twiddle(tw, k * r * tstep, INV));
-        dft_small<R, INV>(v);
-        const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
-    }
-}
-
-template <bool INV>
-__device__ float2* fft_rt(float2* a, float2* b, const FftPlan& fp, int nseq, int ld,
-                          const float2* __restrict__ tw)
-{
-    int Ns = 1;
-    for (int s = 0; s < fp.nstages; ++s) {
-        const int R = fp.radix[s];
-        switch (R) {
-        case 4: stage_rt<4, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        case 2: stage_rt<2, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        case 3: stage_rt<3, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        default: stage_rt<5, INV>(a, b, fp.M, Ns, nseq, ld, tw); break;
-        }
-        __syncthreads();
-        float2* t = a;
-        a = b;
-        b = t;
-        Ns *= R;
-    }
-    return a;
-}
-
-// --------------------------------------------- compile-time power-of-two
-
-__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
-
-// In-place transform of nseq sequences (stride ld) of length M; the block has
-// exactly nseq * M / 4 threads, one radix-4 butterfly each per stage.
-template <int M, bool INV>
-__device__ __forceinline__ void fft_pow2(float2* buf, int ld, const float2* __restrict__ tw)
-{
-    constexpr int LOG2M = ilog2(M);
-    constexpr int NB = M / 4;
-    const int q = threadIdx.x / NB, j = threadIdx.x % NB;
-    float2* s = buf + q * ld;
-#pragma unroll
-    for (int lns = 0; lns + 2 <= LOG2M; lns += 2) {
-        const int Ns = 1 << lns;
-        const int k = j & (Ns - 1);
-        float2 v[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = s[j + r * NB];
-        __syncthreads();
-#pragma unroll
-        for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], twiddle(tw, (k * r) << (LOG2M - lns - 2), INV));
-        dft_small<4, INV>(v);
-        const int base = ((j >> lns) << (lns + 2)) + k;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) s[base + r * Ns] = v[r];
-        __syncthreads();
-    }
-    if (LOG2M & 1) {  // last stage radix 2, Ns = M/2: butterflies jj and jj + M/2
-        float2 a[2], b[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            a[h] = s[j + h * NB];
-            b[h] = s[j + h * NB + M / 2];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int jj = j + h * NB;
-            float2 v[2] = {a[h], cmul(b[h], twiddle(tw, jj, INV))};
-            dft_small<2, INV>(v);
-            s[jj] = v[0];
-            s[jj + M / 2] = v[1];
-        }
-        __syncthreads();
-    }
-}
-
-// Transform dispatch: MC > 0 compile-time size (in place, nseq*MC/4 threads),
-// MC == 0 runtime plan (ping-pong, any block size).  Returns the buffer with
-// the result; ends with __syncthreads().
-template <int MC, bool INV>
-__device__ __forceinline__ float2* fft_block(float2* a, float2* b, const FftPlan& fp, int nseq,
-                                             int ld, const float2* __restrict__ tw)
-{
-    if constexpr (MC > 0) {
-        fft_pow2<MC, INV>(a, ld, tw);
-        return a;
-    } else {
-        return fft_rt<INV>(a, b, fp, nseq, ld, tw);
-    }
-}
-
-// --------------------------------------------- CG helpers
-
-__device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
-// d = -g + beta d_old (d = -g on a restart, so a stale d_old never enters).
-__device__ __forceinline__ float2 new_direction(float2 g, float2 dold, float beta, bool restart)
-{
-    return restart ? make_float2(-g.x, -g.y) : make_float2(fmaf(beta, dold.x, -g.x), fmaf(beta, dold.y, -g.y));
-}
+using namespace fftd;
 
 // ------------------------------------------------------------- row pass 1
 
-// MODE 0: row FFTs of `in` (rows [0, rows), n_in nonzero inputs per row at
-// stride ld_in) into X (stride M).
-// MODE 1 (CG): the input rows are the new direction d = -g + beta d_old,
-// written to c.d_new; also the block sums of
-//   q1   = Re<d, 2 (Tf - D)>
-//   num0 = sum_e lambda b(|z_e|) Re(conj(z_e) w_e),  den0 = sum_e lambda b(|z_e|) |w_e|^2
-// (first line-search step, t = 0), finished by the last block into scal.
+// MODE 0: row FFTs of `in` into X.  MODE 1 (CG): the rows of the new
+// direction, with q1 and the first line-search sums reduced over the grid
+// and finished by the last block into scal (see fft_device.cuh).
 template <int MC, int MODE>
-__global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, int rows,
-                           float2* __restrict__ X, FftPlan fp, const float2* __restrict__ tw,
-                           int rpc, CgPass c)
+__global__ void __launch_bounds__(1024) k_rows_fwd(const float2* in, int ld_in, int n_in, int rows, float2* X, FftPlan fp,
+                           const float2* __restrict__ tw, int rpc, CgPass c)
 {
     extern __shared__ float2 sm[];
-    const int M = fp.M;
     float2* a = sm;
-    float2* b = sm + rpc * M;
+    float2* b = sm + rpc * seq_len<MC>(fp.M);
     const int r0 = blockIdx.x * rpc;
     const int nr = min(rpc, rows - r0);
-    const int N = n_in;
     float beta = 0.f;
     bool restart = true;
     if (MODE == 1) {
@@ -260,63 +74,11 @@ __global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, i
         beta = (float)bd;
         restart = bd == 0.0;
     }
-    for (int e = threadIdx.x; e < rpc * M; e += blockDim.x) {
-        const int q = e / M, m = e - q * M;
-        float2 v = make_float2(0.f, 0.f);
-        if (q < nr && m < N) {
-            const int64_t o = (int64_t)(r0 + q) * ld_in + m;
-            if (MODE == 0) {
-                v = in[o];
-            } else {
-                v = new_direction(c.g[o], c.d_old[o], beta, restart);
-                c.d_new[o] = v;
-            }
-        }
-        a[e] = v;
-    }
-    __syncthreads();
+    float acc[3] = {0.f, 0.f, 0.f};
+    rows_fwd_group<MC, MODE>(in, ld_in, n_in, r0, nr, rpc, X, fp, tw, c, beta, restart, a, b, acc);
     if (MODE == 1) {
-        const Reg reg = c.reg;
-        float q1 = 0.f, num = 0.f, den = 0.f;
-        for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
-            const int q = e / N, m = e - q * N;
-            const int n = r0 + q;
-            const int64_t o = (int64_t)n * N + m;
-            const bool has_r = m + 1 < N, has_d = n + 1 < N;
-            const int64_t od = has_d ? o + N : o;
-            // every load first (clamped neighbours, masked contributions)
-            const float2 dn = a[q * M + m];
-            const float2 dr = a[q * M + (has_r ? m + 1 : m)];
-            const float2 fp_ = c.f[o], fr = c.f[has_r ? o + 1 : o], fd = c.f[od];
-            const float2 gd = c.g[od], dold_d = c.d_old[od];
-            const float2 tfv = c.Tf[o], dv = c.D[o];
-            q1 += 2.f * redot(dn, f2sub(tfv, dv));
-            if (reg.lambda1 != 0.f) {
-                {
-                    const float2 w = f2sub(dr, dn);
-                    const float2 z = f2sub(fr, fp_);
-                    const float bw = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
-                    num = fmaf(bw, redot(z, w), num);
-                    den = fmaf(bw, redot(w, w), den);
-                }
-                {
-                    const float2 dd = new_direction(gd, dold_d, beta, restart);
-                    const float2 w = f2sub(dd, dn);
-                    const float2 z = f2sub(fd, fp_);
-                    const float bw = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
-                    num = fmaf(bw, redot(z, w), num);
-                    den = fmaf(bw, redot(w, w), den);
-                }
-            }
-            if (reg.lambda0 != 0.f) {
-                const float bw = reg.lambda0 * phi_weight(reg.kind, reg.alpha0, redot(fp_, fp_));
-                num = fmaf(bw, redot(fp_, dn), num);
-                den = fmaf(bw, redot(dn, dn), den);
-            }
-        }
-        float v[3] = {q1, num, den};
         FF bt[3];
-        block_partial<3>(v, bt);
+        block_partial<3>(acc, bt);
         store_parts<3>(bt, c.parts, kMaxParts);
         if (last_block(c.counter)) {
             FF t[3];
@@ -329,44 +91,26 @@ __global__ void k_rows_fwd(const float2* __restrict__ in, int ld_in, int n_in, i
             }
         }
     }
-    float2* res = fft_block<MC, false>(a, b, fp, nr, M, tw);
-    for (int e = threadIdx.x; e < nr * M; e += blockDim.x) {
-        const int q = e / M, m = e - q * M;
-        X[(int64_t)(r0 + q) * M + m] = res[e];
-    }
 }
 
 // ------------------------------------------------------------- row pass 3
 
-// Row IFFTs of X (rows [0, rows)), first n_out columns to out (stride n_out).
-// With dotx: s = Re<dotx, out> reduced over the grid; MODE 0 stores it in
-// scal[dot_scalar]; MODE 1 (CG) stores q2 = s and the first line-search step
+// Row IFFTs of X, first n_out columns to out.  With dotx: s = Re<dotx, out>
+// over the grid; MODE 0 stores it in scal[dot_scalar]; MODE 1 (CG) stores
+// q2 = s and the first line-search step
 //   t1 = -(q1 + num0) / (2 q2 + den0)   (0 when the curvature is not > 0).
 template <int MC, int MODE>
-__global__ void k_rows_inv(const float2* __restrict__ X, int rows, float2* __restrict__ out,
-                           int n_out, FftPlan fp, const float2* __restrict__ tw, int rpc,
-                           const float2* __restrict__ dotx, CgPass c, int dot_scalar)
+__global__ void __launch_bounds__(1024) k_rows_inv(const float2* X, int rows, float2* out, int n_out, FftPlan fp,
+                           const float2* __restrict__ tw, int rpc, const float2* dotx, CgPass c,
+                           int dot_scalar)
 {
     extern __shared__ float2 sm[];
-    const int M = fp.M;
     float2* a = sm;
-    float2* b = sm + rpc * M;
+    float2* b = sm + rpc * seq_len<MC>(fp.M);
     const int r0 = blockIdx.x * rpc;
     const int nr = min(rpc, rows - r0);
-    for (int e = threadIdx.x; e < rpc * M; e += blockDim.x) {
-        const int q = e / M;
-        a[e] = q < nr ? X[(int64_t)r0 * M + e] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2* res = fft_block<MC, true>(a, b, fp, nr, M, tw);
     float acc = 0.f;
-    for (int e = threadIdx.x; e < nr * n_out; e += blockDim.x) {
-        const int q = e / n_out, m = e - q * n_out;
-        const float2 v = res[q * M + m];
-        const int64_t o = (int64_t)(r0 + q) * n_out + m;
-        out[o] = v;
-        if (dotx) acc += redot(dotx[o], v);
-    }
+    rows_inv_group<MC>(X, r0, nr, rpc, out, n_out, fp, tw, dotx, a, b, acc);
     if (dotx) {
         float v[1] = {acc};
         FF bt[1];
@@ -392,64 +136,39 @@ __global__ void k_rows_inv(const float2* __restrict__ X, int rows, float2* __res
 
 // ------------------------------------------------------------- column pass
 
-// Columns [x0, x0+cpc) of the N x M buffer X: FFT of the n_in nonzero rows,
-// multiply by Chat[x][ky], IFFT, keep rows < n_out.  Sequences sit at stride
-// M+1 in shared memory (spreads the banks of the transposed loads).
 template <int MC>
-__global__ void k_cols_filter(float2* X, int n_in, int n_out, FftPlan fp, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(1024) k_cols_filter(float2* X, int n_in, int n_out, FftPlan fp, const float2* __restrict__ tw,
                               const float* __restrict__ Chat, int cpc)
 {
     extern __shared__ float2 sm[];
-    const int M = fp.M;
-    const int ld = M + 1;
-    float2* a = sm;
-    float2* b = sm + cpc * ld;
+    const int ld = seq_len<MC>(fp.M) + 4;
     const int x0 = blockIdx.x * cpc;
-    const int nc = min(cpc, M - x0);
-    for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
-        const int y = e / cpc, cc = e - y * cpc;
-        a[cc * ld + y] = (y < n_in && cc < nc) ? X[(int64_t)y * M + x0 + cc] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2* res = fft_block<MC, false>(a, b, fp, cpc, ld, tw);
-    for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
-        const int cc = e / M, ky = e - cc * M;
-        const float h = cc < nc ? __ldg(&Chat[(int64_t)(x0 + cc) * M + ky]) : 0.f;
-        const float2 v = res[cc * ld + ky];
-        res[cc * ld + ky] = make_float2(v.x * h, v.y * h);
-    }
-    __syncthreads();
-    float2* other = res == a ? b : a;
-    float2* res2 = fft_block<MC, true>(res, other, fp, cpc, ld, tw);
-    for (int e = threadIdx.x; e < cpc * n_out; e += blockDim.x) {
-        const int y = e / cpc, cc = e - y * cpc;
-        if (cc < nc) X[(int64_t)y * M + x0 + cc] = res2[cc * ld + y];
-    }
+    cols_group<MC>(X, n_in, n_out, x0, min(cpc, fp.M - x0), cpc, fp, tw, Chat, sm, sm + cpc * ld);
 }
 
 // Column FFTs of the M x M circulant and the real spectrum:
 // Chat[x][ky] = Re(FFT2 c)[ky][x] / M^2.
 template <int MC>
-__global__ void k_cols_spectrum(const float2* cwork, FftPlan fp, const float2* __restrict__ tw,
+__global__ void __launch_bounds__(1024) k_cols_spectrum(const float2* cwork, FftPlan fp, const float2* __restrict__ tw,
                                 float* Chat, int cpc)
 {
     extern __shared__ float2 sm[];
     const int M = fp.M;
-    const int ld = M + 1;
+    const int ld = seq_len<MC>(M) + 4;
     float2* a = sm;
     float2* b = sm + cpc * ld;
     const int x0 = blockIdx.x * cpc;
     const int nc = min(cpc, M - x0);
     for (int e = threadIdx.x; e < cpc * M; e += blockDim.x) {
         const int y = e / cpc, cc = e - y * cpc;
-        a[cc * ld + y] = cc < nc ? cwork[(int64_t)y * M + x0 + cc] : make_float2(0.f, 0.f);
+        a[cc * ld + sidx<MC>(y)] = cc < nc ? cwork[(int64_t)y * M + x0 + cc] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     float2* res = fft_block<MC, false>(a, b, fp, cpc, ld, tw);
     const float inv = 1.0f / ((float)M * (float)M);
     for (int e = threadIdx.x; e < nc * M; e += blockDim.x) {
         const int cc = e / M, ky = e - cc * M;
-        Chat[(int64_t)(x0 + cc) * M + ky] = res[cc * ld + ky].x * inv;
+        Chat[(int64_t)(x0 + cc) * M + ky] = res[cc * ld + sidx<MC>(ky)].x * inv;
     }
 }
 
@@ -495,7 +214,7 @@ Shape row_shape(int M, bool pow2)
     if (pow2) {
         const int nb = M / 4;
         const int rpc = nb >= 256 ? 1 : 256 / nb;
-        return Shape{rpc, rpc * nb, (size_t)rpc * M * sizeof(float2)};
+        return Shape{rpc, rpc * nb, (size_t)rpc * seq_len<1>(M) * sizeof(float2)};
     }
     const int rpc = M >= 1024 ? 1 : 1024 / M;
     return Shape{rpc, 256, 2 * (size_t)rpc * M * sizeof(float2)};
@@ -506,12 +225,13 @@ Shape col_shape(int M, bool pow2)
     if (pow2) {
         const int nb = M / 4;
         int cpc = nb >= 1024 ? 1 : 1024 / nb;
-        while (cpc > 1 && (size_t)cpc * (M + 1) * sizeof(float2) > (size_t)kFftSmemCap) cpc /= 2;
-        return Shape{cpc, cpc * nb, (size_t)cpc * (M + 1) * sizeof(float2)};
+        const size_t ld = seq_len<1>(M) + 4;
+        while (cpc > 1 && (size_t)cpc * ld * sizeof(float2) > (size_t)kFftSmemCap) cpc /= 2;
+        return Shape{cpc, cpc * nb, (size_t)cpc * ld * sizeof(float2)};
     }
     int cpc = M >= 1024 ? 4 : (M >= 512 ? 8 : 16);
-    while (cpc > 1 && 2 * (size_t)cpc * (M + 1) * sizeof(float2) > (size_t)kFftSmemCap) --cpc;
-    return Shape{cpc, 256, 2 * (size_t)cpc * (M + 1) * sizeof(float2)};
+    while (cpc > 1 && 2 * (size_t)cpc * (M + 4) * sizeof(float2) > (size_t)kFftSmemCap) --cpc;
+    return Shape{cpc, 256, 2 * (size_t)cpc * (M + 4) * sizeof(float2)};
 }
 
 template <int MC>

@@ -47,7 +47,11 @@ enum PartSlot {
 constexpr int kUpdVals = 6;  // sums of the update kernel
 
 // Arrival counters of the last-block reductions, one per kernel kind.
-enum Counter { C_ROWA = 0, C_ROWC = 1, C_LS = 2, C_UPD = 3, C_MISC = 4, C_AMAX = 5, C_N = 8 };
+enum Counter {
+    C_ROWA = 0, C_ROWC = 1, C_LS = 2, C_UPD = 3, C_MISC = 4, C_AMAX = 5,
+    C_BAR = 8,  // grid barrier of the persistent loop: arrivals, generation, abort
+    C_N = 16
+};
 
 // Bits of the device error word (plan->dflag).
 enum DeviceError { E_TRAJ = 1, E_TIMEOUT = 2 };
@@ -67,7 +71,8 @@ enum Scalar {
     S_TMP = 10,   // result of a one-off dot
     S_NUM0 = 11,  // penalty part of h'(0)
     S_DEN0 = 12,  // penalty part of the majorant curvature at t = 0
-    S_NSCAL = 16
+    S_PROF = 16,  // 16 slots: time (ns) block 0 of the persistent loop spent per phase
+    S_NSCAL = 32
 };
 
 struct Reg {
@@ -182,6 +187,10 @@ int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2
                   const float2* Td, float2* g, int first, double* Jout);
 int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step);
 int cg_iteration(spirec_plan p, int k, double* Jdev);
+// The whole loop (first gradient + iters iterations) as one persistent
+// cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only.
+bool loop_supported(int M);
+int launch_cg_loop(spirec_plan p, int iters);
 
 // tensor-core contractions (FP16x3 / BF16x3)
 int launch_gram_tc(spirec_plan p);

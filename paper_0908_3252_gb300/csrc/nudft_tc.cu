@@ -13,11 +13,11 @@
 // same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for FP16).
 //
 // Pipeline per CTA (544 threads):
-//   warps 0-15 producers: per stage of 32 samples, build the factor tables
-//              exp(i2pi k (base + 16a)) and exp(i2pi k b), multiply them out
-//              into the four operand tiles (A_hi, A_lo, B_hi, B_lo) in the
-//              128-byte-swizzled K-major layout the MMA reads, then arrive on
-//              full[stage];
+//   warps 0-15 producers: per stage of 32 samples, each thread forms the
+//              phasors of one A row and one B column (exact fixed-point phase,
+//              fast hardware sin/cos), splits them into the four operand tiles
+//              (A_hi, A_lo, B_hi, B_lo) in the 128-byte-swizzled K-major
+//              layout the MMA reads, then arrives on full[stage];
 //   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
 //              issues 12 tcgen05.mma (K = 16 each) and commits to empty[stage];
 //   warps 0-15 drain: every SEG stages (512 samples) the finished accumulator
@@ -51,16 +51,13 @@ constexpr int TC_KS = 32;           // samples per stage (64 real K per operand 
 constexpr int TC_STAGES = 2;
 constexpr int TC_PRODUCERS = 512;   // 16 warps
 constexpr int TC_THREADS = TC_PRODUCERS + 32;
-constexpr int TC_TAB = 24;          // 8 base + 16 offset phasors per sample
 constexpr int TC_SEG = 16;          // stages per accumulator segment
 constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = 2 * TC_COLS * 128;      // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr uint32_t TAB_OFF = TC_STAGES * STAGE_BYTES;
-constexpr uint32_t TAB_BYTES = 2 * TC_KS * TC_TAB * 8;
 constexpr int TRAJ_RING = 4;
 constexpr uint32_t TRAJ_BUF = 3 * TC_KS * 8;                // ka, kb (int64) and w (float2)
-constexpr uint32_t TRAJ_OFF = TAB_OFF + TAB_BYTES;
+constexpr uint32_t TRAJ_OFF = TC_STAGES * STAGE_BYTES;
 constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
@@ -253,6 +250,19 @@ __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo)
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
+// exp(+i 2 pi k j) from the fixed-point k: kq * j mod 2^64 is the exact
+// phase (two's complement wraps it), its top 32 bits a signed fraction of a
+// cycle, and the fast hardware sin/cos runs on an argument in [-pi, pi)
+// (absolute error about 4e-7, below the split-precision contraction's own).
+__device__ __forceinline__ float2 phasor_fast(int64_t kq, int j)
+{
+    const uint64_t th = (uint64_t)kq * (uint64_t)(int64_t)j;
+    const float ang = (float)(int)(th >> 32) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    float sn, cs;
+    __sincosf(ang, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
 __device__ __forceinline__ uint4 neg4(uint4 v)
 {
     const uint32_t s = 0x80008000u;  // sign bits of both packed halves
@@ -313,8 +323,6 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    float2* tabA = reinterpret_cast<float2*>(smem + TAB_OFF);
-    float2* tabB = tabA + TC_KS * TC_TAB;
     const uint32_t bar_full = sbase + BAR_OFF;           // 2 x 8 B: stage filled
     const uint32_t bar_empty = sbase + BAR_OFF + 16;     // 2 x 8 B: stage consumed
     const uint32_t bar_acc_full = sbase + BAR_OFF + 32;  // 2 x 8 B: segment accumulated
@@ -382,7 +390,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
-            producers_sync();  // stage s is free; the previous tables are no longer read
+            producers_sync();  // stage s is free
             if (*abort_flag) break;
             if (tid == 0 && it + 2 < nloc) issue_traj(it + 2);
             if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1)) {
@@ -394,47 +402,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
-            // factor tables: [A|B][l][8 base, 16 offset]
-            for (int e = tid; e < 2 * TC_KS * TC_TAB; e += TC_PRODUCERS) {
-                const int which = e / (TC_KS * TC_TAB);
-                const int rem = e - which * TC_KS * TC_TAB;
-                const int l = rem / TC_TAB, idx = rem - l * TC_TAB;
-                const int64_t lg = l0 + l;
-                float2 v = make_float2(0.f, 0.f);
-                if (lg < L) {
-                    if (which == 0) {
-                        const int j = idx < 8 ? i0 + 16 * idx + oa : idx - 8;
-                        v = phasor_q(ka_s[l], j);
-                        if (sa < 0) v.y = -v.y;
-                    } else {
-                        const int j = idx < 8 ? c0 + 16 * idx + ob : idx - 8;
-                        v = phasor_q(kb_s[l], j);
-                        if (sb < 0) v.y = -v.y;
-                        if (WEIGHTED && idx < 8) {
-                            float2 ww = w_s[l];
-                            ww.x *= wmul;
-                            ww.y *= wmul;
-                            v = cmul(v, ww);
-                        }
-                    }
-                }
-                (which == 0 ? tabA : tabB)[l * TC_TAB + idx] = v;
-            }
-            producers_sync();
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
             for (int q = 0; q < 512 / TC_PRODUCERS; ++q) {
                 const int u = tid + TC_PRODUCERS * q;
                 const int r = u & 127, g = u >> 7;  // row (A) or column (B), sample group
+                const int ja = i0 + r + oa, jb = c0 + r + ob;
                 float re[8], im[8];
                 // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int l = 8 * g + e;
-                    const float2 v = cmul(tabA[l * TC_TAB + (r >> 4)], tabA[l * TC_TAB + 8 + (r & 15)]);
+                    float2 v = phasor_fast(ka_s[l], ja);
+                    if (l0 + l >= L) v = make_float2(0.f, 0.f);
                     re[e] = v.x;
-                    im[e] = v.y;
+                    im[e] = sa < 0 ? -v.y : v.y;
                 }
                 uint4 rh, rl, ih, il;
                 split8<BF16>(re, rh, rl);
@@ -447,7 +430,15 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int l = 8 * g + e;
-                    const float2 v = cmul(tabB[l * TC_TAB + (r >> 4)], tabB[l * TC_TAB + 8 + (r & 15)]);
+                    float2 v = phasor_fast(kb_s[l], jb);
+                    if (sb < 0) v.y = -v.y;
+                    if (WEIGHTED) {
+                        float2 ww = w_s[l];
+                        ww.x *= wmul;
+                        ww.y *= wmul;
+                        v = cmul(v, ww);
+                    }
+                    if (l0 + l >= L) v = make_float2(0.f, 0.f);
                     re[e] = v.x;
                     im[e] = v.y;
                 }

@@ -28,12 +28,26 @@ __device__ __forceinline__ FF ff_add(FF a, FF b)
 
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
+// Warp-level float-float sum (valid in lane 0).
+__device__ __forceinline__ FF warp_sum_ff(FF a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF other;
+        other.hi = __shfl_down_sync(0xffffffffu, a.hi, o);
+        other.lo = __shfl_down_sync(0xffffffffu, a.lo, o);
+        a = ff_add(a, other);
+    }
+    return a;
+}
+
 // Block totals of K per-thread FP32 values; valid in thread 0 only.
 // Contains __syncthreads(); call from all threads of the block.
 template <int K>
 __device__ __forceinline__ void block_partial(float (&v)[K], FF (&out)[K])
 {
     __shared__ float ws[32][K];
+    __shared__ FF wt[K];
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
@@ -44,15 +58,17 @@ __device__ __forceinline__ void block_partial(float (&v)[K], FF (&out)[K])
 #pragma unroll
         for (int k = 0; k < K; ++k) ws[warp][k] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            FF acc{ws[0][k], 0.f};
-            for (int w = 1; w < nw; ++w) acc = ff_add(acc, FF{ws[w][k], 0.f});
-            out[k] = acc;
-        }
+    // warp k (k < K) adds the warp sums of value k as a float-float tree
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp < K) {
+        FF a{lane < nw ? ws[lane][warp] : 0.f, 0.f};
+        a = warp_sum_ff(a);
+        if (lane == 0) wt[warp] = a;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = wt[k];
 }
 
 // True in every thread of the last block of the grid to arrive.  Thread 0
@@ -82,45 +98,41 @@ __device__ __forceinline__ void store_parts(const FF (&v)[K], float2* parts, int
     }
 }
 
-// Grid totals of K values from n block partials, read past L1 in index order
-// (float-float throughout); valid in thread 0 only.
+// Grid total of one value from n block partials (float-float, index order
+// per lane, then a fixed shuffle tree); valid in lane 0 of the calling warp.
+// Loads are issued eight at a time before they are added.
+__device__ __forceinline__ FF warp_sum_parts(const float2* parts, int n)
+{
+    const int lane = threadIdx.x & 31;
+    FF acc{0.f, 0.f};
+    for (int base = 0; base < n; base += 32 * 8) {
+        float2 v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = base + lane + 32 * j;
+            v[j] = i < n ? __ldcg(parts + i) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc = ff_add(acc, FF{v[j].x, v[j].y});
+    }
+    return warp_sum_ff(acc);
+}
+
+// Grid totals of K values from n block partials; warp k sums value k.
+// Valid in thread 0 only.  Needs K <= blockDim.x / 32.
 template <int K>
 __device__ __forceinline__ void sum_parts_ff(const float2* parts, int stride, int n, FF (&tot)[K])
 {
-    __shared__ FF ws[32][K];
-    FF acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = FF{0.f, 0.f};
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const float2 p = __ldcg(parts + k * stride + i);
-            acc[k] = ff_add(acc[k], FF{p.x, p.y});
-        }
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            FF other;
-            other.hi = __shfl_down_sync(0xffffffffu, acc[k].hi, o);
-            other.lo = __shfl_down_sync(0xffffffffu, acc[k].lo, o);
-            acc[k] = ff_add(acc[k], other);
-        }
+    __shared__ FF ws[K];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) ws[warp][k] = acc[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            FF a = ws[0][k];
-            for (int w = 1; w < nw; ++w) a = ff_add(a, ws[w][k]);
-            tot[k] = a;
-        }
+    if (warp < K) {
+        const FF a = warp_sum_parts(parts + warp * stride, n);
+        if (lane == 0) ws[warp] = a;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] = ws[k];
 }
 
 }  // namespace spirec

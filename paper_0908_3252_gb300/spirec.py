@@ -66,6 +66,7 @@ SIGNATURES = {
     "spirec_sync": (ctypes.c_int, [_P]),
     "spirec_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "spirec_launch_count": (ctypes.c_int, [_P, _P]),
+    "spirec_plan_scalars": (ctypes.c_int, [_P, _P, _I32]),
     "spirec_timing": (ctypes.c_int, [_P, _I32]),
     "spirec_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "spirec_last_error": (ctypes.c_char_p, []),
@@ -229,6 +230,12 @@ def spirec_plan_info(plan):
     _check(load().spirec_plan_info(plan, ctypes.byref(N), ctypes.byref(L), ctypes.byref(M),
                                    ctypes.byref(prec), ctypes.byref(nbytes)))
     return dict(N=N.value, L=L.value, M=M.value, precision=prec.value, device_bytes=nbytes.value)
+
+
+def spirec_plan_scalars(plan, n=32):
+    out = (ctypes.c_double * n)()
+    _check(load().spirec_plan_scalars(plan, out, n))
+    return list(out)
 
 
 def spirec_launch_count(plan):

@@ -251,3 +251,28 @@ def test_errors(sp):
     with pytest.raises(sp.SpirecError) as e:
         sp.Plan(8, 20, 10, 0, torch.cuda.current_stream().cuda_stream)  # M < 2N-1
     assert e.value.code == sp.SPIREC_EINVAL
+
+
+def test_persistent_loop_matches_kernel_graph(sp, monkeypatch):
+    """The persistent cooperative loop (default for power-of-two M) and the
+    graph of stand-alone kernels run the same iteration; only their
+    summation trees differ, so J agrees to 1e-5 and both match the oracle."""
+    w = workload_c1()
+    N, reg = w["N"], w["reg"]
+    res = {}
+    for mode in ("loop", "graph"):
+        if mode == "graph":
+            monkeypatch.setenv("SPIREC_NO_LOOP", "1")
+        else:
+            monkeypatch.delenv("SPIREC_NO_LOOP", raising=False)
+        with _plan(sp, w, 0) as p:
+            assert p.M == 64
+            sp.spirec_set_data(p.h, w["s"])
+            sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+            res[mode] = sp.spirec_solve(p.h, None, w["iters"], N)
+    xo, Jo, _ = O.solve(w["kx"], w["ky"], w["s"], reg, np.zeros((N, N)), w["iters"])
+    for mode in res:
+        x, J = res[mode]
+        assert rel(J, Jo) < 1e-5, mode
+        assert rel(x, xo) < ITER_TOL, mode
+    assert rel(res["loop"][1], res["graph"][1]) < 1e-5
