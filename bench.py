@@ -40,9 +40,9 @@ UNIT = "iters/s"
 ITERS = 50
 
 
-def workload(seed=3):
+def workload(seed=3, S=4096):
     from paper_0908_3252_gb300 import synth
-    N, I, S = 512, 32, 4096
+    N, I = 512, 32
     g = synth.rng(seed)
     f_true = synth.phantom(N, "edges_texture", g)
     kx, ky = synth.spiral(N, I, S, "archimedean")
@@ -50,6 +50,13 @@ def workload(seed=3):
                 lambda1=0.05, alpha1=0.05, lambda0=0.0, alpha0=0.05, phi=0,
                 name=f"512x512 edges+texture phantom, Archimedean spiral {I}x{S} (L={I * S}), "
                      f"30 dB, Huber a=0.05 l=0.05, M=1024, {ITERS} CG iters")
+
+
+def apply_size_args(args):
+    """--samples / --iters shrink the workload for profiling captures only;
+    the default is the metric's configuration."""
+    global ITERS
+    ITERS = args.iters
 
 
 def dist_env():
@@ -163,7 +170,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    w = workload()
+    w = workload(S=args.samples)
     vals = []
     for i in range(args.warmup + args.steps):
         r = oracle_sample(w, budget_s=3.0)
@@ -202,7 +209,7 @@ def run_ours(args):
 
     prec = {"fp32": spirec.SPIREC_FP32, "fp16x3": spirec.SPIREC_MIXED_FP16X3,
             "bf16x3": spirec.SPIREC_MIXED_BF16X3}[args.precision]
-    w = workload(seed=3 + rank)
+    w = workload(seed=3 + rank, S=args.samples)
     N, M = w["N"], w["M"]
     L = w["kx"].shape[0]
     stream = torch.cuda.Stream(device=dev)
@@ -402,7 +409,11 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--samples", type=int, default=4096,
+                    help="samples per interleave (4096 = the metric's 131072-sample spiral)")
+    ap.add_argument("--iters", type=int, default=50, help="CG iterations per step (50 = the metric's)")
     args = ap.parse_args()
+    apply_size_args(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
