@@ -116,6 +116,21 @@ def clocks_stop(proc, f, gpu_index):
             "reasons": sorted(reasons)}
 
 
+def job_throughput(local_seconds, units_per_rank, device="cpu"):
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's time (max over ranks through torch.distributed when it
+    is initialised, any backend).  Returns (value, max_seconds)."""
+    import torch
+    import torch.distributed as dist
+    t, ws = float(local_seconds), 1
+    if dist.is_available() and dist.is_initialized():
+        ws = dist.get_world_size()
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return ws * units_per_rank / t, t
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -267,12 +282,7 @@ def run_ours(args):
         J = J_d.cpu().numpy()
         x_gpu = x_d.cpu().numpy()
 
-    t_s = ms / 1000.0
-    if ws > 1:
-        tt = torch.tensor([t_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_s = float(tt.item())
-    value = ws * ITERS * args.steps / t_s
+    value, t_s = job_throughput(ms / 1000.0, ITERS * args.steps, dev)
 
     # ---- end to end through the host-pointer API (pinned buffers)
     kx_h = torch.from_numpy(w["kx"]).pin_memory().numpy()
@@ -296,12 +306,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e_t = sum(e2e_times)
-    if ws > 1:
-        tt = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
-    e2e_value = ws * ITERS * args.steps / e2e_t
+    e2e_value, _ = job_throughput(sum(e2e_times), ITERS * args.steps, dev)
     spirec.spirec_plan_destroy(h)
 
     # ---- FP32 plain path on the same workload (the metric's comparison)
