@@ -59,6 +59,96 @@ def apply_size_args(args):
     ITERS = args.iters
 
 
+def run_batch(spirec, prec, frames=64, iters=50, seed=4):
+    """Dynamic series: `frames` frames, sizes from {128, 192, 256}, each
+    sampling 4 of 16 golden-angle interleaves x 2048 (L = 8192), moving
+    ellipse phantoms; every frame's trajectory, data and solve are enqueued on
+    its own plan's stream, then all are awaited (one timed region)."""
+    import torch
+    from paper_0908_3252_gb300 import synth
+    g = synth.rng(seed)
+    kx16, ky16 = synth.spiral(256, 16, 2048, "archimedean", "golden")
+    items = []
+    for i in range(frames):
+        N = int(g.choice([128, 192, 256]))
+        sub = np.sort(g.choice(16, 4, replace=False))
+        idx = np.concatenate([np.arange(j * 2048, (j + 1) * 2048) for j in sub])
+        kx, ky = kx16[idx], ky16[idx]
+        L = kx.shape[0]
+        f = synth.ellipses(N, 10, synth.rng(1000 + i)).astype(np.complex64)
+        st = torch.cuda.Stream()
+        M = 256 if N == 128 else 512
+        p = spirec.Plan(N, L, M, prec, st.cuda_stream)
+        kx_d, ky_d = torch.from_numpy(kx).cuda(), torch.from_numpy(ky).cuda()
+        torch.cuda.synchronize()
+        spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
+        y = torch.zeros(L, dtype=torch.complex64, device="cuda")
+        spirec.spirec_forward_dev(p.h, torch.from_numpy(f).cuda(), y)
+        spirec.spirec_sync(p.h)
+        s_d = torch.from_numpy(synth.add_noise(y.cpu().numpy().astype(np.complex128), 30.0, g)
+                               .astype(np.complex64)).cuda()
+        spirec.spirec_set_reg(p.h, 0.05, 0.05, 0.0, 0.05, 0)
+        x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+        items.append((p, st, kx_d, ky_d, s_d, x))
+
+    def once():
+        for p, st, kx_d, ky_d, s_d, x in items:
+            spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
+            spirec.spirec_set_data_dev(p.h, s_d)
+        spirec.spirec_batch_solve([it[0].h for it in items], [it[5] for it in items], iters)
+
+    once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    once()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    sizes = sorted({it[0].N for it in items})
+    for it in items:
+        it[0].close()
+    return {"frames": frames, "sizes": sizes, "iters": iters, "seconds": dt,
+            "frames_per_s": frames / dt, "iters_per_s": frames * iters / dt,
+            "what": "per frame: trajectory (G, spectrum), data (D), 50 CG iterations; one stream per frame"}
+
+
+def run_serving(spirec, prec, requests=200, rate=200.0, iters=50, seed=5, slots=8):
+    """Poisson request stream: sizes N in {64..384} step 64, L uniform in
+    [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
+    lambda1 U[0.01, 0.2], Huber alpha 0.05, 50 iterations; p50/p99 latency
+    from submission to result, and requests/s over the whole stream."""
+    from paper_0908_3252_gb300 import synth
+    g = synth.rng(seed)
+    reqs = []
+    for _ in range(requests):
+        N = int(g.choice(np.arange(64, 385, 64)))
+        L = int(g.integers(8000, 200001))
+        I = (L + 2047) // 2048
+        kx, ky = synth.spiral(N, I, 2048)
+        kx, ky = kx[:L].copy(), ky[:L].copy()
+        s = synth.complex_normal(L, g).astype(np.complex64)
+        reqs.append((N, kx, ky, s, float(g.uniform(0.01, 0.2))))
+    gaps = g.exponential(1.0 / rate, requests)
+    srv = spirec.spirec_server_create(64 << 30, slots, prec)
+    try:
+        t0 = time.perf_counter()
+        next_t = t0
+        tickets = []
+        for (N, kx, ky, s, lam), gap in zip(reqs, gaps):
+            next_t += gap
+            delay = next_t - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((spirec.spirec_server_submit(srv, N, kx, ky, s, lam, 0.05, 0.0, 0.05, 0, iters), N))
+        for t, N in tickets:
+            spirec.spirec_server_wait(srv, t, N, timeout_ms=600000)
+        dt = time.perf_counter() - t0
+        st = spirec.spirec_server_stats(srv)
+    finally:
+        spirec.spirec_server_destroy(srv)
+    return {"requests": requests, "arrival_rate_per_s": rate, "slots": slots, "p50_ms": st["p50_s"] * 1e3,
+            "p99_ms": st["p99_s"] * 1e3, "requests_per_s": requests / dt, "failed": st["failed"]}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -340,6 +430,14 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    # ---- many reconstructions: batched dynamic series and a served stream
+    if not args.no_batch:
+        extra["batch"] = run_batch(spirec, prec)
+    if not args.no_serving:
+        extra["serving"] = run_serving(spirec, prec)
+        if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
+            extra["serving_fp32_plain"] = run_serving(spirec, spirec.SPIREC_FP32)
+
     # ---- roofline of the dominant stage
     pk = peaks()
     dom = max(stages, key=lambda k: stages[k][0])
@@ -414,6 +512,8 @@ def main():
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame dynamic-series batch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
     ap.add_argument("--samples", type=int, default=4096,
                     help="samples per interleave (4096 = the metric's 131072-sample spiral)")
     ap.add_argument("--iters", type=int, default=50, help="CG iterations per step (50 = the metric's)")

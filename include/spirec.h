@@ -110,7 +110,11 @@ int spirec_plan_destroy(spirec_plan plan);
  *   and the real spectrum of the M x M circulant that holds conj(G).
  * Each k is reduced exactly: it is stored as a 64-bit fixed-point fraction of a
  * cycle, so k * index mod 1 is exact before the trig call.
- * SPIREC_EINVAL if any |k| > 0.5 or a value is not finite.  Invalidates D. */
+ * SPIREC_EINVAL if any |k| > 0.5 or a value is not finite.  Invalidates D.
+ * The host variant waits for the build and reports a bad trajectory at once;
+ * the _dev variant does not block and reports it (SPIREC_EINVAL, or
+ * SPIREC_ETIMEOUT for a tensor-core pipeline timeout) at the plan's next host
+ * synchronisation: spirec_sync or spirec_solve. */
 int spirec_set_trajectory(spirec_plan plan, const double* kx, const double* ky);
 int spirec_set_trajectory_dev(spirec_plan plan, const double* kx, const double* ky);
 
@@ -185,7 +189,8 @@ int spirec_objective_grad_dev(spirec_plan plan, const float* x, double* J_host, 
 int spirec_toeplitz_noalloc(const float* x, const float* spectrum, float* Tx, int32_t N, int32_t M,
                             void* stream);
 
-/* Wait for all work of the plan. */
+/* Wait for all work of the plan and report device-side errors raised since
+ * the last trajectory upload (bad trajectory values, pipeline timeouts). */
 int spirec_sync(spirec_plan plan);
 
 /* Plan facts: any pointer may be NULL. */
@@ -200,6 +205,58 @@ int spirec_plan_info(spirec_plan plan, int32_t* N, int64_t* L, int32_t* M, int32
 #define SPIREC_NUM_STAGES 4
 int spirec_timing(spirec_plan plan, int32_t enable);
 int spirec_timing_read(spirec_plan plan, double* out_ms, int64_t* out_count);
+
+/* ---- many reconstructions on one GPU ---- */
+
+/* Solve n plans at once: each plan's solve is enqueued on its own stream (so
+ * their kernels overlap on the device), then all are awaited.  x0 (array of
+ * n DEVICE pointers, or NULL for zeros), x_out (n DEVICE pointers), J_hist
+ * (n DEVICE pointers or NULL).  Trajectories and data are set per plan
+ * beforehand (the _dev setters do not block).  Returns the first error. */
+int spirec_batch_solve(const spirec_plan* plans, int32_t n, const float* const* x0, int32_t iters,
+                       float* const* x_out, double* const* J_hist);
+
+/* One reconstruction request; every pointer is HOST memory and is copied at
+ * submission. */
+typedef struct {
+    int32_t N;           /* image side */
+    int64_t L;           /* samples */
+    const double* kx;    /* L values in [-0.5, 0.5] */
+    const double* ky;
+    const float* s;      /* 2L floats, interleaved complex */
+    double lambda1, alpha1, lambda0, alpha0;
+    int32_t phi;         /* spirec_phi */
+    int32_t iters;       /* CG iterations */
+} spirec_request;
+
+typedef struct spirec_server_s* spirec_server;
+
+/* A request loop with continuous batching: max_slots worker threads, each
+ * with its own stream and resident plan (reused while requests keep the same
+ * N and L).  A queued request is admitted, first come first served, when a
+ * slot is idle and its device footprint fits hbm_budget_bytes next to the
+ * plans already resident; admitted requests run concurrently and their
+ * kernels overlap.  Each result equals the result of the same request run
+ * alone (launch shapes and summation orders depend only on its own sizes).
+ * precision: spirec_precision of every plan. */
+int spirec_server_create(spirec_server* out, size_t hbm_budget_bytes, int32_t max_slots, int32_t precision);
+/* Queue a request; *ticket identifies it.  SPIREC_EBUSY if the request alone
+ * exceeds the budget, SPIREC_EINVAL for bad fields (checked again on the GPU
+ * path, e.g. |k| > 0.5, and then reported by spirec_server_wait). */
+int spirec_server_submit(spirec_server srv, const spirec_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms for a request: x_out (2N^2 floats, host, may be
+ * NULL), J (final criterion) and latency_s (submission to completion).
+ * SPIREC_ETIMEOUT if not finished in time (the request stays queued and can
+ * be waited for again); the request's own error status otherwise.  A ticket
+ * can be collected once. */
+int spirec_server_wait(spirec_server srv, uint64_t ticket, int32_t timeout_ms, float* x_out, double* J,
+                       double* latency_s);
+/* Latency percentiles (seconds) of the completed requests and the counts of
+ * completed, failed and still queued requests; any pointer may be NULL. */
+int spirec_server_stats(spirec_server srv, double* p50_s, double* p99_s, int64_t* completed, int64_t* failed,
+                        int64_t* queued);
+/* Finish the running requests, drop the queued ones, release everything. */
+int spirec_server_destroy(spirec_server srv);
 
 /* Copy the plan's FP64 device scalars to the host (diagnostics; syncs the
  * plan).  out receives min(n, SPIREC_NUM_SCALARS) values in this order:

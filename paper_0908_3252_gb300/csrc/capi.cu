@@ -202,7 +202,11 @@ int flags_status(int flags)
     return SPIREC_OK;
 }
 
-int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev)
+// Fixed-point trajectory, G and the kernel spectrum.  With check_now the host
+// waits and reports a bad trajectory at once; otherwise (the _dev entry
+// point, which must not block) the device error word is reported at the next
+// host synchronisation of the plan (spirec_solve, spirec_sync).
+int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, bool check_now)
 {
     p->have_traj = false;
     p->have_data = false;
@@ -220,10 +224,15 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev)
     if ((rc = tstart(p, 1, &e)) != SPIREC_OK) return rc;
     if ((rc = launch_spectrum(p)) != SPIREC_OK) return rc;
     if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
-    int flags = 0;
-    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
-    if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
     p->have_traj = true;
+    if (check_now) {
+        int flags = 0;
+        if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+        if ((rc = flags_status(flags)) != SPIREC_OK) {
+            p->have_traj = false;
+            return rc;
+        }
+    }
     return SPIREC_OK;
 }
 
@@ -499,7 +508,7 @@ int spirec_set_trajectory(spirec_plan p, const double* kx, const double* ky)
     Join j(p);
     SPIREC_CK(cudaMemcpyAsync(p->kstage, kx, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
     SPIREC_CK(cudaMemcpyAsync(p->kstage + p->L, ky, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
-    return build_trajectory(p, p->kstage, p->kstage + p->L);
+    return build_trajectory(p, p->kstage, p->kstage + p->L, true);
 }
 
 int spirec_set_trajectory_dev(spirec_plan p, const double* kx, const double* ky)
@@ -511,7 +520,7 @@ int spirec_set_trajectory_dev(spirec_plan p, const double* kx, const double* ky)
         return SPIREC_EINVAL;
     }
     Join j(p);
-    return build_trajectory(p, kx, ky);
+    return build_trajectory(p, kx, ky, false);
 }
 
 int spirec_set_data(spirec_plan p, const float* s)
@@ -759,8 +768,9 @@ int spirec_sync(spirec_plan p)
 {
     int rc = check_plan(p);
     if (rc) return rc;
-    SPIREC_CK(cudaStreamSynchronize(p->stream));
-    return SPIREC_OK;
+    int flags = 0;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    return flags_status(flags);
 }
 
 int spirec_plan_info(spirec_plan p, int32_t* N, int64_t* L, int32_t* M, int32_t* precision,

@@ -301,8 +301,12 @@ struct LaunchLoop {
                 set_error("loop kernel does not fit on an SM");
                 return SPIREC_EUNSUPPORTED;
             }
-            int grid = sms * per_sm;
+            // about two pixels per thread: the whole GPU at 512^2, a fraction of
+            // it for small images, so loops of concurrent solves can co-reside
+            int grid = (int)(((int64_t)p->N * p->N + 2 * kLoopThreads - 1) / (2 * kLoopThreads));
+            if (grid > sms * per_sm) grid = sms * per_sm;
             if (grid > kMaxParts) grid = kMaxParts;
+            if (grid < 1) grid = 1;
             LoopArgs A{};
             A.N = p->N;
             A.iters = iters;

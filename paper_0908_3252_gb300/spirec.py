@@ -69,6 +69,12 @@ SIGNATURES = {
     "spirec_plan_scalars": (ctypes.c_int, [_P, _P, _I32]),
     "spirec_timing": (ctypes.c_int, [_P, _I32]),
     "spirec_timing_read": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_batch_solve": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
+    "spirec_server_create": (ctypes.c_int, [_P, ctypes.c_size_t, _I32, _I32]),
+    "spirec_server_submit": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _I32, _P, _P, _P]),
+    "spirec_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "spirec_server_destroy": (ctypes.c_int, [_P]),
     "spirec_last_error": (ctypes.c_char_p, []),
     "spirec_version": (ctypes.c_char_p, []),
 }
@@ -253,6 +259,59 @@ def spirec_timing_read(plan):
     cnt = (ctypes.c_int64 * SPIREC_NUM_STAGES)()
     _check(load().spirec_timing_read(plan, ms, cnt))
     return {STAGES[i]: (ms[i], cnt[i]) for i in range(SPIREC_NUM_STAGES)}
+
+
+class SpirecRequest(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("L", ctypes.c_int64), ("kx", ctypes.c_void_p), ("ky", ctypes.c_void_p),
+                ("s", ctypes.c_void_p), ("lambda1", ctypes.c_double), ("alpha1", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("alpha0", ctypes.c_double), ("phi", ctypes.c_int32),
+                ("iters", ctypes.c_int32)]
+
+
+def spirec_batch_solve(plans, x_out, iters, x0=None, J_hist=None):
+    """plans: list of handles; x_out/x0/J_hist: lists of CUDA tensors."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    X = (ctypes.c_void_p * n)(*[t.data_ptr() for t in x_out])
+    X0 = (ctypes.c_void_p * n)(*[t.data_ptr() for t in x0]) if x0 is not None else None
+    JH = (ctypes.c_void_p * n)(*[t.data_ptr() for t in J_hist]) if J_hist is not None else None
+    return _check(load().spirec_batch_solve(P, n, X0, int(iters), X, JH))
+
+
+def spirec_server_create(hbm_budget_bytes, max_slots, precision):
+    srv = ctypes.c_void_p()
+    _check(load().spirec_server_create(ctypes.byref(srv), int(hbm_budget_bytes), int(max_slots), int(precision)))
+    return srv
+
+
+def spirec_server_submit(srv, N, kx, ky, s, lambda1, alpha1, lambda0, alpha0, phi, iters):
+    kx, ky, s = _f64(kx), _f64(ky), _c64(s)
+    req = SpirecRequest(int(N), kx.shape[0], kx.ctypes.data, ky.ctypes.data, s.ctypes.data, float(lambda1),
+                        float(alpha1), float(lambda0), float(alpha0), int(phi), int(iters))
+    t = ctypes.c_uint64()
+    _check(load().spirec_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def spirec_server_wait(srv, ticket, N, timeout_ms=60000):
+    """Returns (x (N,N) complex64, J, latency_s)."""
+    x = np.zeros((N, N), np.complex64)
+    J, lat = ctypes.c_double(), ctypes.c_double()
+    _check(load().spirec_server_wait(srv, ctypes.c_uint64(ticket), int(timeout_ms), _host_ptr(x),
+                                     ctypes.byref(J), ctypes.byref(lat)))
+    return x, J.value, lat.value
+
+
+def spirec_server_stats(srv):
+    p50, p99 = ctypes.c_double(), ctypes.c_double()
+    c, f, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().spirec_server_stats(srv, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(c),
+                                      ctypes.byref(f), ctypes.byref(q)))
+    return dict(p50_s=p50.value, p99_s=p99.value, completed=c.value, failed=f.value, queued=q.value)
+
+
+def spirec_server_destroy(srv):
+    return _check(load().spirec_server_destroy(srv))
 
 
 # ---- small convenience owner used by the tests and the benchmark
