@@ -261,9 +261,10 @@ int spirec_server_destroy(spirec_server srv);
 /* Copy the plan's FP64 device scalars to the host (diagnostics; syncs the
  * plan).  out receives min(n, SPIREC_NUM_SCALARS) values in this order:
  * 0 ||s||^2, 1 q1, 2 q2, 3-5 line-search steps t1..t3, 6 <g,g>, 7 beta,
- * 8 J, 9 R, 16-27 nanoseconds block 0 of the persistent CG loop spent in each
- * phase of its last solve (work, then barrier + reduction, for the six
- * phases). */
+ * 8 J, 9 R, 16-25 nanoseconds block 0 of the persistent CG loop spent in the
+ * iterations of its last solve, per phase: work, then barrier + reduction,
+ * for the column pass, the row pass, the two further line-search steps and
+ * the update, in that order. */
 #define SPIREC_NUM_SCALARS 32
 int spirec_plan_scalars(spirec_plan plan, double* out, int32_t n);
 

@@ -119,7 +119,7 @@ int dalloc(spirec_plan p, T** ptr, size_t count)
 void free_plan(spirec_plan p)
 {
     if (!p) return;
-    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s,
+    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage};
     for (void* b : bufs)
@@ -332,10 +332,15 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
+    rc = SPIREC_EUNSUPPORTED;
     if (loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
         // first gradient and every iteration in one persistent kernel
-        if ((rc = launch_cg_loop(p, iters)) != SPIREC_OK) return rc;
-    } else {
+        rc = launch_cg_loop(p, iters);
+        if (rc != SPIREC_OK && rc != SPIREC_EUNSUPPORTED) return rc;
+        p->result_slot = 0;
+    }
+    if (rc == SPIREC_EUNSUPPORTED) {
+        p->result_slot = iters & 1;
         // gradient at x0, J(x0), beta = 0 (the first direction is -g)
         if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->Tf, nullptr, p->g, 1, p->Jdev)) !=
             SPIREC_OK)
@@ -428,6 +433,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->Chat, (size_t)M * M));
     TRY(dalloc(p, &p->cwork, (size_t)M * M));
     TRY(dalloc(p, &p->X, (size_t)N * M));
+    if (loop_supported(M)) TRY(dalloc(p, &p->Xd, (size_t)N * M));
     TRY(dalloc(p, &p->D, NN));
     TRY(dalloc(p, &p->s, (size_t)L + 32));
     TRY(dalloc(p, &p->ystage, (size_t)L + 32));
@@ -602,7 +608,7 @@ int spirec_solve(spirec_plan p, const float* x0, int32_t iters, float* x_out, do
     Join j(p);
     if ((rc = solve_core(p, x0, false, iters)) != SPIREC_OK) return rc;
     const size_t img = (size_t)p->N * p->N * sizeof(float2);
-    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[iters & 1], img, cudaMemcpyDeviceToHost, p->stream));
+    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[p->result_slot], img, cudaMemcpyDeviceToHost, p->stream));
     double Jlast = 0.0;
     SPIREC_CK(cudaMemcpyAsync(&Jlast, p->Jdev + iters, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     if (J_hist)
@@ -630,7 +636,7 @@ int spirec_solve_dev(spirec_plan p, const float* x0, int32_t iters, float* x_out
     Join j(p);
     if ((rc = solve_core(p, x0, true, iters)) != SPIREC_OK) return rc;
     const size_t img = (size_t)p->N * p->N * sizeof(float2);
-    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[iters & 1], img, cudaMemcpyDeviceToDevice, p->stream));
+    SPIREC_CK(cudaMemcpyAsync(x_out, p->f[p->result_slot], img, cudaMemcpyDeviceToDevice, p->stream));
     if (J_hist)
         SPIREC_CK(cudaMemcpyAsync(J_hist, p->Jdev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToDevice,
                                   p->stream));

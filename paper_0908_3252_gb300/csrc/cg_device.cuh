@@ -16,17 +16,13 @@ __device__ __forceinline__ float2 f2axpy(float t, float2 d, float2 f)
 }
 __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
 
-// Line-search sums at step t for pixel p: its right and down edges (Omega1)
-// and the pixel (Omega0).  num += lambda b(|x|) Re(conj(x) w),
-// den += lambda b(|x|) |w|^2 with x = z + t w.  All loads first.
-__device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const float2* d, const Reg& reg,
-                                         float tf, float& num, float& den)
+// Line-search terms of one pixel from its values: the right and down edges
+// (Omega1, masked by has_r / has_d) and the pixel (Omega0).
+// num += lambda b(|x|) Re(conj(x) w), den += lambda b(|x|) |w|^2 with x = z + t w.
+__device__ __forceinline__ void ls_terms(float2 fp, float2 dp, float2 fr, float2 dr, float2 fd, float2 dd,
+                                         bool has_r, bool has_d, const Reg& reg, float tf, float& num,
+                                         float& den)
 {
-    const int n = p / N, m = p - n * N;
-    const bool has_r = m + 1 < N, has_d = n + 1 < N;
-    const int pr = has_r ? p + 1 : p, pd = has_d ? p + N : p;
-    const float2 fp = __ldcg(f + p), dp = __ldcg(d + p), fr = __ldcg(f + pr), dr = __ldcg(d + pr);
-    const float2 fd = __ldcg(f + pd), dd = __ldcg(d + pd);
     if (reg.lambda1 != 0.f) {
         {
             const float2 w = f2sub(dr, dp);
@@ -51,6 +47,19 @@ __device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const fl
     }
 }
 
+// Line-search sums at step t for pixel p of the global iterates (clamped
+// neighbours, masked terms).  All loads first.
+__device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const float2* d, const Reg& reg,
+                                         float tf, float& num, float& den)
+{
+    const int n = p / N, m = p - n * N;
+    const bool has_r = m + 1 < N, has_d = n + 1 < N;
+    const int pr = has_r ? p + 1 : p, pd = has_d ? p + N : p;
+    const float2 fp = __ldcg(f + p), dp = __ldcg(d + p), fr = __ldcg(f + pr), dr = __ldcg(d + pr);
+    const float2 fd = __ldcg(f + pd), dd = __ldcg(d + pd);
+    ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, tf, num, den);
+}
+
 // t_{j+1} from t_j and the grid sums (majorize-minimize step; t stays when
 // the curvature is not positive).
 __device__ __forceinline__ double ls_next(double t, double q1, double q2, double num, double den)
@@ -60,11 +69,43 @@ __device__ __forceinline__ double ls_next(double t, double q1, double q2, double
     return c > 0.0 ? t - h1 / c : t;
 }
 
+// Gradient at a pixel from its values: g = 2 (Tf - D) + grad R(f), and its
+// share rv of R (right and down edges, the pixel).  An edge from p to q with
+// z = f_q - f_p adds +psi(z) at q and -psi(z) at p, psi(z) = b(|z|) z.
+// Masked neighbours carry the centre value (z = 0).
+__device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float2 fdn, float2 fr, float2 tf,
+                                          float2 dv, bool has_u, bool has_l, bool has_d, bool has_r,
+                                          const Reg& reg, float& rv)
+{
+    float2 gp = make_float2(2.f * (tf.x - dv.x), 2.f * (tf.y - dv.y));
+    rv = 0.f;
+    if (reg.lambda1 != 0.f) {
+        const float l1 = reg.lambda1;
+        const float2 zu = f2sub(fc, fu), zl = f2sub(fc, fl), zd = f2sub(fdn, fc), zr = f2sub(fr, fc);
+        const float ru = redot(zu, zu), rl = redot(zl, zl), rd = redot(zd, zd), rr = redot(zr, zr);
+        const float bu = has_u ? l1 * phi_weight(reg.kind, reg.alpha1, ru) : 0.f;
+        const float bl = has_l ? l1 * phi_weight(reg.kind, reg.alpha1, rl) : 0.f;
+        const float bd = has_d ? l1 * phi_weight(reg.kind, reg.alpha1, rd) : 0.f;
+        const float br = has_r ? l1 * phi_weight(reg.kind, reg.alpha1, rr) : 0.f;
+        gp = f2axpy(bu, zu, gp);
+        gp = f2axpy(bl, zl, gp);
+        gp = f2axpy(-bd, zd, gp);
+        gp = f2axpy(-br, zr, gp);
+        rv = (has_d ? l1 * phi_value(reg.kind, reg.alpha1, rd) : 0.f) +
+             (has_r ? l1 * phi_value(reg.kind, reg.alpha1, rr) : 0.f);
+    }
+    if (reg.lambda0 != 0.f) {
+        const float r2 = redot(fc, fc);
+        gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fc, gp);
+        rv = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), rv);
+    }
+    return gp;
+}
+
 // Gradient and step at pixel p.  Unless FIRST: f_out = f_in + t d,
 // Tf += t Td.  g = 2 (Tf - D) + grad R(f); per-thread sums
 //   a[0] <g,g>, a[1] Re<g, g_old>, a[2] Re<g, d>, a[3] R(f), a[4] Re<f, D>, a[5] Re<f, Tf>.
-// An edge from p to q with z = f_q - f_p adds +psi(z) at q and -psi(z) at p,
-// psi(z) = b(|z|) z.  All loads first (clamped neighbours, masked terms).
+// All loads first (clamped neighbours, masked terms).
 template <bool FIRST>
 __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, float2* f_out,
                                              const float2* d, float2* Tf, const float2* Td,
@@ -94,28 +135,8 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
         Tf[p] = tf;
         f_out[p] = fc;
     }
-    float2 gp = make_float2(2.f * (tf.x - dv.x), 2.f * (tf.y - dv.y));
-    float rv = 0.f;
-    if (reg.lambda1 != 0.f) {
-        const float l1 = reg.lambda1;
-        const float2 zu = f2sub(fc, fu), zl = f2sub(fc, fl), zd = f2sub(fdn, fc), zr = f2sub(fr, fc);
-        const float ru = redot(zu, zu), rl = redot(zl, zl), rd = redot(zd, zd), rr = redot(zr, zr);
-        const float bu = has_u ? l1 * phi_weight(reg.kind, reg.alpha1, ru) : 0.f;
-        const float bl = has_l ? l1 * phi_weight(reg.kind, reg.alpha1, rl) : 0.f;
-        const float bd = has_d ? l1 * phi_weight(reg.kind, reg.alpha1, rd) : 0.f;
-        const float br = has_r ? l1 * phi_weight(reg.kind, reg.alpha1, rr) : 0.f;
-        gp = f2axpy(bu, zu, gp);
-        gp = f2axpy(bl, zl, gp);
-        gp = f2axpy(-bd, zd, gp);
-        gp = f2axpy(-br, zr, gp);
-        rv = (has_d ? l1 * phi_value(reg.kind, reg.alpha1, rd) : 0.f) +
-             (has_r ? l1 * phi_value(reg.kind, reg.alpha1, rr) : 0.f);
-    }
-    if (reg.lambda0 != 0.f) {
-        const float r2 = redot(fc, fc);
-        gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fc, gp);
-        rv = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), rv);
-    }
+    float rv;
+    const float2 gp = grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
     a[0] += redot(gp, gp);
     if (!FIRST) {
         a[1] += redot(gp, gold);
@@ -130,7 +151,7 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
 // Scalars after an update: J = ||s||^2 - 2 Re<f,D> + Re<f,Tf> + R and the
 // Polak-Ribiere beta = max(0, (<g,g> - Re<g,g_old>) / <g_old,g_old>), set to
 // 0 when Re<g, -g + beta d> >= 0 (restart) or on the first gradient.
-__device__ __forceinline__ void update_finish(const double (&s)[kUpdVals], double ss, double gg_old,
+__device__ __forceinline__ void update_finish(const double* s, double ss, double gg_old,
                                               bool first, double* J, double* beta)
 {
     *J = ss - 2.0 * s[4] + s[5] + s[3];

@@ -1,18 +1,34 @@
 // cg_loop.cu -- the whole Polak-Ribiere loop (section 3.3 on the rewritten
 // criterion of section 3.4) as ONE persistent cooperative kernel.
 //
-// Two 512-thread blocks per SM, resident for the whole solve.  Each iteration
-// runs the six phases of the stand-alone path (fft.cu, cg.cu), separated by
-// grid barriers instead of kernel boundaries:
-//   P1 rows:    d = -g + beta d_old, q1, line-search sums at t = 0, row FFTs
-//   P2 columns: FFT * Chat * IFFT
-//   P3 rows:    row IFFTs -> T d, q2            -> t1
-//   P4, P5:     line-search steps at t1, t2     -> t2, t3
-//   P6:         f += t3 d, T f += t3 T d, g, J  -> beta
-// After each reducing phase every block sums the per-block partials itself
-// (same order in every block), so all blocks hold the same FP64 scalars and
-// no extra barrier is needed to broadcast them.  Partials of consecutive
-// phases use different slots, so a fast block never overwrites a partial a
+// Block b owns the image rows [R0, R0 + RB) for the whole solve and keeps in
+// shared memory f and d of those rows plus one halo row on each side, and
+// T f, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
+// halo row of g per side pass through global memory (L2):
+//   X   the row FFTs of g, overwritten by the column-filtered rows Y,
+//   Xd  the row FFTs of the current direction d (kept across iterations).
+//
+// One iteration, five grid synchronisations:
+//   B  columns  Xd = -X + beta Xd (the row FFTs of d = -g + beta d_old, by
+//               linearity of the DFT); column FFT * Chat * IFFT -> Y in X
+//               [barrier]
+//   C  rows     row IFFTs of Y -> T d; d = -g + beta d_old on the cached
+//               rows; sums q1 = Re<d, 2(Tf - D)>, q2 = Re<d, T d> and the
+//               penalty terms of h'(0) and of the curvature at t = 0
+//               [reduce 4 -> t1]
+//   D, E        majorize-minimize steps of the line search at t1, t2, from
+//               shared memory            [reduce 2 -> t2]  [reduce 2 -> t3]
+//   A  update   f += t3 d, T f += t3 T d, g = 2 (T f - D) + grad R(f), the six
+//               sums of J and beta; row FFTs of g -> X
+//               [reduce 6 -> J, beta]
+// An initial update without a step gives g(x0), J(x0) and beta = 0.  Every
+// halo value is recomputed by the block that caches it from the same
+// operands as its owner uses, so all copies of a pixel are bitwise equal.
+//
+// After each reduction thread 0 combines the per-block float-float partials
+// (same order in every block) and derives the FP64 scalars; the other
+// threads read FP32 copies from shared memory.  Consecutive reductions use
+// different partial slots, so a fast block never overwrites a partial that a
 // slow block is still reading.
 //
 // The grid barrier is an arrival counter plus a generation word in global
@@ -33,16 +49,17 @@ namespace {
 
 constexpr int kLoopThreads = 512;
 constexpr unsigned long long kBarrierNs = 2000000000ull;  // 2 s
+constexpr int kMaxGroupsPerBlock = 8;
+constexpr int kProf = 10;
 
 struct LoopArgs {
-    int N, iters;
-    float2* f[2];
-    float2* dbuf[2];
-    float2* g;
-    float2* Tf;
-    float2* Td;
+    int N, iters, RB;  // RB: rows owned per block
+    float2* f0;        // x0 in, the last iterate out
+    float2* g;         // gradient rows (halo exchange)
+    float2* Tf;        // T x0 in, T f out
     const float2* D;
     float2* X;
+    float2* Xd;
     const float* Chat;
     const float2* tw;
     FftPlan fp;
@@ -53,6 +70,34 @@ struct LoopArgs {
     unsigned* bar;  // [0] arrivals, [1] generation, [2] abort
     int* err;
 };
+
+// Loop scalars, one copy per block.  Thread 0 writes them between two
+// __syncthreads(); the FP64 values are used by thread 0 only.
+struct LoopShared {
+    double red[8];  // grid sums of the last reduction
+    double ss, gg, J, beta, q1, q2, t;
+    float beta_f, t_f;
+    int restart, ok;
+    unsigned gen;
+    unsigned long long prof[kProf], tmark;
+};
+
+template <int MC>
+struct Geo {
+    static constexpr int RPC = 4 * kLoopThreads / MC;  // rows per FFT group: RPC * MC = 4 * threads
+    static constexpr int CBPT = MC >= 256 ? 2 : 1;     // column groups: CBPT butterflies per thread
+    static constexpr int CPC = CBPT * RPC;
+    static constexpr int LDR = fftd::seq_len<MC>(MC);
+    static constexpr int LDC = LDR + 4;
+    static constexpr int FBUF = RPC * LDR > CPC * LDC ? RPC * LDR : CPC * LDC;
+};
+
+// dynamic shared memory of a block owning RB rows of an N-wide image
+template <int MC>
+size_t loop_smem(int N, int RB)
+{
+    return ((size_t)Geo<MC>::FBUF + (size_t)(2 * (RB + 2) + 4 * RB) * N) * sizeof(float2);
+}
 
 __device__ __forceinline__ uint64_t gtimer()
 {
@@ -65,13 +110,12 @@ __device__ __forceinline__ uint64_t gtimer()
 // a timeout.  Arrival is a release add, the wait an acquire load, so the
 // block's writes (ordered before thread 0 by the __syncthreads) are visible
 // to every block that passes, without separate full fences.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* err)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, LoopShared& S, int* err)
 {
-    __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned g = gen;
+        S.ok = 1;
+        const unsigned g = S.gen;
         unsigned old;
         asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
         if (old == gridDim.x - 1) {
@@ -85,197 +129,395 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* 
                 if (cur != g) break;
                 asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(ab) : "l"(bar + 2) : "memory");
                 if (ab) {
-                    ok = 0;
+                    S.ok = 0;
                     break;
                 }
                 if (gtimer() - t0 > kBarrierNs) {
                     atomicExch(&bar[2], 1u);
                     atomicOr(err, E_TIMEOUT);
-                    ok = 0;
+                    S.ok = 0;
                     break;
                 }
                 __nanosleep(20);
             }
         }
-        gen = g + 1;
+        S.gen = g + 1;
     }
     __syncthreads();
-    return ok != 0;
+    return S.ok != 0;
 }
 
 // Block partials of K values to parts slot `slot`, barrier, then the grid
-// totals (index order, float-float) in every thread as FP64.
+// totals (index order, float-float) as FP64 in S.red, readable by every
+// thread on return.
 template <int K>
 __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned* bar,
-                                            unsigned& gen, int* err, double (&out)[K])
+                                            LoopShared& S, int* err)
 {
-    __shared__ double bc[K];
     FF bt[K];
     block_partial<K>(v, bt);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < K; ++k)
             parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-    if (!grid_barrier(bar, gen, err)) return false;
+    if (!grid_barrier(bar, S, err)) return false;
     // warp k sums value k over the blocks
     const int warp = threadIdx.x >> 5;
     if (warp < K) {
         const FF a = warp_sum_parts(parts + (slot + warp) * kMaxParts, gridDim.x);
-        if ((threadIdx.x & 31) == 0) bc[warp] = ff_to_double(a);
+        if ((threadIdx.x & 31) == 0) S.red[warp] = ff_to_double(a);
     }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = bc[k];
     __syncthreads();
     return true;
 }
 
-// partial slots of the loop (distinct per consecutive phase)
-constexpr int L_P1 = 0;   // 3
-constexpr int L_P3 = 3;   // 1
-constexpr int L_P4 = 4;   // 2
-constexpr int L_P5 = 6;   // 2
-constexpr int L_P6 = 8;   // 6
+// partial slots (distinct for consecutive reductions)
+constexpr int L_A = 0;   // 6
+constexpr int L_C = 6;   // 4
+constexpr int L_D = 10;  // 2
+constexpr int L_E = 12;  // 2
+
+// The rows one block works on: own rows [R0, R0 + nown), cached rows
+// [hlo, hhi] (the own rows and the existing halo rows).
+struct Rows {
+    int N, R0, nown, hlo, hhi;
+    __device__ __forceinline__ int cache(int r) const { return (r - R0 + 1) * N; }  // row offset in cf, cd
+    __device__ __forceinline__ bool own(int r) const { return r >= R0 && r < R0 + nown; }
+};
+
+// ---------------------------------------------------------------- phase A
+
+// Step (unless FIRST), gradient and the six update sums over the own rows
+// (the sums of cgd::update_pixel); with do_fft the row FFTs of g go to X.
+template <int MC, bool FIRST>
+__device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, float2* fbuf, float2* cf,
+                                             const float2* cd, float2* cTf, const float2* cD, float2* cg,
+                                             const float2* cTd, float t, bool do_fft, float (&a)[kUpdVals])
+{
+    using G = Geo<MC>;
+    const int N = R.N;
+    const Reg reg = A.reg;
+    if (!FIRST) {
+        const int nc = (R.hhi - R.hlo + 1) * N;
+        float2* fr0 = cf + R.cache(R.hlo);
+        const float2* dr0 = cd + R.cache(R.hlo);
+        for (int e = threadIdx.x; e < nc; e += kLoopThreads) fr0[e] = cgd::f2axpy(t, dr0[e], fr0[e]);
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) cTf[e] = cgd::f2axpy(t, cTd[e], cTf[e]);
+        __syncthreads();
+    }
+    for (int g0 = 0; g0 < R.nown; g0 += G::RPC) {
+        const int nr = min(G::RPC, R.nown - g0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = threadIdx.x + i * kLoopThreads;
+            const int q = e / MC, m = e - q * MC;
+            float2 gp = make_float2(0.f, 0.f);
+            if (q < nr && m < N) {
+                const int oq = g0 + q, n = R.R0 + oq;
+                const int o = oq * N + m;  // index in the own-row caches
+                const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
+                const float2* row = cf + R.cache(n);
+                const float2 fc = row[m];
+                const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
+                const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
+                const float2 tf = cTf[o], dv = cD[o];
+                float rv;
+                gp = cgd::grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+                a[0] += cgd::redot(gp, gp);
+                if (!FIRST) {
+                    a[1] += cgd::redot(gp, cg[o]);
+                    a[2] += cgd::redot(gp, cd[R.cache(n) + m]);
+                }
+                a[3] += rv;
+                a[4] += cgd::redot(fc, dv);
+                a[5] += cgd::redot(fc, tf);
+                cg[o] = gp;
+                A.g[(int64_t)n * N + m] = gp;
+            }
+            if (do_fft) fbuf[q * G::LDR + fftd::sidx<MC>(m)] = gp;
+        }
+        if (do_fft) {
+            __syncthreads();
+            fftd::fft_pow2<MC, false, 1>(fbuf, G::LDR, A.tw);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = threadIdx.x + i * kLoopThreads;
+                const int q = e / MC, m = e - q * MC;
+                if (q < nr) A.X[(int64_t)(R.R0 + g0 + q) * MC + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------- phase C
+
+// Row IFFTs of Y (in X) -> T d of the own rows; the new direction on every
+// cached row; the four sums of the first line-search step.
+template <int MC>
+__device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* cf,
+                                           float2* cd, const float2* cTf, const float2* cD, const float2* cg,
+                                           float2* cTd, float beta, bool restart, float (&acc)[4])
+{
+    using G = Geo<MC>;
+    const int N = R.N;
+    for (int g0 = 0; g0 < R.nown; g0 += G::RPC) {
+        const int nr = min(G::RPC, R.nown - g0);
+        float2 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = threadIdx.x + i * kLoopThreads;
+            const int q = e / MC, m = e - q * MC;
+            v[i] = q < nr ? __ldcg(A.X + (int64_t)(R.R0 + g0 + q) * MC + m) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = threadIdx.x + i * kLoopThreads;
+            const int q = e / MC, m = e - q * MC;
+            fbuf[q * G::LDR + fftd::sidx<MC>(m)] = v[i];
+        }
+        __syncthreads();
+        fftd::fft_pow2<MC, true, 1>(fbuf, G::LDR, A.tw);
+        for (int e = threadIdx.x; e < nr * N; e += kLoopThreads) {
+            const int q = e / N, m = e - q * N;
+            cTd[(g0 + q) * N + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
+        }
+        __syncthreads();
+    }
+    // d = -g + beta d_old on the cached rows (halo g from its owner, via L2)
+    {
+        const int nc = (R.hhi - R.hlo + 1) * N;
+        float2* dr0 = cd + R.cache(R.hlo);
+        for (int e = threadIdx.x; e < nc; e += kLoopThreads) {
+            const int rq = e / N, m = e - rq * N, r = R.hlo + rq;
+            const float2 g = R.own(r) ? cg[(r - R.R0) * N + m] : __ldcg(A.g + (int64_t)r * N + m);
+            dr0[e] = fftd::new_direction(g, dr0[e], beta, restart);
+        }
+    }
+    __syncthreads();
+    const Reg reg = A.reg;
+    for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
+        const int q = e / N, m = e - q * N, n = R.R0 + q;
+        const bool has_r = m + 1 < N, has_d = n + 1 < N;
+        const float2* fr0 = cf + R.cache(n);
+        const float2* dr0 = cd + R.cache(n);
+        const float2 fp = fr0[m], dp = dr0[m];
+        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
+        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
+        acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
+        cgd::ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, 0.f, acc[1], acc[2]);
+        acc[3] += cgd::redot(dp, cTd[e]);
+    }
+}
+
+// ------------------------------------------------------------ phases D, E
+
+__device__ __forceinline__ void phase_ls(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
+                                         float t, float (&acc)[2])
+{
+    const int N = R.N;
+    for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
+        const int q = e / N, m = e - q * N, n = R.R0 + q;
+        const bool has_r = m + 1 < N, has_d = n + 1 < N;
+        const float2* fr0 = cf + R.cache(n);
+        const float2* dr0 = cd + R.cache(n);
+        const float2 fp = fr0[m], dp = dr0[m];
+        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
+        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
+        cgd::ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, t, acc[0], acc[1]);
+    }
+}
+
+// ------------------------------------------------------------------ kernel
 
 template <int MC>
 __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
 {
     static_assert(MC > 0, "the loop kernel needs a compile-time FFT size");
+    using G = Geo<MC>;
     extern __shared__ float2 sm[];
-    constexpr int RPC = 4 * kLoopThreads / MC;  // rows per group: 512 threads = RPC * MC / 4
-    constexpr int CBPT = MC >= 256 ? 2 : 1;      // column groups: CBPT butterflies per thread
-    constexpr int CPC = CBPT * RPC;
-    const int N = A.N, M = MC;
-    const int P = N * N;
-    const int row_groups = (N + RPC - 1) / RPC;
-    const int col_groups = (M + CPC - 1) / CPC;
-    const Reg reg = A.reg;
-    unsigned gen = 0;
-    if (threadIdx.x == 0) gen = *(volatile unsigned*)&A.bar[1];
-    // block 0 keeps, per phase, its work time and its barrier+reduce time
-    const bool prof = blockIdx.x == 0 && threadIdx.x == 0;
-    uint64_t tprof[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    uint64_t tmark = prof ? gtimer() : 0;
+    __shared__ LoopShared S;
+    const int N = A.N, RB = A.RB;
+    Rows R;
+    R.N = N;
+    R.R0 = blockIdx.x * RB;
+    R.nown = min(RB, N - R.R0);
+    R.hlo = R.R0 > 0 ? R.R0 - 1 : R.R0;
+    R.hhi = min(R.R0 + R.nown, N - 1);
+    float2* fbuf = sm;
+    float2* cf = fbuf + G::FBUF;      // rows R0-1 .. R0+RB: f
+    float2* cd = cf + (RB + 2) * N;   // the same rows: d
+    float2* cTf = cd + (RB + 2) * N;  // own rows: T f, D, g, T d
+    float2* cD = cTf + RB * N;
+    float2* cg = cD + RB * N;
+    float2* cTd = cg + RB * N;
+    const int col_groups = MC / G::CPC;
+    const bool prof = blockIdx.x == 0;
+    if (threadIdx.x == 0) {
+        S.gen = *(volatile unsigned*)&A.bar[1];
+        S.ss = A.scal[S_SS];
+        for (int i = 0; i < kProf; ++i) S.prof[i] = 0;
+    }
+    // block 0 keeps, per phase, its work time and its synchronisation time
     auto mark = [&](int i) {
-        if (prof) {
+        if (prof && threadIdx.x == 0) {
             const uint64_t now = gtimer();
-            tprof[i] += now - tmark;
-            tmark = now;
+            S.prof[i] += now - S.tmark;
+            S.tmark = now;
         }
     };
 
-    // ---- gradient at x0, J(x0); the first direction is -g (beta = 0)
-    double ss = A.scal[S_SS];
-    double gg, beta, J;
+    // ---- caches: f of the cached rows, T f and D of the own rows
     {
-        float a[kUpdVals];
-#pragma unroll
-        for (int i = 0; i < kUpdVals; ++i) a[i] = 0.f;
-        for (int p = blockIdx.x * kLoopThreads + threadIdx.x; p < P; p += gridDim.x * kLoopThreads)
-            cgd::update_pixel<true>(p, N, A.f[0], A.f[0], A.dbuf[1], A.Tf, A.Td, A.D, A.g, reg, 0.f, a);
-        double s[kUpdVals];
-        if (!grid_reduce<kUpdVals>(a, A.parts, L_P6, A.bar, gen, A.err, s)) return;
-        cgd::update_finish(s, ss, 0.0, true, &J, &beta);
-        gg = s[0];
-        if (blockIdx.x == 0 && threadIdx.x == 0) A.Jdev[0] = J;
+        const int nc = (R.hhi - R.hlo + 1) * N;
+        const float2* src = A.f0 + (int64_t)R.hlo * N;
+        float2* dst = cf + R.cache(R.hlo);
+        for (int e = threadIdx.x; e < nc; e += kLoopThreads) dst[e] = __ldcg(src + e);
+        const int64_t o = (int64_t)R.R0 * N;
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
+            cTf[e] = __ldcg(A.Tf + o + e);
+            cD[e] = __ldg(A.D + o + e);
+        }
+    }
+    __syncthreads();
+
+    // ---- gradient at x0, J(x0); the first direction is -g (beta = 0)
+    {
+        float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        phase_update<MC, true>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+        if (!grid_reduce<kUpdVals>(a, A.parts, L_A, A.bar, S, A.err)) return;
+        if (threadIdx.x == 0) {
+            double J, beta;
+            cgd::update_finish(S.red, S.ss, 0.0, true, &J, &beta);
+            S.gg = S.red[0];
+            S.J = J;
+            S.beta = 0.0;
+            S.beta_f = 0.f;
+            S.restart = 1;
+            S.tmark = gtimer();
+            if (blockIdx.x == 0) A.Jdev[0] = J;
+        }
+        __syncthreads();
     }
 
     for (int k = 0; k < A.iters; ++k) {
-        const float2* fin = A.f[k & 1];
-        float2* fout = A.f[(k + 1) & 1];
-        float2* dk = A.dbuf[k & 1];
-        // ---- P1
-        CgPass c{};
-        c.g = A.g;
-        c.d_old = A.dbuf[(k + 1) & 1];
-        c.d_new = dk;
-        c.f = fin;
-        c.Tf = A.Tf;
-        c.D = A.D;
-        c.reg = reg;
-        double q1, num0, den0;
-        {
-            float acc[3] = {0.f, 0.f, 0.f};
-            for (int gi = blockIdx.x; gi < row_groups; gi += gridDim.x) {
-                const int r0 = gi * RPC;
-                fftd::rows_fwd_group<MC, 1>(nullptr, N, N, r0, min(RPC, N - r0), RPC, A.X, A.fp, A.tw, c,
-                                            (float)beta, beta == 0.0, sm, nullptr, acc);
-            }
-            mark(0);
-            double s[3];
-            if (!grid_reduce<3>(acc, A.parts, L_P1, A.bar, gen, A.err, s)) return;
-            q1 = s[0];
-            num0 = s[1];
-            den0 = s[2];
-            mark(1);
-        }
-        // ---- P2
+        const float beta = S.beta_f;
+        const bool restart = S.restart != 0;
+        // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
-            const int x0 = gi * CPC;
-            fftd::cols_group<MC, CBPT>(A.X, N, N, x0, min(CPC, M - x0), CPC, A.fp, A.tw, A.Chat, sm, nullptr);
+            const int x0 = gi * G::CPC;
+            fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, G::CPC, G::CPC, A.fp, A.tw, A.Chat, fbuf, nullptr,
+                                            A.Xd, beta, restart);
+            __syncthreads();  // the next group refills fbuf
         }
-        mark(2);
-        if (!grid_barrier(A.bar, gen, A.err)) return;
-        mark(3);
-        // ---- P3
-        double q2, t;
+        mark(0);
+        if (!grid_barrier(A.bar, S, A.err)) return;
+        mark(1);
+        // ---- C: rows, direction, first line-search sums
         {
-            float acc[1] = {0.f};
-            for (int gi = blockIdx.x; gi < row_groups; gi += gridDim.x) {
-                const int r0 = gi * RPC;
-                fftd::rows_inv_group<MC>(A.X, r0, min(RPC, N - r0), RPC, A.Td, N, A.fp, A.tw, dk, sm, nullptr,
-                                         acc[0]);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            phase_rows<MC>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+            mark(2);
+            if (!grid_reduce<4>(acc, A.parts, L_C, A.bar, S, A.err)) return;
+            if (threadIdx.x == 0) {
+                S.q1 = S.red[0];
+                S.q2 = S.red[3];
+                const double curv = 2.0 * S.q2 + S.red[2];
+                S.t = curv > 0.0 ? -(S.q1 + S.red[1]) / curv : 0.0;
+                S.t_f = (float)S.t;
             }
-            mark(4);
-            double s[1];
-            if (!grid_reduce<1>(acc, A.parts, L_P3, A.bar, gen, A.err, s)) return;
-            q2 = s[0];
-            const double curv = 2.0 * q2 + den0;
-            t = curv > 0.0 ? -(q1 + num0) / curv : 0.0;
-            mark(5);
+            __syncthreads();
+            mark(3);
         }
-        // ---- P4, P5: majorize-minimize steps at t1 and t2
+        // ---- D, E: majorize-minimize steps at t1 and t2
 #pragma unroll 1
         for (int j = 0; j < 2; ++j) {
             float acc[2] = {0.f, 0.f};
-            const float tf = (float)t;
-            for (int p = blockIdx.x * kLoopThreads + threadIdx.x; p < P; p += gridDim.x * kLoopThreads)
-                cgd::ls_pixel(p, N, fin, dk, reg, tf, acc[0], acc[1]);
-            mark(6 + 2 * j);
-            double s[2];
-            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_P4 : L_P5, A.bar, gen, A.err, s)) return;
-            t = cgd::ls_next(t, q1, q2, s[0], s[1]);
-            mark(7 + 2 * j);
-        }
-        // ---- P6
-        {
-            float a[kUpdVals];
-#pragma unroll
-            for (int i = 0; i < kUpdVals; ++i) a[i] = 0.f;
-            const float tf = (float)t;
-            for (int p = blockIdx.x * kLoopThreads + threadIdx.x; p < P; p += gridDim.x * kLoopThreads)
-                cgd::update_pixel<false>(p, N, fin, fout, dk, A.Tf, A.Td, A.D, A.g, reg, tf, a);
-            mark(10);
-            double s[kUpdVals];
-            if (!grid_reduce<kUpdVals>(a, A.parts, L_P6, A.bar, gen, A.err, s)) return;
-            cgd::update_finish(s, ss, gg, false, &J, &beta);
-            gg = s[0];
-            mark(11);
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                A.Jdev[k + 1] = J;
-                A.scal[S_Q1] = q1;
-                A.scal[S_Q2] = q2;
-                A.scal[S_T3] = t;
+            phase_ls(A.reg, R, cf, cd, S.t_f, acc);
+            mark(4 + 2 * j);
+            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, A.bar, S, A.err)) return;
+            if (threadIdx.x == 0) {
+                S.t = cgd::ls_next(S.t, S.q1, S.q2, S.red[0], S.red[1]);
+                S.t_f = (float)S.t;
             }
+            __syncthreads();
+            mark(5 + 2 * j);
+        }
+        // ---- A: step, gradient, row FFTs of g for the next iteration
+        {
+            float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            phase_update<MC, false>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+            mark(8);
+            if (!grid_reduce<kUpdVals>(a, A.parts, L_A, A.bar, S, A.err)) return;
+            if (threadIdx.x == 0) {
+                double J, beta_n;
+                cgd::update_finish(S.red, S.ss, S.gg, false, &J, &beta_n);
+                S.gg = S.red[0];
+                S.J = J;
+                S.beta = beta_n;
+                S.beta_f = (float)beta_n;
+                S.restart = beta_n == 0.0;
+                if (blockIdx.x == 0) {
+                    A.Jdev[k + 1] = J;
+                    A.scal[S_Q1] = S.q1;
+                    A.scal[S_Q2] = S.q2;
+                    A.scal[S_T3] = S.t;
+                }
+            }
+            __syncthreads();
+            mark(9);
         }
     }
-    if (prof)
-        for (int i = 0; i < 12; ++i) A.scal[S_PROF + i] = (double)tprof[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.scal[S_GG] = gg;
-        A.scal[S_BETA] = beta;
-        A.scal[S_J] = J;
+    // ---- the iterate and T f back to global memory
+    {
+        const int64_t o = (int64_t)R.R0 * N;
+        const float2* fo = cf + R.cache(R.R0);
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
+            A.f0[o + e] = fo[e];
+            A.Tf[o + e] = cTf[e];
+        }
     }
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        for (int i = 0; i < kProf; ++i) A.scal[S_PROF + i] = (double)S.prof[i];
+        A.scal[S_GG] = S.gg;
+        A.scal[S_BETA] = S.beta;
+        A.scal[S_J] = S.J;
+    }
+}
+
+// The block shape for an N-wide image: RB = gpb * RPC rows per block with
+// the fewest groups per block gpb whose grid is co-resident (every block
+// must be resident for the grid barrier).  False when no shape fits.
+template <int MC>
+bool loop_shape(int N, int* RB_out, int* grid_out, size_t* smem_out)
+{
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    auto kern = k_cg_loop<MC>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+    for (int gpb = 1; gpb <= kMaxGroupsPerBlock; ++gpb) {
+        const int RB = gpb * Geo<MC>::RPC;
+        const int grid = (N + RB - 1) / RB;
+        const size_t smem = loop_smem<MC>(N, RB);
+        if (smem + fa.sharedSizeBytes > (size_t)optin) return false;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return false;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem) != cudaSuccess)
+            return false;
+        if (per_sm >= 1 && grid <= sms * per_sm && grid <= kMaxParts) {
+            *RB_out = RB;
+            *grid_out = grid;
+            *smem_out = smem;
+            return true;
+        }
+        if (RB >= N) return false;
+    }
+    return false;
 }
 
 struct LaunchLoop {
@@ -288,37 +530,23 @@ struct LaunchLoop {
             set_error("no compile-time FFT size for M=%d", p->M);
             return SPIREC_EUNSUPPORTED;
         } else {
-            constexpr int RPC = 4 * kLoopThreads / MC;
-            constexpr int CPC = (MC >= 256 ? 2 : 1) * RPC;
-            const size_t smem = (size_t)CPC * (fftd::seq_len<MC>(MC) + 4) * sizeof(float2);
-            auto kern = k_cg_loop<MC>;
-            SPIREC_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            int dev = 0, sms = 0, per_sm = 0;
-            SPIREC_CK(cudaGetDevice(&dev));
-            SPIREC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            SPIREC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem));
-            if (per_sm < 1) {
-                set_error("loop kernel does not fit on an SM");
+            int RB = 0, grid = 0;
+            size_t smem = 0;
+            if (!p->Xd || !loop_shape<MC>(p->N, &RB, &grid, &smem)) {
+                cudaGetLastError();
+                set_error("the persistent loop does not fit N=%d, M=%d", p->N, p->M);
                 return SPIREC_EUNSUPPORTED;
             }
-            // about two pixels per thread: the whole GPU at 512^2, a fraction of
-            // it for small images, so loops of concurrent solves can co-reside
-            int grid = (int)(((int64_t)p->N * p->N + 2 * kLoopThreads - 1) / (2 * kLoopThreads));
-            if (grid > sms * per_sm) grid = sms * per_sm;
-            if (grid > kMaxParts) grid = kMaxParts;
-            if (grid < 1) grid = 1;
             LoopArgs A{};
             A.N = p->N;
             A.iters = iters;
-            A.f[0] = p->f[0];
-            A.f[1] = p->f[1];
-            A.dbuf[0] = p->dbuf[0];
-            A.dbuf[1] = p->dbuf[1];
+            A.RB = RB;
+            A.f0 = p->f[0];
             A.g = p->g;
             A.Tf = p->Tf;
-            A.Td = p->Td;
             A.D = p->D;
             A.X = p->X;
+            A.Xd = p->Xd;
             A.Chat = p->Chat;
             A.tw = p->twiddle;
             A.fp = p->fft;
@@ -332,8 +560,8 @@ struct LaunchLoop {
             SPIREC_CK(cudaMemsetAsync(A.bar, 0, sizeof(unsigned), p->stream));
             SPIREC_CK(cudaMemsetAsync(A.bar + 2, 0, sizeof(unsigned), p->stream));
             void* args[] = {&A};
-            SPIREC_CK(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kLoopThreads), args, smem,
-                                                  p->stream));
+            SPIREC_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<MC>, dim3(grid), dim3(kLoopThreads), args,
+                                                  smem, p->stream));
             p->launches += 1;
             return SPIREC_OK;
         }

@@ -118,6 +118,7 @@ struct spirec_plan_s {
     float* Chat;   // M x M real, transposed: Chat[kx*M + ky]
     float2* cwork; // M x M complex (spectrum build)
     float2* X;     // N x M complex (Toeplitz rows)
+    float2* Xd;    // N x M complex: row FFTs of the CG direction (persistent loop only)
     float2* D;     // N x N
     float2* s;     // L (+32 padding)
     float2* ystage;  // L (+32 padding): a caller's y staged for the tensor-core adjoint
@@ -149,6 +150,7 @@ struct spirec_plan_s {
     cudaGraphExec_t graph;
     int graph_iters;
     int graph_parity_out;
+    int result_slot;  // the last solve left its iterate in f[result_slot]
 
     // timing
     bool timing;
@@ -188,7 +190,9 @@ int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2
 int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step);
 int cg_iteration(spirec_plan p, int k, double* Jdev);
 // The whole loop (first gradient + iters iterations) as one persistent
-// cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only.
+// cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only, and
+// SPIREC_EUNSUPPORTED (nothing enqueued) when the image does not fit its
+// shared-memory caches.  The iterate ends in f[0].
 bool loop_supported(int M);
 int launch_cg_loop(spirec_plan p, int iters);
 
