@@ -11,7 +11,7 @@
 // One iteration, five grid synchronisations:
 //   B  columns  Xd = -X + beta Xd (the row FFTs of d = -g + beta d_old, by
 //               linearity of the DFT); column FFT * Chat * IFFT -> Y in X
-//               [barrier]
+//               [synchronisation without a value]
 //   C  rows     row IFFTs of Y -> T d; d = -g + beta d_old on the cached
 //               rows; sums q1 = Re<d, 2(Tf - D)>, q2 = Re<d, T d> and the
 //               penalty terms of h'(0) and of the curvature at t = 0
@@ -25,18 +25,19 @@
 // halo value is recomputed by the block that caches it from the same
 // operands as its owner uses, so all copies of a pixel are bitwise equal.
 //
-// After each reduction thread 0 combines the per-block float-float partials
-// (same order in every block) and derives the FP64 scalars; the other
-// threads read FP32 copies from shared memory.  Consecutive reductions use
-// different partial slots, so a fast block never overwrites a partial that a
-// slow block is still reading.
+// After each reduction one warp per value sums the per-block float-float
+// partials (same order in every block) and thread 0 derives the FP64
+// scalars; the other threads read FP32 copies from shared memory.
 //
-// The grid barrier is an arrival counter plus a generation word in global
-// memory.  Its wait is bounded in time: on expiry the block raises an abort
-// word and an error bit, every block returns at its next barrier, and the
-// host reports SPIREC_ETIMEOUT.  The cooperative launch guarantees that all
-// blocks are resident, so the barrier cannot wait on an unscheduled block.
+// Every grid synchronisation is a reduction over block partials behind an
+// arrival counter (see grid_reduce).  Its wait is bounded in time: on expiry the block raises an
+// abort word and an error bit, every block returns at its next
+// synchronisation, and the host reports SPIREC_ETIMEOUT.  The cooperative
+// launch guarantees that all blocks are resident, so no wait depends on an
+// unscheduled block.
 #include <stdint.h>
+
+#include <mutex>
 
 #include "cg_device.cuh"
 #include "fft_device.cuh"
@@ -66,8 +67,9 @@ struct LoopArgs {
     Reg reg;
     double* scal;
     double* Jdev;
-    float2* parts;
-    unsigned* bar;  // [0] arrivals, [1] generation, [2] abort
+    float2* parts;     // block partials, P_NSLOTS x kMaxParts
+    unsigned* counter;  // arrivals, zero at the launch
+    unsigned* abort_word;
     int* err;
 };
 
@@ -78,7 +80,6 @@ struct LoopShared {
     double ss, gg, J, beta, q1, q2, t;
     float beta_f, t_f;
     int restart, ok;
-    unsigned gen;
     unsigned long long prof[kProf], tmark;
 };
 
@@ -106,62 +107,66 @@ __device__ __forceinline__ uint64_t gtimer()
     return t;
 }
 
-// Grid-wide barrier; false (in every thread of the block) after an abort or
-// a timeout.  Arrival is a release add, the wait an acquire load, so the
-// block's writes (ordered before thread 0 by the __syncthreads) are visible
-// to every block that passes, without separate full fences.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, LoopShared& S, int* err)
+// ------------------------------------------------ grid-wide reductions
+//
+// A grid synchronisation is a reduction: thread 0 of every block writes the
+// block's K float-float partials, adds one to an arrival counter with a
+// release reduction (no return value awaited) and polls the counter with
+// acquire loads until all blocks of this synchronisation have arrived (the
+// counter grows monotonically during a launch: the n-th synchronisation
+// waits for n * gridDim.x).  Then one warp per value sums the partials of
+// all blocks in index order.
+
+__device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned target, unsigned* abort_word, int* err)
 {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        S.ok = 1;
-        const unsigned g = S.gen;
-        unsigned old;
-        asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
-        if (old == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.u32 [%0], 0;" ::"l"(bar) : "memory");
-            asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(bar + 1), "r"(g + 1) : "memory");
-        } else {
-            const uint64_t t0 = gtimer();
-            for (;;) {
-                unsigned cur, ab;
-                asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
-                if (cur != g) break;
-                asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(ab) : "l"(bar + 2) : "memory");
-                if (ab) {
-                    S.ok = 0;
-                    break;
-                }
-                if (gtimer() - t0 > kBarrierNs) {
-                    atomicExch(&bar[2], 1u);
-                    atomicOr(err, E_TIMEOUT);
-                    S.ok = 0;
-                    break;
-                }
-                __nanosleep(20);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
+    const uint64_t t0 = gtimer();
+    for (unsigned spins = 1;; ++spins) {
+        unsigned cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(counter) : "memory");
+        if ((int)(cur - target) >= 0) return true;
+        if ((spins & 15) == 0) {
+            unsigned ab;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(abort_word) : "memory");
+            if (ab) return false;
+            if (gtimer() - t0 > kBarrierNs) {
+                atomicExch(abort_word, 1u);
+                atomicOr(err, E_TIMEOUT);
+                return false;
             }
         }
-        S.gen = g + 1;
+        __nanosleep(16);
     }
+}
+
+// The synchronisation alone (no values).
+__device__ __forceinline__ bool grid_sync(unsigned& seq, LoopShared& S, unsigned* counter, unsigned* abort_word,
+                                          int* err)
+{
+    __syncthreads();
+    ++seq;
+    if (threadIdx.x == 0) S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
     __syncthreads();
     return S.ok != 0;
 }
 
-// Block partials of K values to parts slot `slot`, barrier, then the grid
-// totals (index order, float-float) as FP64 in S.red, readable by every
-// thread on return.
+// Block partials of K values to slot `slot`, the synchronisation, then the
+// grid totals as FP64 in S.red, readable by every thread on return.  seq
+// counts the synchronisations of the launch (the same in every thread).
 template <int K>
-__device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned* bar,
-                                            LoopShared& S, int* err)
+__device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned& seq, LoopShared& S,
+                                            unsigned* counter, unsigned* abort_word, int* err)
 {
     FF bt[K];
-    block_partial<K>(v, bt);
-    if (threadIdx.x == 0)
+    block_partial<K>(v, bt);  // ends with __syncthreads(): the block's writes precede thread 0
+    ++seq;
+    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-            parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-    if (!grid_barrier(bar, S, err)) return false;
-    // warp k sums value k over the blocks
+        for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
+        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!S.ok) return false;
     const int warp = threadIdx.x >> 5;
     if (warp < K) {
         const FF a = warp_sum_parts(parts + (slot + warp) * kMaxParts, gridDim.x);
@@ -171,7 +176,9 @@ __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int sl
     return true;
 }
 
-// partial slots (distinct for consecutive reductions)
+// partial slots: consecutive synchronisations use different slots (a fast
+// block may write the next partials while a slow one still reads these), and
+// a slot's next use is at least two synchronisations later
 constexpr int L_A = 0;   // 6
 constexpr int L_C = 6;   // 4
 constexpr int L_D = 10;  // 2
@@ -353,8 +360,8 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
     float2* cTd = cg + RB * N;
     const int col_groups = MC / G::CPC;
     const bool prof = blockIdx.x == 0;
+    unsigned seq = 0;
     if (threadIdx.x == 0) {
-        S.gen = *(volatile unsigned*)&A.bar[1];
         S.ss = A.scal[S_SS];
         for (int i = 0; i < kProf; ++i) S.prof[i] = 0;
     }
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
     {
         float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         phase_update<MC, true>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
-        if (!grid_reduce<kUpdVals>(a, A.parts, L_A, A.bar, S, A.err)) return;
+        if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
         if (threadIdx.x == 0) {
             double J, beta;
             cgd::update_finish(S.red, S.ss, 0.0, true, &J, &beta);
@@ -411,14 +418,14 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
             __syncthreads();  // the next group refills fbuf
         }
         mark(0);
-        if (!grid_barrier(A.bar, S, A.err)) return;
+        if (!grid_sync(seq, S, A.counter, A.abort_word, A.err)) return;
         mark(1);
         // ---- C: rows, direction, first line-search sums
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             phase_rows<MC>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
             mark(2);
-            if (!grid_reduce<4>(acc, A.parts, L_C, A.bar, S, A.err)) return;
+            if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
                 S.q1 = S.red[0];
                 S.q2 = S.red[3];
@@ -435,7 +442,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
             float acc[2] = {0.f, 0.f};
             phase_ls(A.reg, R, cf, cd, S.t_f, acc);
             mark(4 + 2 * j);
-            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, A.bar, S, A.err)) return;
+            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
                 S.t = cgd::ls_next(S.t, S.q1, S.q2, S.red[0], S.red[1]);
                 S.t_f = (float)S.t;
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             phase_update<MC, false>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
-            if (!grid_reduce<kUpdVals>(a, A.parts, L_A, A.bar, S, A.err)) return;
+            if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
                 double J, beta_n;
                 cgd::update_finish(S.red, S.ss, S.gg, false, &J, &beta_n);
@@ -499,13 +506,26 @@ bool loop_shape(int N, int* RB_out, int* grid_out, size_t* smem_out)
     auto kern = k_cg_loop<MC>;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return false;
+    const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+    // the cap is a property of the function shared by every plan and thread:
+    // set once to the largest shape, never lowered (a concurrent launch with
+    // a larger shape would fail)
+    {
+        static std::mutex mu;
+        static int set_cap[64] = {0};
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 0 || dev >= 64) return false;
+        if (set_cap[dev] < (int)cap) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) != cudaSuccess)
+                return false;
+            set_cap[dev] = (int)cap;
+        }
+    }
     for (int gpb = 1; gpb <= kMaxGroupsPerBlock; ++gpb) {
         const int RB = gpb * Geo<MC>::RPC;
         const int grid = (N + RB - 1) / RB;
         const size_t smem = loop_smem<MC>(N, RB);
-        if (smem + fa.sharedSizeBytes > (size_t)optin) return false;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return false;
+        if (smem > cap) return false;
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem) != cudaSuccess)
             return false;
@@ -554,11 +574,11 @@ struct LaunchLoop {
             A.scal = p->scal;
             A.Jdev = p->Jdev;
             A.parts = reinterpret_cast<float2*>(p->part);
-            A.bar = p->counters + C_BAR;
+            A.counter = p->counters + C_BAR;
+            A.abort_word = p->counters + C_BAR + 2;
             A.err = p->dflag;
-            // arrivals and abort start at zero; the generation word carries over
-            SPIREC_CK(cudaMemsetAsync(A.bar, 0, sizeof(unsigned), p->stream));
-            SPIREC_CK(cudaMemsetAsync(A.bar + 2, 0, sizeof(unsigned), p->stream));
+            // no arrivals, no abort
+            SPIREC_CK(cudaMemsetAsync(A.counter, 0, 3 * sizeof(unsigned), p->stream));
             void* args[] = {&A};
             SPIREC_CK(cudaLaunchCooperativeKernel((const void*)k_cg_loop<MC>, dim3(grid), dim3(kLoopThreads), args,
                                                   smem, p->stream));
