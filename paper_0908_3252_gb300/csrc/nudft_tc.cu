@@ -2,15 +2,25 @@
 // NUDFT: G (Eq. AnnMatG) and D = H^H s (Eq. AnnMatGD).
 //
 // Both are complex GEMMs C[i][c] = sum_l A(l,i) B(l,c) of depth K = L whose
-// operands are phases generated on the fly (phase.cuh).  A CTA owns a tile of
-// 128 complex rows x 128 complex columns and runs it as ONE real GEMM
-//      [Ar Ai] (128 x 2K)  x  [[Br Bi]; [-Bi Br]] (2K x 256)
-// so the accumulator (128 lanes x 256 FP32 columns of tensor memory) holds
-// Re C in columns 0..127 and Im C in columns 128..255.
+// operands are phases generated on the fly (phase.cuh).  A tile is 128
+// complex rows x 256 complex columns; the accumulator (all 512 columns of
+// tensor memory, 128 lanes) holds Re C in columns 0..255 and Im C in
+// columns 256..511, built from four real MMAs (M = 128, N = 256) per K slice:
+//      Re C += Ar Br^T - Ai Bi^T      Im C += Ar Bi^T + Ai Br^T
+// (the minus by the instruction's negate-A bit), so each operand is stored
+// once, as [re | im] along K.
 //
 // Split precision: every operand value x is stored as x_hi = fp16(x) (or
-// bf16) and x_lo = fp16(x - x_hi); three MMAs hi*hi + hi*lo + lo*hi feed the
-// same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for FP16).
+// bf16) and x_lo = fp16(x - x_hi); the products hi*hi + hi*lo + lo*hi feed
+// the same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for
+// FP16).
+//
+// Work split (stream-K): the tiles x sample-chunks units are cut into equal
+// contiguous ranges, one per CTA and one CTA per SM, so every SM does the
+// same work whatever the tile count; a range may end in one tile and go on
+// in the next.  CTA c writes its partial of tile t to slot c + t (unique,
+// since both grow along the ranges) and k_reduce_tc adds the partials of
+// each tile in CTA order.
 //
 // Pipeline per CTA (544 threads):
 //   warps 0-15 producers: per stage of 32 samples, each thread forms the
@@ -19,16 +29,19 @@
 //              (A_hi, A_lo, B_hi, B_lo) in the 128-byte-swizzled K-major
 //              layout the MMA reads, then arrives on full[stage];
 //   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
-//              issues 12 tcgen05.mma (K = 16 each) and commits to empty[stage];
-//   warps 0-15 drain: every SEG stages (512 samples) the finished accumulator
-//              is read with tcgen05.ld and added, in FP32 with round-to-
-//              nearest, to the CTA's split-K partial tile in global memory
-//              (column-major, so each lane row maps to consecutive addresses).
+//              issues 24 tcgen05.mma (M = 128, N = 256, K = 16 each) and
+//              commits to empty[stage];
+//   warps 0-15 drain: at the end of every segment (at most SEG stages of one
+//              tile) the finished accumulator is read with tcgen05.ld and
+//              added to the CTA's column-major partial tile in global memory
+//              by fire-and-forget reductions (red.global.add.f32, coalesced
+//              along the rows, round-to-nearest; the first segment of a tile
+//              stores).  The MMA waits for the drain (one accumulator), which
+//              issues in well under a microsecond.
 // The tensor core's FP32 accumulation loses about one unit in the last place
 // per accumulation step (truncation-like, measured: 2.8e-4 relative after
-// 12k steps); draining every 192 steps bounds that error, and the two TMEM
-// accumulators (2 x 256 columns) let the MMA run on while one is drained.
-// Two stages of 96 KB double-buffer generation against the tensor core.  The
+// 12k steps); draining every 16 stages bounds that error.  Two stages of
+// 96 KB buffer generation against the tensor core.  The
 // stage's 32 samples of the trajectory (and of the data, for D) arrive by TMA
 // bulk copy (cp.async.bulk) into a 4-deep shared-memory ring two stages
 // ahead, so the table builders never wait on global memory.
@@ -46,21 +59,24 @@ namespace spirec {
 namespace {
 
 constexpr int TC_ROWS = 128;        // complex rows per tile (MMA M)
-constexpr int TC_COLS = 128;        // complex columns per tile (MMA N = 256 real)
-constexpr int TC_KS = 32;           // samples per stage (64 real K per operand set)
+constexpr int TC_COLS = 256;        // complex columns per tile (MMA N)
+constexpr int TC_KS = 32;           // samples per stage
 constexpr int TC_STAGES = 2;
 constexpr int TC_PRODUCERS = 512;   // 16 warps
 constexpr int TC_THREADS = TC_PRODUCERS + 32;
-constexpr int TC_SEG = 16;          // stages per accumulator segment
+constexpr int TC_SEG = 16;          // stages per accumulator segment (at most)
+constexpr int TC_TILE_FLOATS = 2 * TC_COLS * TC_ROWS;  // partial tile: 512 columns x 128 rows
 constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
-constexpr uint32_t B_BYTES = 2 * TC_COLS * 128;      // 256 rows x 64 halves
-constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int TRAJ_RING = 4;
 constexpr uint32_t TRAJ_BUF = 3 * TC_KS * 8;                // ka, kb (int64) and w (float2)
 constexpr uint32_t TRAJ_OFF = TC_STAGES * STAGE_BYTES;
 constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+static_assert(8 * (2 * TC_STAGES + 2 + TRAJ_RING) + 8 <= 128, "barrier area");
+constexpr int kMaxCtas = 152;       // CTAs of one contraction (one per SM)
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kErrTimeout = E_TIMEOUT;
@@ -263,10 +279,10 @@ __device__ __forceinline__ float2 phasor_fast(int64_t kq, int j)
     return make_float2(cs, sn);
 }
 
-__device__ __forceinline__ uint4 neg4(uint4 v)
+// *p += v at the memory (round-to-nearest FP32 add, no reply).
+__device__ __forceinline__ void red_global(float* p, float v)
 {
-    const uint32_t s = 0x80008000u;  // sign bits of both packed halves
-    return make_uint4(v.x ^ s, v.y ^ s, v.z ^ s, v.w ^ s);
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 // 2^-e with 2^e >= sqrt(amax2): scales the weights into (-1, 1).
@@ -280,9 +296,12 @@ __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
     return ldexpf(1.f, -e);
 }
 
-// Adds (first: stores) one accumulator buffer into the column-major partial
-// tile; warp w reads TMEM lanes 32 (w % 4).. and complex columns
-// [32 (w / 4), 32 (w / 4) + 32) (real part at column c, imaginary at 128 + c).
+// Adds (first: stores) the accumulator into the column-major partial tile
+// [512 columns][128 rows]; warp w reads TMEM lanes 32 (w % 4).. and complex
+// columns [64 (w / 4), 64 (w / 4) + 64) (real part at column c, imaginary at
+// 256 + c).  Lanes are consecutive rows, so each warp instruction covers one
+// 128-byte line; a thread's adds to one address come in program order, so
+// the partial is the same sum in the same order on every run.
 __device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, int warp, int lane,
                                                   bool first)
 {
@@ -290,70 +309,94 @@ __device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, i
     const int quarter = warp >> 2;
     const int row = lbase + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < 32; cc += 16) {
+    for (int cc = 0; cc < 64; cc += 16) {
         float re[16], im[16];
-        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(32 * quarter + cc);
+        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(64 * quarter + cc);
         tmem_ld16(ta, re);
-        tmem_ld16(ta + 128, im);
+        tmem_ld16(ta + TC_COLS, im);
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = 32 * quarter + cc + j;
+            const int col = 64 * quarter + cc + j;
             float* pr = ptile + (size_t)col * TC_ROWS + row;
-            float* pi = ptile + (size_t)(128 + col) * TC_ROWS + row;
+            float* pi = ptile + (size_t)(TC_COLS + col) * TC_ROWS + row;
             if (first) {
                 *pr = re[j];
                 *pi = im[j];
             } else {
-                *pr += re[j];
-                *pi += im[j];
+                red_global(pr, re[j]);
+                red_global(pi, im[j]);
             }
         }
     }
 }
 
-// C partial for split blockIdx.z over samples [ch0*32, ch1*32):
+// The unit range [u0, u1) of CTA c among P over U units (tiles x chunks).
+__host__ __device__ __forceinline__ int64_t unit_start(int64_t c, int64_t U, int64_t P) { return c * U / P; }
+
+// Segment bookkeeping along a CTA's stages: a segment is at most TC_SEG
+// stages of one tile.  Producers and the MMA issuer step it identically.
+struct SegWalk {
+    int64_t u0, K;
+    int seg = -1, pos = 0;
+    int64_t tile = -1;
+    bool first_of_tile = false;
+    // advance to stage it (called for it = 0, 1, 2, ...)
+    __device__ __forceinline__ void step(int it)
+    {
+        const int64_t u = u0 + it;
+        const int64_t t = u / K;
+        if (it == 0 || t != tile || pos == TC_SEG - 1) {
+            first_of_tile = it == 0 || t != tile;
+            ++seg;
+            pos = 0;
+            tile = t;
+        } else {
+            ++pos;
+        }
+    }
+    // stage it (current) closes its segment
+    __device__ __forceinline__ bool closes(int it, int n) const
+    {
+        const int64_t u = u0 + it;
+        return it == n - 1 || (u + 1) % K == 0 || pos == TC_SEG - 1;
+    }
+};
+
+// Partials of CTA blockIdx.x over its units [u0, u1) (unit = tile * K +
+// chunk of 32 samples; tile = row tile * tilesC + column tile):
 //   A(l,i) = exp(sa i2pi ka_l (i + oa)),  B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
 template <bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
-                const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L,
-                int R, int C, int oa, int ob, int sa, int sb, int64_t chunks_per_split,
-                float* __restrict__ part, int* err)
+                const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L, int tilesC,
+                int oa, int ob, int sa, int sb, int64_t K, int64_t U, float* __restrict__ part, int* err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_full = sbase + BAR_OFF;           // 2 x 8 B: stage filled
-    const uint32_t bar_empty = sbase + BAR_OFF + 16;     // 2 x 8 B: stage consumed
-    const uint32_t bar_acc_full = sbase + BAR_OFF + 32;  // 2 x 8 B: segment accumulated
-    const uint32_t bar_acc_empty = sbase + BAR_OFF + 48; // 2 x 8 B: accumulator drained
-    const uint32_t bar_traj = sbase + BAR_OFF + 64;      // 4 x 8 B: trajectory chunk landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + BAR_OFF + 96);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + BAR_OFF + 100);
+    const uint32_t bar_full = sbase + BAR_OFF;                // stage filled
+    const uint32_t bar_empty = bar_full + 8 * TC_STAGES;      // stage consumed
+    const uint32_t bar_acc_full = bar_empty + 8 * TC_STAGES;  // segment accumulated
+    const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained
+    const uint32_t bar_traj = bar_acc_empty + 8;              // TRAJ_RING: trajectory chunk landed
+    const uint32_t misc = BAR_OFF + 8 * (2 * TC_STAGES + 2 + TRAJ_RING);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
     const uint32_t traj_s = sbase + TRAJ_OFF;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.y * TC_ROWS, c0 = blockIdx.x * TC_COLS;
-    const int64_t nchunks = (L + TC_KS - 1) / TC_KS;
-    const int64_t ch0 = (int64_t)blockIdx.z * chunks_per_split;
-    int64_t ch1 = ch0 + chunks_per_split;
-    if (ch1 > nchunks) ch1 = nchunks;
-    const int nloc = ch1 > ch0 ? (int)(ch1 - ch0) : 0;
-    const int nseg = (nloc + TC_SEG - 1) / TC_SEG;
-    // partial tile of this split: column-major [256 real columns][128 rows]
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
-    float* ptile = part + ((int64_t)blockIdx.z * gridDim.x * gridDim.y + tile) * (256 * TC_ROWS);
+    const int64_t P = gridDim.x;
+    const int64_t u0 = unit_start(blockIdx.x, U, P);
+    const int n = (int)(unit_start(blockIdx.x + 1, U, P) - u0);
 
     if (tid == 0) {
-        mbar_init(bar_full, TC_PRODUCERS);
-        mbar_init(bar_full + 8, TC_PRODUCERS);
-        mbar_init(bar_empty, 1);
-        mbar_init(bar_empty + 8, 1);
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(bar_full + 8 * i, TC_PRODUCERS);
+            mbar_init(bar_empty + 8 * i, 1);
+        }
         mbar_init(bar_acc_full, 1);
-        mbar_init(bar_acc_full + 8, 1);
         mbar_init(bar_acc_empty, TC_PRODUCERS);
-        mbar_init(bar_acc_empty + 8, TC_PRODUCERS);
         for (int r = 0; r < TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -369,7 +412,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
         // TMA feed of the trajectory (and data) chunk of stage `it` into ring slot it % 4
         auto issue_traj = [&](int it) {
-            const int64_t l0 = (ch0 + it) * TC_KS;
+            const int64_t l0 = ((u0 + it) % K) * TC_KS;
             int64_t cnt = L - l0;
             if (cnt > TC_KS) cnt = TC_KS;
             const uint32_t bytes = (uint32_t)(((cnt + 1) & ~1) * 8);  // multiple of 16; arrays are padded
@@ -382,51 +425,57 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             if (WEIGHTED) bulk_g2s(buf + 2 * TC_KS * 8, w + l0, bytes, bar);
         };
         if (tid == 0)
-            for (int it = 0; it < 2 && it < nloc; ++it) issue_traj(it);
-        for (int it = 0; it < nloc; ++it) {
-            const int s = it & 1;
-            const uint32_t use = (uint32_t)(it >> 1);
-            if (tid == 0 && it >= 2 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+            for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
+        const int r = tid & 127, g = tid >> 7;  // operand row (A) / column (B), sample group
+        SegWalk sw{u0, K};
+        int64_t dtile = 0;  // tile of the segment being accumulated
+        bool dfirst = true;
+        for (int it = 0; it < n; ++it) {
+            const int s = it % TC_STAGES;
+            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            if (tid == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
             producers_sync();  // stage s is free
             if (*abort_flag) break;
-            if (tid == 0 && it + 2 < nloc) issue_traj(it + 2);
+            if (tid == 0 && it + 2 < n) issue_traj(it + 2);
             if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
-            const int64_t l0 = (ch0 + it) * TC_KS;
+            sw.step(it);
+            const int64_t u = u0 + it, t = u / K;
+            const int64_t l0 = (u % K) * TC_KS;
+            const int i0 = (int)(t / tilesC) * TC_ROWS, c0 = (int)(t % tilesC) * TC_COLS;
             const uint8_t* tbuf = smem + TRAJ_OFF + (it % TRAJ_RING) * TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
+            const int ja = i0 + r + oa;
+            float re[8], im[8];
+            uint4 rh, rl, ih, il;
+            // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
 #pragma unroll
-            for (int q = 0; q < 512 / TC_PRODUCERS; ++q) {
-                const int u = tid + TC_PRODUCERS * q;
-                const int r = u & 127, g = u >> 7;  // row (A) or column (B), sample group
-                const int ja = i0 + r + oa, jb = c0 + r + ob;
-                float re[8], im[8];
-                // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int l = 8 * g + e;
-                    float2 v = phasor_fast(ka_s[l], ja);
-                    if (l0 + l >= L) v = make_float2(0.f, 0.f);
-                    re[e] = v.x;
-                    im[e] = sa < 0 ? -v.y : v.y;
-                }
-                uint4 rh, rl, ih, il;
-                split8<BF16>(re, rh, rl);
-                split8<BF16>(im, ih, il);
-                st_shared_v4(aH + sw128(r, g), rh);
-                st_shared_v4(aH + sw128(r, 4 + g), ih);
-                st_shared_v4(aL + sw128(r, g), rl);
-                st_shared_v4(aL + sw128(r, 4 + g), il);
-                // B column r: row r = [Br | -Bi], row 128 + r = [Bi | Br]
+            for (int e = 0; e < 8; ++e) {
+                const int l = 8 * g + e;
+                float2 v = phasor_fast(ka_s[l], ja);
+                if (l0 + l >= L) v = make_float2(0.f, 0.f);
+                re[e] = v.x;
+                im[e] = sa < 0 ? -v.y : v.y;
+            }
+            split8<BF16>(re, rh, rl);
+            split8<BF16>(im, ih, il);
+            st_shared_v4(aH + sw128(r, g), rh);
+            st_shared_v4(aH + sw128(r, 4 + g), ih);
+            st_shared_v4(aL + sw128(r, g), rl);
+            st_shared_v4(aL + sw128(r, 4 + g), il);
+            // B columns r and 128 + r: [Br | Bi]
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int rb = r + 128 * h, jb = c0 + rb + ob;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int l = 8 * g + e;
@@ -444,55 +493,56 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
                 }
                 split8<BF16>(re, rh, rl);
                 split8<BF16>(im, ih, il);
-                st_shared_v4(bH + sw128(r, g), rh);
-                st_shared_v4(bH + sw128(r, 4 + g), neg4(ih));
-                st_shared_v4(bH + sw128(128 + r, g), ih);
-                st_shared_v4(bH + sw128(128 + r, 4 + g), rh);
-                st_shared_v4(bL + sw128(r, g), rl);
-                st_shared_v4(bL + sw128(r, 4 + g), neg4(il));
-                st_shared_v4(bL + sw128(128 + r, g), il);
-                st_shared_v4(bL + sw128(128 + r, 4 + g), rl);
+                st_shared_v4(bH + sw128(rb, g), rh);
+                st_shared_v4(bH + sw128(rb, 4 + g), ih);
+                st_shared_v4(bL + sw128(rb, g), rl);
+                st_shared_v4(bL + sw128(rb, 4 + g), il);
             }
             fence_proxy_async();
             mbar_arrive(bar_full + 8 * s);
-            // the MMA now has this stage queued: drain the previous segment
-            if (it % TC_SEG == 0 && it > 0) {
-                const int j = it / TC_SEG - 1;
-                if (!mbar_wait(bar_acc_full + 8 * (j & 1), (uint32_t)(j >> 1) & 1)) {
-                    atomicOr(err, kErrTimeout);
-                    *abort_flag = 1;
+            if (sw.pos == 0) {
+                // the MMA now has the first stage of a new segment queued:
+                // drain the previous one
+                if (sw.seg > 0) {
+                    const int j = sw.seg - 1;
+                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+                        atomicOr(err, kErrTimeout);
+                        *abort_flag = 1;
+                    }
+                    tc_fence_after();
+                    drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
+                    tc_fence_before();
+                    mbar_arrive(bar_acc_empty);
                 }
-                tc_fence_after();
-                drain_accumulator(tmem + 256u * (j & 1), ptile, warp, lane, j == 0);
-                tc_fence_before();
-                mbar_arrive(bar_acc_empty + 8 * (j & 1));
+                dtile = sw.tile;
+                dfirst = sw.first_of_tile;
             }
         }
-        // last segment (or zeros when this split has no samples)
-        if (nseg == 0) {
-            for (int e = tid; e < 256 * TC_ROWS; e += TC_PRODUCERS) ptile[e] = 0.f;
-        } else if (!*abort_flag) {
-            const int j = nseg - 1;
-            if (!mbar_wait(bar_acc_full + 8 * (j & 1), (uint32_t)(j >> 1) & 1)) {
+        // the last segment
+        if (sw.seg >= 0 && !*abort_flag) {
+            const int j = sw.seg;
+            if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
                 atomicOr(err, kErrTimeout);
             } else {
                 tc_fence_after();
-                drain_accumulator(tmem + 256u * (j & 1), ptile, warp, lane, j == 0);
+                drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
             }
         }
     } else if (lane == 0) {
         // ------------------------------------------------ MMA issuer
         // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and 10,
-        // both K-major, N = 256 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
+        // negate A at bit 13, both K-major, N = 256 (N>>3 at bit 17), M = 128
+        // (M>>4 at bit 24).
         const uint32_t fmt = BF16 ? 1u : 0u;
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-        for (int it = 0; it < nloc; ++it) {
-            const int s = it & 1;
-            const uint32_t use = (uint32_t)(it >> 1);
-            const int seg = it / TC_SEG, pos = it - seg * TC_SEG;
-            const uint32_t tacc = tmem + 256u * (seg & 1);
-            if (pos == 0 && seg >= 2 &&
-                !mbar_wait(bar_acc_empty + 8 * (seg & 1), (uint32_t)((seg - 2) >> 1) & 1)) {
+        const uint32_t idesc_neg = idesc | (1u << 13);
+        SegWalk sw{u0, K};
+        for (int it = 0; it < n; ++it) {
+            const int s = it % TC_STAGES;
+            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            sw.step(it);
+            const uint32_t tre = tmem, tim = tmem + TC_COLS;
+            if (sw.pos == 0 && sw.seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(sw.seg - 1) & 1)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
@@ -504,14 +554,20 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t off = 32u * kk;  // 16 halves along K
-                mma_f16(tacc, sdesc(aH + off), sdesc(bH + off), idesc, (pos > 0 || kk > 0) ? 1u : 0u);
-                mma_f16(tacc, sdesc(aH + off), sdesc(bL + off), idesc, 1u);
-                mma_f16(tacc, sdesc(aL + off), sdesc(bH + off), idesc, 1u);
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint32_t oR = 32u * kk, oI = 64u + 32u * kk;  // 16 samples of re, of im
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
+                    const uint32_t A = q == 2 ? aL : aH, B = q == 1 ? bL : bH;
+                    const uint32_t acc = (sw.pos > 0 || kk > 0 || q > 0) ? 1u : 0u;
+                    mma_f16(tre, sdesc(A + oR), sdesc(B + oR), idesc, acc);
+                    mma_f16(tre, sdesc(A + oI), sdesc(B + oI), idesc_neg, 1u);
+                    mma_f16(tim, sdesc(A + oR), sdesc(B + oI), idesc, acc);
+                    mma_f16(tim, sdesc(A + oI), sdesc(B + oR), idesc, 1u);
+                }
             }
             mma_commit(bar_empty + 8 * s);
-            if (pos == TC_SEG - 1 || it == nloc - 1) mma_commit(bar_acc_full + 8 * (seg & 1));
+            if (sw.closes(it, n)) mma_commit(bar_acc_full);
         }
     }
 
@@ -524,15 +580,15 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
     }
 }
 
-// out[i][c] = scale * 2^e * sum_z part[z][tile(i,c)]: the partial tiles are
-// column-major [256 real columns][128 rows]; 2^e undoes the weight scaling.
-__global__ void k_reduce_tc(const float* __restrict__ part, int S, int R, int C, int tilesC,
-                            float scale, const unsigned* __restrict__ amax2, float2* __restrict__ out)
+// out[i][c] = scale * 2^e * (sum of the partials of tile(i, c) in CTA order);
+// 2^e undoes the weight scaling.  The CTAs holding units of tile t are
+// c_lo..c_hi, the last CTAs whose ranges start at or before the tile's first
+// and last unit; CTA c keeps its partial of tile t in slot c + t.
+__global__ void k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K, int64_t P, int R, int C,
+                            int tilesC, float scale, const unsigned* __restrict__ amax2, float2* __restrict__ out)
 {
     float sc = scale;
     if (amax2) sc = scale / weight_scale_inv(amax2);
-    const int tilesR = (R + TC_ROWS - 1) / TC_ROWS;
-    const int64_t tiles = (int64_t)tilesR * tilesC;
     const int64_t RC = (int64_t)R * C;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < RC;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -540,11 +596,14 @@ __global__ void k_reduce_tc(const float* __restrict__ part, int S, int R, int C,
         const int c = (int)(e / R), i = (int)(e - (int64_t)c * R);
         const int64_t t = (int64_t)(i / TC_ROWS) * tilesC + c / TC_COLS;
         const int row = i % TC_ROWS, col = c % TC_COLS;
+        const int64_t c_lo = ((t * K + 1) * P - 1) / U;
+        const int64_t c_hi = ((t + 1) * K * P - 1) / U;
         float ar = 0.f, ai = 0.f;
-        for (int z = 0; z < S; ++z) {
-            const float* pt = part + ((int64_t)z * tiles + t) * (256 * TC_ROWS);
+        for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
+            if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
+            const float* pt = part + (cc + t) * TC_TILE_FLOATS;
             ar += pt[col * TC_ROWS + row];
-            ai += pt[(128 + col) * TC_ROWS + row];
+            ai += pt[(TC_COLS + col) * TC_ROWS + row];
         }
         out[(int64_t)i * C + c] = make_float2(ar * sc, ai * sc);
     }
@@ -564,22 +623,26 @@ __global__ void k_absmax2(const float2* __restrict__ y, int64_t n, unsigned* ama
     if ((threadIdx.x & 31) == 0 && isfinite(m)) atomicMax(amax2, __float_as_uint(m));
 }
 
-constexpr int kSMs = 152;
-
 int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const float2* w, int R,
                   int C, int oa, int ob, int sa, int sb, float scale, float2* out)
 {
-    const int64_t nchunks = (p->L + TC_KS - 1) / TC_KS;
+    const int64_t K = (p->L + TC_KS - 1) / TC_KS;
     const int tilesR = (R + TC_ROWS - 1) / TC_ROWS, tilesC = (C + TC_COLS - 1) / TC_COLS;
-    const int tiles = tilesR * tilesC;
-    int64_t S = kSMs / tiles;
-    if (S < 1) S = 1;
-    if (S > nchunks) S = nchunks;
+    const int64_t T = (int64_t)tilesR * tilesC;
+    const int64_t U = T * K;
+    int dev = 0, sms = 0;
+    SPIREC_CK(cudaGetDevice(&dev));
+    SPIREC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
+    if (P > U) P = U;
+    // slots c + t < P + T must fit the partial buffer
+    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float)));
+    if (P + T > cap) P = cap - T;
+    if (P < 1) {
+        set_error("partial buffer too small for %lld tiles", (long long)T);
+        return SPIREC_EUNSUPPORTED;
+    }
     const int64_t RC = (int64_t)R * C;
-    const size_t tile_bytes = 256 * TC_ROWS * sizeof(float);
-    while (S > 1 && (size_t)(S * tiles) * tile_bytes > p->kpart_bytes) --S;
-    const int64_t cps = (nchunks + S - 1) / S;
-    const int Seff = (int)((nchunks + cps - 1) / cps);
     unsigned* amax = nullptr;
     if (w && w != p->s) {
         // the kernel reads padded, plan-owned sample arrays
@@ -590,30 +653,30 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
         amax = p->counters + C_AMAX;
         SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
         int blocks = (int)((p->L + 255) / 256);
-        if (blocks > 4 * kSMs) blocks = 4 * kSMs;
+        if (blocks > 4 * kMaxCtas) blocks = 4 * kMaxCtas;
         k_absmax2<<<blocks, 256, 0, p->stream>>>(w, p->L, amax);
         SPIREC_CK(cudaGetLastError());
         p->launches += 1;
     }
-    dim3 grid(tilesC, tilesR, Seff);
+    const dim3 grid((unsigned)P);
     float* part = p->kpart;
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
     if (bf16 && w)
         k_tc_phase_gemm<true, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else if (bf16)
         k_tc_phase_gemm<true, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else if (w)
         k_tc_phase_gemm<false, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else
         k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, R, C, oa, ob, sa, sb, cps, part, p->dflag);
+            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     SPIREC_CK(cudaGetLastError());
     int rblocks = (int)((RC + 255) / 256);
-    if (rblocks > 4 * kSMs) rblocks = 4 * kSMs;
-    k_reduce_tc<<<rblocks, 256, 0, p->stream>>>(part, Seff, R, C, tilesC, scale, amax, out);
+    if (rblocks > 4 * kMaxCtas) rblocks = 4 * kMaxCtas;
+    k_reduce_tc<<<rblocks, 256, 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
     SPIREC_CK(cudaGetLastError());
     p->launches += 2;
     return SPIREC_OK;
@@ -621,11 +684,12 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
 
 }  // namespace
 
-size_t kpart_floats_tc(int, int64_t, int precision)
+size_t kpart_floats_tc(int N, int64_t, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
-    // S * tiles <= 152 and R * C <= tiles * 128 * 128
-    return (size_t)kSMs * TC_ROWS * TC_COLS * 2;
+    // slots c + t < P + T; G (N x 2N-1) has the most tiles
+    const size_t T = (size_t)((N + TC_ROWS - 1) / TC_ROWS) * (size_t)((2 * N - 1 + TC_COLS - 1) / TC_COLS);
+    return ((size_t)kMaxCtas + T) * TC_TILE_FLOATS;
 }
 
 int tc_setup_attributes()
