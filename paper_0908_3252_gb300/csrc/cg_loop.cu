@@ -1,9 +1,11 @@
 // cg_loop.cu -- the whole Polak-Ribiere loop (section 3.3 on the rewritten
 // criterion of section 3.4) as ONE persistent cooperative kernel.
 //
-// Block b owns the image rows [R0, R0 + RB) for the whole solve and keeps in
-// shared memory f and d of those rows plus one halo row on each side, and
-// T f, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
+// One 512-thread block per SM (up to 128 registers a thread, so nothing
+// spills: with the row caches in shared memory little L1 is left for local
+// memory).  Block b owns the image rows [R0, R0 + RB) for the whole solve
+// and keeps in shared memory f and d of those rows plus one halo row on each
+// side, and T f, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
 // halo row of g per side pass through global memory (L2):
 //   X   the row FFTs of g, overwritten by the column-filtered rows Y,
 //   Xd  the row FFTs of the current direction d (kept across iterations).
@@ -91,13 +93,15 @@ struct Geo {
     static constexpr int LDR = fftd::seq_len<MC>(MC);
     static constexpr int LDC = LDR + 4;
     static constexpr int FBUF = RPC * LDR > CPC * LDC ? RPC * LDR : CPC * LDC;
+    static constexpr int TW = (fftd::staged_twiddles_size(MC) + 1) & ~1;  // keeps 16-byte alignment
 };
 
-// dynamic shared memory of a block owning RB rows of an N-wide image
+// dynamic shared memory of a block owning RB rows of an N-wide image: the
+// FFT buffer, the staged twiddle table, the row caches
 template <int MC>
 size_t loop_smem(int N, int RB)
 {
-    return ((size_t)Geo<MC>::FBUF + (size_t)(2 * (RB + 2) + 4 * RB) * N) * sizeof(float2);
+    return ((size_t)Geo<MC>::FBUF + Geo<MC>::TW + (size_t)(2 * (RB + 2) + 4 * RB) * N) * sizeof(float2);
 }
 
 __device__ __forceinline__ uint64_t gtimer()
@@ -197,7 +201,8 @@ struct Rows {
 // Step (unless FIRST), gradient and the six update sums over the own rows
 // (the sums of cgd::update_pixel); with do_fft the row FFTs of g go to X.
 template <int MC, bool FIRST>
-__device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, float2* fbuf, float2* cf,
+__device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
+                                             float2* cf,
                                              const float2* cd, float2* cTf, const float2* cD, float2* cg,
                                              const float2* cTd, float t, bool do_fft, float (&a)[kUpdVals])
 {
@@ -245,7 +250,7 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
         }
         if (do_fft) {
             __syncthreads();
-            fftd::fft_pow2<MC, false, 1>(fbuf, G::LDR, A.tw);
+            fftd::fft_pow2<MC, false, 1, true>(fbuf, G::LDR, stw);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int e = threadIdx.x + i * kLoopThreads;
@@ -262,7 +267,8 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
 // Row IFFTs of Y (in X) -> T d of the own rows; the new direction on every
 // cached row; the four sums of the first line-search step.
 template <int MC>
-__device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* cf,
+__device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
+                                           const float2* cf,
                                            float2* cd, const float2* cTf, const float2* cD, const float2* cg,
                                            float2* cTd, float beta, bool restart, float (&acc)[4])
 {
@@ -284,7 +290,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
             fbuf[q * G::LDR + fftd::sidx<MC>(m)] = v[i];
         }
         __syncthreads();
-        fftd::fft_pow2<MC, true, 1>(fbuf, G::LDR, A.tw);
+        fftd::fft_pow2<MC, true, 1, true>(fbuf, G::LDR, stw);
         for (int e = threadIdx.x; e < nr * N; e += kLoopThreads) {
             const int q = e / N, m = e - q * N;
             cTd[(g0 + q) * N + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
@@ -338,7 +344,7 @@ __device__ __forceinline__ void phase_ls(const Reg& reg, const Rows& R, const fl
 // ------------------------------------------------------------------ kernel
 
 template <int MC>
-__global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
+__global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
 {
     static_assert(MC > 0, "the loop kernel needs a compile-time FFT size");
     using G = Geo<MC>;
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
     R.hlo = R.R0 > 0 ? R.R0 - 1 : R.R0;
     R.hhi = min(R.R0 + R.nown, N - 1);
     float2* fbuf = sm;
-    float2* cf = fbuf + G::FBUF;      // rows R0-1 .. R0+RB: f
+    float2* stw = fbuf + G::FBUF;     // staged twiddles of exp(-2 pi i k / M)
+    float2* cf = stw + G::TW;         // rows R0-1 .. R0+RB: f
     float2* cd = cf + (RB + 2) * N;   // the same rows: d
     float2* cTf = cd + (RB + 2) * N;  // own rows: T f, D, g, T d
     float2* cD = cTf + RB * N;
@@ -374,8 +381,9 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
         }
     };
 
-    // ---- caches: f of the cached rows, T f and D of the own rows
+    // ---- caches: twiddles, f of the cached rows, T f and D of the own rows
     {
+        fftd::build_staged_twiddles<MC>(A.tw, stw);
         const int nc = (R.hhi - R.hlo + 1) * N;
         const float2* src = A.f0 + (int64_t)R.hlo * N;
         float2* dst = cf + R.cache(R.hlo);
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
     // ---- gradient at x0, J(x0); the first direction is -g (beta = 0)
     {
         float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        phase_update<MC, true>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+        phase_update<MC, true>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
         if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
         if (threadIdx.x == 0) {
             double J, beta;
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
         // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * G::CPC;
-            fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, G::CPC, G::CPC, A.fp, A.tw, A.Chat, fbuf, nullptr,
+            fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, G::CPC, G::CPC, A.fp, stw, A.Chat, fbuf, nullptr,
                                             A.Xd, beta, restart);
             __syncthreads();  // the next group refills fbuf
         }
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
         // ---- C: rows, direction, first line-search sums
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            phase_rows<MC>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+            phase_rows<MC>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
             mark(2);
             if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) k_cg_loop(LoopArgs A)
         // ---- A: step, gradient, row FFTs of g for the next iteration
         {
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            phase_update<MC, false>(A, R, fbuf, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+            phase_update<MC, false>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
             if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {

@@ -69,9 +69,12 @@ __device__ __forceinline__ void dft_small(float2* v)
     }
 }
 
+// Twiddle e of the table; TWS: the table is in shared memory (a plain
+// load), else in global memory (read-only path).
+template <bool TWS = false>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e, bool inv)
 {
-    float2 w = __ldg(tw + e);
+    float2 w = TWS ? tw[e] : __ldg(tw + e);
     if (inv) w.y = -w.y;
     return w;
 }
@@ -142,11 +145,38 @@ __device__ float2* fft_rt(float2* a, float2* b, const FftPlan& fp, int nseq, int
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
+// Staged twiddle table (shared memory) for fft_pow2 of size M: the radix-4
+// stage with span Ns keeps w^((k r) M / (4 Ns)) at (Ns - 1) + (r - 1) Ns + k
+// (r = 1..3, k < Ns), so the lanes of a warp, which hold consecutive k, read
+// consecutive entries or the same one (no bank conflicts); the radix-2 stage
+// of an odd log2 M keeps w^jj at r4_entries + jj.  From the plain table
+// tw[e] = w^e.  Entries: staged_twiddles_size(M) <= 3M/2.
+__host__ __device__ constexpr int staged_r4_entries(int M) { return (1 << (2 * (ilog2(M) / 2))) - 1; }
+__host__ __device__ constexpr int staged_twiddles_size(int M)
+{
+    return staged_r4_entries(M) + ((ilog2(M) & 1) ? M / 2 : 0);
+}
+template <int M>
+__device__ __forceinline__ void build_staged_twiddles(const float2* __restrict__ tw, float2* stw)
+{
+    constexpr int LOG2M = ilog2(M);
+    for (int lns = 0; lns + 2 <= LOG2M; lns += 2) {
+        const int Ns = 1 << lns;
+        for (int i = threadIdx.x; i < 3 * Ns; i += blockDim.x) {
+            const int r = i / Ns + 1, k = i - (r - 1) * Ns;
+            stw[Ns - 1 + i] = __ldg(tw + ((k * r) << (LOG2M - lns - 2)));
+        }
+    }
+    if (LOG2M & 1)
+        for (int jj = threadIdx.x; jj < M / 2; jj += blockDim.x) stw[staged_r4_entries(M) + jj] = __ldg(tw + jj);
+}
+
 // In-place transform of BPT * blockDim.x / (M/4) sequences (stride ld,
 // padded index) of length M: BPT radix-4 butterflies per thread per stage
 // (plus one radix-2 stage for odd log2 M), values held in registers between
-// a read and a write phase.
-template <int M, bool INV, int BPT = 1>
+// a read and a write phase.  TWS: tw is the staged table in shared memory
+// (build_staged_twiddles), else the plain table in global memory.
+template <int M, bool INV, int BPT = 1, bool TWS = false>
 __device__ __forceinline__ void fft_pow2(float2* buf, int ld, const float2* __restrict__ tw)
 {
     constexpr int LOG2M = ilog2(M);
@@ -167,7 +197,9 @@ __device__ __forceinline__ void fft_pow2(float2* buf, int ld, const float2* __re
         __syncthreads();
         float2 w[4];
 #pragma unroll
-        for (int r = 1; r < 4; ++r) w[r] = twiddle(tw, (k * r) << (LOG2M - lns - 2), INV);
+        for (int r = 1; r < 4; ++r)
+            w[r] = TWS ? twiddle<true>(tw, Ns - 1 + (r - 1) * Ns + k, INV)
+                       : twiddle<false>(tw, (k * r) << (LOG2M - lns - 2), INV);
         const int base = ((j >> lns) << (lns + 2)) + k;
 #pragma unroll
         for (int b = 0; b < BPT; ++b) {
@@ -198,7 +230,8 @@ __device__ __forceinline__ void fft_pow2(float2* buf, int ld, const float2* __re
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int jj = j + h * NB;
-                float2 v[2] = {a[b][h], cmul(c[b][h], twiddle(tw, jj, INV))};
+                float2 v[2] = {a[b][h],
+                               cmul(c[b][h], twiddle<TWS>(tw, TWS ? staged_r4_entries(M) + jj : jj, INV))};
                 dft_small<2, INV>(v);
                 s[sidx<M>(jj)] = v[0];
                 s[sidx<M>(jj + M / 2)] = v[1];
@@ -400,7 +433,8 @@ __device__ __forceinline__ void rows_inv_group(const float2* X, int r0, int nr, 
 // MODE 1 (CG, compile-time M only): the column input is the row FFT of the
 // new direction, formed from the row FFTs of g (in X) and of the old
 // direction (in Xd) as -X + beta Xd (-X on a restart) by linearity of the
-// DFT, and written back to Xd before the transform.
+// DFT, and written back to Xd before the transform; the twiddle table is in
+// shared memory and Chat is read through L2 only.
 template <int MC, int BPT = 1, int MODE = 0>
 __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x0, int nc, int cpc,
                                            const FftPlan& fp, const float2* __restrict__ tw,
@@ -427,7 +461,9 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
             if constexpr (MODE == 1)
                 o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
             const int hc = e / M, hk = e - hc * M;
-            h[i] = hc < nc ? __ldg(&Chat[(int64_t)(x0 + hc) * M + hk]) : 0.f;
+            h[i] = hc < nc ? (MODE == 1 ? __ldcg(&Chat[(int64_t)(x0 + hc) * M + hk])
+                                        : __ldg(&Chat[(int64_t)(x0 + hc) * M + hk]))
+                           : 0.f;
         }
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -442,7 +478,8 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
             a[cc * ld + sidx<MC>(y)] = v[i];
         }
         __syncthreads();
-        res = fft_block<MC, false, BPT>(a, b, fp, cpc, ld, tw);
+        fft_pow2<MC, false, BPT, MODE == 1>(a, ld, tw);
+        res = a;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int e = threadIdx.x + i * blockDim.x;
@@ -469,7 +506,13 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
     }
     __syncthreads();
     float2* other = res == a ? b : a;
-    float2* res2 = fft_block<MC, true, BPT>(res, other, fp, cpc, ld, tw);
+    float2* res2;
+    if constexpr (MC > 0) {
+        fft_pow2<MC, true, BPT, MODE == 1>(res, ld, tw);
+        res2 = res;
+    } else {
+        res2 = fft_block<MC, true, BPT>(res, other, fp, cpc, ld, tw);
+    }
     for (int e = threadIdx.x; e < cpc * n_out; e += blockDim.x) {
         const int y = e / cpc, cc = e - y * cpc;
         if (cc < nc) X[(int64_t)y * M + x0 + cc] = res2[cc * ld + sidx<MC>(y)];
