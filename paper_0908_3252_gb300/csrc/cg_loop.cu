@@ -90,9 +90,12 @@ struct Geo {
     static constexpr int RPC = 4 * kLoopThreads / MC;  // rows per FFT group: RPC * MC = 4 * threads
     static constexpr int CBPT = MC >= 256 ? 2 : 1;     // column groups: CBPT butterflies per thread
     static constexpr int CPC = CBPT * RPC;
+    // the wide column group (twice the butterflies per thread), when it fits
+    static constexpr int CBPT2 = CBPT;  // (wider column groups spill registers)
+    static constexpr int CPC2 = CBPT2 * RPC;
     static constexpr int LDR = fftd::seq_len<MC>(MC);
     static constexpr int LDC = LDR + 4;
-    static constexpr int FBUF = RPC * LDR > CPC * LDC ? RPC * LDR : CPC * LDC;
+    static constexpr int FBUF = 2 * RPC * LDR > CPC2 * LDC ? 2 * RPC * LDR : CPC2 * LDC;
     static constexpr int TW = (fftd::staged_twiddles_size(MC) + 1) & ~1;  // keeps 16-byte alignment
 };
 
@@ -200,7 +203,8 @@ struct Rows {
 
 // Step (unless FIRST), gradient and the six update sums over the own rows
 // (the sums of cgd::update_pixel); with do_fft the row FFTs of g go to X.
-template <int MC, bool FIRST>
+// Rows go through the FFT RX * RPC at a time (RX butterflies per thread).
+template <int MC, bool FIRST, int RX>
 __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
                                              float2* cf,
                                              const float2* cd, float2* cTf, const float2* cD, float2* cg,
@@ -217,10 +221,10 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
         for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) cTf[e] = cgd::f2axpy(t, cTd[e], cTf[e]);
         __syncthreads();
     }
-    for (int g0 = 0; g0 < R.nown; g0 += G::RPC) {
-        const int nr = min(G::RPC, R.nown - g0);
+    for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
+        const int nr = min(RX * G::RPC, R.nown - g0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 4 * RX; ++i) {
             const int e = threadIdx.x + i * kLoopThreads;
             const int q = e / MC, m = e - q * MC;
             float2 gp = make_float2(0.f, 0.f);
@@ -250,9 +254,9 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
         }
         if (do_fft) {
             __syncthreads();
-            fftd::fft_pow2<MC, false, 1, true>(fbuf, G::LDR, stw);
+            fftd::fft_pow2<MC, false, RX, true>(fbuf, G::LDR, stw);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 4 * RX; ++i) {
                 const int e = threadIdx.x + i * kLoopThreads;
                 const int q = e / MC, m = e - q * MC;
                 if (q < nr) A.X[(int64_t)(R.R0 + g0 + q) * MC + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
@@ -264,9 +268,10 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
 
 // ---------------------------------------------------------------- phase C
 
-// Row IFFTs of Y (in X) -> T d of the own rows; the new direction on every
-// cached row; the four sums of the first line-search step.
-template <int MC>
+// Row IFFTs of Y (in X) -> T d of the own rows, RX * RPC rows at a time; the
+// new direction on every cached row; the four sums of the first line-search
+// step.
+template <int MC, int RX>
 __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
                                            const float2* cf,
                                            float2* cd, const float2* cTf, const float2* cD, const float2* cg,
@@ -274,23 +279,23 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 {
     using G = Geo<MC>;
     const int N = R.N;
-    for (int g0 = 0; g0 < R.nown; g0 += G::RPC) {
-        const int nr = min(G::RPC, R.nown - g0);
-        float2 v[4];
+    for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
+        const int nr = min(RX * G::RPC, R.nown - g0);
+        float2 v[4 * RX];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 4 * RX; ++i) {
             const int e = threadIdx.x + i * kLoopThreads;
             const int q = e / MC, m = e - q * MC;
             v[i] = q < nr ? __ldcg(A.X + (int64_t)(R.R0 + g0 + q) * MC + m) : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 4 * RX; ++i) {
             const int e = threadIdx.x + i * kLoopThreads;
             const int q = e / MC, m = e - q * MC;
             fbuf[q * G::LDR + fftd::sidx<MC>(m)] = v[i];
         }
         __syncthreads();
-        fftd::fft_pow2<MC, true, 1, true>(fbuf, G::LDR, stw);
+        fftd::fft_pow2<MC, true, RX, true>(fbuf, G::LDR, stw);
         for (int e = threadIdx.x; e < nr * N; e += kLoopThreads) {
             const int q = e / N, m = e - q * N;
             cTd[(g0 + q) * N + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
@@ -365,7 +370,11 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     float2* cD = cTf + RB * N;
     float2* cg = cD + RB * N;
     float2* cTd = cg + RB * N;
-    const int col_groups = MC / G::CPC;
+    // column groups: the wide ones when every block still gets one
+    const bool wide_cols = G::CBPT2 > G::CBPT && MC / G::CPC2 >= (int)gridDim.x;
+    const int cpc = wide_cols ? G::CPC2 : G::CPC;
+    const int col_groups = MC / cpc;
+    const bool rx2 = RB >= 2 * G::RPC;  // rows: two FFT groups per batch
     const bool prof = blockIdx.x == 0;
     unsigned seq = 0;
     if (threadIdx.x == 0) {
@@ -399,7 +408,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     // ---- gradient at x0, J(x0); the first direction is -g (beta = 0)
     {
         float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        phase_update<MC, true>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+        if (rx2)
+            phase_update<MC, true, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+        else
+            phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
         if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
         if (threadIdx.x == 0) {
             double J, beta;
@@ -420,9 +432,13 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         const bool restart = S.restart != 0;
         // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
-            const int x0 = gi * G::CPC;
-            fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, G::CPC, G::CPC, A.fp, stw, A.Chat, fbuf, nullptr,
-                                            A.Xd, beta, restart);
+            const int x0 = gi * cpc;
+            if (wide_cols)
+                fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
+                                                 beta, restart);
+            else
+                fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
+                                                beta, restart);
             __syncthreads();  // the next group refills fbuf
         }
         mark(0);
@@ -431,7 +447,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         // ---- C: rows, direction, first line-search sums
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            phase_rows<MC>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+            if (rx2)
+                phase_rows<MC, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+            else
+                phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
             mark(2);
             if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
@@ -461,7 +480,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         // ---- A: step, gradient, row FFTs of g for the next iteration
         {
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            phase_update<MC, false>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+            if (rx2)
+                phase_update<MC, false, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+            else
+                phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
             if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
