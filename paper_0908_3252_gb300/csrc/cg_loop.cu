@@ -43,6 +43,7 @@
 
 #include "cg_device.cuh"
 #include "fft_device.cuh"
+#include "fft_reg.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -95,8 +96,18 @@ struct Geo {
     static constexpr int CPC2 = CBPT2 * RPC;
     static constexpr int LDR = fftd::seq_len<MC>(MC);
     static constexpr int LDC = LDR + 4;
-    static constexpr int FBUF = 2 * RPC * LDR > CPC2 * LDC ? 2 * RPC * LDR : CPC2 * LDC;
-    static constexpr int TW = (fftd::staged_twiddles_size(MC) + 1) & ~1;  // keeps 16-byte alignment
+    // M = 1024: the column pass runs one column per warp as a four-step
+    // 32 x 32 FFT (cols_fourstep), FS_COLS columns per group, each column's
+    // shared-memory area LDF long (the 32 x 33 transpose, odd row stride)
+    static constexpr bool FOURSTEP = MC == 1024;
+    static constexpr int FS_COLS = 8;
+    static constexpr int LDF = 1058;
+    static constexpr int FB_ROWS = 2 * RPC * LDR;
+    static constexpr int FB_COLS = FOURSTEP ? FS_COLS * LDF : CPC2 * LDC;
+    static constexpr int FBUF = FB_ROWS > FB_COLS ? FB_ROWS : FB_COLS;
+    // staged radix-4 twiddles, then (four-step) the 32 x 32 table w^(k1 l)
+    static constexpr int TW_R4 = (fftd::staged_twiddles_size(MC) + 1) & ~1;  // keeps 16-byte alignment
+    static constexpr int TW = TW_R4 + (FOURSTEP ? 1024 : 0);
 };
 
 // dynamic shared memory of a block owning RB rows of an N-wide image: the
@@ -198,6 +209,92 @@ struct Rows {
     __device__ __forceinline__ int cache(int r) const { return (r - R0 + 1) * N; }  // row offset in cf, cd
     __device__ __forceinline__ bool own(int r) const { return r >= R0 && r < R0 + nown; }
 };
+
+// ------------------------------------------------- phase B, M = 1024
+
+// Columns [x0, x0 + 8) of the M = 1024 Toeplitz pass, one warp per column.
+// The block loads the 8 columns of X (row FFTs of g) and Xd (of the old
+// direction) as 64-byte row pieces, forms Xd = -X + beta Xd (-X on a
+// restart), stores it, and parks the columns in shared memory.  Warp c then
+// holds element n = lane + 32 j of its column in register j and runs
+//   DFT over j (registers) -> x w^(lane k1) -> transpose (shared, this warp's
+//   area) -> DFT over the registers = X[lane + 32 k2], k2 bit-reversed
+// times Chat, and the same steps with conjugate twiddles backwards (DIT first,
+// so the bit-reversed order is consumed in place).  Rows < n_in of the result
+// go back to X.  t2[k1 * 32 + l] = w^(k1 l), w = exp(-2 pi i / 1024).
+__device__ __forceinline__ void cols_fourstep(float2* X, float2* Xd, int n_in, int x0, const float* __restrict__ Chat,
+                                              const float2* t2, float2* fbuf, float beta, bool restart)
+{
+    constexpr int M = 1024, COLS = 8, LDF = 1058;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        // 8 columns x 512 rows (rows >= n_in are zero), 8 per thread
+        float2 v[8], o[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kLoopThreads;
+            const int y = e >> 3, cc = e & 7;
+            const bool in = y < n_in;
+            v[i] = in ? __ldcg(X + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
+            o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int e = tid + i * kLoopThreads;
+            const int y = e >> 3, cc = e & 7;
+            if (y < n_in) {
+                v[i] = fftd::new_direction(v[i], o[i], beta, restart);
+                Xd[(int64_t)y * M + x0 + cc] = v[i];
+            }
+            fbuf[cc * LDF + y] = v[i];
+        }
+    }
+    __syncthreads();
+    if (warp < COLS) {
+        float2* area = fbuf + warp * LDF;
+        const float* ch = Chat + (int64_t)(x0 + warp) * M;
+        float2 x[32];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = area[lane + 32 * j];
+        __syncwarp();
+        // forward: DFT over registers, twiddles, transpose, DFT over registers
+        freg::dft32_dif<false, true>(x);
+#pragma unroll
+        for (int k1 = 0; k1 < 32; ++k1) area[k1 * 33 + lane] = cmul(x[freg::bitrev5(k1)], t2[k1 * 32 + lane]);
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
+        __syncwarp();
+        float h[32];
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) h[k2] = __ldcg(ch + lane + 32 * k2);
+        freg::dft32_dif<false>(x);  // X[lane + 32 k2] in x[bitrev5(k2)]
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+            float2& r = x[freg::bitrev5(k2)];
+            r = make_float2(r.x * h[k2], r.y * h[k2]);
+        }
+        // inverse: DIT over registers (bit-reversed in), conjugate twiddles,
+        // transpose, DIF over registers
+        freg::dft32_dit<true>(x);
+#pragma unroll
+        for (int m1 = 0; m1 < 32; ++m1) area[m1 * 33 + lane] = cmul(x[m1], conjf2(t2[m1 * 32 + lane]));
+        __syncwarp();
+#pragma unroll
+        for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
+        __syncwarp();
+        freg::dft32_dif<true>(x);  // y[lane + 32 m2] in x[bitrev5(m2)]
+#pragma unroll
+        for (int m2 = 0; m2 < 16; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int e = tid + i * kLoopThreads;
+        const int y = e >> 3, cc = e & 7;
+        if (y < n_in) X[(int64_t)y * M + x0 + cc] = fbuf[cc * LDF + y];
+    }
+}
 
 // ---------------------------------------------------------------- phase A
 
@@ -372,7 +469,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     float2* cTd = cg + RB * N;
     // column groups: the wide ones when every block still gets one
     const bool wide_cols = G::CBPT2 > G::CBPT && MC / G::CPC2 >= (int)gridDim.x;
-    const int cpc = wide_cols ? G::CPC2 : G::CPC;
+    const int cpc = G::FOURSTEP ? G::FS_COLS : wide_cols ? G::CPC2 : G::CPC;
     const int col_groups = MC / cpc;
     const bool rx2 = RB >= 2 * G::RPC;  // rows: two FFT groups per batch
     const bool prof = blockIdx.x == 0;
@@ -393,6 +490,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     // ---- caches: twiddles, f of the cached rows, T f and D of the own rows
     {
         fftd::build_staged_twiddles<MC>(A.tw, stw);
+        if constexpr (G::FOURSTEP)
+            for (int e = threadIdx.x; e < 1024; e += kLoopThreads)
+                stw[G::TW_R4 + e] = __ldg(A.tw + (((e >> 5) * (e & 31)) & (MC - 1)));
         const int nc = (R.hhi - R.hlo + 1) * N;
         const float2* src = A.f0 + (int64_t)R.hlo * N;
         float2* dst = cf + R.cache(R.hlo);
@@ -433,7 +533,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * cpc;
-            if (wide_cols)
+            if constexpr (G::FOURSTEP)
+                cols_fourstep(A.X, A.Xd, N, x0, A.Chat, stw + G::TW_R4, fbuf, beta, restart);
+            else if (wide_cols)
                 fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
                                                  beta, restart);
             else

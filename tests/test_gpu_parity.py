@@ -276,3 +276,42 @@ def test_persistent_loop_matches_kernel_graph(sp, monkeypatch):
         assert rel(J, Jo) < 1e-5, mode
         assert rel(x, xo) < ITER_TOL, mode
     assert rel(res["loop"][1], res["graph"][1]) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def w260():
+    """A ragged 260x260 image (M = 1024: the loop's four-step column pass,
+    4-row blocks, the last block holding fewer rows) with 2100 samples."""
+    N = 260
+    g = synth.rng(21)
+    f_true = synth.phantom(N, "ellipses_phase", g)
+    kx, ky = synth.spiral(N, 3, 700, "variable")
+    s = c64(synth.add_noise(O.forward(kx, ky, f_true), 30.0, g))
+    reg = O.Reg(0.05, 0.05, 0.01, 0.1, O.PHI_HUBER)
+    w = dict(N=N, kx=kx, ky=ky, f_true=f_true, s=s, reg=reg, iters=3)
+    xo, Jo, _ = O.solve(kx, ky, s, reg, np.zeros((N, N)), 3)
+    return w, xo, Jo
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_persistent_loop_m1024(sp, monkeypatch, w260, prec):
+    """The M = 1024 persistent loop and the stand-alone kernel graph against
+    the oracle after 3 iterations, and against each other."""
+    w, xo, Jo = w260
+    N, reg = w["N"], w["reg"]
+    res = {}
+    for mode in ("loop", "graph"):
+        if mode == "graph":
+            monkeypatch.setenv("SPIREC_NO_LOOP", "1")
+        else:
+            monkeypatch.delenv("SPIREC_NO_LOOP", raising=False)
+        with _plan(sp, w, prec, M=1024) as p:
+            assert p.M == 1024
+            sp.spirec_set_data(p.h, w["s"])
+            sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+            res[mode] = sp.spirec_solve(p.h, None, w["iters"], N)
+    for mode, (x, J) in res.items():
+        assert np.all(np.diff(J) <= 1e-6 * J[0]), mode
+        assert rel(J, Jo) < TOL[prec], mode
+        assert rel(x, xo) < TOL[prec], mode
+    assert rel(res["loop"][0], res["graph"][0]) < TOL[prec]
