@@ -212,6 +212,27 @@ struct Rows {
 
 // ------------------------------------------------- phase B, M = 1024
 
+// One warp: the length-1024 DFT (conjugate twiddles when INV) of the
+// sequence whose element lane + 32 j is in x[j], as four steps: DFT over the
+// registers, twiddles w^(lane k1) from t2, transpose through this warp's
+// shared area (32 x 33), DFT over the registers.  Element lane + 32 k2 of the
+// result ends in x[bitrev5(k2)].
+template <bool INV>
+__device__ __forceinline__ void fourstep1024(float2 (&x)[32], float2* area, const float2* t2, int lane)
+{
+    freg::dft32_dif<INV>(x);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) {
+        const float2 w = t2[k1 * 32 + lane];
+        area[k1 * 33 + lane] = cmul(x[freg::bitrev5(k1)], INV ? conjf2(w) : w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
+    __syncwarp();
+    freg::dft32_dif<INV>(x);
+}
+
 // Columns [x0, x0 + 8) of the M = 1024 Toeplitz pass, one warp per column.
 // The block loads the 8 columns of X (row FFTs of g) and Xd (of the old
 // direction) as 64-byte row pieces, forms Xd = -X + beta Xd (-X on a
@@ -376,7 +397,28 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 {
     using G = Geo<MC>;
     const int N = R.N;
-    for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
+    if constexpr (G::FOURSTEP) {
+        // one warp per row (at most FS_COLS warps: one shared area each): the
+        // rows of Y -> T d (columns < N)
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int g0 = 0; g0 < R.nown; g0 += G::FS_COLS) {
+            const int q = g0 + warp;
+            if (warp < G::FS_COLS && q < R.nown) {
+                const float2* yr = A.X + (int64_t)(R.R0 + q) * MC;
+                float2 x[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) x[j] = __ldcg(yr + lane + 32 * j);
+                fourstep1024<true>(x, fbuf + warp * G::LDF, stw + G::TW_R4, lane);
+#pragma unroll
+                for (int m2 = 0; m2 < 16; ++m2) {
+                    const int m = lane + 32 * m2;
+                    if (m < N) cTd[q * N + m] = x[freg::bitrev5(m2)];
+                }
+            }
+            __syncwarp();  // the area is reused by the next row of this warp
+        }
+    }
+    for (int g0 = 0; g0 < (G::FOURSTEP ? 0 : R.nown); g0 += RX * G::RPC) {
         const int nr = min(RX * G::RPC, R.nown - g0);
         float2 v[4 * RX];
 #pragma unroll
