@@ -278,35 +278,47 @@ def test_persistent_loop_matches_kernel_graph(sp, monkeypatch):
     assert rel(res["loop"][1], res["graph"][1]) < 1e-5
 
 
-@pytest.fixture(scope="module")
-def w260():
-    """A ragged 260x260 image (M = 1024: the loop's four-step column pass,
-    4-row blocks, the last block holding fewer rows) with 2100 samples."""
-    N = 260
-    g = synth.rng(21)
-    f_true = synth.phantom(N, "ellipses_phase", g)
-    kx, ky = synth.spiral(N, 3, 700, "variable")
-    s = c64(synth.add_noise(O.forward(kx, ky, f_true), 30.0, g))
-    reg = O.Reg(0.05, 0.05, 0.01, 0.1, O.PHI_HUBER)
-    w = dict(N=N, kx=kx, ky=ky, f_true=f_true, s=s, reg=reg, iters=3)
-    xo, Jo, _ = O.solve(kx, ky, s, reg, np.zeros((N, N)), 3)
-    return w, xo, Jo
+_LARGE = {}
+
+
+def _large_case(N, I, S, seed):
+    """A ragged large image and its 3-iteration oracle solve (cached)."""
+    key = (N, I, S, seed)
+    if key not in _LARGE:
+        g = synth.rng(seed)
+        f_true = synth.phantom(N, "ellipses_phase", g)
+        kx, ky = synth.spiral(N, I, S, "variable")
+        s = c64(synth.add_noise(O.forward(kx, ky, f_true), 30.0, g))
+        reg = O.Reg(0.05, 0.05, 0.01, 0.1, O.PHI_HUBER)
+        w = dict(N=N, kx=kx, ky=ky, f_true=f_true, s=s, reg=reg, iters=3)
+        xo, Jo, _ = O.solve(kx, ky, s, reg, np.zeros((N, N)), 3)
+        _LARGE[key] = (w, xo, Jo)
+    return _LARGE[key]
+
+
+# (N, M, interleaves, samples): the M = 1024 loop (four-step column pass,
+# 4-row blocks, a last block with fewer rows), the M = 512 loop (radix-4
+# passes, 4-row groups), and M = 2048, whose row caches do not fit a block:
+# the solve falls back to the kernel graph
+LARGE_CASES = [(260, 1024, 3, 700, 21), (200, 512, 3, 500, 31), (520, 2048, 2, 400, 41)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_persistent_loop_m1024(sp, monkeypatch, w260, prec):
-    """The M = 1024 persistent loop and the stand-alone kernel graph against
-    the oracle after 3 iterations, and against each other."""
-    w, xo, Jo = w260
-    N, reg = w["N"], w["reg"]
+@pytest.mark.parametrize("case", LARGE_CASES, ids=lambda c: f"N{c[0]}_M{c[1]}")
+def test_large_images_loop_and_graph(sp, monkeypatch, case, prec):
+    """Persistent loop (or its fallback) and the stand-alone kernel graph
+    against the oracle after 3 iterations, and against each other."""
+    N, M, I, S, seed = case
+    w, xo, Jo = _large_case(N, I, S, seed)
+    reg = w["reg"]
     res = {}
     for mode in ("loop", "graph"):
         if mode == "graph":
             monkeypatch.setenv("SPIREC_NO_LOOP", "1")
         else:
             monkeypatch.delenv("SPIREC_NO_LOOP", raising=False)
-        with _plan(sp, w, prec, M=1024) as p:
-            assert p.M == 1024
+        with _plan(sp, w, prec, M=M) as p:
+            assert p.M == M
             sp.spirec_set_data(p.h, w["s"])
             sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
             res[mode] = sp.spirec_solve(p.h, None, w["iters"], N)
