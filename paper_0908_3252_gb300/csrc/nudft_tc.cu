@@ -583,21 +583,26 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
 // out[i][c] = scale * 2^e * (sum of the partials of tile(i, c) in CTA order);
 // 2^e undoes the weight scaling.  The CTAs holding units of tile t are
 // c_lo..c_hi, the last CTAs whose ranges start at or before the tile's first
-// and last unit; CTA c keeps its partial of tile t in slot c + t.
-__global__ void k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K, int64_t P, int R, int C,
-                            int tilesC, float scale, const unsigned* __restrict__ amax2, float2* __restrict__ out)
+// and last unit; CTA c keeps its partial of tile t in slot c + t.  A block
+// sums a 32 x 32 patch: reads run down the rows of the column-major partials,
+// the patch turns in shared memory, writes run along the rows of out.
+__global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
+                                                   int R, int C, int tilesC, float scale,
+                                                   const unsigned* __restrict__ amax2, float2* __restrict__ out)
 {
+    __shared__ float2 patch[32][33];
     float sc = scale;
     if (amax2) sc = scale / weight_scale_inv(amax2);
-    const int64_t RC = (int64_t)R * C;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < RC;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        // consecutive threads walk down a column (rows are contiguous in a tile)
-        const int c = (int)(e / R), i = (int)(e - (int64_t)c * R);
-        const int64_t t = (int64_t)(i / TC_ROWS) * tilesC + c / TC_COLS;
-        const int row = i % TC_ROWS, col = c % TC_COLS;
-        const int64_t c_lo = ((t * K + 1) * P - 1) / U;
-        const int64_t c_hi = ((t + 1) * K * P - 1) / U;
+    const int i0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int64_t t = (int64_t)(i0 / TC_ROWS) * tilesC + c0 / TC_COLS;
+    const int64_t c_lo = ((t * K + 1) * P - 1) / U;
+    const int64_t c_hi = ((t + 1) * K * P - 1) / U;
+    const int row = (i0 % TC_ROWS) + tx;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int cl = ty + 8 * j;
+        const int col = (c0 % TC_COLS) + cl;
         float ar = 0.f, ai = 0.f;
         for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
             if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
@@ -605,7 +610,13 @@ __global__ void k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K
             ar += pt[col * TC_ROWS + row];
             ai += pt[(TC_COLS + col) * TC_ROWS + row];
         }
-        out[(int64_t)i * C + c] = make_float2(ar * sc, ai * sc);
+        patch[cl][tx] = make_float2(ar * sc, ai * sc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = i0 + ty + 8 * j, c = c0 + tx;
+        if (i < R && c < C) out[(int64_t)i * C + c] = patch[tx][ty + 8 * j];
     }
 }
 
@@ -642,7 +653,6 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
         set_error("partial buffer too small for %lld tiles", (long long)T);
         return SPIREC_EUNSUPPORTED;
     }
-    const int64_t RC = (int64_t)R * C;
     unsigned* amax = nullptr;
     if (w && w != p->s) {
         // the kernel reads padded, plan-owned sample arrays
@@ -674,9 +684,8 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
         k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
             ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     SPIREC_CK(cudaGetLastError());
-    int rblocks = (int)((RC + 255) / 256);
-    if (rblocks > 4 * kMaxCtas) rblocks = 4 * kMaxCtas;
-    k_reduce_tc<<<rblocks, 256, 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
+    const dim3 rgrid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
+    k_reduce_tc<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
     SPIREC_CK(cudaGetLastError());
     p->launches += 2;
     return SPIREC_OK;
