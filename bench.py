@@ -115,6 +115,59 @@ def run_batch(spirec, prec, frames=64, iters=50, seed=4):
             "what": "per frame: trajectory (G, spectrum), data (D), 50 CG iterations; one stream per frame"}
 
 
+def run_paper_experiment(spirec, prec, iters=50, reps=20):
+    """The paper's simulated experiment (section 4.1) with a stand-in for its
+    phantom: 128 x 128 two-vessel image (intensity ~255), 6 spiral arms x 512
+    samples, 30 dB, Huber phi with lambda1 = 0.1, alpha1 = 20, lambda0 = 0.5,
+    alpha0 = 10, 50 iterations.  The paper's figures of merit (quadratic
+    error in ROI1, variance in ROI2) for that reconstruction and for the
+    unregularized one, and the solve rate (trajectory, data and 50
+    iterations per reconstruction)."""
+    import torch
+    from paper_0908_3252_gb300 import synth
+    N = 128
+    f, roi = synth.vessels(N)
+    kx, ky = synth.spiral(N, 6, 512, "archimedean")
+    L = kx.shape[0]
+    st = torch.cuda.Stream()
+    p = spirec.Plan(N, L, 0, prec, st.cuda_stream)
+    kx_d, ky_d = torch.from_numpy(kx).cuda(), torch.from_numpy(ky).cuda()
+    torch.cuda.synchronize()
+    spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
+    y = torch.zeros(L, dtype=torch.complex64, device="cuda")
+    spirec.spirec_forward_dev(p.h, torch.from_numpy(f.astype(np.complex64)).cuda(), y)
+    spirec.spirec_sync(p.h)
+    s_d = torch.from_numpy(synth.add_noise(y.cpu().numpy().astype(np.complex128), 30.0, synth.rng(51))
+                           .astype(np.complex64)).cuda()
+    x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    J = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+    out = {"N": N, "samples": L, "iters": iters}
+    for name, reg in (("regularized", (0.1, 20.0, 0.5, 10.0, 0)), ("unregularized", (0.0, 20.0, 0.0, 10.0, 0))):
+        spirec.spirec_set_reg(p.h, *reg)
+        with torch.cuda.stream(st):
+            spirec.spirec_set_data_dev(p.h, s_d)
+            spirec.spirec_solve_dev(p.h, None, iters, x, J)
+        torch.cuda.synchronize()
+        xr = x.cpu().numpy().astype(np.complex128)
+        err = float(np.sum(np.abs(xr - f)[roi["roi1"]] ** 2) / np.sum(np.abs(f)[roi["roi1"]] ** 2))
+        out[name] = {"roi1_quadratic_error": err, "roi2_variance": float(np.var(np.abs(xr)[roi["roi2"]]))}
+    spirec.spirec_set_reg(p.h, 0.1, 20.0, 0.5, 10.0, 0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
+        spirec.spirec_set_data_dev(p.h, s_d)
+        spirec.spirec_solve_dev(p.h, None, iters, x, J)
+    e1.record(st)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1000.0 / reps
+    p.close()
+    out["ms_per_reconstruction"] = dt * 1e3
+    out["iters_per_s"] = iters / dt
+    return out
+
+
 def run_serving(spirec, prec, requests=200, rate=200.0, iters=50, seed=5, slots=8):
     """Poisson request stream: sizes N in {64..384} step 64, L uniform in
     [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
@@ -459,6 +512,8 @@ def run_ours(args):
     # ---- many reconstructions: batched dynamic series and a served stream
     if not args.no_batch:
         extra["batch"] = run_batch(spirec, prec)
+    if not args.no_paper_experiment:
+        extra["paper_experiment"] = run_paper_experiment(spirec, prec)
     if not args.no_serving:
         extra["serving"] = run_serving(spirec, prec)
         if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
@@ -557,6 +612,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame dynamic-series batch")
     ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
+    ap.add_argument("--no-paper-experiment", action="store_true",
+                    help="skip the 128x128 two-vessel experiment with the paper's hyperparameters")
     ap.add_argument("--samples", type=int, default=4096,
                     help="samples per interleave (4096 = the metric's 131072-sample spiral)")
     ap.add_argument("--iters", type=int, default=50, help="CG iterations per step (50 = the metric's)")

@@ -8,6 +8,7 @@ recipes below stand in for them with the same kind of structure:
 
 * ellipse phantoms (additive ellipses, optional smooth complex phase),
 * bars of 2-4 px width at random orientations plus fine texture,
+* two vessels with parabolic and blunt flow phase on a variable background,
 * Archimedean, variable-density and golden-angle interleaved spirals with
   |k| <= 0.5 cycles/pixel (section 2 normalises k to [-0.5, 0.5]),
 * circular complex Gaussian noise scaled to an SNR in dB.
@@ -90,6 +91,37 @@ def phantom(N: int, kind: str, g: np.random.Generator) -> np.ndarray:
         base = ellipses(N, 10, g) * smooth_phase(N, g)
         return base + bars(N, 40, g) + g.uniform(-0.05, 0.05, (N, N))
     raise ValueError(kind)
+
+
+def vessels(N: int = 128) -> tuple[np.ndarray, dict]:
+    """Two vessels on a variable background, the kind of object of the
+    paper's simulated model (section 4.1; its exact phantom is not
+    available): magnitude with homogeneous regions and sharp edges on an
+    intensity scale of about 255, zero phase outside the vessels, a parabolic
+    flow profile in one vessel and a blunt one in the other.
+
+    Background 60 + 40 x (x = m / N), a tissue square [0.3, 0.7]^2 at 120,
+    vessel 1 (parabolic) centred at (row 0.5, col 0.45), radius 0.12 N,
+    vessel 2 (blunt) at (row 0.25, col 0.75), radius 0.10 N, both at 220;
+    phase (pi/2)(1 - (r/R)^2) and (pi/2)(1 - (r/R)^8).  Returns the image and
+    two masks: 'roi1' the central square [0.35, 0.65]^2, 'roi2' the inner
+    disk (r < 0.7 R) of the blunt vessel, where the magnitude is constant."""
+    n, m = _grid(N)
+    y, x = n / N, m / N
+    mag = 60.0 + 40.0 * x
+    tissue = (np.abs(x - 0.5) <= 0.2) & (np.abs(y - 0.5) <= 0.2)
+    mag = np.where(tissue, 120.0, mag)
+    phase = np.zeros((N, N))
+    roi2 = np.zeros((N, N), bool)
+    for (cy, cx, R, power) in ((0.5, 0.45, 0.12, 2), (0.25, 0.75, 0.10, 8)):
+        r = np.hypot(y - cy, x - cx) / R
+        inside = r <= 1.0
+        mag = np.where(inside, 220.0, mag)
+        phase = np.where(inside, 0.5 * np.pi * (1.0 - r ** power), phase)
+        if power == 8:
+            roi2 = r < 0.7
+    roi1 = (np.abs(x - 0.5) <= 0.15) & (np.abs(y - 0.5) <= 0.15)
+    return mag * np.exp(1j * phase), {"roi1": roi1, "roi2": roi2}
 
 
 def spiral(N: int, interleaves: int, samples: int, kind: str = "archimedean",
