@@ -168,6 +168,39 @@ def run_paper_experiment(spirec, prec, iters=50, reps=20):
     return out
 
 
+def run_direct_mode(spirec, prec, w, s_host):
+    """The paper's claim for its rewriting (section 3.4): the cost of one CG
+    iteration when H^H H is applied by the Toeplitz FFT convolution against
+    the original formulation, which applies the exact forward and adjoint
+    NUDFT every iteration (SPIREC_MODE_DIRECT).  Steady state, per
+    iteration: (time of a 10-iteration solve - time of a 2-iteration solve) / 8,
+    on the metric's 512^2 workload with G, Chat and D in place."""
+    import torch
+    N, M, L = w["N"], w["M"], w["kx"].shape[0]
+    st = torch.cuda.Stream()
+    p = spirec.Plan(N, L, M, prec, st.cuda_stream, w["kx"], w["ky"])
+    spirec.spirec_set_data(p.h, s_host)
+    spirec.spirec_set_reg(p.h, w["lambda1"], w["alpha1"], w["lambda0"], w["alpha0"], w["phi"])
+    x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    out = {}
+    for name, mode in (("toeplitz", spirec.SPIREC_MODE_TOEPLITZ), ("direct", spirec.SPIREC_MODE_DIRECT)):
+        spirec.spirec_set_mode(p.h, mode)
+        t = {}
+        for iters in (2, 10, 2, 10):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            spirec.spirec_solve_dev(p.h, None, iters, x, None)
+            e1.record(st)
+            torch.cuda.synchronize()
+            t[iters] = e0.elapsed_time(e1)  # the second (warm) run of each count stays
+        out[name + "_ms_per_iter"] = (t[10] - t[2]) / 8.0
+    p.close()
+    out["rewriting_speedup"] = out["direct_ms_per_iter"] / out["toeplitz_ms_per_iter"]
+    return out
+
+
 def run_serving(spirec, prec, requests=200, rate=200.0, iters=50, seed=5, slots=8):
     """Poisson request stream: sizes N in {64..384} step 64, L uniform in
     [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
@@ -514,6 +547,8 @@ def run_ours(args):
         extra["batch"] = run_batch(spirec, prec)
     if not args.no_paper_experiment:
         extra["paper_experiment"] = run_paper_experiment(spirec, prec)
+    if not args.no_direct:
+        extra["direct_mode"] = run_direct_mode(spirec, prec, w, s)
     if not args.no_serving:
         extra["serving"] = run_serving(spirec, prec)
         if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
@@ -612,6 +647,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame dynamic-series batch")
     ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
+    ap.add_argument("--no-direct", action="store_true",
+                    help="skip the per-iteration comparison with the direct (non-rewritten) formulation")
     ap.add_argument("--no-paper-experiment", action="store_true",
                     help="skip the 128x128 two-vessel experiment with the paper's hyperparameters")
     ap.add_argument("--samples", type=int, default=4096,

@@ -147,6 +147,18 @@ int spirec_solve(spirec_plan plan, const float* x0, int32_t iters, float* x_out,
 int spirec_solve_dev(spirec_plan plan, const float* x0, int32_t iters, float* x_out,
                      double* J_hist);
 
+/* How solve applies the normal operator H^H H to the direction each
+ * iteration.  SPIREC_MODE_TOEPLITZ (the default, section 3.4 and Appendix B):
+ * by the M x M zero-padded FFT convolution with the kernel spectrum built
+ * once from G.  SPIREC_MODE_DIRECT (the original formulation, Eq. CritLS): by
+ * the exact forward and adjoint NUDFT, T d = H^H (H d), every iteration (on
+ * the tensor cores for the mixed precisions); the minimiser and its results
+ * are the same up to rounding, the cost per iteration is that of two NUDFTs.
+ * SPIREC_EINVAL for another value.  Takes effect at the next solve. */
+#define SPIREC_MODE_TOEPLITZ 0
+#define SPIREC_MODE_DIRECT 1
+int spirec_set_mode(spirec_plan plan, int32_t mode);
+
 /* ---- operator access (device pointers, enqueued on the plan's stream) ---- */
 
 /* y = H x (Eq. ModDirect): x 2N^2 floats, y 2L floats.  Needs a trajectory. */

@@ -119,7 +119,7 @@ int dalloc(spirec_plan p, T** ptr, size_t count)
 void free_plan(spirec_plan p)
 {
     if (!p) return;
-    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s,
+    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage};
     for (void* b : bufs)
@@ -324,16 +324,19 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
     const size_t img = (size_t)p->N * p->N * sizeof(float2);
     cudaEvent_t e;
     if ((rc = tstart(p, 3, &e)) != SPIREC_OK) return rc;
+    const bool direct = p->mode == SPIREC_MODE_DIRECT;
     if (x0) {
         SPIREC_CK(cudaMemcpyAsync(p->f[0], x0, img,
                                   x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-        if ((rc = launch_toeplitz(p, p->f[0], p->Tf, -1)) != SPIREC_OK) return rc;
+        if ((rc = direct ? launch_normal_direct(p, p->f[0], p->Tf, false) : launch_toeplitz(p, p->f[0], p->Tf, -1)) !=
+            SPIREC_OK)
+            return rc;
     } else {
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
     rc = SPIREC_EUNSUPPORTED;
-    if (loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
+    if (!direct && loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
         // first gradient and every iteration in one persistent kernel
         rc = launch_cg_loop(p, iters);
         if (rc != SPIREC_OK && rc != SPIREC_EUNSUPPORTED) return rc;
@@ -434,6 +437,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->cwork, (size_t)M * M));
     TRY(dalloc(p, &p->X, (size_t)N * M));
     if (loop_supported(M)) TRY(dalloc(p, &p->Xd, (size_t)N * M));
+    if ((p->fsplit_bytes = fsplit_bytes_tc(N, precision)) > 0) TRY(dalloc(p, &p->fsplit, p->fsplit_bytes));
     TRY(dalloc(p, &p->D, NN));
     TRY(dalloc(p, &p->s, (size_t)L + 32));
     TRY(dalloc(p, &p->ystage, (size_t)L + 32));
@@ -594,6 +598,26 @@ int spirec_set_reg(spirec_plan p, double lambda1, double alpha1, double lambda0,
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
     }
+    return SPIREC_OK;
+}
+
+int spirec_set_mode(spirec_plan p, int32_t mode)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (mode != SPIREC_MODE_TOEPLITZ && mode != SPIREC_MODE_DIRECT) {
+        set_error("mode must be SPIREC_MODE_TOEPLITZ or SPIREC_MODE_DIRECT, not %d", mode);
+        return SPIREC_EINVAL;
+    }
+    if (mode == SPIREC_MODE_DIRECT && !p->ydir) {
+        if ((rc = dalloc(p, &p->ydir, (size_t)p->L + 32)) != SPIREC_OK) return rc;
+    }
+    if (p->mode != mode && p->graph) {  // the captured iteration is mode-specific
+        cudaStreamSynchronize(p->stream);
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->mode = mode;
     return SPIREC_OK;
 }
 

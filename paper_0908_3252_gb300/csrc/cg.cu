@@ -163,6 +163,51 @@ int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2
     return SPIREC_OK;
 }
 
+// q2 = Re<d, T d> and the first line-search step
+//   t1 = -(q1 + num0) / (2 q2 + den0)   (0 when the curvature is not > 0),
+// as the fused row pass 3 of the FFT path computes them.
+__global__ void k_q2_t1(const float2* d, const float2* Td, int64_t n, float2* parts, unsigned* counter,
+                        double* scal)
+{
+    float v[1] = {0.f};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = __ldcg(d + i), b = __ldcg(Td + i);
+        v[0] += fmaf(a.x, b.x, a.y * b.y);
+    }
+    FF bt[1];
+    block_partial<1>(v, bt);
+    store_parts<1>(bt, parts, kMaxParts);
+    if (last_block(counter)) {
+        FF t[1];
+        sum_parts_ff<1>(parts, kMaxParts, gridDim.x, t);
+        if (threadIdx.x == 0) {
+            const double q2 = ff_to_double(t[0]);
+            scal[S_Q2] = q2;
+            const double curv = 2.0 * q2 + scal[S_DEN0];
+            scal[S_T1] = curv > 0.0 ? -(scal[S_Q1] + scal[S_NUM0]) / curv : 0.0;
+            *counter = 0u;
+        }
+    }
+}
+
+int launch_normal_direct(spirec_plan p, const float2* x, float2* Tx, bool dot_q2_t1)
+{
+    if (!p->ydir) {
+        set_error("direct mode needs spirec_set_mode first");
+        return SPIREC_ESTATE;
+    }
+    int rc;
+    if ((rc = launch_forward(p, x, p->ydir)) != SPIREC_OK) return rc;
+    if ((rc = launch_adjoint(p, p->ydir, Tx)) != SPIREC_OK) return rc;
+    if (dot_q2_t1) {
+        k_q2_t1<<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(x, Tx, (int64_t)p->N * p->N, slot(p, P_ROWC),
+                                                                  p->counters + C_ROWC, p->scal);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 1;
+    }
+    return SPIREC_OK;
+}
+
 int cg_iteration(spirec_plan p, int k, double* Jdev)
 {
     const int N = p->N;
@@ -181,12 +226,18 @@ int cg_iteration(spirec_plan p, int k, double* Jdev)
     a.parts = slot(p, P_ROWA);
     a.counter = p->counters + C_ROWA;
     a.scal = p->scal;
+    // the new direction d, q1 and the t = 0 line-search sums (with the row
+    // FFTs of d, which only the FFT path uses)
     if ((rc = launch_rows_fwd(p, nullptr, N, N, N, 1, &a)) != SPIREC_OK) return rc;
-    if ((rc = launch_cols(p, N, N)) != SPIREC_OK) return rc;
-    CgPass c = a;
-    c.parts = slot(p, P_ROWC);
-    c.counter = p->counters + C_ROWC;
-    if ((rc = launch_rows_inv(p, p->Td, 1, dk, &c, 0)) != SPIREC_OK) return rc;
+    if (p->mode == SPIREC_MODE_DIRECT) {
+        if ((rc = launch_normal_direct(p, dk, p->Td, true)) != SPIREC_OK) return rc;
+    } else {
+        if ((rc = launch_cols(p, N, N)) != SPIREC_OK) return rc;
+        CgPass c = a;
+        c.parts = slot(p, P_ROWC);
+        c.counter = p->counters + C_ROWC;
+        if ((rc = launch_rows_inv(p, p->Td, 1, dk, &c, 0)) != SPIREC_OK) return rc;
+    }
     for (int j = 1; j <= 2; ++j)
         if ((rc = launch_line_search(p, fin, dk, j)) != SPIREC_OK) return rc;
     return launch_update(p, fin, fout, dk, p->Tf, p->Td, p->g, 0, Jdev ? Jdev + k + 1 : nullptr);

@@ -134,6 +134,8 @@ struct spirec_plan_s {
     unsigned* counters;  // C_N
     double* Jdev;  // J history (device), capacity Jcap
     int Jcap;
+    uint8_t* fsplit;  // the image split into hi/lo operand tiles (tensor-core forward)
+    size_t fsplit_bytes;
     float* kpart;  // split-K partial sums of the contractions
     size_t kpart_bytes;
     size_t device_bytes;
@@ -151,6 +153,8 @@ struct spirec_plan_s {
     int graph_iters;
     int graph_parity_out;
     int result_slot;  // the last solve left its iterate in f[result_slot]
+    int mode;         // SPIREC_MODE_TOEPLITZ or SPIREC_MODE_DIRECT
+    float2* ydir;     // L (+32): H d of the direct mode
 
     // timing
     bool timing;
@@ -189,6 +193,9 @@ int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2
                   const float2* Td, float2* g, int first, double* Jout);
 int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step);
 int cg_iteration(spirec_plan p, int k, double* Jdev);
+// T x as H^H (H x) (direct mode); with dot_q2_t1 also q2 = Re<x, T x> and the
+// first line-search step into scal (as the fused row pass of the FFT path).
+int launch_normal_direct(spirec_plan p, const float2* x, float2* Tx, bool dot_q2_t1);
 // The whole loop (first gradient + iters iterations) as one persistent
 // cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only, and
 // SPIREC_EUNSUPPORTED (nothing enqueued) when the image does not fit its
@@ -199,6 +206,8 @@ int launch_cg_loop(spirec_plan p, int iters);
 // tensor-core contractions (FP16x3 / BF16x3)
 int launch_gram_tc(spirec_plan p);
 int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x);
+int launch_forward_tc(spirec_plan p, const float2* x, float2* y);
+size_t fsplit_bytes_tc(int N, int precision);  // the forward's split-image buffer
 size_t kpart_floats_tc(int N, int64_t L, int precision);  // split-K buffer need
 int tc_setup_attributes();
 

@@ -282,6 +282,7 @@ int launch_adjoint(spirec_plan p, const float2* y, float2* x)
 
 int launch_forward(spirec_plan p, const float2* x, float2* y)
 {
+    if (p->precision != SPIREC_FP32) return launch_forward_tc(p, x, y);
     const int64_t lblocks = (p->L + TN - 1) / TN;
     const int nblocks = (p->N + TM - 1) / TM;
     int ns = (int)((4 * 152 + lblocks - 1) / lblocks);

@@ -620,6 +620,265 @@ __global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ par
     }
 }
 
+// ------------------------------------------------------------ forward H f
+
+// The forward NUDFT (Hf)_l = (1/N) sum_n e^{+i2pi ky_l n} sum_m f[n][m]
+// e^{+i2pi kx_l m} (Eq. ModDirect) as the contraction
+//      P[l][m] = sum_n e^{+i2pi ky_l n} f[n][m]        (tensor cores, K = n)
+// followed by the per-sample dot product y_l = (1/N) sum_m P[l][m]
+// e^{+i2pi kx_l m}.  A tile is 128 samples (TMEM lanes) x 256 image columns
+// m, so each thread of the epilogue owns one sample and sums its own lane's
+// columns: no reduction across lanes.  A (the phases) is generated by the
+// producers; B (the image, split into hi/lo and laid out exactly as a stage
+// expects, k_split_image) arrives per stage by one 64 KB TMA bulk copy.
+// CTA c takes the sample tiles c, c + P, ...; per tile the m-tiles in order,
+// per m-tile the 32-row chunks of n.
+
+constexpr uint32_t FW_YPART = TC_STAGES * STAGE_BYTES;  // 4 x 128 float2
+constexpr uint32_t FW_BAR = FW_YPART + 4 * TC_ROWS * 8;
+constexpr uint32_t FW_SMEM = FW_BAR + 128 + 1024;
+static_assert(FW_SMEM <= 232448, "shared memory per CTA");
+constexpr uint32_t FW_BLOCK = 2 * B_BYTES;  // one m-tile x 32-row chunk: hi then lo
+
+// Image f (N x N, row n, column m) -> per (m-tile, n-chunk) block the B
+// operand of a stage: rows m (256), K = 32 values of n as [re | im], hi and
+// lo halves, 128-byte-swizzled K-major.  Rows m >= N and n >= N are zero.
+// The values are scaled by 2^-e, 2^e >= max |f| (amax2 = max |f|^2), so the
+// FP16 halves stay in range; k_tc_forward undoes the scale.
+template <bool BF16>
+__global__ void k_split_image(const float2* __restrict__ f, int N, int kchunks, const unsigned* __restrict__ amax2,
+                              uint8_t* __restrict__ FB)
+{
+    const float wmul = weight_scale_inv(amax2);
+    const int mtiles = (N + TC_COLS - 1) / TC_COLS;
+    const int64_t total = (int64_t)mtiles * TC_COLS * kchunks * 4;  // (m, chunk, group of 8 n)
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e % (mtiles * TC_COLS));  // consecutive threads: consecutive m
+        const int64_t rest = e / (mtiles * TC_COLS);
+        const int g = (int)(rest & 3), kc = (int)(rest >> 2);
+        float re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = 32 * kc + 8 * g + j;
+            const float2 v = (m < N && n < N) ? f[(int64_t)n * N + m] : make_float2(0.f, 0.f);
+            re[j] = v.x * wmul;
+            im[j] = v.y * wmul;
+        }
+        uint4 rh, rl, ih, il;
+        split8<BF16>(re, rh, rl);
+        split8<BF16>(im, ih, il);
+        const int mt = m / TC_COLS, r = m % TC_COLS;
+        uint8_t* blk = FB + ((int64_t)mt * kchunks + kc) * FW_BLOCK;
+        *reinterpret_cast<uint4*>(blk + sw128(r, g)) = rh;
+        *reinterpret_cast<uint4*>(blk + sw128(r, 4 + g)) = ih;
+        *reinterpret_cast<uint4*>(blk + B_BYTES + sw128(r, g)) = rl;
+        *reinterpret_cast<uint4*>(blk + B_BYTES + sw128(r, 4 + g)) = il;
+    }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, const uint8_t* __restrict__ FB,
+             const unsigned* __restrict__ amax2, int64_t L, int N, int kchunks, float scale, float2* __restrict__ y,
+             int* err)
+{
+    scale /= weight_scale_inv(amax2);  // undoes k_split_image's 2^-e
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar_full = sbase + FW_BAR;             // TC_STAGES: A generated and B landed
+    const uint32_t bar_empty = bar_full + 8 * TC_STAGES;  // TC_STAGES: stage consumed
+    const uint32_t bar_acc_full = bar_empty + 8 * TC_STAGES;
+    const uint32_t bar_acc_empty = bar_acc_full + 8;
+    const uint32_t misc = FW_BAR + 8 * (2 * TC_STAGES + 2);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
+    float2* ypart = reinterpret_cast<float2*>(smem + FW_YPART);  // [4 column quarters][128 samples]
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int mtiles = (N + TC_COLS - 1) / TC_COLS;
+    const int64_t ntiles = (L + TC_ROWS - 1) / TC_ROWS;
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int per_tile = mtiles * kchunks;
+    const int n = (int)(my_tiles * per_tile);
+
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(bar_full + 8 * i, TC_PRODUCERS + 1);
+            mbar_init(bar_empty + 8 * i, 1);
+        }
+        mbar_init(bar_acc_full, 1);
+        mbar_init(bar_acc_empty, TC_PRODUCERS);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == TC_PRODUCERS / 32) tmem_alloc(smem_u32(tmem_slot), 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < TC_PRODUCERS / 32) {
+        // ------------------------------------------------ producers
+        const int r = tid & 127, g = tid >> 7;  // A row (sample in the tile), group of 8 n
+        int64_t ka = 0;                          // ky of this thread's sample (fixed point)
+        int64_t cur_tile = -1;
+        float2 ysum = make_float2(0.f, 0.f);     // threads 0..127: y of sample tid over m-tiles
+        // the epilogue of the segment (tile t, m-tile mt): this warp's 64 columns
+        auto epilogue = [&](int64_t t, int mt) {
+            const int lq = warp & 3, cq = warp >> 2;
+            const int rs = 32 * lq + lane;
+            const int64_t l = t * TC_ROWS + rs;
+            const int64_t kx = l < L ? kxq[l] : 0;
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+            for (int cc = 0; cc < 64; cc += 16) {
+                float re[16], im[16];
+                const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(64 * cq + cc);
+                tmem_ld16(ta, re);
+                tmem_ld16(ta + TC_COLS, im);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 w = phasor_fast(kx, mt * TC_COLS + 64 * cq + cc + j);
+                    acc.x = fmaf(re[j], w.x, fmaf(-im[j], w.y, acc.x));
+                    acc.y = fmaf(re[j], w.y, fmaf(im[j], w.x, acc.y));
+                }
+            }
+            ypart[cq * TC_ROWS + rs] = acc;
+            producers_sync();
+            if (tid < TC_ROWS) {
+                const float2 a = ypart[tid], b = ypart[TC_ROWS + tid], c = ypart[2 * TC_ROWS + tid],
+                             d = ypart[3 * TC_ROWS + tid];
+                ysum.x += ((a.x + b.x) + c.x) + d.x;
+                ysum.y += ((a.y + b.y) + c.y) + d.y;
+                if (mt == mtiles - 1) {
+                    const int64_t lo = t * TC_ROWS + tid;
+                    if (lo < L) y[lo] = make_float2(ysum.x * scale, ysum.y * scale);
+                    ysum = make_float2(0.f, 0.f);
+                }
+            }
+        };
+        int64_t seg_t = 0;  // the segment being accumulated
+        int seg_mt = 0;
+        for (int it = 0; it < n; ++it) {
+            const int s = it % TC_STAGES;
+            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            const int64_t t = blockIdx.x + (int64_t)(it / per_tile) * gridDim.x;
+            const int rem = it % per_tile, mt = rem / kchunks, kc = rem % kchunks;
+            if (tid == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+                *abort_flag = 1;
+                atomicOr(err, kErrTimeout);
+            }
+            producers_sync();  // stage s is free
+            if (*abort_flag) break;
+            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES;
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(bar_full + 8 * s, FW_BLOCK);
+                bulk_g2s(bH, FB + ((int64_t)mt * kchunks + kc) * FW_BLOCK, FW_BLOCK, bar_full + 8 * s);
+            }
+            if (t != cur_tile) {
+                const int64_t l = t * TC_ROWS + r;
+                ka = l < L ? kyq[l] : 0;
+                cur_tile = t;
+            }
+            const bool valid = t * TC_ROWS + r < L;
+            float re[8], im[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                float2 v = phasor_fast(ka, 32 * kc + 8 * g + e);
+                if (!valid) v = make_float2(0.f, 0.f);
+                re[e] = v.x;
+                im[e] = v.y;
+            }
+            uint4 rh, rl, ih, il;
+            split8<BF16>(re, rh, rl);
+            split8<BF16>(im, ih, il);
+            st_shared_v4(aH + sw128(r, g), rh);
+            st_shared_v4(aH + sw128(r, 4 + g), ih);
+            st_shared_v4(aL + sw128(r, g), rl);
+            st_shared_v4(aL + sw128(r, 4 + g), il);
+            fence_proxy_async();
+            mbar_arrive(bar_full + 8 * s);
+            if (kc == 0) {
+                if (it > 0) {
+                    // the MMA has the first stage of a new segment queued: the
+                    // epilogue of the previous one
+                    const int j = it / kchunks - 1;
+                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+                        atomicOr(err, kErrTimeout);
+                        *abort_flag = 1;
+                    }
+                    tc_fence_after();
+                    epilogue(seg_t, seg_mt);
+                    tc_fence_before();
+                    mbar_arrive(bar_acc_empty);
+                }
+                seg_t = t;
+                seg_mt = mt;
+            }
+        }
+        if (n > 0 && !*abort_flag) {
+            const int j = n / kchunks - 1;
+            if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+                atomicOr(err, kErrTimeout);
+            } else {
+                tc_fence_after();
+                epilogue(seg_t, seg_mt);
+            }
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------ MMA issuer
+        const uint32_t fmt = BF16 ? 1u : 0u;
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idesc_neg = idesc | (1u << 13);
+        const uint32_t tre = tmem, tim = tmem + TC_COLS;
+        for (int it = 0; it < n; ++it) {
+            const int s = it % TC_STAGES;
+            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            const int kc = (it % per_tile) % kchunks;
+            const int seg = it / kchunks;
+            if (kc == 0 && seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(seg - 1) & 1)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            if (!mbar_wait(bar_full + 8 * s, use & 1)) {
+                atomicOr(err, kErrTimeout);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const uint32_t oR = 32u * kk, oI = 64u + 32u * kk;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
+                    const uint32_t A = q == 2 ? aL : aH, B = q == 1 ? bL : bH;
+                    const uint32_t acc = (kc > 0 || kk > 0 || q > 0) ? 1u : 0u;
+                    mma_f16(tre, sdesc(A + oR), sdesc(B + oR), idesc, acc);
+                    mma_f16(tre, sdesc(A + oI), sdesc(B + oI), idesc_neg, 1u);
+                    mma_f16(tim, sdesc(A + oR), sdesc(B + oI), idesc, acc);
+                    mma_f16(tim, sdesc(A + oI), sdesc(B + oR), idesc, 1u);
+                }
+            }
+            mma_commit(bar_empty + 8 * s);
+            if (kc == kchunks - 1) mma_commit(bar_acc_full);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == TC_PRODUCERS / 32) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
 // amax2 = max_l |y_l|^2 as float bits (non-negative floats order like unsigned).
 __global__ void k_absmax2(const float2* __restrict__ y, int64_t n, unsigned* amax2)
 {
@@ -693,6 +952,59 @@ int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const flo
 
 }  // namespace
 
+int launch_forward_tc(spirec_plan p, const float2* x, float2* yout)
+{
+    const int N = p->N;
+    const int kchunks = (N + TC_KS - 1) / TC_KS;
+    const int mtiles = (N + TC_COLS - 1) / TC_COLS;
+    const size_t fb_bytes = (size_t)mtiles * kchunks * FW_BLOCK;
+    if (!p->fsplit || p->fsplit_bytes < fb_bytes) {
+        set_error("plan has no split-image buffer for the forward contraction");
+        return SPIREC_ESTATE;
+    }
+    const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
+    unsigned* amax = p->counters + C_AMAX;
+    {
+        const int64_t NN = (int64_t)N * N;
+        SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
+        int blocks = (int)((NN + 255) / 256);
+        if (blocks > 4 * kMaxCtas) blocks = 4 * kMaxCtas;
+        k_absmax2<<<blocks, 256, 0, p->stream>>>(x, NN, amax);
+        SPIREC_CK(cudaGetLastError());
+        const int64_t total = (int64_t)mtiles * TC_COLS * kchunks * 4;
+        blocks = (int)((total + 255) / 256);
+        if (blocks > 8 * kMaxCtas) blocks = 8 * kMaxCtas;
+        if (bf16)
+            k_split_image<true><<<blocks, 256, 0, p->stream>>>(x, N, kchunks, amax, p->fsplit);
+        else
+            k_split_image<false><<<blocks, 256, 0, p->stream>>>(x, N, kchunks, amax, p->fsplit);
+        SPIREC_CK(cudaGetLastError());
+    }
+    int dev = 0, sms = 0;
+    SPIREC_CK(cudaGetDevice(&dev));
+    SPIREC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t ntiles = (p->L + TC_ROWS - 1) / TC_ROWS;
+    int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
+    if (P > ntiles) P = ntiles;
+    const float scale = 1.0f / (float)N;
+    if (bf16)
+        k_tc_forward<true><<<(unsigned)P, TC_THREADS, FW_SMEM, p->stream>>>(p->kxq, p->kyq, p->fsplit, amax, p->L,
+                                                                           N, kchunks, scale, yout, p->dflag);
+    else
+        k_tc_forward<false><<<(unsigned)P, TC_THREADS, FW_SMEM, p->stream>>>(p->kxq, p->kyq, p->fsplit, amax,
+                                                                            p->L, N, kchunks, scale, yout, p->dflag);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 3;
+    return SPIREC_OK;
+}
+
+size_t fsplit_bytes_tc(int N, int precision)
+{
+    if (precision == SPIREC_FP32) return 0;
+    const size_t kchunks = (size_t)(N + TC_KS - 1) / TC_KS, mtiles = (size_t)(N + TC_COLS - 1) / TC_COLS;
+    return mtiles * kchunks * FW_BLOCK;
+}
+
 size_t kpart_floats_tc(int N, int64_t, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
@@ -707,6 +1019,8 @@ int tc_setup_attributes()
     SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
     return SPIREC_OK;
 }
 

@@ -80,6 +80,7 @@ size_t plan_bytes(int N, int64_t L, int M, int precision)
     b += 2 * ((size_t)L + 32) * 8;               // data + staging
     b += 10 * NN * 8;                            // iterates, directions, gradients, D, scratch
     b += (size_t)M * 8 + (size_t)P_NSLOTS * kMaxParts * 8 + 4096;
+    b += fsplit_bytes_tc(N, precision);  // split image of the tensor-core forward
     size_t a = 8 * (size_t)N * (2 * N - 1) * 2, c = 4 * (size_t)L * 2, t = kpart_floats_tc(N, L, precision);
     b += std::max(std::max(a, c), t) * 4;        // split-K partials
     return b;

@@ -36,6 +36,8 @@ SPIREC_MIXED_BF16X3 = 2
 SPIREC_PHI_HUBER = 0
 SPIREC_PHI_HYPERBOLIC = 1
 SPIREC_PHI_QUADRATIC = 2
+SPIREC_MODE_TOEPLITZ = 0
+SPIREC_MODE_DIRECT = 1
 
 SPIREC_NUM_STAGES = 4
 STAGES = ("gram", "spectrum", "adjoint_d", "iterations")
@@ -53,6 +55,7 @@ SIGNATURES = {
     "spirec_set_data": (ctypes.c_int, [_P, _P]),
     "spirec_set_data_dev": (ctypes.c_int, [_P, _P]),
     "spirec_set_reg": (ctypes.c_int, [_P, _D, _D, _D, _D, _I32]),
+    "spirec_set_mode": (ctypes.c_int, [_P, _I32]),
     "spirec_solve": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "spirec_solve_dev": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "spirec_forward_dev": (ctypes.c_int, [_P, _P, _P]),
@@ -176,6 +179,10 @@ def spirec_set_data_dev(plan, s):
 def spirec_set_reg(plan, lambda1, alpha1, lambda0, alpha0, phi):
     return _check(load().spirec_set_reg(plan, float(lambda1), float(alpha1), float(lambda0),
                                         float(alpha0), int(phi)))
+
+
+def spirec_set_mode(plan, mode):
+    return _check(load().spirec_set_mode(plan, int(mode)))
 
 
 def spirec_solve(plan, x0, iters, N):

@@ -83,7 +83,7 @@ def test_forward_sampled(sp, traj, plan):
     y = from_dev(y)
     idx = g.integers(0, kx.shape[0], 24)
     want = O.forward(kx[idx], ky[idx], x)
-    assert rel(y[idx], want) < 1e-5
+    assert rel(y[idx], want) < TOL[prec]
 
 
 def test_toeplitz_sparse_sampled(sp, traj, plan):

@@ -92,16 +92,20 @@ def test_adjoint_D(sp, prec, wname):
 
 
 @pytest.mark.parametrize("wname", ["c1", "ragged"])
-def test_forward(sp, wname):
+@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("scale", [1.0, 3e5, 1e-6])
+def test_forward(sp, wname, prec, scale):
+    """H x (Eq. ModDirect); the mixed paths run it as a tensor-core
+    contraction on an FP16/BF16 split of x, scaled by a power of two into
+    range (images of 3e5 would overflow FP16 unscaled, 1e-6 would underflow)."""
     w = workload_c1() if wname == "c1" else workload_ragged()
-    N = w["N"]
-    x = c64(w["f_true"])
-    with _plan(sp, w, 0) as p:
+    x = c64(scale * w["f_true"])
+    with _plan(sp, w, prec) as p:
         xd = to_dev(x)
         y = empty_c64((w["kx"].shape[0],))
         sp.spirec_forward_dev(p.h, xd, y)
         got = from_dev(y)
-    assert rel(got, O.forward(w["kx"], w["ky"], x)) < 1e-5
+    assert rel(got, O.forward(w["kx"], w["ky"], x)) < TOL[prec]
 
 
 @pytest.mark.parametrize("wname", ["c1", "ragged"])
@@ -327,3 +331,46 @@ def test_large_images_loop_and_graph(sp, monkeypatch, case, prec):
         assert rel(J, Jo) < TOL[prec], mode
         assert rel(x, xo) < TOL[prec], mode
     assert rel(res["loop"][0], res["graph"][0]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECISIONS)
+def test_direct_mode_matches_oracle_and_toeplitz_mode(sp, prec):
+    """SPIREC_MODE_DIRECT applies H^H H by the exact forward and adjoint
+    NUDFT every iteration (the original formulation); it must reach the
+    oracle's J history and iterates as the Toeplitz mode does."""
+    w = workload_c1()
+    N, reg, iters = w["N"], w["reg"], w["iters"]
+    xo, Jo, _ = O.solve(w["kx"], w["ky"], w["s"], reg, np.zeros((N, N)), iters)
+    res = {}
+    for mode in (sp.SPIREC_MODE_TOEPLITZ, sp.SPIREC_MODE_DIRECT):
+        with _plan(sp, w, prec) as p:
+            sp.spirec_set_mode(p.h, mode)
+            sp.spirec_set_data(p.h, w["s"])
+            sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+            res[mode] = sp.spirec_solve(p.h, None, iters, N)
+    x, J = res[sp.SPIREC_MODE_DIRECT]
+    assert np.all(np.diff(J) <= 1e-6 * J[0])
+    assert rel(J, Jo) < TOL[prec]
+    assert rel(x, xo) < ITER_TOL
+    assert rel(x, res[sp.SPIREC_MODE_TOEPLITZ][0]) < ITER_TOL
+
+
+def test_direct_mode_from_x0_and_errors(sp):
+    w = workload_ragged()
+    N, reg = w["N"], w["reg"]
+    g = synth.rng(8)
+    x0 = (0.5 * w["f_true"] + 0.05 * synth.complex_normal(w["f_true"].shape, g)).astype(np.complex64)
+    xo, Jo, _ = O.solve(w["kx"], w["ky"], w["s"], reg, c64(x0), 3)
+    with _plan(sp, w, 0) as p:
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_set_mode(p.h, 7)
+        assert e.value.code == sp.SPIREC_EINVAL
+        sp.spirec_set_mode(p.h, sp.SPIREC_MODE_DIRECT)
+        sp.spirec_set_data(p.h, w["s"])
+        sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+        x, J = sp.spirec_solve(p.h, x0, 3, N)
+        # switching back to the Toeplitz mode on the same plan
+        sp.spirec_set_mode(p.h, sp.SPIREC_MODE_TOEPLITZ)
+        xt, Jt = sp.spirec_solve(p.h, x0, 3, N)
+    assert rel(J, Jo) < 1e-5 and rel(x, xo) < 1e-5
+    assert rel(Jt, Jo) < 1e-5 and rel(xt, xo) < 1e-5
