@@ -201,7 +201,7 @@ def run_direct_mode(spirec, prec, w, s_host):
     return out
 
 
-def run_serving(spirec, prec, requests=200, rate=200.0, iters=50, seed=5, slots=8):
+def run_serving(spirec, prec, requests=2000, rate=200.0, iters=50, seed=5, slots=8):
     """Poisson request stream: sizes N in {64..384} step 64, L uniform in
     [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
     lambda1 U[0.01, 0.2], Huber alpha 0.05, 50 iterations; p50/p99 latency
