@@ -66,12 +66,21 @@ def apply_size_args(args):
 def run_batch(spirec, prec, frames=64, iters=50, seed=4):
     """Dynamic series: `frames` frames, sizes from {128, 192, 256}, each
     sampling 4 of 16 golden-angle interleaves x 2048 (L = 8192), moving
-    ellipse phantoms; every frame's trajectory, data and solve are enqueued on
-    its own plan's stream, then all are awaited (one timed region)."""
+    ellipse phantoms; every frame's trajectory, data and solve on its own
+    plan's stream, the whole series captured as one CUDA graph and timed as
+    one replay.  Timed twice: with each frame's G and spectrum built from its
+    samples, and set from a per-interleave kernel cache (the spectrum of a
+    subset is the sum of its interleaves' spectra; the cache is built once
+    per image size, outside the timed region, and its build time reported)."""
     import torch
     from paper_0908_3252_gb300 import synth
     g = synth.rng(seed)
     kx16, ky16 = synth.spiral(256, 16, 2048, "archimedean", "golden")
+    offsets = np.arange(0, 16 * 2048 + 1, 2048)
+    Ms = {128: 256, 192: 512, 256: 512}
+    t0 = time.perf_counter()
+    caches = {N: spirec.spirec_kcache_create(N, M, prec, offsets, kx16, ky16) for N, M in Ms.items()}
+    cache_s = time.perf_counter() - t0
     items = []
     for i in range(frames):
         N = int(g.choice([128, 192, 256]))
@@ -81,8 +90,7 @@ def run_batch(spirec, prec, frames=64, iters=50, seed=4):
         L = kx.shape[0]
         f = synth.ellipses(N, 10, synth.rng(1000 + i)).astype(np.complex64)
         st = torch.cuda.Stream()
-        M = 256 if N == 128 else 512
-        p = spirec.Plan(N, L, M, prec, st.cuda_stream)
+        p = spirec.Plan(N, L, Ms[N], prec, st.cuda_stream)
         kx_d, ky_d = torch.from_numpy(kx).cuda(), torch.from_numpy(ky).cuda()
         torch.cuda.synchronize()
         spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
@@ -93,51 +101,60 @@ def run_batch(spirec, prec, frames=64, iters=50, seed=4):
                                .astype(np.complex64)).cuda()
         spirec.spirec_set_reg(p.h, 0.05, 0.05, 0.0, 0.05, 0)
         x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
-        items.append((p, st, kx_d, ky_d, s_d, x))
+        items.append((p, st, kx_d, ky_d, s_d, x, caches[N], sub.astype(np.int32)))
 
-    def once():
-        for p, st, kx_d, ky_d, s_d, x in items:
+    def frame(it, cached):
+        p, st, kx_d, ky_d, s_d, x, cache, sub = it
+        if cached:
+            spirec.spirec_set_trajectory_cached(p.h, cache, sub)
+        else:
             spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
-            spirec.spirec_set_data_dev(p.h, s_d)
-        spirec.spirec_batch_solve([it[0].h for it in items], [it[5] for it in items], iters)
+        spirec.spirec_set_data_dev(p.h, s_d)
+        spirec.spirec_solve_dev(p.h, None, iters, x, None)
 
-    once()  # warm-up: every plan's buffers and kernels are in place
-    torch.cuda.synchronize()
-    # the whole series as ONE CUDA graph: fork from a capture stream to every
-    # frame's stream, each frame's trajectory, data and solve, join back
-    cap = torch.cuda.Stream()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=cap):
-        fork = torch.cuda.Event()
-        fork.record(cap)
-        joins = []
-        for p, st, kx_d, ky_d, s_d, x in items:
-            st.wait_event(fork)
-            spirec.spirec_set_trajectory_dev(p.h, kx_d, ky_d)
-            spirec.spirec_set_data_dev(p.h, s_d)
-            spirec.spirec_solve_dev(p.h, None, iters, x, None)
-            e = torch.cuda.Event()
-            e.record(st)
-            joins.append(e)
-        for e in joins:
-            cap.wait_event(e)
-    graph.replay()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(cap)
-    graph.replay()
-    e1.record(cap)
-    torch.cuda.synchronize()
-    dt = e0.elapsed_time(e1) / 1000.0
+    def timed_graph(cached):
+        for it in items:  # warm-up: every plan's buffers and kernels are in place
+            frame(it, cached)
+        torch.cuda.synchronize()
+        # the whole series as ONE CUDA graph: fork from a capture stream to
+        # every frame's stream, each frame's trajectory, data and solve, join
+        cap = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            fork = torch.cuda.Event()
+            fork.record(cap)
+            joins = []
+            for it in items:
+                it[1].wait_event(fork)
+                frame(it, cached)
+                e = torch.cuda.Event()
+                e.record(it[1])
+                joins.append(e)
+            for e in joins:
+                cap.wait_event(e)
+        graph.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(cap)
+        graph.replay()
+        e1.record(cap)
+        torch.cuda.synchronize()
+        del graph
+        return e0.elapsed_time(e1) / 1000.0
+
+    dt_built = timed_graph(False)
+    dt = timed_graph(True)
     sizes = sorted({it[0].N for it in items})
-    del graph
     for it in items:
         it[0].close()
+    for c in caches.values():
+        spirec.spirec_kcache_destroy(c)
     return {"frames": frames, "sizes": sizes, "iters": iters, "seconds": dt,
             "frames_per_s": frames / dt, "iters_per_s": frames * iters / dt,
-            "what": "per frame: trajectory (G, spectrum), data (D), 50 CG iterations; the 64 frames "
-                    "on their own streams, captured as one CUDA graph and timed as one replay"}
+            "frames_per_s_built_G": frames / dt_built, "kernel_cache_build_s": cache_s,
+            "what": "per frame: trajectory (spectrum from the kernel cache), data (D), 50 CG iterations; "
+                    "the 64 frames on their own streams, captured as one CUDA graph and timed as one replay"}
 
 
 def run_paper_experiment(spirec, prec, iters=50, reps=20):

@@ -147,6 +147,29 @@ int spirec_solve(spirec_plan plan, const float* x0, int32_t iters, float* x_out,
 int spirec_solve_dev(spirec_plan plan, const float* x0, int32_t iters, float* x_out,
                      double* J_hist);
 
+/* ---- per-interleave kernel cache (series that reuse subsets of one set of
+ * interleaves, e.g. dynamic imaging) ----
+ * G (Eq. AnnMatG) is a sum over the samples, and the kernel spectrum is
+ * linear in G, so the G and spectrum of a union of interleaves are the sums
+ * of the interleaves' own.  A cache holds, for one (N, M, precision), the
+ * fixed-point samples, G and spectrum of each of n interleaves; setting a
+ * plan's trajectory from it copies the chosen samples and adds the cached G
+ * and spectra (in the listed order) instead of building them. */
+typedef struct spirec_kcache_s* spirec_kcache;
+/* offsets: n + 1 increasing sample offsets into the HOST arrays kx, ky
+ * (offsets[0] = 0, interleave i is [offsets[i], offsets[i+1])).  Builds every
+ * interleave's G and spectrum with the plan machinery (synchronous).  Same
+ * argument rules as spirec_plan_create; SPIREC_EINVAL for bad offsets or
+ * trajectory values. */
+int spirec_kcache_create(spirec_kcache* out, int32_t N, int32_t M, int32_t precision, int32_t n,
+                         const int64_t* offsets, const double* kx, const double* ky, void* stream);
+int spirec_kcache_destroy(spirec_kcache cache);
+/* The plan's trajectory becomes interleaves which[0..count-1] of the cache,
+ * concatenated in that order (their sample counts must add up to the plan's
+ * L; 1 <= count <= 64; the plan's N and M equal the cache's, on the same
+ * device).  Invalidates D, like spirec_set_trajectory. */
+int spirec_set_trajectory_cached(spirec_plan plan, spirec_kcache cache, const int32_t* which, int32_t count);
+
 /* How solve applies the normal operator H^H H to the direction each
  * iteration.  SPIREC_MODE_TOEPLITZ (the default, section 3.4 and Appendix B):
  * by the M x M zero-padded FFT convolution with the kernel spectrum built

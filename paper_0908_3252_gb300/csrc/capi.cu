@@ -7,9 +7,21 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
+
+// the per-interleave kernel cache (spirec_kcache_*)
+struct spirec_kcache_s {
+    int N = 0, M = 0, precision = 0, n = 0, device = 0;
+    std::vector<int64_t> off;  // n + 1 sample offsets
+    int64_t* kxq = nullptr;    // all samples, fixed point (device)
+    int64_t* kyq = nullptr;
+    float* spec = nullptr;     // n x M x M kernel spectra
+    float2* G = nullptr;       // n x N x (2N-1) halves of G
+};
 
 namespace spirec {
 
@@ -73,6 +85,23 @@ bool smooth235(int m)
     for (int f : {2, 3, 5})
         while (m % f == 0) m /= f;
     return m == 1;
+}
+
+constexpr int kCacheMaxTerms = 64;
+struct CacheTerms {
+    int n;
+    int idx[kCacheMaxTerms];
+};
+
+// dst[e] = sum_j src[idx[j] * stride + e], j in the listed order.
+__global__ void k_sum_cached(const float* __restrict__ src, int64_t stride, CacheTerms t, float* __restrict__ dst)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < stride;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int j = 0; j < t.n; ++j) acc += __ldg(src + t.idx[j] * stride + e);
+        dst[e] = acc;
+    }
 }
 
 struct Join {
@@ -504,6 +533,151 @@ int spirec_plan_destroy(spirec_plan plan)
     if (!plan) return SPIREC_OK;
     cudaStreamSynchronize(plan->stream);
     free_plan(plan);
+    return SPIREC_OK;
+}
+
+static void free_kcache(spirec_kcache c)
+{
+    if (!c) return;
+    void* bufs[] = {c->kxq, c->kyq, c->spec, c->G};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete c;
+}
+
+int spirec_kcache_create(spirec_kcache* out, int32_t N, int32_t M, int32_t precision, int32_t n,
+                         const int64_t* offsets, const double* kx, const double* ky, void* stream)
+{
+    if (!out || !offsets || !kx || !ky || n < 1) {
+        set_error("kcache_create: null argument or n < 1");
+        return SPIREC_EINVAL;
+    }
+    *out = nullptr;
+    if (offsets[0] != 0) {
+        set_error("offsets[0] must be 0");
+        return SPIREC_EINVAL;
+    }
+    for (int i = 0; i < n; ++i)
+        if (offsets[i + 1] <= offsets[i]) {
+            set_error("offsets must increase (interleave %d is empty)", i);
+            return SPIREC_EINVAL;
+        }
+    spirec_kcache c = new (std::nothrow) spirec_kcache_s;
+    if (!c) {
+        set_error("host allocation failed");
+        return SPIREC_ENOMEM;
+    }
+    c->n = n;
+    c->off.assign(offsets, offsets + n + 1);
+    const int64_t Ltot = offsets[n];
+    // one helper plan per distinct interleave length builds G and the spectrum
+    std::map<int64_t, spirec_plan> helpers;
+    int rc = SPIREC_OK;
+    auto fail = [&](int code) {
+        for (auto& h : helpers) spirec_plan_destroy(h.second);
+        free_kcache(c);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
+    for (int i = 0; i < n; ++i) {
+        const int64_t Li = offsets[i + 1] - offsets[i];
+        spirec_plan h = nullptr;
+        auto it = helpers.find(Li);
+        if (it == helpers.end()) {
+            if ((rc = spirec_plan_create(&h, N, Li, M, precision, stream, nullptr, nullptr)) != SPIREC_OK)
+                return fail(rc);
+            helpers[Li] = h;
+            if (i == 0) {
+                c->N = h->N;
+                c->M = h->M;
+                c->precision = h->precision;
+                const size_t MM = (size_t)c->M * c->M, NG = (size_t)c->N * (2 * c->N - 1);
+                if ((e = cudaMalloc((void**)&c->kxq, sizeof(int64_t) * (size_t)(Ltot + 32))) != cudaSuccess ||
+                    (e = cudaMalloc((void**)&c->kyq, sizeof(int64_t) * (size_t)(Ltot + 32))) != cudaSuccess ||
+                    (e = cudaMalloc((void**)&c->spec, sizeof(float) * MM * n)) != cudaSuccess ||
+                    (e = cudaMalloc((void**)&c->G, sizeof(float2) * NG * n)) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(cuda_fail(e, "cudaMalloc (kernel cache)"));
+                }
+            }
+        } else {
+            h = it->second;
+        }
+        if ((rc = spirec_set_trajectory(h, kx + offsets[i], ky + offsets[i])) != SPIREC_OK) return fail(rc);
+        const size_t MM = (size_t)c->M * c->M, NG = (size_t)c->N * (2 * c->N - 1);
+        const cudaMemcpyKind d2d = cudaMemcpyDeviceToDevice;
+        if ((e = cudaMemcpyAsync(c->kxq + offsets[i], h->kxq, sizeof(int64_t) * Li, d2d, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c->kyq + offsets[i], h->kyq, sizeof(int64_t) * Li, d2d, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c->spec + MM * i, h->Chat, sizeof(float) * MM, d2d, h->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c->G + NG * i, h->G, sizeof(float2) * NG, d2d, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+            return fail(cuda_fail(e, "kernel cache copy"));
+    }
+    for (auto& h : helpers) spirec_plan_destroy(h.second);
+    *out = c;
+    return SPIREC_OK;
+}
+
+int spirec_kcache_destroy(spirec_kcache c)
+{
+    if (!c) return SPIREC_OK;
+    cudaDeviceSynchronize();
+    free_kcache(c);
+    return SPIREC_OK;
+}
+
+int spirec_set_trajectory_cached(spirec_plan p, spirec_kcache c, const int32_t* which, int32_t count)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!c || !which || count < 1 || count > kCacheMaxTerms) {
+        set_error("set_trajectory_cached: null cache or list, or count not in [1, %d]", kCacheMaxTerms);
+        return SPIREC_EINVAL;
+    }
+    if (c->N != p->N || c->M != p->M || c->device != p->device) {
+        set_error("cache is for N=%d, M=%d on device %d; plan N=%d, M=%d on device %d", c->N, c->M, c->device, p->N,
+                  p->M, p->device);
+        return SPIREC_EINVAL;
+    }
+    CacheTerms t{};
+    t.n = count;
+    int64_t total = 0;
+    for (int j = 0; j < count; ++j) {
+        if (which[j] < 0 || which[j] >= c->n) {
+            set_error("interleave %d not in the cache (n = %d)", which[j], c->n);
+            return SPIREC_EINVAL;
+        }
+        t.idx[j] = which[j];
+        total += c->off[which[j] + 1] - c->off[which[j]];
+    }
+    if (total != p->L) {
+        set_error("the listed interleaves hold %lld samples, the plan %lld", (long long)total, (long long)p->L);
+        return SPIREC_EINVAL;
+    }
+    Join j(p);
+    p->have_traj = false;
+    p->have_data = false;
+    SPIREC_CK(cudaMemsetAsync(p->dflag, 0, sizeof(int), p->stream));
+    int64_t pos = 0;
+    for (int k = 0; k < count; ++k) {
+        const int64_t o = c->off[which[k]], Li = c->off[which[k] + 1] - o;
+        SPIREC_CK(cudaMemcpyAsync(p->kxq + pos, c->kxq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
+        SPIREC_CK(cudaMemcpyAsync(p->kyq + pos, c->kyq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
+        pos += Li;
+    }
+    const int64_t MM = (int64_t)p->M * p->M, NG2 = 2 * (int64_t)p->N * (2 * p->N - 1);
+    int blocks = (int)((MM + 255) / 256);
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    k_sum_cached<<<blocks, 256, 0, p->stream>>>(c->spec, MM, t, p->Chat);
+    SPIREC_CK(cudaGetLastError());
+    blocks = (int)((NG2 + 255) / 256);
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    k_sum_cached<<<blocks, 256, 0, p->stream>>>(reinterpret_cast<const float*>(c->G), NG2, t,
+                                                reinterpret_cast<float*>(p->G));
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 2;
+    p->have_traj = true;
     return SPIREC_OK;
 }
 

@@ -56,6 +56,9 @@ SIGNATURES = {
     "spirec_set_data_dev": (ctypes.c_int, [_P, _P]),
     "spirec_set_reg": (ctypes.c_int, [_P, _D, _D, _D, _D, _I32]),
     "spirec_set_mode": (ctypes.c_int, [_P, _I32]),
+    "spirec_kcache_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _I32, _I32, _I32, _P, _P, _P, _P]),
+    "spirec_kcache_destroy": (ctypes.c_int, [_P]),
+    "spirec_set_trajectory_cached": (ctypes.c_int, [_P, _P, _P, _I32]),
     "spirec_solve": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "spirec_solve_dev": (ctypes.c_int, [_P, _P, _I32, _P, _P]),
     "spirec_forward_dev": (ctypes.c_int, [_P, _P, _P]),
@@ -179,6 +182,26 @@ def spirec_set_data_dev(plan, s):
 def spirec_set_reg(plan, lambda1, alpha1, lambda0, alpha0, phi):
     return _check(load().spirec_set_reg(plan, float(lambda1), float(alpha1), float(lambda0),
                                         float(alpha0), int(phi)))
+
+
+def spirec_kcache_create(N, M, precision, offsets, kx, ky, stream=None):
+    """Per-interleave kernel cache: offsets (n + 1 sample offsets into kx, ky)."""
+    off = np.ascontiguousarray(offsets, np.int64)
+    kx = np.ascontiguousarray(kx, np.float64)
+    ky = np.ascontiguousarray(ky, np.float64)
+    h = _P()
+    _check(load().spirec_kcache_create(ctypes.byref(h), int(N), int(M), int(precision), int(off.shape[0] - 1),
+                                       _host_ptr(off), _host_ptr(kx), _host_ptr(ky), stream))
+    return h
+
+
+def spirec_kcache_destroy(cache):
+    return _check(load().spirec_kcache_destroy(cache))
+
+
+def spirec_set_trajectory_cached(plan, cache, which):
+    w = np.ascontiguousarray(which, np.int32)
+    return _check(load().spirec_set_trajectory_cached(plan, cache, _host_ptr(w), int(w.shape[0])))
 
 
 def spirec_set_mode(plan, mode):
