@@ -33,11 +33,11 @@
 //              commits to empty[stage];
 //   warps 0-15 drain: at the end of every segment (at most SEG stages of one
 //              tile) the finished accumulator is read with tcgen05.ld and
-//              added to the CTA's column-major partial tile in global memory
-//              by fire-and-forget reductions (red.global.add.f32, coalesced
-//              along the rows, round-to-nearest; the first segment of a tile
-//              stores).  The MMA waits for the drain (one accumulator), which
-//              issues in well under a microsecond.
+//              added to the CTA's partial tile in global memory by
+//              fire-and-forget vector reductions (red.global.add.v4.f32,
+//              round-to-nearest; the first segment of a tile stores), laid
+//              out so that a warp's 32 lanes cover 512 contiguous bytes.  The
+//              MMA waits for the drain (one accumulator).
 // The tensor core's FP32 accumulation loses about one unit in the last place
 // per accumulation step (truncation-like, measured: 2.8e-4 relative after
 // 12k steps); draining every 16 stages bounds that error.  Two stages of
@@ -285,6 +285,20 @@ __device__ __forceinline__ void red_global(float* p, float v)
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_global_v4(float* p, const float* v)
+{
+    asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+}
+
+// p[0..3] += v[0..3] at the memory (round-to-nearest FP32 adds, no reply).
+__device__ __forceinline__ void red_global_v4(float* p, const float* v)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3])
+                 : "memory");
+}
+
 // 2^-e with 2^e >= sqrt(amax2): scales the weights into (-1, 1).
 __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
 {
@@ -296,12 +310,12 @@ __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
     return ldexpf(1.f, -e);
 }
 
-// Adds (first: stores) the accumulator into the column-major partial tile
-// [512 columns][128 rows]; warp w reads TMEM lanes 32 (w % 4).. and complex
-// columns [64 (w / 4), 64 (w / 4) + 64) (real part at column c, imaginary at
-// 256 + c).  Lanes are consecutive rows, so each warp instruction covers one
-// 128-byte line; a thread's adds to one address come in program order, so
-// the partial is the same sum in the same order on every run.
+// Adds (first: stores) the accumulator into the partial tile, laid out as
+// [column / 4][row][column % 4] (512 columns: real part at c, imaginary at
+// 256 + c; 128 rows): a thread's four consecutive columns are one 16-byte
+// vector, and the 32 lanes (consecutive rows) of a warp cover 512 contiguous
+// bytes.  Fire-and-forget vector reductions; a thread's adds to one address
+// come in program order, so the partial is the same sum on every run.
 __device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, int warp, int lane,
                                                   bool first)
 {
@@ -315,16 +329,16 @@ __device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, i
         tmem_ld16(ta, re);
         tmem_ld16(ta + TC_COLS, im);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int col = 64 * quarter + cc + j;
-            float* pr = ptile + (size_t)col * TC_ROWS + row;
-            float* pi = ptile + (size_t)(TC_COLS + col) * TC_ROWS + row;
+        for (int v = 0; v < 4; ++v) {
+            const int cg = (64 * quarter + cc) / 4 + v;  // column group of the real part
+            float* pr = ptile + ((size_t)cg * TC_ROWS + row) * 4;
+            float* pi = ptile + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4;
             if (first) {
-                *pr = re[j];
-                *pi = im[j];
+                st_global_v4(pr, re + 4 * v);
+                st_global_v4(pi, im + 4 * v);
             } else {
-                red_global(pr, re[j]);
-                red_global(pi, im[j]);
+                red_global_v4(pr, re + 4 * v);
+                red_global_v4(pi, im + 4 * v);
             }
         }
     }
@@ -584,8 +598,8 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
 // 2^e undoes the weight scaling.  The CTAs holding units of tile t are
 // c_lo..c_hi, the last CTAs whose ranges start at or before the tile's first
 // and last unit; CTA c keeps its partial of tile t in slot c + t.  A block
-// sums a 32 x 32 patch: reads run down the rows of the column-major partials,
-// the patch turns in shared memory, writes run along the rows of out.
+// sums a 32 x 32 patch: each thread reads four columns of one row as a
+// vector, the patch turns in shared memory, writes run along the rows of out.
 __global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
                                                    int R, int C, int tilesC, float scale,
                                                    const unsigned* __restrict__ amax2, float2* __restrict__ out)
@@ -599,18 +613,22 @@ __global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ par
     const int64_t c_lo = ((t * K + 1) * P - 1) / U;
     const int64_t c_hi = ((t + 1) * K * P - 1) / U;
     const int row = (i0 % TC_ROWS) + tx;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int cl = ty + 8 * j;
-        const int col = (c0 % TC_COLS) + cl;
-        float ar = 0.f, ai = 0.f;
+    {
+        // thread (tx, ty): row tx of the patch, columns 4 ty .. 4 ty + 3
+        const int cg = ((c0 % TC_COLS) >> 2) + ty;
+        float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = ar;
         for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
             if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
             const float* pt = part + (cc + t) * TC_TILE_FLOATS;
-            ar += pt[col * TC_ROWS + row];
-            ai += pt[(TC_COLS + col) * TC_ROWS + row];
+            const float4 r = *reinterpret_cast<const float4*>(pt + ((size_t)cg * TC_ROWS + row) * 4);
+            const float4 m = *reinterpret_cast<const float4*>(pt + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4);
+            ar.x += r.x; ar.y += r.y; ar.z += r.z; ar.w += r.w;
+            ai.x += m.x; ai.y += m.y; ai.z += m.z; ai.w += m.w;
         }
-        patch[cl][tx] = make_float2(ar * sc, ai * sc);
+        patch[4 * ty + 0][tx] = make_float2(ar.x * sc, ai.x * sc);
+        patch[4 * ty + 1][tx] = make_float2(ar.y * sc, ai.y * sc);
+        patch[4 * ty + 2][tx] = make_float2(ar.z * sc, ai.z * sc);
+        patch[4 * ty + 3][tx] = make_float2(ar.w * sc, ai.w * sc);
     }
     __syncthreads();
 #pragma unroll
