@@ -293,6 +293,70 @@ int spirec_server_stats(spirec_server srv, double* p50_s, double* p99_s, int64_t
 /* Finish the running requests, drop the queued ones, release everything. */
 int spirec_server_destroy(spirec_server srv);
 
+/* ------------------------------------------------------------- autotuning
+ *
+ * Launch parameters that change speed, not the arithmetic of a term: how the
+ * sample sum of the contractions G (Eq. AnnMatG) and D = H^H y (Eq. AnnMatGD)
+ * is split over the SMs, and how many image rows one block of the persistent
+ * CG loop owns.  A split changes the grouping of the FP32 partial sums, so
+ * results move within the contraction's rounding (never beyond the stated
+ * tolerances); a row count changes the block order of the loop's reductions.
+ * For one table, a shape always gets the same value: a solve gives the same
+ * result alone and among other solves.
+ *
+ * The values live in one process-wide table keyed by (knob, N, M, precision,
+ * L class, SM count), the L class being the smallest c with 2^c >= L (the
+ * loop's key ignores L).  A shape without an entry uses the built-in
+ * heuristic.  Knobs and their values:
+ *   SPIREC_KNOB_GRAM_SPLIT     G: tensor-core paths, the number of CTAs the
+ *                              stream-K schedule spreads the work over
+ *                              (1..152); FP32 path, the number of slices the
+ *                              samples are cut into (>= 1).
+ *   SPIREC_KNOB_ADJOINT_SPLIT  the same for D and every other H^H y.
+ *   SPIREC_KNOB_LOOP_ROWS      persistent CG loop: image rows per block.
+ * A value that does not fit the device or the plan at launch time (too many
+ * CTAs for the split-K buffer, a loop shape whose blocks are not
+ * co-resident) is clipped, or, for the loop, replaced by the heuristic. */
+#define SPIREC_KNOB_GRAM_SPLIT 0
+#define SPIREC_KNOB_ADJOINT_SPLIT 1
+#define SPIREC_KNOB_LOOP_ROWS 2
+#define SPIREC_NUM_KNOBS 3
+
+/* Objectives: LATENCY minimises the time of one launch; THROUGHPUT the
+ * SM-time (launch time x SMs the launch occupies), for many solves that share
+ * the GPU (batched frames, the request loop). */
+#define SPIREC_TUNE_LATENCY 0
+#define SPIREC_TUNE_THROUGHPUT 1
+
+/* Time every candidate value of each knob on the plan's own trajectory, data
+ * and regularisation (all three set first: SPIREC_ESTATE otherwise) with CUDA
+ * events on the plan's stream (one warm-up and the median of three runs),
+ * store the best under the plan's key, and rebuild G, the spectrum and D with
+ * it, so that the plan's state equals that of a new plan of the same shape.
+ * The loop is timed over loop_iters iterations from x0 = 0 (>= 1; skipped in
+ * direct mode and for M the loop does not handle).  chosen[SPIREC_NUM_KNOBS]
+ * receives the stored values (0: knob not tuned); best_ms (may be NULL) the
+ * median milliseconds of the winners.  Blocks the host until done. */
+int spirec_autotune(spirec_plan plan, int32_t objective, int32_t loop_iters, int32_t* chosen, double* best_ms);
+
+/* Set (value > 0) or remove (value == 0) a table entry.  sms == 0 means the
+ * current device's SM count (needs a CUDA device; SPIREC_ECUDA otherwise).
+ * SPIREC_EINVAL for an unknown knob or precision, N < 2, M < 2N - 1, L < 1,
+ * sms < 0 or value < 0.  Host-only: no device work. */
+int spirec_tune_set(int32_t knob, int32_t N, int32_t M, int32_t precision, int64_t L, int32_t sms, int32_t value);
+/* The entry for a shape, 0 if none (arguments as spirec_tune_set). */
+int spirec_tune_get(int32_t knob, int32_t N, int32_t M, int32_t precision, int64_t L, int32_t sms,
+                    int32_t* value);
+/* Number of entries; spirec_tune_clear removes them all. */
+int spirec_tune_count(int64_t* count);
+int spirec_tune_clear(void);
+/* Write the table to a text file (one entry per line after a header line)
+ * or add the entries of such a file to it (entries of the file replace equal
+ * keys).  SPIREC_EINVAL for a file that cannot be opened or a malformed line;
+ * a failed load leaves the table unchanged. */
+int spirec_tune_save(const char* path);
+int spirec_tune_load(const char* path);
+
 /* Copy the plan's FP64 device scalars to the host (diagnostics; syncs the
  * plan).  out receives min(n, SPIREC_NUM_SCALARS) values in this order:
  * 0 ||s||^2, 1 q1, 2 q2, 3-5 line-search steps t1..t3, 6 <g,g>, 7 beta,

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <new>
 #include <vector>
@@ -303,7 +304,8 @@ int ensure_J(spirec_plan p, int iters)
 int run_iterations(spirec_plan p, int iters)
 {
     if (iters == 0) return SPIREC_OK;
-    if (!p->graph || p->graph_iters != iters) {
+    // re-capture when the tuning table changed: the graph holds launch shapes
+    if (!p->graph || p->graph_iters != iters || p->graph_tune_gen != tune_generation()) {
         if (p->graph) {
             cudaGraphExecDestroy(p->graph);
             p->graph = nullptr;
@@ -328,6 +330,7 @@ int run_iterations(spirec_plan p, int iters)
             return cuda_fail(e, "cudaGraphInstantiate");
         }
         p->graph_iters = iters;
+        p->graph_tune_gen = tune_generation();
     }
     SPIREC_CK(cudaGraphLaunch(p->graph, p->stream));
     p->launches += p->graph_kernels;
@@ -380,6 +383,140 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
     }
     return tstop(p, e);
+}
+
+// ------------------------------------------------------------ autotuning
+
+// CUDA events that are destroyed on every path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+// Median milliseconds of three runs of fn after one warm-up, timed with
+// events on the plan's stream.
+template <class F>
+int time_median(spirec_plan p, F fn, double* ms)
+{
+    EventPair ev;
+    SPIREC_CK(cudaEventCreate(&ev.a));
+    SPIREC_CK(cudaEventCreate(&ev.b));
+    int rc = fn();
+    if (rc != SPIREC_OK) return rc;
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+        SPIREC_CK(cudaEventRecord(ev.a, p->stream));
+        if ((rc = fn()) != SPIREC_OK) return rc;
+        SPIREC_CK(cudaEventRecord(ev.b, p->stream));
+        SPIREC_CK(cudaEventSynchronize(ev.b));
+        SPIREC_CK(cudaEventElapsedTime(&t[r], ev.a, ev.b));
+    }
+    if (t[0] > t[1]) std::swap(t[0], t[1]);
+    if (t[1] > t[2]) std::swap(t[1], t[2]);
+    if (t[0] > t[1]) std::swap(t[0], t[1]);
+    *ms = t[1];
+    return SPIREC_OK;
+}
+
+// Candidates of a contraction split around the heuristic's value v0: for the
+// tensor-core schedule fractions of the CTA count down to 1/32 (few CTAs
+// leave the other SMs to concurrent solves), for the FP32 one halvings and
+// doublings of the slice count.  The heuristic's value comes first.
+std::vector<int> split_candidates(int precision, int v0)
+{
+    std::vector<int> c;
+    auto add = [&](int v) {
+        if (v < 1) v = 1;
+        for (int x : c)
+            if (x == v) return;
+        c.push_back(v);
+    };
+    add(v0);
+    if (precision != SPIREC_FP32) {
+        for (int num : {24, 16, 12, 8, 4, 2, 1}) add(v0 * num / 32);
+    } else {
+        for (int f : {2, 4}) add(v0 / f);
+        for (int f : {2, 4}) add(v0 * f);
+    }
+    return c;
+}
+
+int tune_contraction(spirec_plan p, int knob, int objective, int sms, int* chosen, double* best_ms)
+{
+    int rc;
+    if ((rc = tune_store(knob, p, sms, 0)) != SPIREC_OK) return rc;
+    int v0 = 0, used0 = 0;
+    if ((rc = contraction_split(p, knob, &v0, &used0)) != SPIREC_OK) return rc;
+    std::vector<int> seen;
+    double best_score = 0.0;
+    int best = 0;
+    for (int c : split_candidates(p->precision, v0)) {
+        if ((rc = tune_store(knob, p, sms, c)) != SPIREC_OK) return rc;
+        int v = 0, used = 0;
+        if ((rc = contraction_split(p, knob, &v, &used)) != SPIREC_OK) return rc;
+        bool dup = false;
+        for (int x : seen) dup = dup || x == v;  // clipped onto a value already timed
+        if (dup) continue;
+        seen.push_back(v);
+        double ms = 0.0;
+        if (knob == SPIREC_KNOB_GRAM_SPLIT)
+            rc = time_median(p, [&] { return launch_gram(p); }, &ms);
+        else
+            rc = time_median(p, [&] { return launch_adjoint(p, p->s, p->D); }, &ms);
+        if (rc != SPIREC_OK) return rc;
+        const double score = objective == SPIREC_TUNE_THROUGHPUT ? ms * used : ms;
+        if (best == 0 || score < best_score) {
+            best = v;
+            best_score = score;
+            *best_ms = ms;
+        }
+    }
+    *chosen = best;
+    return tune_store(knob, p, sms, best);
+}
+
+int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, double* best_ms)
+{
+    *chosen = 0;
+    if (p->mode == SPIREC_MODE_DIRECT || !loop_supported(p->M) || !p->Xd || getenv("SPIREC_NO_LOOP"))
+        return SPIREC_OK;
+    int rc;
+    if ((rc = ensure_J(p, iters)) != SPIREC_OK) return rc;
+    if ((rc = tune_store(SPIREC_KNOB_LOOP_ROWS, p, sms, 0)) != SPIREC_OK) return rc;
+    int RB[8], grid[8];
+    const int n = loop_candidates(p, RB, grid, 8);
+    const size_t img = (size_t)p->N * p->N * sizeof(float2);
+    double best_score = 0.0;
+    int best = 0;
+    for (int i = 0; i < n; ++i) {
+        if ((rc = tune_store(SPIREC_KNOB_LOOP_ROWS, p, sms, RB[i])) != SPIREC_OK) return rc;
+        double ms = 0.0;
+        rc = time_median(
+            p,
+            [&]() -> int {
+                SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
+                SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
+                return launch_cg_loop(p, iters);
+            },
+            &ms);
+        if (rc != SPIREC_OK) return rc;
+        int flags = 0;
+        if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+        if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
+        const double score = objective == SPIREC_TUNE_THROUGHPUT ? ms * (grid[i] < sms ? grid[i] : sms) : ms;
+        if (best == 0 || score < best_score) {
+            best = RB[i];
+            best_score = score;
+            *best_ms = ms;
+        }
+    }
+    p->result_slot = 0;
+    *chosen = best;
+    return tune_store(SPIREC_KNOB_LOOP_ROWS, p, sms, best);
 }
 
 }  // namespace
@@ -964,6 +1101,49 @@ int spirec_objective_grad_dev(spirec_plan p, const float* x, double* J_host, flo
     if (J_host) {
         SPIREC_CK(cudaMemcpyAsync(J_host, p->scal + S_J, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
         SPIREC_CK(cudaStreamSynchronize(p->stream));
+    }
+    return SPIREC_OK;
+}
+
+int spirec_autotune(spirec_plan p, int32_t objective, int32_t loop_iters, int32_t* chosen, double* best_ms)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!chosen) {
+        set_error("chosen must not be NULL");
+        return SPIREC_EINVAL;
+    }
+    if (objective != SPIREC_TUNE_LATENCY && objective != SPIREC_TUNE_THROUGHPUT) {
+        set_error("objective must be SPIREC_TUNE_LATENCY or SPIREC_TUNE_THROUGHPUT, not %d", objective);
+        return SPIREC_EINVAL;
+    }
+    if (loop_iters < 1) {
+        set_error("loop_iters must be >= 1");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj || !p->have_data || !p->have_reg) {
+        set_error("autotune needs the plan's trajectory, data and regularisation");
+        return SPIREC_ESTATE;
+    }
+    int sms = 0;
+    if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
+    int got[SPIREC_NUM_KNOBS] = {0, 0, 0};
+    double ms[SPIREC_NUM_KNOBS] = {0.0, 0.0, 0.0};
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    if ((rc = tune_contraction(p, SPIREC_KNOB_GRAM_SPLIT, objective, sms, &got[0], &ms[0])) != SPIREC_OK) return rc;
+    if ((rc = tune_contraction(p, SPIREC_KNOB_ADJOINT_SPLIT, objective, sms, &got[1], &ms[1])) != SPIREC_OK)
+        return rc;
+    // G, the spectrum and D as a new plan of this shape computes them
+    if ((rc = launch_gram(p)) != SPIREC_OK) return rc;
+    if ((rc = launch_spectrum(p)) != SPIREC_OK) return rc;
+    if ((rc = launch_adjoint(p, p->s, p->D)) != SPIREC_OK) return rc;
+    if ((rc = tune_loop(p, objective, loop_iters, sms, &got[2], &ms[2])) != SPIREC_OK) return rc;
+    int flags = 0;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
+    for (int k = 0; k < SPIREC_NUM_KNOBS; ++k) {
+        chosen[k] = got[k];
+        if (best_ms) best_ms[k] = ms[k];
     }
     return SPIREC_OK;
 }

@@ -666,15 +666,13 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     }
 }
 
-// The block shape for an N-wide image: RB = gpb * RPC rows per block with
-// the fewest groups per block gpb whose grid is co-resident (every block
-// must be resident for the grid barrier).  False when no shape fits.
+// Sets the function's shared-memory cap (once per device, to the largest
+// size any shape may ask for) and returns it.
 template <int MC>
-bool loop_shape(int N, int* RB_out, int* grid_out, size_t* smem_out)
+bool loop_cap(size_t* cap_out)
 {
-    int dev = 0, sms = 0, optin = 0;
+    int dev = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return false;
     auto kern = k_cg_loop<MC>;
@@ -684,29 +682,79 @@ bool loop_shape(int N, int* RB_out, int* grid_out, size_t* smem_out)
     // the cap is a property of the function shared by every plan and thread:
     // set once to the largest shape, never lowered (a concurrent launch with
     // a larger shape would fail)
-    {
-        static std::mutex mu;
-        static int set_cap[64] = {0};
-        std::lock_guard<std::mutex> lk(mu);
-        if (dev < 0 || dev >= 64) return false;
-        if (set_cap[dev] < (int)cap) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) != cudaSuccess)
-                return false;
-            set_cap[dev] = (int)cap;
+    static std::mutex mu;
+    static int set_cap[64] = {0};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) return false;
+    if (set_cap[dev] < (int)cap) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) != cudaSuccess)
+            return false;
+        set_cap[dev] = (int)cap;
+    }
+    *cap_out = cap;
+    return true;
+}
+
+// Whether blocks of RB rows fit: shared memory within the cap and every
+// block of the grid co-resident (the grid synchronisations need that).
+template <int MC>
+bool loop_fits(int N, int RB, size_t cap, int sms, int* grid_out, size_t* smem_out)
+{
+    const int grid = (N + RB - 1) / RB;
+    const size_t smem = loop_smem<MC>(N, RB);
+    if (smem > cap) return false;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_loop<MC>, kLoopThreads, smem) != cudaSuccess)
+        return false;
+    if (per_sm < 1 || grid > sms * per_sm || grid > kMaxParts) return false;
+    *grid_out = grid;
+    *smem_out = smem;
+    return true;
+}
+
+// The shapes RB = gpb * RPC, gpb = 1 .. kMaxGroupsPerBlock (up to the first
+// that holds the whole image), that fit; at most max.
+template <int MC>
+int loop_shapes(int N, int* RB, int* grid, int max)
+{
+    int sms = 0;
+    size_t cap = 0;
+    if (device_sms(&sms) != SPIREC_OK || !loop_cap<MC>(&cap)) return 0;
+    int n = 0;
+    for (int gpb = 1; gpb <= kMaxGroupsPerBlock && n < max; ++gpb) {
+        const int rb = gpb * Geo<MC>::RPC;
+        int gr = 0;
+        size_t smem = 0;
+        if (loop_fits<MC>(N, rb, cap, sms, &gr, &smem)) {
+            RB[n] = rb;
+            grid[n] = gr;
+            ++n;
         }
+        if (rb >= N) break;
+    }
+    cudaGetLastError();
+    return n;
+}
+
+// The block shape of a launch: the tuned rows per block of the plan's shape
+// when that fits, else the fewest groups per block gpb whose grid is
+// co-resident (every block on its own SM when the image allows).
+template <int MC>
+bool loop_shape(const spirec_plan_s* p, int* RB_out, int* grid_out, size_t* smem_out)
+{
+    int sms = 0;
+    size_t cap = 0;
+    if (device_sms(&sms) != SPIREC_OK || !loop_cap<MC>(&cap)) return false;
+    const int N = p->N;
+    const int tuned = tune_lookup(SPIREC_KNOB_LOOP_ROWS, p, sms);
+    if (tuned > 0 && loop_fits<MC>(N, tuned, cap, sms, grid_out, smem_out)) {
+        *RB_out = tuned;
+        return true;
     }
     for (int gpb = 1; gpb <= kMaxGroupsPerBlock; ++gpb) {
         const int RB = gpb * Geo<MC>::RPC;
-        const int grid = (N + RB - 1) / RB;
-        const size_t smem = loop_smem<MC>(N, RB);
-        if (smem > cap) return false;
-        int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLoopThreads, smem) != cudaSuccess)
-            return false;
-        if (per_sm >= 1 && grid <= sms * per_sm && grid <= kMaxParts) {
+        if (loop_fits<MC>(N, RB, cap, sms, grid_out, smem_out)) {
             *RB_out = RB;
-            *grid_out = grid;
-            *smem_out = smem;
             return true;
         }
         if (RB >= N) return false;
@@ -726,7 +774,7 @@ struct LaunchLoop {
         } else {
             int RB = 0, grid = 0;
             size_t smem = 0;
-            if (!p->Xd || !loop_shape<MC>(p->N, &RB, &grid, &smem)) {
+            if (!p->Xd || !loop_shape<MC>(p, &RB, &grid, &smem)) {
                 cudaGetLastError();
                 set_error("the persistent loop does not fit N=%d, M=%d", p->N, p->M);
                 return SPIREC_EUNSUPPORTED;
@@ -765,6 +813,47 @@ struct LaunchLoop {
 }  // namespace
 
 bool loop_supported(int M) { return M >= 64 && M <= 2048 && (M & (M - 1)) == 0; }
+
+namespace {
+struct Shapes {
+    const spirec_plan_s* p;
+    int* RB;
+    int* grid;
+    int max;
+    bool current;
+    template <int MC>
+    int run()
+    {
+        if constexpr (MC == 0) {
+            return 0;
+        } else {
+            if (current) {
+                size_t smem = 0;
+                return loop_shape<MC>(p, RB, grid, &smem) ? 1 : 0;
+            }
+            return loop_shapes<MC>(p->N, RB, grid, max);
+        }
+    }
+};
+
+int shapes_for(const spirec_plan_s* p, int* RB, int* grid, int max, bool current)
+{
+    Shapes s{p, RB, grid, max, current};
+    switch (p->M) {
+    case 64: return s.run<64>();
+    case 128: return s.run<128>();
+    case 256: return s.run<256>();
+    case 512: return s.run<512>();
+    case 1024: return s.run<1024>();
+    case 2048: return s.run<2048>();
+    default: return s.run<0>();
+    }
+}
+}  // namespace
+
+int loop_candidates(spirec_plan p, int* RB, int* grid, int max) { return shapes_for(p, RB, grid, max, false); }
+
+int loop_current(spirec_plan p, int* RB, int* grid) { return shapes_for(p, RB, grid, 1, true); }
 
 int launch_cg_loop(spirec_plan p, int iters)
 {

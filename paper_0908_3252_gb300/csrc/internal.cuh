@@ -151,6 +151,7 @@ struct spirec_plan_s {
     // CUDA graph of the iteration loop
     cudaGraphExec_t graph;
     int graph_iters;
+    unsigned graph_tune_gen;  // tuning-table generation the graph was captured under
     int graph_parity_out;
     int result_slot;  // the last solve left its iterate in f[result_slot]
     int mode;         // SPIREC_MODE_TOEPLITZ or SPIREC_MODE_DIRECT
@@ -210,6 +211,26 @@ int launch_forward_tc(spirec_plan p, const float2* x, float2* y);
 size_t fsplit_bytes_tc(int N, int precision);  // the forward's split-image buffer
 size_t kpart_floats_tc(int N, int64_t L, int precision);  // split-K buffer need
 int tc_setup_attributes();
+
+// Tuned launch parameters (tune.cu).  tune_lookup gives the table entry of
+// the plan's shape for the knob on a device with `sms` SMs, 0 if none;
+// tune_store sets (value > 0) or removes it.  The generation grows with every
+// change (graphs captured under an older one are re-captured).
+int l_class(int64_t L);
+int tune_lookup(int knob, const spirec_plan_s* p, int sms);
+int tune_store(int knob, const spirec_plan_s* p, int sms, int value);
+unsigned tune_generation();
+int device_sms(int* sms);
+
+// The split of the G (SPIREC_KNOB_GRAM_SPLIT) or D (SPIREC_KNOB_ADJOINT_SPLIT)
+// contraction that a launch of this plan uses now (the table entry, else the
+// heuristic, clipped), and the SMs it occupies (nudft_simt.cu).
+int contraction_split(spirec_plan p, int knob, int* value, int* sms_used);
+// Loop shapes the plan can launch: rows per block and grid, at most `max`
+// (cg_loop.cu); the shape a launch uses now.
+int loop_candidates(spirec_plan p, int* RB, int* grid, int max);
+int loop_current(spirec_plan p, int* RB, int* grid);
+int tc_ctas(spirec_plan p, int knob, int sms, int64_t* P);  // nudft_tc.cu
 
 int vec_blocks(int N);
 constexpr int kVecThreads = 256;

@@ -226,24 +226,35 @@ k_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq,
     if (tid < TN && l0 + tid < L) ypart[(int64_t)blockIdx.y * L + l0 + tid] = yacc;
 }
 
-int choose_splits(int64_t tiles, int64_t nchunks, size_t part_cap_elems, int64_t RC)
+// Sample slices of the contraction: the tuned value of the shape, else about
+// six resident CTAs per SM over the device; bounded by the work and by the
+// partial-sum buffer.
+int choose_splits(spirec_plan p, int knob, int sms, int64_t tiles, int64_t nchunks, int64_t RC)
 {
-    // aim for ~6 resident CTAs per SM over 152 SMs, bounded by the work and by
-    // the partial-sum buffer
-    int64_t S = (6 * 152 + tiles - 1) / tiles;
+    const size_t part_cap_elems = p->kpart_bytes / sizeof(float2);
+    const int tuned = tune_lookup(knob, p, sms);
+    int64_t S = tuned > 0 ? tuned : (6 * sms + tiles - 1) / tiles;
     if (S > nchunks) S = nchunks;
     if (S < 1) S = 1;
     while (S > 1 && (size_t)(S * RC) > part_cap_elems) --S;
     return (int)S;
 }
 
-int phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const float2* w, int R,
+void simt_shape(const spirec_plan_s* p, int knob, int* R, int* C)
+{
+    *R = p->N;
+    *C = knob == SPIREC_KNOB_GRAM_SPLIT ? 2 * p->N - 1 : p->N;
+}
+
+int phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, const float2* w, int R,
                int C, int oa, int ob, int sa, int sb, float scale, float2* out)
 {
     const int64_t nchunks = (p->L + KC - 1) / KC;
     const int64_t tiles = (int64_t)((R + TM - 1) / TM) * ((C + TN - 1) / TN);
     const int64_t RC = (int64_t)R * C;
-    const int S = choose_splits(tiles, nchunks, p->kpart_bytes / sizeof(float2), RC);
+    int sms = 0, rc;
+    if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
+    const int S = choose_splits(p, knob, sms, tiles, nchunks, RC);
     const int64_t cps = (nchunks + S - 1) / S;
     const int Seff = (int)((nchunks + cps - 1) / cps);
     dim3 grid((C + TN - 1) / TN, (R + TM - 1) / TM, Seff);
@@ -268,7 +279,7 @@ int launch_gram(spirec_plan p)
     if (p->precision != SPIREC_FP32) return launch_gram_tc(p);
     const int N = p->N;
     // G[u][v+N-1] = (1/N^2) sum_l exp(i2pi kx_l u) exp(i2pi ky_l v)
-    return phase_gemm(p, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
+    return phase_gemm(p, SPIREC_KNOB_GRAM_SPLIT, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
                       1.0f / ((float)N * (float)N), p->G);
 }
 
@@ -277,7 +288,34 @@ int launch_adjoint(spirec_plan p, const float2* y, float2* x)
     if (p->precision != SPIREC_FP32) return launch_adjoint_tc(p, y, x);
     const int N = p->N;
     // x[n][m] = (1/N) sum_l exp(-i2pi ky_l n) * (y_l exp(-i2pi kx_l m))
-    return phase_gemm(p, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
+    return phase_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
+}
+
+int contraction_split(spirec_plan p, int knob, int* value, int* sms_used)
+{
+    int sms = 0, rc;
+    if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
+    if (p->precision != SPIREC_FP32) {
+        int64_t P = 0;
+        if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
+        *value = (int)P;
+        *sms_used = (int)P;  // one CTA per SM (its shared memory)
+        return SPIREC_OK;
+    }
+    int R = 0, C = 0;
+    simt_shape(p, knob, &R, &C);
+    const int64_t nchunks = (p->L + KC - 1) / KC;
+    const int64_t tiles = (int64_t)((R + TM - 1) / TM) * ((C + TN - 1) / TN);
+    const int S = choose_splits(p, knob, sms, tiles, nchunks, (int64_t)R * C);
+    const int64_t cps = (nchunks + S - 1) / S;
+    const int64_t blocks = tiles * ((nchunks + cps - 1) / cps);
+    int per_sm = 0;
+    SPIREC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_phase_gemm<true>, NT, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t used = (blocks + per_sm - 1) / per_sm;
+    *value = S;
+    *sms_used = (int)(used < sms ? used : sms);
+    return SPIREC_OK;
 }
 
 int launch_forward(spirec_plan p, const float2* x, float2* y)

@@ -911,25 +911,24 @@ __global__ void k_absmax2(const float2* __restrict__ y, int64_t n, unsigned* ama
     if ((threadIdx.x & 31) == 0 && isfinite(m)) atomicMax(amax2, __float_as_uint(m));
 }
 
-int tc_phase_gemm(spirec_plan p, const int64_t* ka, const int64_t* kb, const float2* w, int R,
+// Output rows and columns of the two contractions: G is N x (2N - 1), D N x N.
+void tc_shape(const spirec_plan_s* p, int knob, int* R, int* C)
+{
+    *R = p->N;
+    *C = knob == SPIREC_KNOB_GRAM_SPLIT ? 2 * p->N - 1 : p->N;
+}
+
+int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, const float2* w, int R,
                   int C, int oa, int ob, int sa, int sb, float scale, float2* out)
 {
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
     const int tilesR = (R + TC_ROWS - 1) / TC_ROWS, tilesC = (C + TC_COLS - 1) / TC_COLS;
     const int64_t T = (int64_t)tilesR * tilesC;
     const int64_t U = T * K;
-    int dev = 0, sms = 0;
-    SPIREC_CK(cudaGetDevice(&dev));
-    SPIREC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
-    if (P > U) P = U;
-    // slots c + t < P + T must fit the partial buffer
-    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float)));
-    if (P + T > cap) P = cap - T;
-    if (P < 1) {
-        set_error("partial buffer too small for %lld tiles", (long long)T);
-        return SPIREC_EUNSUPPORTED;
-    }
+    int sms = 0, rc;
+    if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
+    int64_t P = 0;
+    if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
     unsigned* amax = nullptr;
     if (w && w != p->s) {
         // the kernel reads padded, plan-owned sample arrays
@@ -1045,14 +1044,38 @@ int tc_setup_attributes()
 int launch_gram_tc(spirec_plan p)
 {
     const int N = p->N;
-    return tc_phase_gemm(p, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
+    return tc_phase_gemm(p, SPIREC_KNOB_GRAM_SPLIT, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
                          1.0f / ((float)N * (float)N), p->G);
 }
 
 int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
 {
     const int N = p->N;
-    return tc_phase_gemm(p, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
+    return tc_phase_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
+}
+
+// The stream-K CTA count: the tuned value of the shape, else one CTA per SM
+// (at most kMaxCtas); never more than the work units, and the partial slots
+// c + t < P + T must fit the split-K buffer.
+int tc_ctas(spirec_plan p, int knob, int sms, int64_t* out)
+{
+    int R = 0, C = 0;
+    tc_shape(p, knob, &R, &C);
+    const int64_t K = (p->L + TC_KS - 1) / TC_KS;
+    const int64_t T = (int64_t)((R + TC_ROWS - 1) / TC_ROWS) * ((C + TC_COLS - 1) / TC_COLS);
+    const int64_t U = T * K;
+    int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
+    const int tuned = tune_lookup(knob, p, sms);
+    if (tuned > 0 && tuned < P) P = tuned;
+    if (P > U) P = U;
+    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float)));
+    if (P + T > cap) P = cap - T;
+    if (P < 1) {
+        set_error("partial buffer too small for %lld tiles", (long long)T);
+        return SPIREC_EUNSUPPORTED;
+    }
+    *out = P;
+    return SPIREC_OK;
 }
 
 }  // namespace spirec

@@ -39,6 +39,13 @@ SPIREC_PHI_QUADRATIC = 2
 SPIREC_MODE_TOEPLITZ = 0
 SPIREC_MODE_DIRECT = 1
 
+SPIREC_KNOB_GRAM_SPLIT = 0
+SPIREC_KNOB_ADJOINT_SPLIT = 1
+SPIREC_KNOB_LOOP_ROWS = 2
+SPIREC_NUM_KNOBS = 3
+SPIREC_TUNE_LATENCY = 0
+SPIREC_TUNE_THROUGHPUT = 1
+
 SPIREC_NUM_STAGES = 4
 STAGES = ("gram", "spectrum", "adjoint_d", "iterations")
 
@@ -81,6 +88,13 @@ SIGNATURES = {
     "spirec_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _I32, _P, _P, _P]),
     "spirec_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "spirec_server_destroy": (ctypes.c_int, [_P]),
+    "spirec_autotune": (ctypes.c_int, [_P, _I32, _I32, _P, _P]),
+    "spirec_tune_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I64, _I32, _I32]),
+    "spirec_tune_get": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I64, _I32, _P]),
+    "spirec_tune_count": (ctypes.c_int, [_P]),
+    "spirec_tune_clear": (ctypes.c_int, []),
+    "spirec_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "spirec_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "spirec_last_error": (ctypes.c_char_p, []),
     "spirec_version": (ctypes.c_char_p, []),
 }
@@ -206,6 +220,42 @@ def spirec_set_trajectory_cached(plan, cache, which):
 
 def spirec_set_mode(plan, mode):
     return _check(load().spirec_set_mode(plan, int(mode)))
+
+
+def spirec_autotune(plan, objective=SPIREC_TUNE_LATENCY, loop_iters=10):
+    """Returns (chosen values, median ms of the winners), one per knob."""
+    chosen = np.zeros(SPIREC_NUM_KNOBS, np.int32)
+    ms = np.zeros(SPIREC_NUM_KNOBS, np.float64)
+    _check(load().spirec_autotune(plan, int(objective), int(loop_iters), _host_ptr(chosen), _host_ptr(ms)))
+    return chosen, ms
+
+
+def spirec_tune_set(knob, N, M, precision, L, value, sms=0):
+    return _check(load().spirec_tune_set(int(knob), int(N), int(M), int(precision), int(L), int(sms), int(value)))
+
+
+def spirec_tune_get(knob, N, M, precision, L, sms=0):
+    v = ctypes.c_int32(0)
+    _check(load().spirec_tune_get(int(knob), int(N), int(M), int(precision), int(L), int(sms), ctypes.byref(v)))
+    return v.value
+
+
+def spirec_tune_count():
+    c = ctypes.c_int64(0)
+    _check(load().spirec_tune_count(ctypes.byref(c)))
+    return c.value
+
+
+def spirec_tune_clear():
+    return _check(load().spirec_tune_clear())
+
+
+def spirec_tune_save(path):
+    return _check(load().spirec_tune_save(os.fsencode(path)))
+
+
+def spirec_tune_load(path):
+    return _check(load().spirec_tune_load(os.fsencode(path)))
 
 
 def spirec_solve(plan, x0, iters, N):
