@@ -262,6 +262,52 @@ def run_direct_mode(spirec, prec, w, s_host):
     return out
 
 
+def run_half_quadratic(spirec, prec, w, s_host, budget=50, ref_iters=400):
+    """The half-quadratic minimiser (section 5's dual optimisation) against
+    PR+ CG at an equal budget of T applies on the metric's 512^2 workload:
+    PR+ CG for `budget` iterations, the half-quadratic one for outer x inner
+    = budget.  Reports each run's final J, its gap to J* (PR+ CG after
+    ref_iters iterations, relative to J(0) - J*) and its time (events on the
+    plan's stream, second of two runs)."""
+    import torch
+    N, M, L = w["N"], w["M"], w["kx"].shape[0]
+    st = torch.cuda.Stream()
+    p = spirec.Plan(N, L, M, prec, st.cuda_stream, w["kx"], w["ky"])
+    spirec.spirec_set_data(p.h, s_host)
+    spirec.spirec_set_reg(p.h, w["lambda1"], w["alpha1"], w["lambda0"], w["alpha0"], w["phi"])
+    x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+
+    def run(kind, inner, iters):
+        spirec.spirec_set_minimiser(p.h, kind, inner)
+        J = torch.zeros(iters + 1, dtype=torch.float64, device="cuda")
+        ms = 0.0
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            spirec.spirec_solve_dev(p.h, None, iters, x, J)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        return J.cpu().numpy(), ms
+
+    Jref, _ = run(spirec.SPIREC_MIN_PRCG, 0, ref_iters)
+    J0, Jstar = float(Jref[0]), float(Jref[-1])
+    out = {"budget_T_applies": budget, "J0": J0, "J_star_prcg_%d" % ref_iters: Jstar, "runs": {}}
+
+    def entry(J, ms):
+        return {"J": float(J[-1]), "gap": (float(J[-1]) - Jstar) / (J0 - Jstar), "ms": ms}
+
+    J, ms = run(spirec.SPIREC_MIN_PRCG, 0, budget)
+    out["runs"]["prcg_%d" % budget] = entry(J, ms)
+    for inner in (2, 5, 10):
+        J, ms = run(spirec.SPIREC_MIN_HALF_QUADRATIC, inner, budget // inner)
+        out["runs"]["hq_%dx%d" % (budget // inner, inner)] = entry(J, ms)
+    p.close()
+    return out
+
+
 def run_serving(spirec, prec, requests=2000, rate=200.0, iters=50, seed=5, slots=8):
     """Poisson request stream: sizes N in {64..384} step 64, L uniform in
     [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
@@ -660,6 +706,8 @@ def run_ours(args):
         extra["paper_experiment"] = run_paper_experiment(spirec, prec)
     if not args.no_direct:
         extra["direct_mode"] = run_direct_mode(spirec, prec, w, s)
+    if not args.no_half_quadratic:
+        extra["half_quadratic"] = run_half_quadratic(spirec, prec, w, s)
     if not args.no_serving:
         extra["serving"] = run_serving(spirec, prec)
         if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
@@ -759,6 +807,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-frame dynamic-series batch")
     ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
+    ap.add_argument("--no-half-quadratic", action="store_true",
+                    help="skip the half-quadratic vs PR+ CG comparison at an equal T-apply budget")
     ap.add_argument("--no-direct", action="store_true",
                     help="skip the per-iteration comparison with the direct (non-rewritten) formulation")
     ap.add_argument("--no-paper-experiment", action="store_true",

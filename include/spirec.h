@@ -132,8 +132,9 @@ int spirec_set_data_dev(spirec_plan plan, const float* s);
 int spirec_set_reg(spirec_plan plan, double lambda1, double alpha1, double lambda0,
                    double alpha0, int32_t phi);
 
-/* Run `iters` iterations of the pseudo-conjugate gradient with the
- * Polak-Ribiere correction (section 3.3) from x0:
+/* Run `iters` iterations of the plan's minimiser from x0 (spirec_set_minimiser;
+ * for the half-quadratic one an iteration is one outer step).  The default is
+ * the pseudo-conjugate gradient with the Polak-Ribiere correction (section 3.3):
  *   d0 = -grad J(x0); per iteration three majorize-minimize steps on
  *   h(t) = J(f + t d) from t = 0, f += t d, beta = max(0, Re<g',g'-g>/<g,g>),
  *   d = -g' + beta d, and d = -g' when Re<g', d> >= 0.
@@ -181,6 +182,27 @@ int spirec_set_trajectory_cached(spirec_plan plan, spirec_kcache cache, const in
 #define SPIREC_MODE_TOEPLITZ 0
 #define SPIREC_MODE_DIRECT 1
 int spirec_set_mode(spirec_plan plan, int32_t mode);
+
+/* Minimiser of spirec_solve.
+ *   SPIREC_MIN_PRCG (default): Polak-Ribiere conjugate gradient (PR+, with a
+ *     descent restart) and three majorize-minimize line-search steps per
+ *     iteration (section 3.3); one T apply per iteration.
+ *   SPIREC_MIN_HALF_QUADRATIC: the dual (half-quadratic) optimisation that
+ *     section 5 names, multiplicative form: each of the solve's iters outer
+ *     steps freezes the weights W_e = lambda_e phi'(r_e) / (2 r_e) at the
+ *     iterate (r_e the modulus of an edge difference or a pixel), which makes
+ *     a quadratic majorant of J touching it there, and takes inner_iters
+ *     linear conjugate-gradient steps on its normal equations
+ *     (T + sum_e W_e delta_e^H delta_e) f = D from the iterate (inner_iters T
+ *     applies).  J never increases; J_hist[k] is J after k outer steps.
+ * inner_iters: 1..1000 (ignored for SPIREC_MIN_PRCG).  Both minimisers work in
+ * either mode; the half-quadratic one runs as a captured graph of kernels, not
+ * in the persistent loop.  SPIREC_EINVAL for an unknown kind or inner_iters
+ * out of range; SPIREC_ENOMEM if its 12 N^2-byte weight buffer cannot be
+ * allocated. */
+#define SPIREC_MIN_PRCG 0
+#define SPIREC_MIN_HALF_QUADRATIC 1
+int spirec_set_minimiser(spirec_plan plan, int32_t kind, int32_t inner_iters);
 
 /* ---- operator access (device pointers, enqueued on the plan's stream) ---- */
 

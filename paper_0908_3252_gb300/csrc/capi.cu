@@ -151,7 +151,7 @@ void free_plan(spirec_plan p)
     if (!p) return;
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
-                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage};
+                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -314,7 +314,10 @@ int run_iterations(spirec_plan p, int iters)
         SPIREC_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t l0 = p->launches;
         int rc = SPIREC_OK;
-        for (int k = 0; k < iters && rc == SPIREC_OK; ++k) rc = cg_iteration(p, k, p->Jdev);
+        const bool hq = p->minimiser == SPIREC_MIN_HALF_QUADRATIC;
+        for (int k = 0; k < iters && rc == SPIREC_OK; ++k)
+            rc = hq ? hq_outer_step(p, k, p->Jdev) : cg_iteration(p, k, p->Jdev);
+        if (hq && rc == SPIREC_OK) rc = launch_hq_objective(p, p->Jdev + iters);  // J of the last iterate
         cudaError_t e = cudaStreamEndCapture(p->stream, &g);
         p->graph_kernels = p->launches - l0;  // captured, not yet run
         p->launches = l0;
@@ -366,6 +369,13 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
     } else {
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
+    }
+    if (p->minimiser == SPIREC_MIN_HALF_QUADRATIC) {
+        // outer steps in a captured graph; the iterate stays in f[0]
+        p->result_slot = 0;
+        rc = iters == 0 ? launch_hq_objective(p, p->Jdev) : run_iterations(p, iters);
+        if (rc != SPIREC_OK) return rc;
+        return tstop(p, e);
     }
     rc = SPIREC_EUNSUPPORTED;
     if (!direct && loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
@@ -482,7 +492,8 @@ int tune_contraction(spirec_plan p, int knob, int objective, int sms, int* chose
 int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, double* best_ms)
 {
     *chosen = 0;
-    if (p->mode == SPIREC_MODE_DIRECT || !loop_supported(p->M) || !p->Xd || getenv("SPIREC_NO_LOOP"))
+    if (p->mode == SPIREC_MODE_DIRECT || p->minimiser == SPIREC_MIN_HALF_QUADRATIC || !loop_supported(p->M) ||
+        !p->Xd || getenv("SPIREC_NO_LOOP"))
         return SPIREC_OK;
     int rc;
     if ((rc = ensure_J(p, iters)) != SPIREC_OK) return rc;
@@ -929,6 +940,32 @@ int spirec_set_mode(spirec_plan p, int32_t mode)
         p->graph = nullptr;
     }
     p->mode = mode;
+    return SPIREC_OK;
+}
+
+int spirec_set_minimiser(spirec_plan p, int32_t kind, int32_t inner_iters)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (kind != SPIREC_MIN_PRCG && kind != SPIREC_MIN_HALF_QUADRATIC) {
+        set_error("minimiser must be SPIREC_MIN_PRCG or SPIREC_MIN_HALF_QUADRATIC, not %d", kind);
+        return SPIREC_EINVAL;
+    }
+    if (kind == SPIREC_MIN_HALF_QUADRATIC && (inner_iters < 1 || inner_iters > 1000)) {
+        set_error("inner_iters must be in [1, 1000], not %d", inner_iters);
+        return SPIREC_EINVAL;
+    }
+    if (kind == SPIREC_MIN_HALF_QUADRATIC && !p->hqw) {
+        if ((rc = dalloc(p, &p->hqw, (size_t)3 * p->N * p->N)) != SPIREC_OK) return rc;
+    }
+    const int inner = kind == SPIREC_MIN_HALF_QUADRATIC ? inner_iters : 0;
+    if ((p->minimiser != kind || p->hq_inner != inner) && p->graph) {  // the captured loop is minimiser-specific
+        cudaStreamSynchronize(p->stream);
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->minimiser = kind;
+    p->hq_inner = inner;
     return SPIREC_OK;
 }
 

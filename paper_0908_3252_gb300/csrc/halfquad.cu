@@ -1,0 +1,261 @@
+// halfquad.cu -- the half-quadratic minimiser (the dual optimisation that
+// section 5 names as a replacement for the conjugate gradient), multiplicative
+// (Geman-Reynolds) form, on the rewritten criterion of section 3.4.
+//
+// phi(sqrt(u)) is concave in u for the Huber, hyperbolic and quadratic phi,
+// so phi(r) is the lower envelope of parabolas w r^2 + psi(w) touching at
+// w = phi'(r) / (2 r).  Freezing those weights at the iterate f^k turns J into
+// a quadratic that lies above J and touches it at f^k; its minimiser solves
+//     A f = D,   A = T + sum_e W_e delta_e^H delta_e,   D = H^H s,
+// with W_e = lambda_e phi'(r_e) / (2 r_e), delta_e f = f_q - f_p on the edge
+// p -> q of Omega1 and f_p on a pixel of Omega0, and T = H^H H the Toeplitz
+// operator.  One outer step = the weights, then n_in linear conjugate-gradient
+// steps on A f = D from f^k:
+//   outer   W from f; J(f) (one reduction)                 k_hq_outer
+//           r = D - T f - P f, p = r, rho = <r, r>          k_hq_residual
+//   inner   T p (zero-padded FFT, or H^H H p in direct mode)
+//           q = T p + P p; alpha = rho / Re<p, q>           k_hq_apply
+//           f += alpha p, T f += alpha T p, r -= alpha q;
+//           beta = <r, r> / rho, rho = <r, r>               k_hq_step
+//           p = r + beta p                                  k_hq_dir
+// P x = sum_e W_e delta_e^H delta_e x (an edge p -> q with z = x_q - x_p adds
+// W_e z at q and -W_e z at p).  T f is carried along (T f += alpha T p), so J
+// needs no extra T apply.  alpha = 0 when Re<p, q> <= 0 and beta = 0 when
+// rho = 0, as in the oracle.  Vectors FP32, sums float-float, scalars FP64.
+#include <stdint.h>
+
+#include "cg_device.cuh"
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace spirec {
+namespace {
+
+using cgd::f2axpy;
+using cgd::f2sub;
+using cgd::redot;
+
+// Weights of the quadratic: Wr[p] of the edge p -> p + 1, Wd[p] of p -> p + N,
+// W0[p] of the pixel (zero where there is no edge or the lambda is zero).
+struct HqW {
+    float* r;
+    float* d;
+    float* o;
+};
+
+// P x at pixel p from the weights and x at p and its four neighbours.
+__device__ __forceinline__ float2 penalty_normal_at(const float2* x, HqW W, int p, int N)
+{
+    const int n = p / N, m = p - n * N;
+    const float2 xc = __ldcg(x + p);
+    float2 out = make_float2(W.o[p] * xc.x, W.o[p] * xc.y);
+    if (m + 1 < N) out = f2axpy(-W.r[p], f2sub(__ldcg(x + p + 1), xc), out);
+    if (m > 0) out = f2axpy(W.r[p - 1], f2sub(xc, __ldcg(x + p - 1)), out);
+    if (n + 1 < N) out = f2axpy(-W.d[p], f2sub(__ldcg(x + p + N), xc), out);
+    if (n > 0) out = f2axpy(W.d[p - N], f2sub(xc, __ldcg(x + p - N)), out);
+    return out;
+}
+
+// Weights at f and J(f) = ||s||^2 - 2 Re<f, D> + Re<f, T f> + R(f).
+__global__ void __launch_bounds__(kVecThreads)
+k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int N, Reg reg, HqW W, float2* parts,
+           unsigned* counter, double* scal, double* Jout)
+{
+    const int P = N * N;
+    float v[3] = {0.f, 0.f, 0.f};  // R, Re<f, D>, Re<f, T f>
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int n = p / N, m = p - n * N;
+        const float2 fc = __ldcg(f + p);
+        float wr = 0.f, wd = 0.f, wo = 0.f;
+        if (reg.lambda1 != 0.f) {
+            if (m + 1 < N) {
+                const float2 z = f2sub(__ldcg(f + p + 1), fc);
+                const float r2 = redot(z, z);
+                wr = 0.5f * reg.lambda1 * phi_weight(reg.kind, reg.alpha1, r2);
+                v[0] = fmaf(reg.lambda1, phi_value(reg.kind, reg.alpha1, r2), v[0]);
+            }
+            if (n + 1 < N) {
+                const float2 z = f2sub(__ldcg(f + p + N), fc);
+                const float r2 = redot(z, z);
+                wd = 0.5f * reg.lambda1 * phi_weight(reg.kind, reg.alpha1, r2);
+                v[0] = fmaf(reg.lambda1, phi_value(reg.kind, reg.alpha1, r2), v[0]);
+            }
+        }
+        if (reg.lambda0 != 0.f) {
+            const float r2 = redot(fc, fc);
+            wo = 0.5f * reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2);
+            v[0] = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), v[0]);
+        }
+        W.r[p] = wr;
+        W.d[p] = wd;
+        W.o[p] = wo;
+        v[1] += redot(fc, __ldg(D + p));
+        v[2] += redot(fc, __ldcg(Tf + p));
+    }
+    FF bt[3];
+    block_partial<3>(v, bt);
+    store_parts<3>(bt, parts, kMaxParts);
+    if (last_block(counter)) {
+        FF t[3];
+        sum_parts_ff<3>(parts, kMaxParts, gridDim.x, t);
+        if (threadIdx.x == 0) {
+            const double R = ff_to_double(t[0]);
+            const double J = scal[S_SS] - 2.0 * ff_to_double(t[1]) + ff_to_double(t[2]) + R;
+            scal[S_J] = J;
+            scal[S_R] = R;
+            if (Jout) *Jout = J;
+            *counter = 0u;
+        }
+    }
+}
+
+// r = D - T f - P f, p = r, rho = <r, r>.
+__global__ void __launch_bounds__(kVecThreads)
+k_hq_residual(const float2* f, const float2* Tf, const float2* __restrict__ D, HqW W, int N, float2* r,
+              float2* pv, float2* parts, unsigned* counter, double* scal)
+{
+    const int P = N * N;
+    float v[1] = {0.f};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const float2 pf = penalty_normal_at(f, W, p, N);
+        const float2 tf = __ldcg(Tf + p), dv = __ldg(D + p);
+        const float2 rv = make_float2(dv.x - tf.x - pf.x, dv.y - tf.y - pf.y);
+        r[p] = rv;
+        pv[p] = rv;
+        v[0] += redot(rv, rv);
+    }
+    FF bt[1];
+    block_partial<1>(v, bt);
+    store_parts<1>(bt, parts, kMaxParts);
+    if (last_block(counter)) {
+        FF t[1];
+        sum_parts_ff<1>(parts, kMaxParts, gridDim.x, t);
+        if (threadIdx.x == 0) {
+            scal[S_HQ_RHO] = ff_to_double(t[0]);
+            *counter = 0u;
+        }
+    }
+}
+
+// q = T p + P p; alpha = rho / Re<p, q> (0 unless Re<p, q> > 0).
+__global__ void __launch_bounds__(kVecThreads)
+k_hq_apply(const float2* pv, const float2* Tp, HqW W, int N, float2* q, float2* parts, unsigned* counter,
+           double* scal)
+{
+    const int P = N * N;
+    float v[1] = {0.f};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const float2 pp = penalty_normal_at(pv, W, p, N);
+        const float2 tp = __ldcg(Tp + p);
+        const float2 qv = make_float2(tp.x + pp.x, tp.y + pp.y);
+        q[p] = qv;
+        v[0] += redot(__ldcg(pv + p), qv);
+    }
+    FF bt[1];
+    block_partial<1>(v, bt);
+    store_parts<1>(bt, parts, kMaxParts);
+    if (last_block(counter)) {
+        FF t[1];
+        sum_parts_ff<1>(parts, kMaxParts, gridDim.x, t);
+        if (threadIdx.x == 0) {
+            const double pq = ff_to_double(t[0]);
+            scal[S_HQ_ALPHA] = pq > 0.0 ? scal[S_HQ_RHO] / pq : 0.0;
+            *counter = 0u;
+        }
+    }
+}
+
+// f += alpha p, T f += alpha T p, r -= alpha q; beta = <r, r> / rho
+// (0 when rho = 0), rho = <r, r>.
+__global__ void __launch_bounds__(kVecThreads)
+k_hq_step(float2* f, float2* Tf, float2* r, const float2* pv, const float2* Tp, const float2* q, int N,
+          float2* parts, unsigned* counter, double* scal)
+{
+    const float a = (float)scal[S_HQ_ALPHA];
+    const int P = N * N;
+    float v[1] = {0.f};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        f[p] = f2axpy(a, __ldcg(pv + p), __ldcg(f + p));
+        Tf[p] = f2axpy(a, __ldcg(Tp + p), __ldcg(Tf + p));
+        const float2 rv = f2axpy(-a, __ldcg(q + p), __ldcg(r + p));
+        r[p] = rv;
+        v[0] += redot(rv, rv);
+    }
+    FF bt[1];
+    block_partial<1>(v, bt);
+    store_parts<1>(bt, parts, kMaxParts);
+    if (last_block(counter)) {
+        FF t[1];
+        sum_parts_ff<1>(parts, kMaxParts, gridDim.x, t);
+        if (threadIdx.x == 0) {
+            const double rho_new = ff_to_double(t[0]), rho = scal[S_HQ_RHO];
+            scal[S_HQ_BETA] = rho > 0.0 ? rho_new / rho : 0.0;
+            scal[S_HQ_RHO] = rho_new;
+            *counter = 0u;
+        }
+    }
+}
+
+// p = r + beta p.
+__global__ void __launch_bounds__(kVecThreads) k_hq_dir(const float2* r, float2* pv, int N, const double* scal)
+{
+    const float b = (float)scal[S_HQ_BETA];
+    const int P = N * N;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        pv[p] = f2axpy(b, __ldcg(pv + p), __ldcg(r + p));
+}
+
+float2* slot(spirec_plan p, int s) { return reinterpret_cast<float2*>(p->part) + (size_t)s * kMaxParts; }
+
+HqW weights_of(spirec_plan p)
+{
+    const size_t P = (size_t)p->N * p->N;
+    return HqW{p->hqw, p->hqw + P, p->hqw + 2 * P};
+}
+
+}  // namespace
+
+int launch_hq_objective(spirec_plan p, double* Jout)
+{
+    if (!p->hqw) {
+        set_error("the half-quadratic minimiser needs spirec_set_minimiser first");
+        return SPIREC_ESTATE;
+    }
+    k_hq_outer<<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(p->f[0], p->Tf, p->D, p->N, p->reg, weights_of(p),
+                                                                 slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
+    return SPIREC_OK;
+}
+
+// Outer step k: the iterate is f[0], T f in Tf; r in g, p in dbuf[0], T p in
+// Td, q in tmp.  J(f^k) goes to Jdev[k].
+int hq_outer_step(spirec_plan p, int k, double* Jdev)
+{
+    const int N = p->N, blocks = vec_blocks(N);
+    const HqW W = weights_of(p);
+    float2 *f = p->f[0], *pv = p->dbuf[0];
+    int rc;
+    if ((rc = launch_hq_objective(p, Jdev ? Jdev + k : nullptr)) != SPIREC_OK) return rc;
+    k_hq_residual<<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, p->D, W, N, p->g, pv, slot(p, P_UPD),
+                                                         p->counters + C_UPD, p->scal);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
+    for (int j = 0; j < p->hq_inner; ++j) {
+        rc = p->mode == SPIREC_MODE_DIRECT ? launch_normal_direct(p, pv, p->Td, false)
+                                           : launch_toeplitz(p, pv, p->Td, -1);
+        if (rc != SPIREC_OK) return rc;
+        k_hq_apply<<<blocks, kVecThreads, 0, p->stream>>>(pv, p->Td, W, N, p->tmp, slot(p, P_UPD),
+                                                          p->counters + C_UPD, p->scal);
+        SPIREC_CK(cudaGetLastError());
+        k_hq_step<<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, p->g, pv, p->Td, p->tmp, N, slot(p, P_UPD),
+                                                         p->counters + C_UPD, p->scal);
+        SPIREC_CK(cudaGetLastError());
+        k_hq_dir<<<blocks, kVecThreads, 0, p->stream>>>(p->g, pv, N, p->scal);
+        SPIREC_CK(cudaGetLastError());
+        p->launches += 3;
+    }
+    return SPIREC_OK;
+}
+
+}  // namespace spirec

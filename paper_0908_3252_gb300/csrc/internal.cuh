@@ -71,6 +71,9 @@ enum Scalar {
     S_TMP = 10,   // result of a one-off dot
     S_NUM0 = 11,  // penalty part of h'(0)
     S_DEN0 = 12,  // penalty part of the majorant curvature at t = 0
+    S_HQ_RHO = 13,    // half-quadratic inner CG: <r, r>
+    S_HQ_ALPHA = 14,  //   step alpha
+    S_HQ_BETA = 15,   //   direction beta
     S_PROF = 16,  // 16 slots: time (ns) block 0 of the persistent loop spent per phase
     S_NSCAL = 32
 };
@@ -155,6 +158,9 @@ struct spirec_plan_s {
     int graph_parity_out;
     int result_slot;  // the last solve left its iterate in f[result_slot]
     int mode;         // SPIREC_MODE_TOEPLITZ or SPIREC_MODE_DIRECT
+    int minimiser;    // SPIREC_MIN_PRCG or SPIREC_MIN_HALF_QUADRATIC
+    int hq_inner;     // linear CG steps per half-quadratic outer step
+    float* hqw;       // 3 x N x N half-quadratic weights (right edge, down edge, pixel)
     float2* ydir;     // L (+32): H d of the direct mode
 
     // timing
@@ -197,6 +203,11 @@ int cg_iteration(spirec_plan p, int k, double* Jdev);
 // T x as H^H (H x) (direct mode); with dot_q2_t1 also q2 = Re<x, T x> and the
 // first line-search step into scal (as the fused row pass of the FFT path).
 int launch_normal_direct(spirec_plan p, const float2* x, float2* Tx, bool dot_q2_t1);
+// Half-quadratic minimiser (halfquad.cu): J of f[0] (and the weights at it)
+// into Jout; one outer step k (weights, J(f^k) -> Jdev[k], hq_inner linear
+// CG steps on the frozen quadratic), iterate in f[0].
+int launch_hq_objective(spirec_plan p, double* Jout);
+int hq_outer_step(spirec_plan p, int k, double* Jdev);
 // The whole loop (first gradient + iters iterations) as one persistent
 // cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only, and
 // SPIREC_EUNSUPPORTED (nothing enqueued) when the image does not fit its

@@ -39,6 +39,9 @@ SPIREC_PHI_QUADRATIC = 2
 SPIREC_MODE_TOEPLITZ = 0
 SPIREC_MODE_DIRECT = 1
 
+SPIREC_MIN_PRCG = 0
+SPIREC_MIN_HALF_QUADRATIC = 1
+
 SPIREC_KNOB_GRAM_SPLIT = 0
 SPIREC_KNOB_ADJOINT_SPLIT = 1
 SPIREC_KNOB_LOOP_ROWS = 2
@@ -63,6 +66,7 @@ SIGNATURES = {
     "spirec_set_data_dev": (ctypes.c_int, [_P, _P]),
     "spirec_set_reg": (ctypes.c_int, [_P, _D, _D, _D, _D, _I32]),
     "spirec_set_mode": (ctypes.c_int, [_P, _I32]),
+    "spirec_set_minimiser": (ctypes.c_int, [_P, _I32, _I32]),
     "spirec_kcache_create": (ctypes.c_int, [ctypes.POINTER(_P), _I32, _I32, _I32, _I32, _P, _P, _P, _P]),
     "spirec_kcache_destroy": (ctypes.c_int, [_P]),
     "spirec_set_trajectory_cached": (ctypes.c_int, [_P, _P, _P, _I32]),
@@ -256,6 +260,10 @@ def spirec_tune_save(path):
 
 def spirec_tune_load(path):
     return _check(load().spirec_tune_load(os.fsencode(path)))
+
+
+def spirec_set_minimiser(plan, kind, inner_iters=0):
+    return _check(load().spirec_set_minimiser(plan, int(kind), int(inner_iters)))
 
 
 def spirec_solve(plan, x0, iters, N):
