@@ -23,6 +23,12 @@
 //   A  update   f += t3 d, T f += t3 T d, g = 2 (T f - D) + grad R(f), the six
 //               sums of J and beta; row FFTs of g -> X
 //               [reduce 6 -> J, beta]
+// At M = 1024 every sequence the FFTs see is half zero (N <= 512 inputs of a
+// 1024-point transform), so each 1024-point DFT splits exactly into two
+// 512-point ones, X[2k + h] = DFT512(x w1024^(h n))[k], and one warp per
+// half runs each as a register four-step (16 x 32): the row buffers hold a
+// row as [h][k] (element 2k + h of the DFT at h * 512 + k), the column pass
+// runs two warps per column, and the row passes two warps per row.
 // An initial update without a step gives g(x0), J(x0) and beta = 0.  Every
 // halo value is recomputed by the block that caches it from the same
 // operands as its owner uses, so all copies of a pixel are bitwise equal.
@@ -65,6 +71,7 @@ struct LoopArgs {
     float2* X;
     float2* Xd;
     const float* Chat;
+    const float* ChatS;  // M = 1024: Chat in the split order of the column pass
     const float2* tw;
     FftPlan fp;
     Reg reg;
@@ -96,17 +103,21 @@ struct Geo {
     static constexpr int CPC2 = CBPT2 * RPC;
     static constexpr int LDR = fftd::seq_len<MC>(MC);
     static constexpr int LDC = LDR + 4;
-    // M = 1024: the column pass runs one column per warp as a four-step
-    // 32 x 32 FFT (cols_fourstep), FS_COLS columns per group, each column's
-    // shared-memory area LDF long (the 32 x 33 transpose, odd row stride)
+    // M = 1024: the split 512-point FFTs (fwd512 / inv512), two warps per
+    // sequence; the column pass takes FS_COLS columns per group, each
+    // column's shared-memory area LDF long: the column itself, then the two
+    // warps' exchange areas of WA each (LDF = 2 mod 16 keeps the staging
+    // stores of 8 neighbouring columns on distinct banks)
     static constexpr bool FOURSTEP = MC == 1024;
     static constexpr int FS_COLS = 8;
-    static constexpr int LDF = 1058;
-    static constexpr int FB_ROWS = 2 * RPC * LDR;
+    static constexpr int WA = 544;  // 16 x 33 (forward), 32 x 17 (inverse)
+    static constexpr int LDF = 1090;
+    static constexpr int FB_ROWS = FOURSTEP ? 16 * WA : 2 * RPC * LDR;
     static constexpr int FB_COLS = FOURSTEP ? FS_COLS * LDF : CPC2 * LDC;
     static constexpr int FBUF = FB_ROWS > FB_COLS ? FB_ROWS : FB_COLS;
-    // staged radix-4 twiddles, then (four-step) the 32 x 32 table w^(k1 l)
-    static constexpr int TW_R4 = (fftd::staged_twiddles_size(MC) + 1) & ~1;  // keeps 16-byte alignment
+    // staged radix-4 twiddles (not at M = 1024), then (M = 1024) the tables
+    // T16[k2][l] = w512^(l k2) and WN[j][l] = w1024^(l + 32 j)
+    static constexpr int TW_R4 = FOURSTEP ? 0 : (fftd::staged_twiddles_size(MC) + 1) & ~1;  // 16-byte aligned
     static constexpr int TW = TW_R4 + (FOURSTEP ? 1024 : 0);
 };
 
@@ -210,110 +221,179 @@ struct Rows {
     __device__ __forceinline__ bool own(int r) const { return r >= R0 && r < R0 + nown; }
 };
 
-// ------------------------------------------------- phase B, M = 1024
+// ------------------------------------------------- split FFTs, M = 1024
 
-// One warp: the length-1024 DFT (conjugate twiddles when INV) of the
-// sequence whose element lane + 32 j is in x[j], as four steps: DFT over the
-// registers, twiddles w^(lane k1) from t2, transpose through this warp's
-// shared area (32 x 33), DFT over the registers.  Element lane + 32 k2 of the
-// result ends in x[bitrev5(k2)].
-template <bool INV>
-__device__ __forceinline__ void fourstep1024(float2 (&x)[32], float2* area, const float2* t2, int lane)
+// x[i] = row[i] + row[i + 16] (lanes 0-15) or (row[i] - row[i + 16]) w32^i
+// (lanes 16-31), i < 16.
+template <int I = 0>
+__device__ __forceinline__ void halves_fwd(float2 (&x)[16], const float2* row, bool half)
 {
-    freg::dft32_dif<INV>(x);
-#pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) {
-        const float2 w = t2[k1 * 32 + lane];
-        area[k1 * 33 + lane] = cmul(x[freg::bitrev5(k1)], INV ? conjf2(w) : w);
+    if constexpr (I < 16) {
+        const float2 u = row[I], v = row[I + 16];
+        x[I] = half ? freg::mulw<false, I>(freg::sub(u, v)) : freg::add(u, v);
+        halves_fwd<I + 1>(x, row, half);
     }
-    __syncwarp();
-#pragma unroll
-    for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
-    __syncwarp();
-    freg::dft32_dif<INV>(x);
 }
 
-// Columns [x0, x0 + 8) of the M = 1024 Toeplitz pass, one warp per column.
-// The block loads the 8 columns of X (row FFTs of g) and Xd (of the old
-// direction) as 64-byte row pieces, forms Xd = -X + beta Xd (-X on a
-// restart), stores it, and parks the columns in shared memory.  Warp c then
-// holds element n = lane + 32 j of its column in register j and runs
-//   DFT over j (registers) -> x w^(lane k1) -> transpose (shared, this warp's
-//   area) -> DFT over the registers = X[lane + 32 k2], k2 bit-reversed
-// times Chat, and the same steps with conjugate twiddles backwards (DIT first,
-// so the bit-reversed order is consumed in place).  Rows < n_in of the result
-// go back to X.  t2[k1 * 32 + l] = w^(k1 l), w = exp(-2 pi i / 1024).
-__device__ __forceinline__ void cols_fourstep(float2* X, float2* Xd, int n_in, int x0, const float* __restrict__ Chat,
-                                              const float2* t2, float2* fbuf, float beta, bool restart)
+// out[i] = x[i] (lanes 0-15) or x[i] w32^-i (lanes 16-31), i < 16.
+template <int I = 0>
+__device__ __forceinline__ void store_odd_twiddled(const float2 (&x)[16], float2* out, bool half)
 {
-    constexpr int M = 1024, COLS = 8, LDF = 1058;
+    if constexpr (I < 16) {
+        out[I] = half ? freg::mulw<true, I>(x[I]) : x[I];
+        store_odd_twiddled<I + 1>(x, out, half);
+    }
+}
+
+// One warp, the 512-point DFT of the sequence whose element lane + 32 j is in
+// x[j] (j < 16): a 16-point DFT over the registers, twiddles w512^(lane k2),
+// an exchange through this warp's area (16 x 33), a radix-2 step across the
+// lane halves (lane = k2 + 16 half: half 0 adds the two halves of the
+// exchanged row k2, half 1 subtracts and twiddles by w32^i), and a 16-point
+// DFT over the registers.  Element lane + 32 q of the result ends in
+// x[bitrev4(q)].  t16[k2 * 32 + l] = w512^(l k2).
+__device__ __forceinline__ void fwd512(float2 (&x)[16], float2* area, const float2* t16, int lane)
+{
+    freg::dft16_dif<false>(x);
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) area[k2 * 33 + lane] = cmul(x[freg::bitrev4(k2)], t16[k2 * 32 + lane]);
+    __syncwarp();
+    halves_fwd(x, area + (lane & 15) * 33, lane >= 16);
+    __syncwarp();
+    freg::dft16_dif<false>(x);
+}
+
+// One warp, u[n] = sum_k Z[k] w512^(-n k) for Z[lane + 32 q] in x[bitrev4(q)]
+// (the order fwd512 leaves): a 16-point inverse DFT over the registers gives,
+// per lane = k2 + 16 half, the inverse DFT over the even (half 0) or odd
+// (half 1, then times w32^-i) k1 of the k = k2 + 16 k1 with this k2; the two
+// combine through the area (32 x 17) into the 32-point inverse DFT over k1,
+// lane n1 takes its values for every k2, twiddles by w512^(-n1 k2) and runs
+// a 16-point inverse DFT over the registers.  u[lane + 32 n2] ends in
+// x[bitrev4(n2)].
+__device__ __forceinline__ void inv512(float2 (&x)[16], float2* area, const float2* t16, int lane)
+{
+    freg::dft16_dit<true>(x);
+    const bool half = lane >= 16;
+    store_odd_twiddled(x, area + lane * 17, half);
+    __syncwarp();
+    const int i = lane & 15;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const float2 e = area[k2 * 17 + i], o = area[(16 + k2) * 17 + i];
+        x[k2] = cmul(half ? freg::sub(e, o) : freg::add(e, o), conjf2(t16[k2 * 32 + lane]));
+    }
+    __syncwarp();
+    freg::dft16_dif<true>(x);
+}
+
+// Columns [x0, x0 + 8) of the M = 1024 Toeplitz pass, two warps per column
+// (warp 2 cc + h: column cc, output parity h).  The block loads the 8
+// columns of X (row FFTs of g) and Xd (of the old direction) as 64-byte row
+// pieces, forms Xd = -X + beta Xd (-X on a restart), stores it, and parks
+// the columns in shared memory.  Warp (cc, h) takes x[n] w1024^(h n) of its
+// column (n = lane + 32 j < 512; rows >= n_in are zero), runs fwd512 (the
+// column spectrum at ky = 2 k + h), multiplies by the spectrum, runs inv512,
+// and multiplies by w1024^(-h n); the two warps' results add up to the
+// filtered column, whose rows < n_in go back to X.  chs holds the spectrum in
+// this split order: chs[c * 1024 + h * 512 + k] = Chat[kx(c)][2 k + h].
+// wn[j * 32 + l] = w1024^(l + 32 j).
+__device__ __forceinline__ void cols_split(float2* X, float2* Xd, int n_in, int x0, const float* __restrict__ chs,
+                                           const float2* t16, const float2* wn, float2* fbuf, float beta,
+                                           bool restart)
+{
+    constexpr int M = 1024, COLS = 8, LDF = 1090, WA = 544;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cc = warp >> 1, h = warp & 1;
     {
         // 8 columns x 512 rows (rows >= n_in are zero), 8 per thread
         float2 v[8], o[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int e = tid + i * kLoopThreads;
-            const int y = e >> 3, cc = e & 7;
+            const int y = e >> 3, c = e & 7;
             const bool in = y < n_in;
-            v[i] = in ? __ldcg(X + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
-            o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
+            v[i] = in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
+            o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int e = tid + i * kLoopThreads;
-            const int y = e >> 3, cc = e & 7;
+            const int y = e >> 3, c = e & 7;
             if (y < n_in) {
                 v[i] = fftd::new_direction(v[i], o[i], beta, restart);
-                Xd[(int64_t)y * M + x0 + cc] = v[i];
+                Xd[(int64_t)y * M + x0 + c] = v[i];
             }
-            fbuf[cc * LDF + y] = v[i];
+            fbuf[c * LDF + y] = v[i];
         }
     }
     __syncthreads();
-    if (warp < COLS) {
-        float2* area = fbuf + warp * LDF;
-        const float* ch = Chat + (int64_t)(x0 + warp) * M;
-        float2 x[32];
+    // the spectrum values of this warp (used after the forward FFT)
+    float hs[16];
+    {
+        const float* ch = chs + (int64_t)(x0 + cc) * M + h * 512 + lane;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = area[lane + 32 * j];
-        __syncwarp();
-        // forward: DFT over registers, twiddles, transpose, DFT over registers
-        freg::dft32_dif<false, true>(x);
+        for (int q = 0; q < 16; ++q) hs[q] = __ldcg(ch + 32 * q);
+    }
+    float2 x[16];
+    {
+        const float2* col = fbuf + cc * LDF + lane;
 #pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) area[k1 * 33 + lane] = cmul(x[freg::bitrev5(k1)], t2[k1 * 32 + lane]);
-        __syncwarp();
+        for (int j = 0; j < 16; ++j) x[j] = h ? cmul(col[32 * j], wn[j * 32 + lane]) : col[32 * j];
+    }
+    __syncthreads();  // the columns are in registers: their areas become the exchange areas
+    float2* area = fbuf + cc * LDF + h * WA;
+    fwd512(x, area, t16, lane);
 #pragma unroll
-        for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
-        __syncwarp();
-        float h[32];
+    for (int q = 0; q < 16; ++q) {
+        float2& r = x[freg::bitrev4(q)];
+        r = make_float2(r.x * hs[q], r.y * hs[q]);
+    }
+    inv512(x, area, t16, lane);
+    if (h) {
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) h[k2] = __ldcg(ch + lane + 32 * k2);
-        freg::dft32_dif<false>(x);  // X[lane + 32 k2] in x[bitrev5(k2)]
+        for (int n2 = 0; n2 < 16; ++n2)
+            area[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
+    }
+    __syncthreads();
+    if (!h) {
+        const float2* other = fbuf + cc * LDF + WA;
+        float2* col = fbuf + cc * LDF;
 #pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) {
-            float2& r = x[freg::bitrev5(k2)];
-            r = make_float2(r.x * h[k2], r.y * h[k2]);
-        }
-        // inverse: DIT over registers (bit-reversed in), conjugate twiddles,
-        // transpose, DIF over registers
-        freg::dft32_dit<true>(x);
-#pragma unroll
-        for (int m1 = 0; m1 < 32; ++m1) area[m1 * 33 + lane] = cmul(x[m1], conjf2(t2[m1 * 32 + lane]));
-        __syncwarp();
-#pragma unroll
-        for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
-        __syncwarp();
-        freg::dft32_dif<true>(x);  // y[lane + 32 m2] in x[bitrev5(m2)]
-#pragma unroll
-        for (int m2 = 0; m2 < 16; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
+        for (int n2 = 0; n2 < 16; ++n2) col[lane + 32 * n2] = freg::add(x[freg::bitrev4(n2)], other[lane + 32 * n2]);
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int e = tid + i * kLoopThreads;
-        const int y = e >> 3, cc = e & 7;
-        if (y < n_in) X[(int64_t)y * M + x0 + cc] = fbuf[cc * LDF + y];
+        const int y = e >> 3, c = e & 7;
+        if (y < n_in) X[(int64_t)y * M + x0 + c] = fbuf[c * LDF + y];
+    }
+    (void)COLS;
+}
+
+// Two warps per row (warp 2 q + h), the split row FFTs at M = 1024 of rows
+// [g0, g0 + 8) of the own-row cache src (N values a row, zero beyond):
+// X[row][h * 512 + k] = DFT1024(src row)[2 k + h].
+__device__ __forceinline__ void rows_fwd_split(const float2* src, int N, int nrows, float2* Xrows, float2* fbuf,
+                                               const float2* t16, const float2* wn)
+{
+    constexpr int M = 1024, WA = 544;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp >> 1, h = warp & 1;
+    if (q < nrows) {
+        float2 x[16];
+        const float2* r = src + q * N;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int m = lane + 32 * j;
+            const float2 v = m < N ? r[m] : make_float2(0.f, 0.f);
+            x[j] = h ? cmul(v, wn[j * 32 + lane]) : v;
+        }
+        fwd512(x, fbuf + warp * WA, t16, lane);
+        float2* out = Xrows + (int64_t)q * M + h * 512 + lane;
+#pragma unroll
+        for (int q2 = 0; q2 < 16; ++q2) out[32 * q2] = x[freg::bitrev4(q2)];
     }
 }
 
@@ -339,6 +419,37 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
         for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) cTf[e] = cgd::f2axpy(t, cTd[e], cTf[e]);
         __syncthreads();
     }
+    if constexpr (G::FOURSTEP) {
+        // gradient of every own pixel, then the split row FFTs of g, two
+        // warps a row, eight rows at a time
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
+            const int oq = e / N, m = e - oq * N, n = R.R0 + oq;
+            const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
+            const float2* row = cf + R.cache(n);
+            const float2 fc = row[m];
+            const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
+            const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
+            const float2 tf = cTf[e], dv = cD[e];
+            float rv;
+            const float2 gp = cgd::grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+            a[0] += cgd::redot(gp, gp);
+            if (!FIRST) {
+                a[1] += cgd::redot(gp, cg[e]);
+                a[2] += cgd::redot(gp, cd[R.cache(n) + m]);
+            }
+            a[3] += rv;
+            a[4] += cgd::redot(fc, dv);
+            a[5] += cgd::redot(fc, tf);
+            cg[e] = gp;
+            A.g[(int64_t)n * N + m] = gp;
+        }
+        if (do_fft) {
+            __syncthreads();  // g of every own row is in cg
+            for (int g0 = 0; g0 < R.nown; g0 += 8)
+                rows_fwd_split(cg + g0 * N, N, min(8, R.nown - g0), A.X + (int64_t)(R.R0 + g0) * MC, fbuf, stw,
+                               stw + 512);
+        }
+    } else {
     for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
         const int nr = min(RX * G::RPC, R.nown - g0);
 #pragma unroll
@@ -382,6 +493,7 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
             __syncthreads();
         }
     }
+    }
 }
 
 // ---------------------------------------------------------------- phase C
@@ -398,24 +510,38 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
     using G = Geo<MC>;
     const int N = R.N;
     if constexpr (G::FOURSTEP) {
-        // one warp per row (at most FS_COLS warps: one shared area each): the
-        // rows of Y -> T d (columns < N)
+        // the split row IFFTs of Y, two warps a row (warp 2 q + h takes the
+        // elements 2 k + h), eight rows at a time: T d = u_0 + w1024^(-m) u_1
+        // on the columns m < N
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int g0 = 0; g0 < R.nown; g0 += G::FS_COLS) {
-            const int q = g0 + warp;
-            if (warp < G::FS_COLS && q < R.nown) {
-                const float2* yr = A.X + (int64_t)(R.R0 + q) * MC;
-                float2 x[32];
+        const int h = warp & 1;
+        float2* area = fbuf + warp * G::WA;
+        for (int g0 = 0; g0 < R.nown; g0 += 8) {
+            const int q = g0 + (warp >> 1);
+            const bool active = q < R.nown;
+            float2 x[16];
+            if (active) {
+                const float2* yr = A.X + (int64_t)(R.R0 + q) * MC + h * 512 + lane;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) x[j] = __ldcg(yr + lane + 32 * j);
-                fourstep1024<true>(x, fbuf + warp * G::LDF, stw + G::TW_R4, lane);
+                for (int q2 = 0; q2 < 16; ++q2) x[freg::bitrev4(q2)] = __ldcg(yr + 32 * q2);
+                inv512(x, area, stw, lane);
+                if (h) {
+                    const float2* wn = stw + 512;
 #pragma unroll
-                for (int m2 = 0; m2 < 16; ++m2) {
-                    const int m = lane + 32 * m2;
-                    if (m < N) cTd[q * N + m] = x[freg::bitrev5(m2)];
+                    for (int n2 = 0; n2 < 16; ++n2)
+                        area[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
                 }
             }
-            __syncwarp();  // the area is reused by the next row of this warp
+            __syncthreads();
+            if (active && !h) {
+                const float2* other = area + G::WA;
+#pragma unroll
+                for (int n2 = 0; n2 < 16; ++n2) {
+                    const int m = lane + 32 * n2;
+                    if (m < N) cTd[q * N + m] = freg::add(x[freg::bitrev4(n2)], other[m]);
+                }
+            }
+            __syncthreads();
         }
     }
     for (int g0 = 0; g0 < (G::FOURSTEP ? 0 : R.nown); g0 += RX * G::RPC) {
@@ -513,7 +639,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     const bool wide_cols = G::CBPT2 > G::CBPT && MC / G::CPC2 >= (int)gridDim.x;
     const int cpc = G::FOURSTEP ? G::FS_COLS : wide_cols ? G::CPC2 : G::CPC;
     const int col_groups = MC / cpc;
-    const bool rx2 = RB >= 2 * G::RPC;  // rows: two FFT groups per batch
+    // rows: two FFT groups per batch (the split FFTs of M = 1024 have no groups)
+    const bool rx2 = !G::FOURSTEP && RB >= 2 * G::RPC;
+    constexpr int RX2 = G::FOURSTEP ? 1 : 2;
     const bool prof = blockIdx.x == 0;
     unsigned seq = 0;
     if (threadIdx.x == 0) {
@@ -531,10 +659,15 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
 
     // ---- caches: twiddles, f of the cached rows, T f and D of the own rows
     {
-        fftd::build_staged_twiddles<MC>(A.tw, stw);
-        if constexpr (G::FOURSTEP)
-            for (int e = threadIdx.x; e < 1024; e += kLoopThreads)
-                stw[G::TW_R4 + e] = __ldg(A.tw + (((e >> 5) * (e & 31)) & (MC - 1)));
+        if constexpr (G::FOURSTEP) {
+            // T16[k2][l] = w512^(l k2) = w1024^(2 l k2); WN[j][l] = w1024^(l + 32 j)
+            for (int e = threadIdx.x; e < 512; e += kLoopThreads) {
+                stw[e] = __ldg(A.tw + ((2 * (e & 31) * (e >> 5)) & (MC - 1)));
+                stw[512 + e] = __ldg(A.tw + e);
+            }
+        } else {
+            fftd::build_staged_twiddles<MC>(A.tw, stw);
+        }
         const int nc = (R.hhi - R.hlo + 1) * N;
         const float2* src = A.f0 + (int64_t)R.hlo * N;
         float2* dst = cf + R.cache(R.hlo);
@@ -551,7 +684,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     {
         float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (rx2)
-            phase_update<MC, true, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+            phase_update<MC, true, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
         else
             phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
         if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
@@ -576,7 +709,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * cpc;
             if constexpr (G::FOURSTEP)
-                cols_fourstep(A.X, A.Xd, N, x0, A.Chat, stw + G::TW_R4, fbuf, beta, restart);
+                cols_split(A.X, A.Xd, N, x0, A.ChatS, stw, stw + 512, fbuf, beta, restart);
             else if (wide_cols)
                 fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
                                                  beta, restart);
@@ -592,7 +725,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             if (rx2)
-                phase_rows<MC, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+                phase_rows<MC, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
             else
                 phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
             mark(2);
@@ -625,7 +758,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         {
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (rx2)
-                phase_update<MC, false, 2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+                phase_update<MC, false, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             else
                 phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
@@ -762,6 +895,17 @@ bool loop_shape(const spirec_plan_s* p, int* RB_out, int* grid_out, size_t* smem
     return false;
 }
 
+// The spectrum in the split order of the M = 1024 column pass:
+// out[c * 1024 + h * 512 + k] = Chat[kx * 1024 + 2 k + h], kx = 2 (c mod 512) + c / 512
+// (column c of the split row layout holds the frequency kx).
+__global__ void k_chat_split(const float* __restrict__ Chat, float* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // < 1024 * 1024
+    const int c = i >> 10, h = (i >> 9) & 1, k = i & 511;
+    const int kx = 2 * (c & 511) + (c >> 9);
+    out[i] = __ldg(Chat + kx * 1024 + 2 * k + h);
+}
+
 struct LaunchLoop {
     spirec_plan p;
     int iters;
@@ -790,6 +934,14 @@ struct LaunchLoop {
             A.X = p->X;
             A.Xd = p->Xd;
             A.Chat = p->Chat;
+            if constexpr (Geo<MC>::FOURSTEP) {
+                // the split-order copy, in the spectrum build's scratch (M x M complex)
+                float* chs = reinterpret_cast<float*>(p->cwork);
+                k_chat_split<<<1024 * 1024 / 256, 256, 0, p->stream>>>(p->Chat, chs);
+                SPIREC_CK(cudaGetLastError());
+                p->launches += 1;
+                A.ChatS = chs;
+            }
             A.tw = p->twiddle;
             A.fp = p->fft;
             A.reg = p->reg;

@@ -1,8 +1,8 @@
-// fft_reg.cuh -- 32-point DFTs held entirely in one thread's registers, the
-// building block of the warp-per-sequence four-step FFT of length
-// 1024 = 32 x 32 (cg_loop.cu): a DFT over each lane's 32 registers, a
-// twiddle multiply, one transpose through shared memory inside the warp,
-// and a DFT over the registers again.
+// fft_reg.cuh -- 32- and 16-point DFTs held entirely in one thread's
+// registers, the building blocks of the warp-level four-step FFTs of the
+// persistent loop (cg_loop.cu): a DFT over each lane's registers, a twiddle
+// multiply, one exchange through shared memory inside the warp, and a DFT
+// over the registers again.
 //
 // Radix-2 in registers, every index a compile-time constant (the loops are
 // fully unrolled), so no data moves between stages.  w = exp(-2 pi i / 32)
@@ -139,6 +139,83 @@ __device__ __forceinline__ void dft32_dit(float2 (&x)[32])
     dit_stage<8>(x);
     dit_twiddle_row<INV, 16, 0>(x);
     dit_stage<16>(x);
+}
+
+// ------------------------------------------------------- 16-point DFTs
+// The same radix-2 forms over 16 registers; w16^m = w^(2m).
+
+__host__ __device__ constexpr int bitrev4(int r)
+{
+    return ((r & 1) << 3) | ((r & 2) << 1) | ((r & 4) >> 1) | ((r & 8) >> 3);
+}
+
+template <int SPAN, bool HALF>
+__device__ __forceinline__ void dif16_stage(float2 (&x)[16])
+{
+#pragma unroll
+    for (int b = 0; b < 16; b += 2 * SPAN) {
+#pragma unroll
+        for (int i = 0; i < SPAN; ++i) {
+            const float2 a = x[b + i];
+            if constexpr (HALF) {
+                x[b + i + SPAN] = a;
+            } else {
+                x[b + i] = add(a, x[b + i + SPAN]);
+                x[b + i + SPAN] = sub(a, x[b + i + SPAN]);
+            }
+        }
+    }
+}
+
+// twiddles w16^(I * 8 / SPAN) = w^(I * 16 / SPAN) on the upper halves
+template <bool INV, int SPAN, int I>
+__device__ __forceinline__ void twiddle16_row(float2 (&x)[16])
+{
+    if constexpr (I < SPAN) {
+#pragma unroll
+        for (int b = 0; b < 16; b += 2 * SPAN) x[b + I + SPAN] = mulw<INV, I * (16 / SPAN)>(x[b + I + SPAN]);
+        twiddle16_row<INV, SPAN, I + 1>(x);
+    }
+}
+
+template <int SPAN>
+__device__ __forceinline__ void dit16_stage(float2 (&x)[16])
+{
+#pragma unroll
+    for (int b = 0; b < 16; b += 2 * SPAN) {
+#pragma unroll
+        for (int i = 0; i < SPAN; ++i) {
+            const float2 a = x[b + i], c = x[b + i + SPAN];
+            x[b + i] = add(a, c);
+            x[b + i + SPAN] = sub(a, c);
+        }
+    }
+}
+
+// Natural order in, bit-reversed out: X[k] ends in x[bitrev4(k)].
+template <bool INV, bool HALF_IN = false>
+__device__ __forceinline__ void dft16_dif(float2 (&x)[16])
+{
+    dif16_stage<8, HALF_IN>(x);
+    twiddle16_row<INV, 8, 0>(x);
+    dif16_stage<4, false>(x);
+    twiddle16_row<INV, 4, 0>(x);
+    dif16_stage<2, false>(x);
+    twiddle16_row<INV, 2, 0>(x);
+    dif16_stage<1, false>(x);
+}
+
+// Bit-reversed order in (x[bitrev4(k)] holds input k), natural order out.
+template <bool INV>
+__device__ __forceinline__ void dft16_dit(float2 (&x)[16])
+{
+    dit16_stage<1>(x);
+    twiddle16_row<INV, 2, 0>(x);
+    dit16_stage<2>(x);
+    twiddle16_row<INV, 4, 0>(x);
+    dit16_stage<4>(x);
+    twiddle16_row<INV, 8, 0>(x);
+    dit16_stage<8>(x);
 }
 
 }  // namespace freg

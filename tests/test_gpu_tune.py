@@ -123,7 +123,7 @@ def test_fewer_ctas_than_tiles(sp, prec):
         assert rel(D[n, m], Do) < TOL[prec], val
 
 
-@pytest.mark.parametrize("N,M", [(48, 128), (100, 256)])
+@pytest.mark.parametrize("N,M", [(48, 128), (100, 256), (260, 1024)])
 def test_every_loop_shape_matches_the_oracle(sp, N, M):
     """The persistent loop with each rows-per-block value the tuner tries,
     and odd ones (the last block owns fewer rows), against the oracle; a
