@@ -221,6 +221,20 @@ struct Rows {
     __device__ __forceinline__ bool own(int r) const { return r >= R0 && r < R0 + nown; }
 };
 
+// (row, column) of the first element of a per-pixel loop over rows of N
+// pixels that starts at threadIdx.x, and of the next one when it strides by
+// the block size (one division a loop, none a pixel).
+__device__ __forceinline__ int first_row(int N) { return (int)threadIdx.x / N; }
+__device__ __forceinline__ int first_col(int N) { return (int)threadIdx.x - first_row(N) * N; }
+__device__ __forceinline__ void step_pixel(int& q, int& m, int N)
+{
+    m += kLoopThreads;
+    while (m >= N) {
+        m -= N;
+        ++q;
+    }
+}
+
 // ------------------------------------------------- split FFTs, M = 1024
 
 // x[i] = row[i] + row[i + 16] (lanes 0-15) or (row[i] - row[i + 16]) w32^i
@@ -422,8 +436,8 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
     if constexpr (G::FOURSTEP) {
         // gradient of every own pixel, then the split row FFTs of g, two
         // warps a row, eight rows at a time
-        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
-            const int oq = e / N, m = e - oq * N, n = R.R0 + oq;
+        for (int e = threadIdx.x, oq = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(oq, m, N)) {
+            const int n = R.R0 + oq;
             const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
             const float2* row = cf + R.cache(n);
             const float2 fc = row[m];
@@ -571,16 +585,16 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
     {
         const int nc = (R.hhi - R.hlo + 1) * N;
         float2* dr0 = cd + R.cache(R.hlo);
-        for (int e = threadIdx.x; e < nc; e += kLoopThreads) {
-            const int rq = e / N, m = e - rq * N, r = R.hlo + rq;
+        for (int e = threadIdx.x, rq = first_row(N), m = first_col(N); e < nc; e += kLoopThreads, step_pixel(rq, m, N)) {
+            const int r = R.hlo + rq;
             const float2 g = R.own(r) ? cg[(r - R.R0) * N + m] : __ldcg(A.g + (int64_t)r * N + m);
             dr0[e] = fftd::new_direction(g, dr0[e], beta, restart);
         }
     }
     __syncthreads();
     const Reg reg = A.reg;
-    for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
-        const int q = e / N, m = e - q * N, n = R.R0 + q;
+    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
+        const int n = R.R0 + q;
         const bool has_r = m + 1 < N, has_d = n + 1 < N;
         const float2* fr0 = cf + R.cache(n);
         const float2* dr0 = cd + R.cache(n);
@@ -599,8 +613,8 @@ __device__ __forceinline__ void phase_ls(const Reg& reg, const Rows& R, const fl
                                          float t, float (&acc)[2])
 {
     const int N = R.N;
-    for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
-        const int q = e / N, m = e - q * N, n = R.R0 + q;
+    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
+        const int n = R.R0 + q;
         const bool has_r = m + 1 < N, has_d = n + 1 < N;
         const float2* fr0 = cf + R.cache(n);
         const float2* dr0 = cd + R.cache(n);
