@@ -279,6 +279,20 @@ __device__ __forceinline__ float2 phasor_fast(int64_t kq, int j)
     return make_float2(cs, sn);
 }
 
+// exp(+i 2 pi k s a) for the fixed-point k, a count a >= 0 and a sign s = +-1
+// folded into scale = s * 2 pi / 2^32: the top 32 bits of kq * a mod 2^64 are
+// hi(kq) a + umulhi(lo(kq), a) mod 2^32 (two integer multiply-adds), the
+// signed fraction of a cycle; negating the angle conjugates the phasor.  The
+// same phase as phasor_fast up to one unit of the 32-bit fraction.
+__device__ __forceinline__ float2 phasor_signed(int64_t kq, uint32_t a, float scale)
+{
+    const uint32_t lo = (uint32_t)(uint64_t)kq, hi = (uint32_t)((uint64_t)kq >> 32);
+    const uint32_t top = __umulhi(lo, a) + hi * a;
+    float sn, cs;
+    __sincosf((float)(int)top * scale, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
 // *p += v at the memory (round-to-nearest FP32 add, no reply).
 __device__ __forceinline__ void red_global(float* p, float v)
 {
@@ -468,17 +482,24 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
-            const int ja = i0 + r + oa;
+            // the signed index s j = +-a of the row (column) and the angle
+            // scale carrying its sign; samples past L (only in the last
+            // chunk) contribute zero
+            constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
+            const int sja = sa * (i0 + r + oa);
+            const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
+            const float sca = sja < 0 ? -kRev : kRev;
+            const bool tail = l0 + TC_KS > L;
             float re[8], im[8];
             uint4 rh, rl, ih, il;
             // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int l = 8 * g + e;
-                float2 v = phasor_fast(ka_s[l], ja);
-                if (l0 + l >= L) v = make_float2(0.f, 0.f);
+                float2 v = phasor_signed(ka_s[l], aa, sca);
+                if (tail && l0 + l >= L) v = make_float2(0.f, 0.f);
                 re[e] = v.x;
-                im[e] = sa < 0 ? -v.y : v.y;
+                im[e] = v.y;
             }
             split8<BF16>(re, rh, rl);
             split8<BF16>(im, ih, il);
@@ -489,19 +510,20 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             // B columns r and 128 + r: [Br | Bi]
 #pragma unroll 1
             for (int h = 0; h < 2; ++h) {
-                const int rb = r + 128 * h, jb = c0 + rb + ob;
+                const int rb = r + 128 * h, sjb = sb * (c0 + rb + ob);
+                const uint32_t ab = (uint32_t)(sjb < 0 ? -sjb : sjb);
+                const float scb = sjb < 0 ? -kRev : kRev;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int l = 8 * g + e;
-                    float2 v = phasor_fast(kb_s[l], jb);
-                    if (sb < 0) v.y = -v.y;
+                    float2 v = phasor_signed(kb_s[l], ab, scb);
                     if (WEIGHTED) {
                         float2 ww = w_s[l];
                         ww.x *= wmul;
                         ww.y *= wmul;
                         v = cmul(v, ww);
                     }
-                    if (l0 + l >= L) v = make_float2(0.f, 0.f);
+                    if (tail && l0 + l >= L) v = make_float2(0.f, 0.f);
                     re[e] = v.x;
                     im[e] = v.y;
                 }
