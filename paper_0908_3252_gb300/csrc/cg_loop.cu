@@ -164,7 +164,6 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
                 return false;
             }
         }
-        __nanosleep(16);
     }
 }
 

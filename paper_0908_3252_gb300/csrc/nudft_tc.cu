@@ -461,11 +461,16 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
         for (int it = 0; it < n; ++it) {
             const int s = it % TC_STAGES;
             const uint32_t use = (uint32_t)(it / TC_STAGES);
-            if (tid == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+            // stage s is free once the MMA has consumed its previous use.
+            // Each warp waits for that itself (no producer-wide barrier), so
+            // warps drift apart by at most the ring depth: a warp past the
+            // wait for stage it knows every producer has finished stage
+            // it - 2, whose trajectory slot the TMA of stage it + 2 reuses.
+            if (lane == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
-            producers_sync();  // stage s is free
+            __syncwarp();
             if (*abort_flag) break;
             if (tid == 0 && it + 2 < n) issue_traj(it + 2);
             if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1)) {
