@@ -364,20 +364,25 @@ __host__ __device__ __forceinline__ int64_t unit_start(int64_t c, int64_t U, int
 // Segment bookkeeping along a CTA's stages: a segment is at most TC_SEG
 // stages of one tile.  Producers and the MMA issuer step it identically.
 struct SegWalk {
-    int64_t u0, K;
+    int64_t K;
+    int64_t tile, kc;  // tile and chunk of the current stage's unit
     int seg = -1, pos = 0;
-    int64_t tile = -1;
     bool first_of_tile = false;
+    // the first unit u0 (one division; every later stage steps the chunk)
+    __device__ __forceinline__ SegWalk(int64_t u0, int64_t K_) : K(K_), tile(u0 / K_), kc(u0 % K_) {}
     // advance to stage it (called for it = 0, 1, 2, ...)
     __device__ __forceinline__ void step(int it)
     {
-        const int64_t u = u0 + it;
-        const int64_t t = u / K;
-        if (it == 0 || t != tile || pos == TC_SEG - 1) {
-            first_of_tile = it == 0 || t != tile;
+        bool new_tile = it == 0;
+        if (it > 0 && ++kc == K) {
+            kc = 0;
+            ++tile;
+            new_tile = true;
+        }
+        if (new_tile || pos == TC_SEG - 1) {
+            first_of_tile = new_tile;
             ++seg;
             pos = 0;
-            tile = t;
         } else {
             ++pos;
         }
@@ -385,8 +390,7 @@ struct SegWalk {
     // stage it (current) closes its segment
     __device__ __forceinline__ bool closes(int it, int n) const
     {
-        const int64_t u = u0 + it;
-        return it == n - 1 || (u + 1) % K == 0 || pos == TC_SEG - 1;
+        return it == n - 1 || kc == K - 1 || pos == TC_SEG - 1;
     }
 };
 
@@ -438,9 +442,12 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
     if (warp < TC_PRODUCERS / 32) {
         // ------------------------------------------------ producers
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
-        // TMA feed of the trajectory (and data) chunk of stage `it` into ring slot it % 4
+        // TMA feed of the trajectory (and data) chunk of stage `it` into ring
+        // slot it % 4; stages are issued in order, kci is the chunk of the next
+        int64_t kci = u0 % K;
         auto issue_traj = [&](int it) {
-            const int64_t l0 = ((u0 + it) % K) * TC_KS;
+            const int64_t l0 = kci * TC_KS;
+            if (++kci == K) kci = 0;
             int64_t cnt = L - l0;
             if (cnt > TC_KS) cnt = TC_KS;
             const uint32_t bytes = (uint32_t)(((cnt + 1) & ~1) * 8);  // multiple of 16; arrays are padded
@@ -456,6 +463,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
         const int r = tid & 127, g = tid >> 7;  // operand row (A) / column (B), sample group
         SegWalk sw{u0, K};
+        int trow = (int)(sw.tile / tilesC), tcol = (int)(sw.tile % tilesC);  // stepped with the tile
         int64_t dtile = 0;  // tile of the segment being accumulated
         bool dfirst = true;
         for (int it = 0; it < n; ++it) {
@@ -478,9 +486,12 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
                 atomicOr(err, kErrTimeout);
             }
             sw.step(it);
-            const int64_t u = u0 + it, t = u / K;
-            const int64_t l0 = (u % K) * TC_KS;
-            const int i0 = (int)(t / tilesC) * TC_ROWS, c0 = (int)(t % tilesC) * TC_COLS;
+            if (it > 0 && sw.kc == 0 && ++tcol == tilesC) {
+                tcol = 0;
+                ++trow;
+            }
+            const int64_t l0 = sw.kc * TC_KS;
+            const int i0 = trow * TC_ROWS, c0 = tcol * TC_COLS;
             const uint8_t* tbuf = smem + TRAJ_OFF + (it % TRAJ_RING) * TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
@@ -513,7 +524,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             st_shared_v4(aL + sw128(r, g), rl);
             st_shared_v4(aL + sw128(r, 4 + g), il);
             // B columns r and 128 + r: [Br | Bi]
-#pragma unroll 1
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int rb = r + 128 * h, sjb = sb * (c0 + rb + ob);
                 const uint32_t ab = (uint32_t)(sjb < 0 ? -sjb : sjb);
