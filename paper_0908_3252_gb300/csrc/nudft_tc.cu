@@ -448,9 +448,9 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
         auto issue_traj = [&](int it) {
             const int64_t l0 = kci * TC_KS;
             if (++kci == K) kci = 0;
-            int64_t cnt = L - l0;
-            if (cnt > TC_KS) cnt = TC_KS;
-            const uint32_t bytes = (uint32_t)(((cnt + 1) & ~1) * 8);  // multiple of 16; arrays are padded
+            // the whole chunk, also past L: the plan's sample arrays have 32
+            // entries of padding, the weights' padding is zero
+            const uint32_t bytes = (uint32_t)TC_KS * 8;
             const uint32_t buf = traj_s + (uint32_t)(it % TRAJ_RING) * TRAJ_BUF;
             const uint32_t bar = bar_traj + 8 * (it % TRAJ_RING);
             fence_proxy_async();
@@ -499,21 +499,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
             // the signed index s j = +-a of the row (column) and the angle
-            // scale carrying its sign; samples past L (only in the last
-            // chunk) contribute zero
+            // scale carrying its sign
             constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
             const int sja = sa * (i0 + r + oa);
             const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
             const float sca = sja < 0 ? -kRev : kRev;
-            const bool tail = l0 + TC_KS > L;
+            // samples past L (only in a tile's last chunk): B is zero there,
+            // through the zero padding of the weights, or the mask below when
+            // unweighted; A then multiplies zeros and needs no mask
+            const int nvalid = l0 + TC_KS > L ? (int)(L - l0) : TC_KS;
             float re[8], im[8];
             uint4 rh, rl, ih, il;
             // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int l = 8 * g + e;
-                float2 v = phasor_signed(ka_s[l], aa, sca);
-                if (tail && l0 + l >= L) v = make_float2(0.f, 0.f);
+                const float2 v = phasor_signed(ka_s[l], aa, sca);
                 re[e] = v.x;
                 im[e] = v.y;
             }
@@ -539,7 +540,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
                         ww.y *= wmul;
                         v = cmul(v, ww);
                     }
-                    if (tail && l0 + l >= L) v = make_float2(0.f, 0.f);
+                    if (!WEIGHTED && l >= nvalid) v = make_float2(0.f, 0.f);
                     re[e] = v.x;
                     im[e] = v.y;
                 }
