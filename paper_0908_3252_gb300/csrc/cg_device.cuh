@@ -19,6 +19,8 @@ __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.
 // Line-search terms of one pixel from its values: the right and down edges
 // (Omega1, masked by has_r / has_d) and the pixel (Omega0).
 // num += lambda b(|x|) Re(conj(x) w), den += lambda b(|x|) |w|^2 with x = z + t w.
+// KIND >= 0 fixes phi at compile time (penalty.cuh).
+template <int KIND = -1>
 __device__ __forceinline__ void ls_terms(float2 fp, float2 dp, float2 fr, float2 dr, float2 fd, float2 dd,
                                          bool has_r, bool has_d, const Reg& reg, float tf, float& num,
                                          float& den)
@@ -27,21 +29,21 @@ __device__ __forceinline__ void ls_terms(float2 fp, float2 dp, float2 fr, float2
         {
             const float2 w = f2sub(dr, dp);
             const float2 x = f2axpy(tf, w, f2sub(fr, fp));
-            const float b = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
+            const float b = has_r ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
             num = fmaf(b, redot(x, w), num);
             den = fmaf(b, redot(w, w), den);
         }
         {
             const float2 w = f2sub(dd, dp);
             const float2 x = f2axpy(tf, w, f2sub(fd, fp));
-            const float b = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
+            const float b = has_d ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(x, x)) : 0.f;
             num = fmaf(b, redot(x, w), num);
             den = fmaf(b, redot(w, w), den);
         }
     }
     if (reg.lambda0 != 0.f) {
         const float2 x = f2axpy(tf, dp, fp);
-        const float b = reg.lambda0 * phi_weight(reg.kind, reg.alpha0, redot(x, x));
+        const float b = reg.lambda0 * phi_weight_k<KIND>(reg.kind, reg.alpha0, redot(x, x));
         num = fmaf(b, redot(x, dp), num);
         den = fmaf(b, redot(dp, dp), den);
     }
@@ -73,6 +75,7 @@ __device__ __forceinline__ double ls_next(double t, double q1, double q2, double
 // share rv of R (right and down edges, the pixel).  An edge from p to q with
 // z = f_q - f_p adds +psi(z) at q and -psi(z) at p, psi(z) = b(|z|) z.
 // Masked neighbours carry the centre value (z = 0).
+template <int KIND = -1>
 __device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float2 fdn, float2 fr, float2 tf,
                                           float2 dv, bool has_u, bool has_l, bool has_d, bool has_r,
                                           const Reg& reg, float& rv)
@@ -83,21 +86,25 @@ __device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float
         const float l1 = reg.lambda1;
         const float2 zu = f2sub(fc, fu), zl = f2sub(fc, fl), zd = f2sub(fdn, fc), zr = f2sub(fr, fc);
         const float ru = redot(zu, zu), rl = redot(zl, zl), rd = redot(zd, zd), rr = redot(zr, zr);
-        const float bu = has_u ? l1 * phi_weight(reg.kind, reg.alpha1, ru) : 0.f;
-        const float bl = has_l ? l1 * phi_weight(reg.kind, reg.alpha1, rl) : 0.f;
-        const float bd = has_d ? l1 * phi_weight(reg.kind, reg.alpha1, rd) : 0.f;
-        const float br = has_r ? l1 * phi_weight(reg.kind, reg.alpha1, rr) : 0.f;
+        float wd, vd, wr, vr;
+        phi_wv_k<KIND>(reg.kind, reg.alpha1, rd, wd, vd);
+        phi_wv_k<KIND>(reg.kind, reg.alpha1, rr, wr, vr);
+        const float bu = has_u ? l1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, ru) : 0.f;
+        const float bl = has_l ? l1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, rl) : 0.f;
+        const float bd = has_d ? l1 * wd : 0.f;
+        const float br = has_r ? l1 * wr : 0.f;
         gp = f2axpy(bu, zu, gp);
         gp = f2axpy(bl, zl, gp);
         gp = f2axpy(-bd, zd, gp);
         gp = f2axpy(-br, zr, gp);
-        rv = (has_d ? l1 * phi_value(reg.kind, reg.alpha1, rd) : 0.f) +
-             (has_r ? l1 * phi_value(reg.kind, reg.alpha1, rr) : 0.f);
+        rv = (has_d ? l1 * vd : 0.f) + (has_r ? l1 * vr : 0.f);
     }
     if (reg.lambda0 != 0.f) {
         const float r2 = redot(fc, fc);
-        gp = f2axpy(reg.lambda0 * phi_weight(reg.kind, reg.alpha0, r2), fc, gp);
-        rv = fmaf(reg.lambda0, phi_value(reg.kind, reg.alpha0, r2), rv);
+        float w0, v0;
+        phi_wv_k<KIND>(reg.kind, reg.alpha0, r2, w0, v0);
+        gp = f2axpy(reg.lambda0 * w0, fc, gp);
+        rv = fmaf(reg.lambda0, v0, rv);
     }
     return gp;
 }

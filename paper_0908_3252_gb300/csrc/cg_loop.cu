@@ -412,6 +412,89 @@ __device__ __forceinline__ void rows_fwd_split(const float2* src, int N, int nro
 
 // ---------------------------------------------------------------- phase A
 
+// Gradient of every own pixel (phi fixed at compile time): g into the
+// own-row cache and global memory (the halo rows of the neighbours), and the
+// six update sums of cgd::update_pixel.
+template <int KIND, bool FIRST>
+__device__ __forceinline__ void grad_rows(const LoopArgs& A, const Rows& R, const float2* cf, const float2* cd,
+                                          const float2* cTf, const float2* cD, float2* cg, float (&a)[kUpdVals])
+{
+    const int N = R.N;
+    const Reg reg = A.reg;
+    for (int e = threadIdx.x, oq = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(oq, m, N)) {
+        const int n = R.R0 + oq;
+        const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
+        const float2* row = cf + R.cache(n);
+        const float2 fc = row[m];
+        const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
+        const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
+        const float2 tf = cTf[e], dv = cD[e];
+        float rv;
+        const float2 gp = cgd::grad_at<KIND>(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+        a[0] += cgd::redot(gp, gp);
+        if (!FIRST) {
+            a[1] += cgd::redot(gp, cg[e]);
+            a[2] += cgd::redot(gp, cd[R.cache(n) + m]);
+        }
+        a[3] += rv;
+        a[4] += cgd::redot(fc, dv);
+        a[5] += cgd::redot(fc, tf);
+        cg[e] = gp;
+        A.g[(int64_t)n * N + m] = gp;
+    }
+}
+
+// Line-search sums of the own pixels at step t (phi fixed at compile time);
+// with T0 also the two first terms of the first step (Re<d, 2(T f - D)> and
+// Re<d, T d>) into acc[0] and acc[3], the penalty terms into acc[1], acc[2].
+template <int KIND, bool T0>
+__device__ __forceinline__ void ls_rows(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
+                                        const float2* cTf, const float2* cD, const float2* cTd, float t,
+                                        float* acc)
+{
+    const int N = R.N;
+    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
+        const int n = R.R0 + q;
+        const bool has_r = m + 1 < N, has_d = n + 1 < N;
+        const float2* fr0 = cf + R.cache(n);
+        const float2* dr0 = cd + R.cache(n);
+        const float2 fp = fr0[m], dp = dr0[m];
+        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
+        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
+        if constexpr (T0) {
+            acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
+            cgd::ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, 0.f, acc[1], acc[2]);
+            acc[3] += cgd::redot(dp, cTd[e]);
+        } else {
+            cgd::ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, t, acc[0], acc[1]);
+        }
+    }
+}
+
+// The per-pixel loops above for the run-time phi.
+template <bool FIRST>
+__device__ __forceinline__ void grad_rows_any(const LoopArgs& A, const Rows& R, const float2* cf, const float2* cd,
+                                              const float2* cTf, const float2* cD, float2* cg, float (&a)[kUpdVals])
+{
+    switch (A.reg.kind) {
+    case SPIREC_PHI_HUBER: grad_rows<SPIREC_PHI_HUBER, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
+    case SPIREC_PHI_HYPERBOLIC: grad_rows<SPIREC_PHI_HYPERBOLIC, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
+    default: grad_rows<SPIREC_PHI_QUADRATIC, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
+    }
+}
+
+template <bool T0>
+__device__ __forceinline__ void ls_rows_any(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
+                                            const float2* cTf, const float2* cD, const float2* cTd, float t,
+                                            float* acc)
+{
+    switch (reg.kind) {
+    case SPIREC_PHI_HUBER: ls_rows<SPIREC_PHI_HUBER, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
+    case SPIREC_PHI_HYPERBOLIC: ls_rows<SPIREC_PHI_HYPERBOLIC, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
+    default: ls_rows<SPIREC_PHI_QUADRATIC, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
+    }
+}
+
 // Step (unless FIRST), gradient and the six update sums over the own rows
 // (the sums of cgd::update_pixel); with do_fft the row FFTs of g go to X.
 // Rows go through the FFT RX * RPC at a time (RX butterflies per thread).
@@ -423,7 +506,6 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
 {
     using G = Geo<MC>;
     const int N = R.N;
-    const Reg reg = A.reg;
     if (!FIRST) {
         const int nc = (R.hhi - R.hlo + 1) * N;
         float2* fr0 = cf + R.cache(R.hlo);
@@ -435,27 +517,7 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
     if constexpr (G::FOURSTEP) {
         // gradient of every own pixel, then the split row FFTs of g, two
         // warps a row, eight rows at a time
-        for (int e = threadIdx.x, oq = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(oq, m, N)) {
-            const int n = R.R0 + oq;
-            const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
-            const float2* row = cf + R.cache(n);
-            const float2 fc = row[m];
-            const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
-            const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
-            const float2 tf = cTf[e], dv = cD[e];
-            float rv;
-            const float2 gp = cgd::grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
-            a[0] += cgd::redot(gp, gp);
-            if (!FIRST) {
-                a[1] += cgd::redot(gp, cg[e]);
-                a[2] += cgd::redot(gp, cd[R.cache(n) + m]);
-            }
-            a[3] += rv;
-            a[4] += cgd::redot(fc, dv);
-            a[5] += cgd::redot(fc, tf);
-            cg[e] = gp;
-            A.g[(int64_t)n * N + m] = gp;
-        }
+        grad_rows_any<FIRST>(A, R, cf, cd, cTf, cD, cg, a);
         if (do_fft) {
             __syncthreads();  // g of every own row is in cg
             for (int g0 = 0; g0 < R.nown; g0 += 8)
@@ -463,49 +525,30 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
                                stw + 512);
         }
     } else {
-    for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
-        const int nr = min(RX * G::RPC, R.nown - g0);
-#pragma unroll
-        for (int i = 0; i < 4 * RX; ++i) {
-            const int e = threadIdx.x + i * kLoopThreads;
-            const int q = e / MC, m = e - q * MC;
-            float2 gp = make_float2(0.f, 0.f);
-            if (q < nr && m < N) {
-                const int oq = g0 + q, n = R.R0 + oq;
-                const int o = oq * N + m;  // index in the own-row caches
-                const bool has_u = n > 0, has_l = m > 0, has_d = n + 1 < N, has_r = m + 1 < N;
-                const float2* row = cf + R.cache(n);
-                const float2 fc = row[m];
-                const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
-                const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
-                const float2 tf = cTf[o], dv = cD[o];
-                float rv;
-                gp = cgd::grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
-                a[0] += cgd::redot(gp, gp);
-                if (!FIRST) {
-                    a[1] += cgd::redot(gp, cg[o]);
-                    a[2] += cgd::redot(gp, cd[R.cache(n) + m]);
-                }
-                a[3] += rv;
-                a[4] += cgd::redot(fc, dv);
-                a[5] += cgd::redot(fc, tf);
-                cg[o] = gp;
-                A.g[(int64_t)n * N + m] = gp;
-            }
-            if (do_fft) fbuf[q * G::LDR + fftd::sidx<MC>(m)] = gp;
-        }
+        // gradient of every own pixel, then the row FFTs of g, RX * RPC rows
+        // at a time
+        grad_rows_any<FIRST>(A, R, cf, cd, cTf, cD, cg, a);
         if (do_fft) {
-            __syncthreads();
-            fftd::fft_pow2<MC, false, RX, true>(fbuf, G::LDR, stw);
+            __syncthreads();  // g of every own row is in cg
+            for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
+                const int nr = min(RX * G::RPC, R.nown - g0);
 #pragma unroll
-            for (int i = 0; i < 4 * RX; ++i) {
-                const int e = threadIdx.x + i * kLoopThreads;
-                const int q = e / MC, m = e - q * MC;
-                if (q < nr) A.X[(int64_t)(R.R0 + g0 + q) * MC + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
+                for (int i = 0; i < 4 * RX; ++i) {
+                    const int e = threadIdx.x + i * kLoopThreads;
+                    const int q = e / MC, m = e - q * MC;
+                    fbuf[q * G::LDR + fftd::sidx<MC>(m)] = q < nr && m < N ? cg[(g0 + q) * N + m] : make_float2(0.f, 0.f);
+                }
+                __syncthreads();
+                fftd::fft_pow2<MC, false, RX, true>(fbuf, G::LDR, stw);
+#pragma unroll
+                for (int i = 0; i < 4 * RX; ++i) {
+                    const int e = threadIdx.x + i * kLoopThreads;
+                    const int q = e / MC, m = e - q * MC;
+                    if (q < nr) A.X[(int64_t)(R.R0 + g0 + q) * MC + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
-    }
     }
 }
 
@@ -591,19 +634,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         }
     }
     __syncthreads();
-    const Reg reg = A.reg;
-    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
-        const int n = R.R0 + q;
-        const bool has_r = m + 1 < N, has_d = n + 1 < N;
-        const float2* fr0 = cf + R.cache(n);
-        const float2* dr0 = cd + R.cache(n);
-        const float2 fp = fr0[m], dp = dr0[m];
-        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
-        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
-        acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
-        cgd::ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, 0.f, acc[1], acc[2]);
-        acc[3] += cgd::redot(dp, cTd[e]);
-    }
+    ls_rows_any<true>(A.reg, R, cf, cd, cTf, cD, cTd, 0.f, acc);
 }
 
 // ------------------------------------------------------------ phases D, E
@@ -611,17 +642,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 __device__ __forceinline__ void phase_ls(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
                                          float t, float (&acc)[2])
 {
-    const int N = R.N;
-    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
-        const int n = R.R0 + q;
-        const bool has_r = m + 1 < N, has_d = n + 1 < N;
-        const float2* fr0 = cf + R.cache(n);
-        const float2* dr0 = cd + R.cache(n);
-        const float2 fp = fr0[m], dp = dr0[m];
-        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
-        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
-        cgd::ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, t, acc[0], acc[1]);
-    }
+    ls_rows_any<false>(reg, R, cf, cd, nullptr, nullptr, nullptr, t, acc);
 }
 
 // ------------------------------------------------------------------ kernel

@@ -25,4 +25,39 @@ __device__ __forceinline__ float phi_value(int kind, float alpha, float r2)
     return r2;
 }
 
+// The same with phi fixed at compile time (KIND >= 0), so a per-pixel loop
+// runs only its own phi; KIND < 0 falls back to the run-time choice.
+template <int KIND>
+__device__ __forceinline__ float phi_weight_k(int kind, float alpha, float r2)
+{
+    if constexpr (KIND < 0) return phi_weight(kind, alpha, r2);
+    else if constexpr (KIND == SPIREC_PHI_HUBER) return r2 <= alpha * alpha ? 2.f : 2.f * alpha * rsqrtf(r2);
+    else if constexpr (KIND == SPIREC_PHI_HYPERBOLIC) return 2.f * alpha * rsqrtf(fmaf(alpha, alpha, r2));
+    else return 2.f;
+}
+
+// b(r) and phi(r) together, one reciprocal square root for both:
+// Huber, r = r2 rsqrt(r2) in the linear part; hyperbolic, s = sqrt(a^2 + r^2)
+// from its rsqrt and phi = 2 a r^2 / (s + a) by a fast division (a few ulp).
+template <int KIND>
+__device__ __forceinline__ void phi_wv_k(int kind, float alpha, float r2, float& w, float& v)
+{
+    if constexpr (KIND < 0) {
+        w = phi_weight(kind, alpha, r2);
+        v = phi_value(kind, alpha, r2);
+    } else if constexpr (KIND == SPIREC_PHI_HUBER) {
+        const float rs = rsqrtf(r2);
+        const bool quad = r2 <= alpha * alpha;
+        w = quad ? 2.f : 2.f * alpha * rs;
+        v = quad ? r2 : fmaf(2.f * alpha, r2 * rs, -alpha * alpha);
+    } else if constexpr (KIND == SPIREC_PHI_HYPERBOLIC) {
+        const float q = fmaf(alpha, alpha, r2), rs = rsqrtf(q);
+        w = 2.f * alpha * rs;
+        v = __fdividef(2.f * alpha * r2, fmaf(q, rs, alpha));
+    } else {
+        w = 2.f;
+        v = r2;
+    }
+}
+
 }  // namespace spirec
