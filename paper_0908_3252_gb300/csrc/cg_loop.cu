@@ -444,31 +444,94 @@ __device__ __forceinline__ void grad_rows(const LoopArgs& A, const Rows& R, cons
     }
 }
 
-// Line-search sums of the own pixels at step t (phi fixed at compile time);
-// with T0 also the two first terms of the first step (Re<d, 2(T f - D)> and
-// Re<d, T d>) into acc[0] and acc[3], the penalty terms into acc[1], acc[2].
-template <int KIND, bool T0>
+// One penalty term of the line search from the precomputed quantities of its
+// edge (or pixel) z, w: |z|^2, Re(conj(z) w), |w|^2.  |z + t w|^2 = az + 2 t
+// bzw + t^2 cw; num += lambda b(|z + t w|) (bzw + t cw), den += lambda b cw.
+// A missing edge has all three zero and adds nothing.
+template <int KIND>
+__device__ __forceinline__ void ls_edge(float lam, float alpha, int kind, float az, float bzw, float cw, float t,
+                                        float& num, float& den)
+{
+    const float x2 = fmaxf(fmaf(t, fmaf(t, cw, 2.f * bzw), az), 0.f);
+    const float b = lam * phi_weight_k<KIND>(kind, alpha, x2);
+    num = fmaf(b, fmaf(t, cw, bzw), num);
+    den = fmaf(b, cw, den);
+}
+
+// Line-search sums of the own pixels at step t (phi fixed at compile time).
+// T0 (the first step, t = 0): also Re<d, 2(T f - D)> into acc[0] and
+// Re<d, T d> into acc[3], the penalty terms into acc[1], acc[2]; with PRE it
+// stores each edge's |z|^2, Re(conj(z) w), |w|^2 (z of f, w of d) in the
+// planes E (plane k at E + k nown N: right edge 0-2, down edge 3-5, pixel
+// 6-8 when lambda0 != 0).  Later steps (!T0) with PRE read the planes
+// instead of f and d.
+template <int KIND, bool T0, bool PRE>
 __device__ __forceinline__ void ls_rows(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
                                         const float2* cTf, const float2* cD, const float2* cTd, float t,
-                                        float* acc)
+                                        float* acc, float* E)
 {
-    const int N = R.N;
-    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < R.nown * N; e += kLoopThreads, step_pixel(q, m, N)) {
-        const int n = R.R0 + q;
-        const bool has_r = m + 1 < N, has_d = n + 1 < N;
-        const float2* fr0 = cf + R.cache(n);
-        const float2* dr0 = cd + R.cache(n);
-        const float2 fp = fr0[m], dp = dr0[m];
-        const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
-        const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
-        if constexpr (T0) {
-            acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
-            cgd::ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, 0.f, acc[1], acc[2]);
-            acc[3] += cgd::redot(dp, cTd[e]);
+    const int N = R.N, P = R.nown * N;
+    const bool l1 = reg.lambda1 != 0.f, l0 = reg.lambda0 != 0.f;
+    for (int e = threadIdx.x, q = first_row(N), m = first_col(N); e < P; e += kLoopThreads, step_pixel(q, m, N)) {
+        if constexpr (PRE && !T0) {
+            if (l1) {
+                ls_edge<KIND>(reg.lambda1, reg.alpha1, reg.kind, E[e], E[P + e], E[2 * P + e], t, acc[0], acc[1]);
+                ls_edge<KIND>(reg.lambda1, reg.alpha1, reg.kind, E[3 * P + e], E[4 * P + e], E[5 * P + e], t, acc[0],
+                              acc[1]);
+            }
+            if (l0)
+                ls_edge<KIND>(reg.lambda0, reg.alpha0, reg.kind, E[6 * P + e], E[7 * P + e], E[8 * P + e], t, acc[0],
+                              acc[1]);
         } else {
-            cgd::ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, t, acc[0], acc[1]);
+            const int n = R.R0 + q;
+            const bool has_r = m + 1 < N, has_d = n + 1 < N;
+            const float2* fr0 = cf + R.cache(n);
+            const float2* dr0 = cd + R.cache(n);
+            const float2 fp = fr0[m], dp = dr0[m];
+            const float2 fr = has_r ? fr0[m + 1] : fp, dr = has_r ? dr0[m + 1] : dp;
+            const float2 fd = has_d ? fr0[m + N] : fp, dd = has_d ? dr0[m + N] : dp;
+            float* num = T0 ? &acc[1] : &acc[0];
+            float* den = T0 ? &acc[2] : &acc[1];
+            if constexpr (T0) {
+                acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
+                acc[3] += cgd::redot(dp, cTd[e]);
+            }
+            if constexpr (PRE) {
+                // (masked neighbours carry the centre value: z = w = 0)
+                if (l1) {
+                    const float2 zr = cgd::f2sub(fr, fp), wr = cgd::f2sub(dr, dp);
+                    const float2 zd = cgd::f2sub(fd, fp), wd = cgd::f2sub(dd, dp);
+                    const float a0 = cgd::redot(zr, zr), b0 = cgd::redot(zr, wr), c0 = cgd::redot(wr, wr);
+                    const float a1 = cgd::redot(zd, zd), b1 = cgd::redot(zd, wd), c1 = cgd::redot(wd, wd);
+                    E[e] = a0;
+                    E[P + e] = b0;
+                    E[2 * P + e] = c0;
+                    E[3 * P + e] = a1;
+                    E[4 * P + e] = b1;
+                    E[5 * P + e] = c1;
+                    ls_edge<KIND>(reg.lambda1, reg.alpha1, reg.kind, a0, b0, c0, t, *num, *den);
+                    ls_edge<KIND>(reg.lambda1, reg.alpha1, reg.kind, a1, b1, c1, t, *num, *den);
+                }
+                if (l0) {
+                    const float a2 = cgd::redot(fp, fp), b2 = cgd::redot(fp, dp), c2 = cgd::redot(dp, dp);
+                    E[6 * P + e] = a2;
+                    E[7 * P + e] = b2;
+                    E[8 * P + e] = c2;
+                    ls_edge<KIND>(reg.lambda0, reg.alpha0, reg.kind, a2, b2, c2, t, *num, *den);
+                }
+            } else {
+                cgd::ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, t, *num, *den);
+            }
         }
     }
+}
+
+// Whether the line-search planes of a block fit in its FFT buffer (free from
+// the row pass to the update): 6 or 9 floats a pixel.
+__device__ __forceinline__ bool ls_planes_fit(const Reg& reg, int npix, int fbuf_float2)
+{
+    const int planes = reg.lambda0 != 0.f ? 9 : 6;
+    return planes * npix <= 2 * fbuf_float2;
 }
 
 // The per-pixel loops above for the run-time phi.
@@ -483,16 +546,29 @@ __device__ __forceinline__ void grad_rows_any(const LoopArgs& A, const Rows& R, 
     }
 }
 
+template <bool T0, bool PRE>
+__device__ __forceinline__ void ls_rows_k(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
+                                          const float2* cTf, const float2* cD, const float2* cTd, float t, float* acc,
+                                          float* E)
+{
+    switch (reg.kind) {
+    case SPIREC_PHI_HUBER: ls_rows<SPIREC_PHI_HUBER, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E); break;
+    case SPIREC_PHI_HYPERBOLIC:
+        ls_rows<SPIREC_PHI_HYPERBOLIC, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
+        break;
+    default: ls_rows<SPIREC_PHI_QUADRATIC, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E); break;
+    }
+}
+
 template <bool T0>
 __device__ __forceinline__ void ls_rows_any(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
                                             const float2* cTf, const float2* cD, const float2* cTd, float t,
-                                            float* acc)
+                                            float* acc, float* E, bool pre)
 {
-    switch (reg.kind) {
-    case SPIREC_PHI_HUBER: ls_rows<SPIREC_PHI_HUBER, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
-    case SPIREC_PHI_HYPERBOLIC: ls_rows<SPIREC_PHI_HYPERBOLIC, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
-    default: ls_rows<SPIREC_PHI_QUADRATIC, T0>(reg, R, cf, cd, cTf, cD, cTd, t, acc); break;
-    }
+    if (pre)
+        ls_rows_k<T0, true>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
+    else
+        ls_rows_k<T0, false>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
 }
 
 // Step (unless FIRST), gradient and the six update sums over the own rows
@@ -634,15 +710,20 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         }
     }
     __syncthreads();
-    ls_rows_any<true>(A.reg, R, cf, cd, cTf, cD, cTd, 0.f, acc);
+    ls_rows_any<true>(A.reg, R, cf, cd, cTf, cD, cTd, 0.f, acc, reinterpret_cast<float*>(fbuf),
+                      ls_planes_fit(A.reg, R.nown * N, G::FBUF));
 }
 
 // ------------------------------------------------------------ phases D, E
 
+// Steps 2 and 3 of the line search, from the planes the row pass left in
+// the FFT buffer when they fit.
+template <int MC>
 __device__ __forceinline__ void phase_ls(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
-                                         float t, float (&acc)[2])
+                                         float2* fbuf, float t, float (&acc)[2])
 {
-    ls_rows_any<false>(reg, R, cf, cd, nullptr, nullptr, nullptr, t, acc);
+    ls_rows_any<false>(reg, R, cf, cd, nullptr, nullptr, nullptr, t, acc, reinterpret_cast<float*>(fbuf),
+                       ls_planes_fit(reg, R.nown * R.N, Geo<MC>::FBUF));
 }
 
 // ------------------------------------------------------------------ kernel
@@ -778,7 +859,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
 #pragma unroll 1
         for (int j = 0; j < 2; ++j) {
             float acc[2] = {0.f, 0.f};
-            phase_ls(A.reg, R, cf, cd, S.t_f, acc);
+            phase_ls<MC>(A.reg, R, cf, cd, fbuf, S.t_f, acc);
             mark(4 + 2 * j);
             if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
