@@ -217,7 +217,6 @@ constexpr int L_E = 12;  // 2
 struct Rows {
     int N, R0, nown, hlo, hhi;
     __device__ __forceinline__ int cache(int r) const { return (r - R0 + 1) * N; }  // row offset in cf, cd
-    __device__ __forceinline__ bool own(int r) const { return r >= R0 && r < R0 + nown; }
 };
 
 // (row, column) of the first element of a per-pixel loop over rows of N
@@ -699,14 +698,34 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         }
         __syncthreads();
     }
-    // d = -g + beta d_old on the cached rows (halo g from its owner, via L2)
+    // d = -g + beta d_old on the cached rows.  The halo rows' g comes from
+    // their owners via L2: those loads go first (columns tid and tid + 512;
+    // N <= 1024), so their latency overlaps the own rows.
     {
-        const int nc = (R.hhi - R.hlo + 1) * N;
-        float2* dr0 = cd + R.cache(R.hlo);
-        for (int e = threadIdx.x, rq = first_row(N), m = first_col(N); e < nc; e += kLoopThreads, step_pixel(rq, m, N)) {
-            const int r = R.hlo + rq;
-            const float2 g = R.own(r) ? cg[(r - R.R0) * N + m] : __ldcg(A.g + (int64_t)r * N + m);
-            dr0[e] = fftd::new_direction(g, dr0[e], beta, restart);
+        const bool up = R.hlo < R.R0, dn = R.hhi >= R.R0 + R.nown;
+        float2 hu[2], hd[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int m = threadIdx.x + k * kLoopThreads;
+            hu[k] = up && m < N ? __ldcg(A.g + (int64_t)R.hlo * N + m) : make_float2(0.f, 0.f);
+            hd[k] = dn && m < N ? __ldcg(A.g + (int64_t)R.hhi * N + m) : make_float2(0.f, 0.f);
+        }
+        float2* own = cd + R.cache(R.R0);
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads)
+            own[e] = fftd::new_direction(cg[e], own[e], beta, restart);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int m = threadIdx.x + k * kLoopThreads;
+            if (m < N) {
+                if (up) {
+                    float2& v = cd[R.cache(R.hlo) + m];
+                    v = fftd::new_direction(hu[k], v, beta, restart);
+                }
+                if (dn) {
+                    float2& v = cd[R.cache(R.hhi) + m];
+                    v = fftd::new_direction(hd[k], v, beta, restart);
+                }
+            }
         }
     }
     __syncthreads();
