@@ -618,10 +618,6 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->D, NN));
     TRY(dalloc(p, &p->s, (size_t)L + 32));
     TRY(dalloc(p, &p->ystage, (size_t)L + 32));
-    // the sample arrays are written over [0, L) only: their padding stays
-    // zero, so a contraction chunk that runs past L gets zero weights
-    TRYCUDA(cudaMemset(p->s, 0, sizeof(float2) * ((size_t)L + 32)));
-    TRYCUDA(cudaMemset(p->ystage, 0, sizeof(float2) * ((size_t)L + 32)));
     TRY(dalloc(p, &p->f[0], NN));
     TRY(dalloc(p, &p->f[1], NN));
     TRY(dalloc(p, &p->dbuf[0], NN));
@@ -644,6 +640,10 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
         p->kpart_bytes = n * sizeof(float);
     }
     TRYCUDA(cudaMemsetAsync(p->counters, 0, C_N * sizeof(unsigned), p->stream));
+    // the sample arrays are written over [0, L) only: their padding stays
+    // zero, so a contraction chunk that runs past L gets zero weights
+    TRYCUDA(cudaMemsetAsync(p->s, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
+    TRYCUDA(cudaMemsetAsync(p->ystage, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
     TRYCUDA(cudaMemsetAsync(p->scal, 0, S_NSCAL * sizeof(double), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[0], 0, NN * sizeof(float2), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[1], 0, NN * sizeof(float2), p->stream));
