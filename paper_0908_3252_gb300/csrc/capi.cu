@@ -151,7 +151,8 @@ void free_plan(spirec_plan p)
     if (!p) return;
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
-                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw};
+                    p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
+                    p->kx128, p->ky128};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph) cudaGraphExecDestroy(p->graph);
@@ -246,6 +247,8 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, 
     k_traj_fixed<<<blocks, 256, 0, p->stream>>>(kx_dev, ky_dev, p->L, p->kxq, p->kyq, p->dflag);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
+    int rc0;
+    if ((rc0 = launch_step128(p)) != SPIREC_OK) return rc0;
     cudaEvent_t e;
     int rc;
     if ((rc = tstart(p, 0, &e)) != SPIREC_OK) return rc;
@@ -607,6 +610,10 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     // whole 16-byte multiples of a 32-sample chunk by TMA bulk copy
     TRY(dalloc(p, &p->kxq, (size_t)L + 32));
     TRY(dalloc(p, &p->kyq, (size_t)L + 32));
+    if (precision != SPIREC_FP32) {
+        TRY(dalloc(p, &p->kx128, (size_t)L + 32));
+        TRY(dalloc(p, &p->ky128, (size_t)L + 32));
+    }
     TRY(dalloc(p, &p->kstage, 2 * (size_t)L));
     TRY(dalloc(p, &p->dflag, 1));
     TRY(dalloc(p, &p->G, (size_t)N * (2 * N - 1)));
@@ -644,6 +651,10 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     // zero, so a contraction chunk that runs past L gets zero weights
     TRYCUDA(cudaMemsetAsync(p->s, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
     TRYCUDA(cudaMemsetAsync(p->ystage, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
+    if (p->kx128) {
+        TRYCUDA(cudaMemsetAsync(p->kx128, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
+        TRYCUDA(cudaMemsetAsync(p->ky128, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
+    }
     TRYCUDA(cudaMemsetAsync(p->scal, 0, S_NSCAL * sizeof(double), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[0], 0, NN * sizeof(float2), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[1], 0, NN * sizeof(float2), p->stream));
@@ -817,6 +828,10 @@ int spirec_set_trajectory_cached(spirec_plan p, spirec_kcache c, const int32_t* 
         SPIREC_CK(cudaMemcpyAsync(p->kxq + pos, c->kxq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
         SPIREC_CK(cudaMemcpyAsync(p->kyq + pos, c->kyq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
         pos += Li;
+    }
+    {
+        const int rc1 = launch_step128(p);
+        if (rc1 != SPIREC_OK) return rc1;
     }
     const int64_t MM = (int64_t)p->M * p->M, NG2 = 2 * (int64_t)p->N * (2 * p->N - 1);
     int blocks = (int)((MM + 255) / 256);

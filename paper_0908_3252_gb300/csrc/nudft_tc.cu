@@ -70,7 +70,7 @@ constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int TRAJ_RING = 4;
-constexpr uint32_t TRAJ_BUF = 3 * TC_KS * 8;                // ka, kb (int64) and w (float2)
+constexpr uint32_t TRAJ_BUF = 4 * TC_KS * 8;  // ka, kb (int64), w and the kb step table (float2)
 constexpr uint32_t TRAJ_OFF = TC_STAGES * STAGE_BYTES;
 constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
@@ -399,7 +399,7 @@ struct SegWalk {
 //   A(l,i) = exp(sa i2pi ka_l (i + oa)),  B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
 template <bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
+k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ kbs,
                 const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L, int tilesC,
                 int oa, int ob, int sa, int sb, int64_t K, int64_t U, float* __restrict__ part, int* err)
 {
@@ -454,10 +454,11 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const uint32_t buf = traj_s + (uint32_t)(it % TRAJ_RING) * TRAJ_BUF;
             const uint32_t bar = bar_traj + 8 * (it % TRAJ_RING);
             fence_proxy_async();
-            mbar_expect_tx(bar, (WEIGHTED ? 3u : 2u) * bytes);
+            mbar_expect_tx(bar, (WEIGHTED ? 4u : 3u) * bytes);
             bulk_g2s(buf, ka + l0, bytes, bar);
             bulk_g2s(buf + TC_KS * 8, kb + l0, bytes, bar);
             if (WEIGHTED) bulk_g2s(buf + 2 * TC_KS * 8, w + l0, bytes, bar);
+            bulk_g2s(buf + 3 * TC_KS * 8, kbs + l0, bytes, bar);
         };
         if (tid == 0)
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
@@ -496,6 +497,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
+            const float2* q_s = reinterpret_cast<const float2*>(tbuf + 3 * TC_KS * 8);
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
             // the signed index s j = +-a of the row (column) and the angle
@@ -524,32 +526,48 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb,
             st_shared_v4(aH + sw128(r, 4 + g), ih);
             st_shared_v4(aL + sw128(r, g), rl);
             st_shared_v4(aL + sw128(r, 4 + g), il);
-            // B columns r and 128 + r: [Br | Bi]
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int rb = r + 128 * h, sjb = sb * (c0 + rb + ob);
+            // B columns r and 128 + r: [Br | Bi]; column 128 + r is column r
+            // times exp(i 2 pi kb (s 128)), the sample's step table (conjugated
+            // for s < 0), so it needs no phase of its own and no weight
+            {
+                const int sjb = sb * (c0 + r + ob);
                 const uint32_t ab = (uint32_t)(sjb < 0 ? -sjb : sjb);
                 const float scb = sjb < 0 ? -kRev : kRev;
+                float2 v[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const int l = 8 * g + e;
-                    float2 v = phasor_signed(kb_s[l], ab, scb);
+                    v[e] = phasor_signed(kb_s[l], ab, scb);
                     if (WEIGHTED) {
                         float2 ww = w_s[l];
                         ww.x *= wmul;
                         ww.y *= wmul;
-                        v = cmul(v, ww);
+                        v[e] = cmul(v[e], ww);
                     }
-                    if (!WEIGHTED && l >= nvalid) v = make_float2(0.f, 0.f);
-                    re[e] = v.x;
-                    im[e] = v.y;
+                    if (!WEIGHTED && l >= nvalid) v[e] = make_float2(0.f, 0.f);
+                    re[e] = v[e].x;
+                    im[e] = v[e].y;
                 }
                 split8<BF16>(re, rh, rl);
                 split8<BF16>(im, ih, il);
-                st_shared_v4(bH + sw128(rb, g), rh);
-                st_shared_v4(bH + sw128(rb, 4 + g), ih);
-                st_shared_v4(bL + sw128(rb, g), rl);
-                st_shared_v4(bL + sw128(rb, 4 + g), il);
+                st_shared_v4(bH + sw128(r, g), rh);
+                st_shared_v4(bH + sw128(r, 4 + g), ih);
+                st_shared_v4(bL + sw128(r, g), rl);
+                st_shared_v4(bL + sw128(r, 4 + g), il);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float2 q = q_s[8 * g + e];
+                    if (sb < 0) q.y = -q.y;
+                    const float2 u = cmul(v[e], q);
+                    re[e] = u.x;
+                    im[e] = u.y;
+                }
+                split8<BF16>(re, rh, rl);
+                split8<BF16>(im, ih, il);
+                st_shared_v4(bH + sw128(r + 128, g), rh);
+                st_shared_v4(bH + sw128(r + 128, 4 + g), ih);
+                st_shared_v4(bL + sw128(r + 128, g), rl);
+                st_shared_v4(bL + sw128(r + 128, 4 + g), il);
             }
             fence_proxy_async();
             mbar_arrive(bar_full + 8 * s);
@@ -985,19 +1003,24 @@ int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb,
     }
     const dim3 grid((unsigned)P);
     float* part = p->kpart;
+    const float2* kbs = kb == p->kxq ? p->kx128 : p->ky128;  // the B side's step table
+    if (!kbs) {
+        set_error("plan has no step tables for the tensor-core contraction");
+        return SPIREC_ESTATE;
+    }
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
     if (bf16 && w)
         k_tc_phase_gemm<true, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else if (bf16)
         k_tc_phase_gemm<true, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else if (w)
         k_tc_phase_gemm<false, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     else
         k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
     SPIREC_CK(cudaGetLastError());
     const dim3 rgrid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
     k_reduce_tc<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
@@ -1051,6 +1074,32 @@ int launch_forward_tc(spirec_plan p, const float2* x, float2* yout)
                                                                             p->L, N, kchunks, scale, yout, p->dflag);
     SPIREC_CK(cudaGetLastError());
     p->launches += 3;
+    return SPIREC_OK;
+}
+
+// exp(+i 2 pi k 128) for both trajectory coordinates: the top 32 bits of
+// kq * 128 mod 2^64 are bits 25..56 of kq.
+__global__ void k_step128(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, int64_t L,
+                          float2* __restrict__ kx128, float2* __restrict__ ky128)
+{
+    constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x) {
+        float sn, cs;
+        __sincosf((float)(int)(uint32_t)(((uint64_t)kxq[l] << 7) >> 32) * kRev, &sn, &cs);
+        kx128[l] = make_float2(cs, sn);
+        __sincosf((float)(int)(uint32_t)(((uint64_t)kyq[l] << 7) >> 32) * kRev, &sn, &cs);
+        ky128[l] = make_float2(cs, sn);
+    }
+}
+
+int launch_step128(spirec_plan p)
+{
+    if (!p->kx128) return SPIREC_OK;  // FP32 plans do not use them
+    int blocks = (int)((p->L + 255) / 256);
+    if (blocks > 8 * kMaxCtas) blocks = 8 * kMaxCtas;
+    k_step128<<<blocks, 256, 0, p->stream>>>(p->kxq, p->kyq, p->L, p->kx128, p->ky128);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
     return SPIREC_OK;
 }
 
