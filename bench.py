@@ -308,6 +308,50 @@ def run_half_quadratic(spirec, prec, w, s_host, budget=50, ref_iters=400):
     return out
 
 
+def run_graph_path(spirec, prec, N=2048, M=4096, interleaves=64, samples=2048, hbm_gbs=None):
+    """The CG iteration as separate kernels in a captured graph (row FFTs with
+    the fused direction and first line-search sums, column filter, row IFFTs
+    with q2, two line-search steps, update), on an image whose working set
+    (about 320 MB: f, d, g, T f, T d, D, the N x M rows, the spectrum) is far
+    beyond the 129 MB L2, so that these FFT and stencil kernels stream through
+    HBM: 2048 x 2048, M = 4096 (beyond the persistent loop's sizes), spiral
+    64 x 2048 (L = 131072).  Steady-state time per iteration from solves of 2
+    and 12 iterations (events, second of two runs), and the algorithmic bytes
+    per iteration (160 N^2) over it."""
+    import torch
+    from paper_0908_3252_gb300 import synth
+    g = synth.rng(7)
+    kx, ky = synth.spiral(N, interleaves, samples, "archimedean")
+    L = kx.shape[0]
+    f = synth.ellipses(N, 10, g).astype(np.complex64)
+    st = torch.cuda.Stream()
+    p = spirec.Plan(N, L, M, prec, st.cuda_stream, kx, ky)
+    y = torch.zeros(L, dtype=torch.complex64, device="cuda")
+    spirec.spirec_forward_dev(p.h, torch.from_numpy(f).cuda(), y)
+    spirec.spirec_set_data_dev(p.h, y)
+    spirec.spirec_set_reg(p.h, 0.05, 0.05, 0.0, 0.05, 0)
+    x = torch.zeros((N, N), dtype=torch.complex64, device="cuda")
+    t = {}
+    for iters in (2, 12, 2, 12):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        spirec.spirec_solve_dev(p.h, None, iters, x, None)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t[iters] = e0.elapsed_time(e1)
+    p.close()
+    ms = (t[12] - t[2]) / 10.0
+    gbs = 160.0 * N * N / (ms / 1e3) / 1e9
+    out = {"N": N, "M": M, "L": L, "ms_per_iter": ms, "algorithmic_bytes_per_iter": 160 * N * N,
+           "algorithmic_GBps": gbs,
+           "path": "stand-alone kernels in a captured graph (M = 4096 is beyond the persistent loop)"}
+    if hbm_gbs:
+        out["frac_of_measured_hbm"] = gbs / hbm_gbs
+    return out
+
+
 def run_serving(spirec, prec, requests=2000, rate=200.0, iters=50, seed=5, slots=8):
     """Poisson request stream: sizes N in {64..384} step 64, L uniform in
     [8000, 200000] (spiral of ceil(L/2048) interleaves truncated to L),
@@ -708,6 +752,8 @@ def run_ours(args):
         extra["direct_mode"] = run_direct_mode(spirec, prec, w, s)
     if not args.no_half_quadratic:
         extra["half_quadratic"] = run_half_quadratic(spirec, prec, w, s)
+    if not args.no_graph_path:
+        extra["graph_path_2048"] = run_graph_path(spirec, prec, hbm_gbs=(peaks() or {}).get("hbm_gbs"))
     if not args.no_serving:
         extra["serving"] = run_serving(spirec, prec)
         if prec != spirec.SPIREC_FP32 and not args.no_fp32_compare:
@@ -809,6 +855,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
     ap.add_argument("--no-half-quadratic", action="store_true",
                     help="skip the half-quadratic vs PR+ CG comparison at an equal T-apply budget")
+    ap.add_argument("--no-graph-path", action="store_true",
+                    help="skip the stand-alone-kernel iteration on a 2048^2 image (HBM-bound FFT and stencil kernels)")
+    ap.add_argument("--only-graph-path", action="store_true",
+                    help="run only that measurement and print its JSON (for profiling its kernels)")
     ap.add_argument("--no-direct", action="store_true",
                     help="skip the per-iteration comparison with the direct (non-rewritten) formulation")
     ap.add_argument("--no-paper-experiment", action="store_true",
@@ -822,6 +872,15 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_graph_path:
+        import torch
+        from paper_0908_3252_gb300 import build, spirec
+        build.build()
+        spirec.load()
+        prec = {"fp32": spirec.SPIREC_FP32, "fp16x3": spirec.SPIREC_MIXED_FP16X3,
+                "bf16x3": spirec.SPIREC_MIXED_BF16X3}[args.precision]
+        print(json.dumps(run_graph_path(spirec, prec, hbm_gbs=(peaks() or {}).get("hbm_gbs"))))
+        return 0
     return run_ours(args)
 
 

@@ -67,7 +67,8 @@ __global__ void k_sumsq(const float2* __restrict__ s, int64_t L, float2* parts, 
 }
 
 // Line-search step `step` (1 or 2) at t = t_step; the last block forms
-// t_{step+1} (cgd::ls_next).
+// t_{step+1} (cgd::ls_next).  KIND: phi fixed at compile time.
+template <int KIND>
 __global__ void __launch_bounds__(kVecThreads)
 k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2* parts,
               unsigned* counter, double* scal)
@@ -77,7 +78,7 @@ k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2
     const int P = N * N;
     float v[2] = {0.f, 0.f};
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-        cgd::ls_pixel(p, N, f, d, reg, tf, v[0], v[1]);
+        cgd::ls_pixel<KIND>(p, N, f, d, reg, tf, v[0], v[1]);
     FF bt[2];
     block_partial<2>(v, bt);
     store_parts<2>(bt, parts, kMaxParts);
@@ -92,7 +93,7 @@ k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2
 }
 
 // Gradient and step (cgd::update_pixel); the last block forms J and beta.
-template <bool FIRST>
+template <bool FIRST, int KIND>
 __global__ void __launch_bounds__(kVecThreads)
 k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const float2* Td,
          const float2* __restrict__ D, float2* g, int N, Reg reg, float2* parts, unsigned* counter,
@@ -104,7 +105,7 @@ k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const f
 #pragma unroll
     for (int i = 0; i < kUpdVals; ++i) a[i] = 0.f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-        cgd::update_pixel<FIRST>(p, N, f_in, f_out, d, Tf, Td, D, g, reg, t, a);
+        cgd::update_pixel<FIRST, KIND>(p, N, f_in, f_out, d, Tf, Td, D, g, reg, t, a);
     FF bt[kUpdVals];
     block_partial<kUpdVals>(a, bt);
     store_parts<kUpdVals>(bt, parts, kMaxParts);
@@ -140,10 +141,35 @@ int launch_data_norm(spirec_plan p)
     return SPIREC_OK;
 }
 
+namespace {
+template <int KIND>
+void line_search_k(spirec_plan p, const float2* f, const float2* d, int step)
+{
+    k_line_search<KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(f, d, p->N, p->reg, step, slot(p, P_LS),
+                                                                         p->counters + C_LS, p->scal);
+}
+
+template <int KIND>
+void update_k(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf, const float2* Td,
+              float2* g, int first, double* Jout)
+{
+    if (first)
+        k_update<true, KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
+            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+    else
+        k_update<false, KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
+            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+}
+}  // namespace
+
+// phi fixed at compile time in the per-pixel work: one kernel per phi
 int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step)
 {
-    k_line_search<<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-        f, d, p->N, p->reg, step, slot(p, P_LS), p->counters + C_LS, p->scal);
+    switch (p->reg.kind) {
+    case SPIREC_PHI_HUBER: line_search_k<SPIREC_PHI_HUBER>(p, f, d, step); break;
+    case SPIREC_PHI_HYPERBOLIC: line_search_k<SPIREC_PHI_HYPERBOLIC>(p, f, d, step); break;
+    default: line_search_k<SPIREC_PHI_QUADRATIC>(p, f, d, step); break;
+    }
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     return SPIREC_OK;
@@ -152,12 +178,11 @@ int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step
 int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf,
                   const float2* Td, float2* g, int first, double* Jout)
 {
-    if (first)
-        k_update<true><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
-    else
-        k_update<false><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+    switch (p->reg.kind) {
+    case SPIREC_PHI_HUBER: update_k<SPIREC_PHI_HUBER>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
+    case SPIREC_PHI_HYPERBOLIC: update_k<SPIREC_PHI_HYPERBOLIC>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
+    default: update_k<SPIREC_PHI_QUADRATIC>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
+    }
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     return SPIREC_OK;

@@ -51,6 +51,7 @@ __device__ __forceinline__ void ls_terms(float2 fp, float2 dp, float2 fr, float2
 
 // Line-search sums at step t for pixel p of the global iterates (clamped
 // neighbours, masked terms).  All loads first.
+template <int KIND = -1>
 __device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const float2* d, const Reg& reg,
                                          float tf, float& num, float& den)
 {
@@ -59,7 +60,7 @@ __device__ __forceinline__ void ls_pixel(int p, int N, const float2* f, const fl
     const int pr = has_r ? p + 1 : p, pd = has_d ? p + N : p;
     const float2 fp = __ldcg(f + p), dp = __ldcg(d + p), fr = __ldcg(f + pr), dr = __ldcg(d + pr);
     const float2 fd = __ldcg(f + pd), dd = __ldcg(d + pd);
-    ls_terms(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, tf, num, den);
+    ls_terms<KIND>(fp, dp, fr, dr, fd, dd, has_r, has_d, reg, tf, num, den);
 }
 
 // t_{j+1} from t_j and the grid sums (majorize-minimize step; t stays when
@@ -113,7 +114,7 @@ __device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float
 // Tf += t Td.  g = 2 (Tf - D) + grad R(f); per-thread sums
 //   a[0] <g,g>, a[1] Re<g, g_old>, a[2] Re<g, d>, a[3] R(f), a[4] Re<f, D>, a[5] Re<f, Tf>.
 // All loads first (clamped neighbours, masked terms).
-template <bool FIRST>
+template <bool FIRST, int KIND = -1>
 __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, float2* f_out,
                                              const float2* d, float2* Tf, const float2* Td,
                                              const float2* __restrict__ D, float2* g, const Reg& reg,
@@ -143,7 +144,7 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
         f_out[p] = fc;
     }
     float rv;
-    const float2 gp = grad_at(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+    const float2 gp = grad_at<KIND>(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
     a[0] += redot(gp, gp);
     if (!FIRST) {
         a[1] += redot(gp, gold);

@@ -58,7 +58,7 @@ using namespace fftd;
 // MODE 0: row FFTs of `in` into X.  MODE 1 (CG): the rows of the new
 // direction, with q1 and the first line-search sums reduced over the grid
 // and finished by the last block into scal (see fft_device.cuh).
-template <int MC, int MODE>
+template <int MC, int MODE, int KIND = -1>
 __global__ void __launch_bounds__(1024) k_rows_fwd(const float2* in, int ld_in, int n_in, int rows, float2* X, FftPlan fp,
                            const float2* __restrict__ tw, int rpc, CgPass c)
 {
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const float2* in, int ld_in, 
         restart = bd == 0.0;
     }
     float acc[3] = {0.f, 0.f, 0.f};
-    rows_fwd_group<MC, MODE>(in, ld_in, n_in, r0, nr, rpc, X, fp, tw, c, beta, restart, a, b, acc);
+    rows_fwd_group<MC, MODE, KIND>(in, ld_in, n_in, r0, nr, rpc, X, fp, tw, c, beta, restart, a, b, acc);
     if (MODE == 1) {
         FF bt[3];
         block_partial<3>(acc, bt);
@@ -239,7 +239,11 @@ int set_attrs()
 {
     const int bytes = kFftSmemCap;
     SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 1, SPIREC_PHI_HUBER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 1, SPIREC_PHI_HYPERBOLIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   bytes));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd<MC, 1, SPIREC_PHI_QUADRATIC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   bytes));
     SPIREC_CK(cudaFuncSetAttribute(k_rows_inv<MC, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SPIREC_CK(cudaFuncSetAttribute(k_rows_inv<MC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     SPIREC_CK(cudaFuncSetAttribute(k_cols_filter<MC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
@@ -295,9 +299,15 @@ struct LaunchRowsFwd {
         if (mode == 0)
             k_rows_fwd<MC, 0><<<blocks, s.threads, s.smem, p->stream>>>(in, ld_in, n_in, rows, p->X, p->fft,
                                                                         p->twiddle, s.per_cta, c);
+        else if (c.reg.kind == SPIREC_PHI_HUBER)  // phi fixed at compile time in the line-search sums
+            k_rows_fwd<MC, 1, SPIREC_PHI_HUBER><<<blocks, s.threads, s.smem, p->stream>>>(
+                in, ld_in, n_in, rows, p->X, p->fft, p->twiddle, s.per_cta, c);
+        else if (c.reg.kind == SPIREC_PHI_HYPERBOLIC)
+            k_rows_fwd<MC, 1, SPIREC_PHI_HYPERBOLIC><<<blocks, s.threads, s.smem, p->stream>>>(
+                in, ld_in, n_in, rows, p->X, p->fft, p->twiddle, s.per_cta, c);
         else
-            k_rows_fwd<MC, 1><<<blocks, s.threads, s.smem, p->stream>>>(in, ld_in, n_in, rows, p->X, p->fft,
-                                                                        p->twiddle, s.per_cta, c);
+            k_rows_fwd<MC, 1, SPIREC_PHI_QUADRATIC><<<blocks, s.threads, s.smem, p->stream>>>(
+                in, ld_in, n_in, rows, p->X, p->fft, p->twiddle, s.per_cta, c);
         SPIREC_CK(cudaGetLastError());
         p->launches += 1;
         return SPIREC_OK;

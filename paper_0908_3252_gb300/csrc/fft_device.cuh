@@ -277,7 +277,7 @@ __device__ __forceinline__ float2 new_direction(float2 g, float2 dold, float bet
 //   acc[2] += sum_e lambda b(|z_e|) |w_e|^2            (curvature at t = 0)
 // over the right/down edges and pixels of these rows.  Then the FFTs and the
 // M outputs of each row into X.
-template <int MC, int MODE>
+template <int MC, int MODE, int KIND = -1>
 __device__ __forceinline__ void rows_fwd_group(const float2* in, int ld_in, int n_in, int r0, int nr,
                                                int rpc, float2* X, const FftPlan& fp,
                                                const float2* __restrict__ tw, const CgPass& c,
@@ -355,7 +355,7 @@ __device__ __forceinline__ void rows_fwd_group(const float2* in, int ld_in, int 
                 {
                     const float2 w = f2sub(dr, dn);
                     const float2 z = f2sub(fr, fp_);
-                    const float bw = has_r ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
+                    const float bw = has_r ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
                     acc[1] = fmaf(bw, redot(z, w), acc[1]);
                     acc[2] = fmaf(bw, redot(w, w), acc[2]);
                 }
@@ -363,13 +363,13 @@ __device__ __forceinline__ void rows_fwd_group(const float2* in, int ld_in, int 
                     const float2 dd = new_direction(gd, dold_d, beta, restart);
                     const float2 w = f2sub(dd, dn);
                     const float2 z = f2sub(fd, fp_);
-                    const float bw = has_d ? reg.lambda1 * phi_weight(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
+                    const float bw = has_d ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
                     acc[1] = fmaf(bw, redot(z, w), acc[1]);
                     acc[2] = fmaf(bw, redot(w, w), acc[2]);
                 }
             }
             if (reg.lambda0 != 0.f) {
-                const float bw = reg.lambda0 * phi_weight(reg.kind, reg.alpha0, redot(fp_, fp_));
+                const float bw = reg.lambda0 * phi_weight_k<KIND>(reg.kind, reg.alpha0, redot(fp_, fp_));
                 acc[1] = fmaf(bw, redot(fp_, dn), acc[1]);
                 acc[2] = fmaf(bw, redot(dn, dn), acc[2]);
             }
