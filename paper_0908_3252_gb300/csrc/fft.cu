@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include "fft_device.cuh"
+#include "fft_reg.cuh"
 #include "internal.cuh"
 #include "phase.cuh"
 #include "reduce.cuh"
@@ -144,6 +145,131 @@ __global__ void __launch_bounds__(1024) k_cols_filter(float2* X, int n_in, int n
     const int ld = seq_len<MC>(fp.M) + 4;
     const int x0 = blockIdx.x * cpc;
     cols_group<MC>(X, n_in, n_out, x0, min(cpc, fp.M - x0), cpc, fp, tw, Chat, sm, sm + cpc * ld);
+}
+
+// ----------------------------------------- column pass, M = 1024 S >= 2048
+
+// One warp, the 1024-point DFT (conjugate twiddles when INV) of the sequence
+// whose element lane + 32 j is in x[j], as four steps: DFT over the
+// registers, twiddles w1024^(lane k1) from t2, transpose through this warp's
+// area (32 x 33), DFT over the registers.  Element lane + 32 k2 of the result
+// ends in x[bitrev5(k2)].  t2[k1 * 32 + l] = w1024^(k1 l).
+template <bool INV>
+__device__ __forceinline__ void dft1024_warp(float2 (&x)[32], float2* area, const float2* t2, int lane)
+{
+    freg::dft32_dif<INV>(x);
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) {
+        const float2 w = t2[k1 * 32 + lane];
+        area[k1 * 33 + lane] = cmul(x[freg::bitrev5(k1)], INV ? conjf2(w) : w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 32; ++l) x[l] = area[lane * 33 + l];
+    __syncwarp();
+    freg::dft32_dif<INV>(x);
+}
+
+// x[k] <-> x[bitrev5(k)]: the bit-reversed register order to the natural one
+// (compile-time indices: a renaming, no data moves).
+__device__ __forceinline__ void unreverse32(float2 (&x)[32])
+{
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int b = freg::bitrev5(k);
+        if (k < b) {
+            const float2 t = x[k];
+            x[k] = x[b];
+            x[b] = t;
+        }
+    }
+}
+
+constexpr int kSplitThreads = 512;
+constexpr int kSplitArea = 1056;  // 32 x 33
+
+// Shared memory of k_cols_split<S>: the staged columns, the warps' areas,
+// the 32 x 32 twiddles.
+template <int S>
+constexpr size_t cols_split_smem()
+{
+    return ((size_t)(16 / S) * (512 * S + 4) + 16 * kSplitArea + 1024) * sizeof(float2);
+}
+
+// The Toeplitz column pass for M = 1024 S (S = 2, 4) when at most M/2 rows
+// are nonzero and at most M/2 are kept (n_in, n_out <= M/2, always the case
+// for N x N images): column FFT * Chat * IFFT with every 1024-point DFT in
+// one warp's registers.  X[S k + r] = DFT1024(z_r)[k] with
+// z_r[m] = sum_t x[m + 1024 t] w_M^(r (m + 1024 t)) (t < S/2, the input
+// folded to 1024 points), so warp r of a column computes the outputs
+// k = r mod S; after the spectrum and the inverse 1024-point DFT u_r, the
+// column's rows are y[n] = sum_r w_M^(-r n) u_r[n mod 1024], summed in a fixed
+// order.  16 warps: 16 / S columns a group, staged from X as row pieces of
+// 16 / S neighbouring columns; CTAs loop over the groups.  tw[e] = w_M^e.
+template <int S>
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, const float* __restrict__ Chat)
+{
+    constexpr int M = 1024 * S, C = 16 / S, H = M / 2, LDS = H + 4;
+    extern __shared__ float2 sm[];
+    float2* stage = sm;
+    float2* areas = stage + C * LDS;
+    float2* t2 = areas + 16 * kSplitArea;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cc = warp / S, r = warp - cc * S;
+    for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
+    for (int x0 = blockIdx.x * C; x0 < M; x0 += gridDim.x * C) {
+        for (int e = tid; e < C * H; e += kSplitThreads) {
+            const int y = e / C, c = e - y * C;
+            stage[c * LDS + y] = y < n_in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        // the warp's folded, twiddled input, through its area (no register
+        // array holds the S/2 loads of each element)
+        float2* area = areas + warp * kSplitArea;
+        {
+            const float2* col = stage + cc * LDS;
+#pragma unroll 4
+            for (int m = lane; m < 1024; m += 32) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < S / 2; ++t) {
+                    const int n = m + 1024 * t;
+                    const float2 v = col[n];
+                    acc = freg::add(acc, r == 0 ? v : cmul(v, __ldg(tw + ((r * n) & (M - 1)))));
+                }
+                area[m] = acc;
+            }
+        }
+        __syncwarp();
+        float2 x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = area[lane + 32 * j];
+        __syncwarp();
+        dft1024_warp<false>(x, area, t2, lane);  // X[S (lane + 32 k2) + r] in x[bitrev5(k2)]
+        unreverse32(x);
+        {
+            const float* ch = Chat + (int64_t)(x0 + cc) * M + r + S * lane;
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) {
+                const float h = __ldg(ch + 32 * S * k2);
+                x[k2] = make_float2(x[k2].x * h, x[k2].y * h);
+            }
+        }
+        dft1024_warp<true>(x, area, t2, lane);  // u_r[lane + 32 m2] in x[bitrev5(m2)]
+#pragma unroll
+        for (int m2 = 0; m2 < 32; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
+        __syncthreads();
+        for (int e = tid; e < C * n_out; e += kSplitThreads) {
+            const int y = e / C, c = e - y * C;
+            const float2* u = areas + c * S * kSplitArea + (y & 1023);
+            float2 acc = u[0];
+#pragma unroll
+            for (int q = 1; q < S; ++q) acc = freg::add(acc, cmul(u[q * kSplitArea], conjf2(__ldg(tw + ((q * y) & (M - 1))))));
+            X[(int64_t)y * M + x0 + c] = acc;
+        }
+        __syncthreads();  // the next group refills the stage and the areas
+    }
 }
 
 // Column FFTs of the M x M circulant and the real spectrum:
@@ -321,6 +447,19 @@ struct LaunchCols {
     template <int MC>
     int operator()()
     {
+        if constexpr (MC == 2048 || MC == 4096) {
+            constexpr int S = MC / 1024;
+            if (2 * n_in <= MC && 2 * n_out <= MC) {
+                int sms = 0;
+                if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
+                const int groups = MC / (16 / S);
+                k_cols_split<S><<<groups < sms ? groups : sms, kSplitThreads, cols_split_smem<S>(), p->stream>>>(
+                    p->X, n_in, n_out, p->twiddle, p->Chat);
+                SPIREC_CK(cudaGetLastError());
+                p->launches += 1;
+                return SPIREC_OK;
+            }
+        }
         k_cols_filter<MC><<<blocks, s.threads, s.smem, p->stream>>>(p->X, n_in, n_out, p->fft, p->twiddle,
                                                                     p->Chat, s.per_cta);
         SPIREC_CK(cudaGetLastError());
@@ -378,6 +517,10 @@ int fft_setup_attributes(int)
 {
     int rc;
     if ((rc = set_attrs<0>()) != SPIREC_OK) return rc;
+    SPIREC_CK(cudaFuncSetAttribute(k_cols_split<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cols_split_smem<2>()));
+    SPIREC_CK(cudaFuncSetAttribute(k_cols_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)cols_split_smem<4>()));
     for (int M = 16; M <= 4096; M *= 2)
         if ((rc = with_size(M, AttrAll{})) != SPIREC_OK) return rc;
     return SPIREC_OK;

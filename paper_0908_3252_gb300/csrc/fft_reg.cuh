@@ -1,8 +1,9 @@
-// fft_reg.cuh -- 16-point DFTs held entirely in one thread's registers, the
-// building blocks of the warp-level 512-point FFTs of the persistent loop
-// (cg_loop.cu): a DFT over each lane's registers, a twiddle multiply, one
-// exchange through shared memory inside the warp, and a DFT over the
-// registers again.
+// fft_reg.cuh -- 16- and 32-point DFTs held entirely in one thread's
+// registers, the building blocks of the warp-level four-step FFTs (512 points
+// in the persistent loop, cg_loop.cu; 1024 points in the column pass of the
+// stand-alone kernels for M >= 2048, fft.cu): a DFT over each lane's
+// registers, a twiddle multiply, one exchange through shared memory inside
+// the warp, and a DFT over the registers again.
 //
 // Radix-2 in registers, every index a compile-time constant (the loops are
 // fully unrolled), so no data moves between stages.  w = exp(-2 pi i / 32)
@@ -32,6 +33,11 @@ __host__ __device__ constexpr float sin32(int m)
     return s[m];
 }
 
+__host__ __device__ constexpr int bitrev5(int r)
+{
+    return ((r & 1) << 4) | ((r & 2) << 2) | (r & 4) | ((r & 8) >> 2) | ((r & 16) >> 4);
+}
+
 __device__ __forceinline__ float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
@@ -47,6 +53,55 @@ __device__ __forceinline__ float2 mulw(float2 v)
         constexpr float c = cos32(M), s = INV ? sin32(M) : -sin32(M);
         return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.y, c, v.x * s));
     }
+}
+
+// ------------------------------------------------------- 32-point DFT
+
+// One radix-2 decimation-in-frequency stage of half-span SPAN.
+template <bool INV, int SPAN, bool HALF>
+__device__ __forceinline__ void dif_stage(float2 (&x)[32])
+{
+#pragma unroll
+    for (int b = 0; b < 32; b += 2 * SPAN) {
+#pragma unroll
+        for (int i = 0; i < SPAN; ++i) {
+            const float2 a = x[b + i];
+            if constexpr (HALF) {  // the upper half is zero
+                x[b + i + SPAN] = a;
+            } else {
+                x[b + i] = add(a, x[b + i + SPAN]);
+                x[b + i + SPAN] = sub(a, x[b + i + SPAN]);
+            }
+        }
+    }
+}
+
+// The twiddles of a DIF stage (applied after its butterflies), split out so
+// that the constant exponent is a template argument.
+template <bool INV, int SPAN, int I>
+__device__ __forceinline__ void dif_twiddle_row(float2 (&x)[32])
+{
+    if constexpr (I < SPAN) {
+#pragma unroll
+        for (int b = 0; b < 32; b += 2 * SPAN) x[b + I + SPAN] = mulw<INV, I * (16 / SPAN)>(x[b + I + SPAN]);
+        dif_twiddle_row<INV, SPAN, I + 1>(x);
+    }
+}
+
+// Natural order in, bit-reversed out: X[k] ends in x[bitrev5(k)].  HALF_IN:
+// x[16..31] are zero on entry (not read).
+template <bool INV, bool HALF_IN = false>
+__device__ __forceinline__ void dft32_dif(float2 (&x)[32])
+{
+    dif_stage<INV, 16, HALF_IN>(x);
+    dif_twiddle_row<INV, 16, 0>(x);
+    dif_stage<INV, 8, false>(x);
+    dif_twiddle_row<INV, 8, 0>(x);
+    dif_stage<INV, 4, false>(x);
+    dif_twiddle_row<INV, 4, 0>(x);
+    dif_stage<INV, 2, false>(x);
+    dif_twiddle_row<INV, 2, 0>(x);
+    dif_stage<INV, 1, false>(x);
 }
 
 // ------------------------------------------------------- 16-point DFTs
