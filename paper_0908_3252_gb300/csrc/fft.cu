@@ -272,6 +272,225 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
     }
 }
 
+// ------------------------------------------- row passes, M = 1024 S >= 2048
+
+// Warp areas of the split row passes: 32 x 33 for the four-step DFT, padded
+// so that whole-row copies, whose neighbouring elements k = S j + r live in
+// the S areas of a row at j, hit distinct banks (area stride = 4 or 8 mod 16).
+template <int S>
+__host__ __device__ constexpr int row_area() { return 1056 + (S == 4 ? 4 : 8); }
+
+// Shared memory of the split row passes: (pass 1 only) the staged rows, then
+// the warps' areas and the 32 x 32 twiddles.
+template <int S, bool STAGE>
+constexpr size_t rows_split_smem()
+{
+    return ((STAGE ? (size_t)(16 / S) * (512 * S + 4) : 0) + 16 * row_area<S>() + 1024) * sizeof(float2);
+}
+
+// Row pass 1 for M = 1024 S (S = 2, 4) with at most M/2 nonzero inputs
+// (n_in <= M/2): the rows (MODE 1: the new direction d = -g + beta d_old,
+// written to d_new, with q1 and the first line-search sums as in
+// rows_fwd_group) staged in shared memory, then warp r of a row computes the
+// outputs k = r mod S of its 1024-point DFT from the folded input
+// sum_t x[m + 1024 t] w_M^(r (m + 1024 t)), and the block writes whole rows
+// of X.  16 / S rows a group; CTAs loop over the groups.
+template <int S, int MODE, int KIND>
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, const float2* __restrict__ tw,
+                 CgPass c)
+{
+    constexpr int M = 1024 * S, R = 16 / S, H = M / 2, LDS = H + 4, A = row_area<S>();
+    extern __shared__ float2 sm[];
+    float2* stage = sm;
+    float2* areas = stage + R * LDS;
+    float2* t2 = areas + 16 * A;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp / S, r = warp - q * S;
+    for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
+    float beta = 0.f;
+    bool restart = true;
+    if (MODE == 1) {
+        const double bd = c.scal[S_BETA];
+        beta = (float)bd;
+        restart = bd == 0.0;
+    }
+    const int N = n_in;
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
+        const int nr = min(R, rows - r0);
+        for (int e = tid; e < R * H; e += kSplitThreads) {
+            const int qq = e / H, m = e - qq * H;
+            float2 v = make_float2(0.f, 0.f);
+            if (qq < nr && m < N) {
+                const int64_t o = (int64_t)(r0 + qq) * ld_in + m;
+                if (MODE == 0) {
+                    v = __ldcg(in + o);
+                } else {
+                    v = new_direction(__ldcg(c.g + o), __ldcg(c.d_old + o), beta, restart);
+                    c.d_new[o] = v;
+                }
+            }
+            stage[qq * LDS + m] = v;
+        }
+        __syncthreads();
+        if (MODE == 1) {
+            const Reg reg = c.reg;
+            for (int e = tid; e < nr * N; e += kSplitThreads) {
+                const int qq = e / N, m = e - qq * N;
+                const int n = r0 + qq;
+                const int64_t o = (int64_t)n * N + m;
+                const bool has_r = m + 1 < N, has_d = n + 1 < N;
+                const int64_t od = has_d ? o + N : o;
+                const float2 dn = stage[qq * LDS + m];
+                const float2 dr = stage[qq * LDS + (has_r ? m + 1 : m)];
+                const float2 fp_ = __ldcg(c.f + o), fr = __ldcg(c.f + (has_r ? o + 1 : o)), fd = __ldcg(c.f + od);
+                const float2 gd = __ldcg(c.g + od), dold_d = __ldcg(c.d_old + od);
+                const float2 tfv = __ldcg(c.Tf + o), dv = __ldg(c.D + o);
+                acc[0] += 2.f * redot(dn, f2sub(tfv, dv));
+                if (reg.lambda1 != 0.f) {
+                    {
+                        const float2 w = f2sub(dr, dn);
+                        const float2 z = f2sub(fr, fp_);
+                        const float bw =
+                            has_r ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
+                        acc[1] = fmaf(bw, redot(z, w), acc[1]);
+                        acc[2] = fmaf(bw, redot(w, w), acc[2]);
+                    }
+                    {
+                        const float2 dd = new_direction(gd, dold_d, beta, restart);
+                        const float2 w = f2sub(dd, dn);
+                        const float2 z = f2sub(fd, fp_);
+                        const float bw =
+                            has_d ? reg.lambda1 * phi_weight_k<KIND>(reg.kind, reg.alpha1, redot(z, z)) : 0.f;
+                        acc[1] = fmaf(bw, redot(z, w), acc[1]);
+                        acc[2] = fmaf(bw, redot(w, w), acc[2]);
+                    }
+                }
+                if (reg.lambda0 != 0.f) {
+                    const float bw = reg.lambda0 * phi_weight_k<KIND>(reg.kind, reg.alpha0, redot(fp_, fp_));
+                    acc[1] = fmaf(bw, redot(fp_, dn), acc[1]);
+                    acc[2] = fmaf(bw, redot(dn, dn), acc[2]);
+                }
+            }
+        }
+        if (q < nr) {
+            float2* area = areas + warp * A;
+            const float2* row = stage + q * LDS;
+#pragma unroll 4
+            for (int m = lane; m < 1024; m += 32) {
+                float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < S / 2; ++t) {
+                    const int n = m + 1024 * t;
+                    const float2 v = row[n];
+                    z = freg::add(z, r == 0 ? v : cmul(v, __ldg(tw + ((r * n) & (M - 1)))));
+                }
+                area[m] = z;
+            }
+            __syncwarp();
+            float2 x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = area[lane + 32 * j];
+            __syncwarp();
+            dft1024_warp<false>(x, area, t2, lane);
+#pragma unroll
+            for (int k2 = 0; k2 < 32; ++k2) area[lane + 32 * k2] = x[freg::bitrev5(k2)];
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * M; e += kSplitThreads) {
+            const int qq = e / M, kk = e - qq * M;
+            X[(int64_t)(r0 + qq) * M + kk] = areas[(qq * S + (kk & (S - 1))) * A + kk / S];
+        }
+        __syncthreads();  // the next group refills the stage and the areas
+    }
+    if (MODE == 1) {
+        FF bt[3];
+        block_partial<3>(acc, bt);
+        store_parts<3>(bt, c.parts, kMaxParts);
+        if (last_block(c.counter)) {
+            FF t[3];
+            sum_parts_ff<3>(c.parts, kMaxParts, gridDim.x, t);
+            if (threadIdx.x == 0) {
+                c.scal[S_Q1] = ff_to_double(t[0]);
+                c.scal[S_NUM0] = ff_to_double(t[1]);
+                c.scal[S_DEN0] = ff_to_double(t[2]);
+                *c.counter = 0u;
+            }
+        }
+    }
+}
+
+// Row pass 3 for M = 1024 S (S = 2, 4), n_out <= M/2: each row of X copied
+// whole into the S warp areas (element S j + r to area r at j), warp r's
+// inverse 1024-point DFT u_r, and out[m] = sum_r w_M^(-r m) u_r[m mod 1024]
+// in a fixed order; with dotx the same grid sum and scalars as k_rows_inv.
+template <int S, int MODE>
+__global__ void __launch_bounds__(kSplitThreads, 1)
+k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2* __restrict__ tw,
+                 const float2* dotx, CgPass c, int dot_scalar)
+{
+    constexpr int M = 1024 * S, R = 16 / S, A = row_area<S>();
+    extern __shared__ float2 sm[];
+    float2* areas = sm;
+    float2* t2 = areas + 16 * A;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp / S;
+    for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
+    float acc = 0.f;
+    for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
+        const int nr = min(R, rows - r0);
+        for (int e = tid; e < nr * M; e += kSplitThreads) {
+            const int qq = e / M, kk = e - qq * M;
+            areas[(qq * S + (kk & (S - 1))) * A + kk / S] = __ldcg(X + (int64_t)(r0 + qq) * M + kk);
+        }
+        __syncthreads();
+        if (q < nr) {
+            float2* area = areas + warp * A;
+            float2 x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = area[lane + 32 * j];
+            __syncwarp();
+            dft1024_warp<true>(x, area, t2, lane);  // u_r[lane + 32 m2] in x[bitrev5(m2)]
+#pragma unroll
+            for (int m2 = 0; m2 < 32; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
+        }
+        __syncthreads();
+        for (int e = tid; e < nr * n_out; e += kSplitThreads) {
+            const int qq = e / n_out, m = e - qq * n_out;
+            const float2* u = areas + qq * S * A + (m & 1023);
+            float2 y = u[0];
+#pragma unroll
+            for (int rr = 1; rr < S; ++rr) y = freg::add(y, cmul(u[rr * A], conjf2(__ldg(tw + ((rr * m) & (M - 1))))));
+            const int64_t o = (int64_t)(r0 + qq) * n_out + m;
+            out[o] = y;
+            if (dotx) acc += redot(__ldcg(dotx + o), y);
+        }
+        __syncthreads();
+    }
+    if (dotx) {
+        float v[1] = {acc};
+        FF bt[1];
+        block_partial<1>(v, bt);
+        store_parts<1>(bt, c.parts, kMaxParts);
+        if (last_block(c.counter)) {
+            FF t[1];
+            sum_parts_ff<1>(c.parts, kMaxParts, gridDim.x, t);
+            if (threadIdx.x == 0) {
+                const double sv = ff_to_double(t[0]);
+                if (MODE == 0) {
+                    c.scal[dot_scalar] = sv;
+                } else {
+                    c.scal[S_Q2] = sv;
+                    const double curv = 2.0 * sv + c.scal[S_DEN0];
+                    c.scal[S_T1] = curv > 0.0 ? -(c.scal[S_Q1] + c.scal[S_NUM0]) / curv : 0.0;
+                }
+                *c.counter = 0u;
+            }
+        }
+    }
+}
+
 // Column FFTs of the M x M circulant and the real spectrum:
 // Chat[x][ky] = Re(FFT2 c)[ky][x] / M^2.
 template <int MC>
@@ -377,6 +596,22 @@ int set_attrs()
     return SPIREC_OK;
 }
 
+template <int S>
+int set_split_row_attrs()
+{
+    const int fb = (int)rows_split_smem<S, true>(), ib = (int)rows_split_smem<S, false>();
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd_split<S, 0, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fb));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd_split<S, 1, SPIREC_PHI_HUBER>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, fb));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd_split<S, 1, SPIREC_PHI_HYPERBOLIC>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, fb));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_fwd_split<S, 1, SPIREC_PHI_QUADRATIC>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, fb));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_inv_split<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ib));
+    SPIREC_CK(cudaFuncSetAttribute(k_rows_inv_split<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ib));
+    return SPIREC_OK;
+}
+
 // Calls f.template operator()<MC>() with the compile-time size for M, or
 // MC = 0 for sizes without a specialisation.
 template <typename F>
@@ -419,9 +654,30 @@ struct LaunchRowsFwd {
     int ld_in, n_in, rows, mode, blocks;
     Shape s;
     CgPass c;
+    int split_grid;  // CTAs of the split passes (M = 2048, 4096): the SM count
+    template <int S, int MODE, int KIND>
+    void split(int grid)
+    {
+        k_rows_fwd_split<S, MODE, KIND><<<grid, kSplitThreads, rows_split_smem<S, true>(), p->stream>>>(
+            in, ld_in, n_in, rows, p->X, p->twiddle, c);
+    }
     template <int MC>
     int operator()()
     {
+        if constexpr (MC == 2048 || MC == 4096) {
+            constexpr int S = MC / 1024;
+            if (2 * n_in <= MC) {
+                const int groups = (rows + 16 / S - 1) / (16 / S);
+                const int grid = groups < split_grid ? groups : split_grid;
+                if (mode == 0) split<S, 0, -1>(grid);
+                else if (c.reg.kind == SPIREC_PHI_HUBER) split<S, 1, SPIREC_PHI_HUBER>(grid);
+                else if (c.reg.kind == SPIREC_PHI_HYPERBOLIC) split<S, 1, SPIREC_PHI_HYPERBOLIC>(grid);
+                else split<S, 1, SPIREC_PHI_QUADRATIC>(grid);
+                SPIREC_CK(cudaGetLastError());
+                p->launches += 1;
+                return SPIREC_OK;
+            }
+        }
         if (mode == 0)
             k_rows_fwd<MC, 0><<<blocks, s.threads, s.smem, p->stream>>>(in, ld_in, n_in, rows, p->X, p->fft,
                                                                         p->twiddle, s.per_cta, c);
@@ -476,9 +732,26 @@ struct LaunchRowsInv {
     int dot_scalar, blocks;
     Shape s;
     CgPass c;
+    int split_grid;
     template <int MC>
     int operator()()
     {
+        if constexpr (MC == 2048 || MC == 4096) {
+            constexpr int S = MC / 1024;
+            if (2 * p->N <= MC) {
+                const int groups = (p->N + 16 / S - 1) / (16 / S);
+                const int grid = groups < split_grid ? groups : split_grid;
+                if (mode == 0)
+                    k_rows_inv_split<S, 0><<<grid, kSplitThreads, rows_split_smem<S, false>(), p->stream>>>(
+                        p->X, p->N, out, p->N, p->twiddle, dotx, c, dot_scalar);
+                else
+                    k_rows_inv_split<S, 1><<<grid, kSplitThreads, rows_split_smem<S, false>(), p->stream>>>(
+                        p->X, p->N, out, p->N, p->twiddle, dotx, c, dot_scalar);
+                SPIREC_CK(cudaGetLastError());
+                p->launches += 1;
+                return SPIREC_OK;
+            }
+        }
         if (mode == 0)
             k_rows_inv<MC, 0><<<blocks, s.threads, s.smem, p->stream>>>(p->X, p->N, out, p->N, p->fft,
                                                                         p->twiddle, s.per_cta, dotx, c, dot_scalar);
@@ -521,6 +794,8 @@ int fft_setup_attributes(int)
                                    (int)cols_split_smem<2>()));
     SPIREC_CK(cudaFuncSetAttribute(k_cols_split<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)cols_split_smem<4>()));
+    if ((rc = set_split_row_attrs<2>()) != SPIREC_OK) return rc;
+    if ((rc = set_split_row_attrs<4>()) != SPIREC_OK) return rc;
     for (int M = 16; M <= 4096; M *= 2)
         if ((rc = with_size(M, AttrAll{})) != SPIREC_OK) return rc;
     return SPIREC_OK;
@@ -537,7 +812,9 @@ int launch_rows_fwd(spirec_plan p, const float2* in, int ld_in, int n_in, int ro
         return SPIREC_EUNSUPPORTED;
     }
     const CgPass c = cg ? *cg : plain_pass(p, 0, nullptr);
-    return with_size(M, LaunchRowsFwd{p, in, ld_in, n_in, rows, mode, blocks, s, c});
+    int sms = 0;
+    if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
+    return with_size(M, LaunchRowsFwd{p, in, ld_in, n_in, rows, mode, blocks, s, c, sms});
 }
 
 int launch_cols(spirec_plan p, int n_in, int n_out)
@@ -559,7 +836,9 @@ int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, co
         return SPIREC_EUNSUPPORTED;
     }
     const CgPass c = cg ? *cg : plain_pass(p, P_MISC, p->counters + C_MISC);
-    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c});
+    int sms = 0;
+    if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
+    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c, sms});
 }
 
 int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar)

@@ -303,8 +303,9 @@ def _large_case(N, I, S, seed):
 # (N, M, interleaves, samples): the M = 1024 loop (split 512-point column
 # and row FFTs, 4-row blocks, a last block with fewer rows), the M = 512 loop
 # (radix-4 passes, 4-row groups), and M = 2048 and 4096, whose row caches do
-# not fit a block: the solve falls back to the kernel graph, whose column
-# pass splits each column into 2 or 4 warp-sized 1024-point DFTs
+# not fit a block: the solve falls back to the kernel graph, whose row and
+# column passes split each row and column into 2 or 4 warp-sized 1024-point
+# DFTs
 LARGE_CASES = [(260, 1024, 3, 700, 21), (200, 512, 3, 500, 31), (520, 2048, 2, 400, 41),
                (600, 4096, 2, 300, 43)]
 
