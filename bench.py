@@ -397,12 +397,76 @@ def dist_env():
     return ws, rank, local
 
 
-def clocks_start():
+# Clock-event reason bits of NVML (nvmlClocksEventReason*).
+_NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+
+class _NvmlClocks:
+    """SM clock and clock-event reasons of this process's GPU, read through
+    NVML every millisecond or so by a host thread while the timed region runs
+    (read-only queries; nothing is set).  The GPU is matched by PCI bus id."""
+
+    def __init__(self, device):
+        import ctypes
+        import threading
+        import torch
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        pr = torch.cuda.get_device_properties(device)
+        self.h = ctypes.c_void_p()
+        bus = getattr(pr, "pci_bus_id", None)
+        rc = -1
+        if bus is not None:
+            pci = "%08X:%02X:%02X.0" % (getattr(pr, "pci_domain_id", 0), bus, getattr(pr, "pci_device_id", 0))
+            rc = self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(self.h))
+        if rc != 0 and self.lib.nvmlDeviceGetHandleByIndex_v2(device, ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0 \
+            else None
+        self.samples = []
+        self.stop_ev = threading.Event()
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.ctypes = ctypes
+
+    def _run(self):
+        ct = self.ctypes
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop_ev.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0 and \
+                    self.reasons_fn(self.h, ct.byref(rs)) == 0:
+                self.samples.append((time.time(), float(mhz.value), int(rs.value)))
+            time.sleep(0.001)
+
+    def start(self):
+        self.thread.start()
+        while not self.samples and self.thread.is_alive():  # running before the region starts
+            time.sleep(0.001)
+
+    def stop(self):
+        self.stop_ev.set()
+        self.thread.join(timeout=5)
+        self.lib.nvmlShutdown()
+
+
+def clocks_start(device=0):
+    """Starts the clock record of the timed region: the NVML sampler when the
+    library loads, else nvidia-smi at its 200 ms period."""
     try:
         f = open(os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
             os.path.join(ROOT, "gpurun_out")) else os.devnull, "w")
     except OSError:
         f = open(os.devnull, "w")
+    try:
+        nv = _NvmlClocks(device)
+        nv.start()
+        return nv, f
+    except Exception:
+        pass
     q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -417,6 +481,19 @@ def clocks_start():
 def clocks_stop(proc, f, gpu_index):
     if proc is None:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    if isinstance(proc, _NvmlClocks):
+        proc.stop()
+        smp = proc.samples
+        f.write("unix_time,sm_mhz,reasons_mask\n")
+        for t, m, r in smp:
+            f.write(f"{t:.4f},{m:.0f},{r:#x}\n")
+        f.close()
+        if not smp:
+            return {"sm_mhz": None, "sm_max_mhz": proc.max_mhz, "reasons": ["no samples"]}
+        reasons = sorted({nm for _, _, r in smp for bit, nm in _NVML_REASONS.items() if r & bit})
+        return {"sm_mhz": statistics.median(m for _, m, _ in smp), "sm_max_mhz": proc.max_mhz,
+                "sm_min_mhz": min(m for _, m, _ in smp), "samples": len(smp), "reasons": reasons,
+                "source": "NVML, sampled every ~1 ms during the timed region"}
     proc.terminate()
     try:
         out, _ = proc.communicate(timeout=5)
@@ -444,7 +521,7 @@ def clocks_stop(proc, f, gpu_index):
     if not sm:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-            "reasons": sorted(reasons)}
+            "reasons": sorted(reasons), "source": "nvidia-smi -lms 200"}
 
 
 def job_throughput(local_seconds, units_per_rank, device="cpu"):
@@ -641,7 +718,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         spirec.spirec_timing(h, 1)
         l0 = spirec.spirec_launch_count(h)
-        proc, cf = clocks_start()
+        proc, cf = clocks_start(torch.cuda.current_device())
         evs = []
         for _ in range(args.steps):
             flush.fill_(1.0)

@@ -27,12 +27,16 @@
 
 namespace spirec {
 
-// One pixel per thread where the partial slots allow (one wave on 152 SMs at
-// N = 512), grid-stride beyond.
+// One pixel per thread up to kVecBlocksPerSm resident blocks an SM (the
+// vector kernels are built to fit that many), grid-stride beyond: a single
+// wave, and few block partials for the last block to add.
 int vec_blocks(int N)
 {
     const int64_t P = (int64_t)N * N;
+    int sms = 0;
+    if (device_sms(&sms) != SPIREC_OK || sms <= 0) sms = 152;
     int64_t b = (P + kVecThreads - 1) / kVecThreads;
+    if (b > (int64_t)kVecBlocksPerSm * sms) b = (int64_t)kVecBlocksPerSm * sms;
     if (b > kMaxParts) b = kMaxParts;
     if (b < 1) b = 1;
     return (int)b;
@@ -69,7 +73,7 @@ __global__ void k_sumsq(const float2* __restrict__ s, int64_t L, float2* parts, 
 // Line-search step `step` (1 or 2) at t = t_step; the last block forms
 // t_{step+1} (cgd::ls_next).  KIND: phi fixed at compile time.
 template <int KIND>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2* parts,
               unsigned* counter, double* scal)
 {
@@ -94,7 +98,7 @@ k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2
 
 // Gradient and step (cgd::update_pixel); the last block forms J and beta.
 template <bool FIRST, int KIND>
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const float2* Td,
          const float2* __restrict__ D, float2* g, int N, Reg reg, float2* parts, unsigned* counter,
          double* scal, double* Jout)

@@ -185,15 +185,57 @@ __device__ __forceinline__ void unreverse32(float2 (&x)[32])
     }
 }
 
-constexpr int kSplitThreads = 512;
+// The split passes run 8 warps a CTA and two CTAs an SM, so that one CTA's
+// loads overlap the other's transforms.
+constexpr int kSplitWarps = 8;
+constexpr int kSplitThreads = 32 * kSplitWarps;
+constexpr int kSplitCtasPerSm = 16 / kSplitWarps;
 constexpr int kSplitArea = 1056;  // 32 x 33
+
+// Input m (m < 1024) of the 1024-point DFT that gives the outputs k = r mod S
+// of an M = 1024 S point DFT of x (x zero from M/2 on):
+//   z_r[m] = w_M^(r m) sum_{t < S/2} x[m + 1024 t] w_S^(r t),
+// as w_M^(r (m + 1024 t)) = w_M^(r m) w_S^(r t).  For S = 4 the factor
+// w_4^r = (-i)^r is applied exactly (a swap and sign changes).
+template <int S>
+__device__ __forceinline__ float2 fold_input(const float2* x, int m, int r, const float2* __restrict__ tw)
+{
+    float2 z = x[m];
+    if constexpr (S == 4) {
+        const float2 v = x[m + 1024];
+        const float2 rv = r == 0 ? v : r == 1 ? make_float2(v.y, -v.x) : r == 2 ? make_float2(-v.x, -v.y)
+                                                                                : make_float2(-v.y, v.x);
+        z = freg::add(z, rv);
+    }
+    return r == 0 ? z : cmul(z, __ldg(tw + r * m));
+}
+
+// Output n (n < M/2) of the inverse M-point DFT from the S inverse 1024-point
+// DFTs u_r of the classes k = r mod S (u_r at u + r * stride, index n mod
+// 1024 applied by the caller): sum_r w_M^(-r n) u_r, by Horner's rule in
+// conj(w_M^n).
+template <int S>
+__device__ __forceinline__ float2 combine_output(const float2* u, int stride, int n, const float2* __restrict__ tw)
+{
+    const float2 c = conjf2(__ldg(tw + n));
+    float2 y = u[(S - 1) * stride];
+#pragma unroll
+    for (int r = S - 2; r >= 0; --r) y = freg::add(u[r * stride], cmul(c, y));
+    return y;
+}
+
+// Stride of a staged column of k_cols_split<S>: the 8 / S columns of one
+// row piece land on distinct banks (offsets 8 float2 apart for two columns,
+// 4 for four).
+template <int S>
+__host__ __device__ constexpr int cols_split_ld() { return 512 * S + (S == 4 ? 8 : 4); }
 
 // Shared memory of k_cols_split<S>: the staged columns, the warps' areas,
 // the 32 x 32 twiddles.
 template <int S>
 constexpr size_t cols_split_smem()
 {
-    return ((size_t)(16 / S) * (512 * S + 4) + 16 * kSplitArea + 1024) * sizeof(float2);
+    return ((size_t)(kSplitWarps / S) * cols_split_ld<S>() + kSplitWarps * kSplitArea + 1024) * sizeof(float2);
 }
 
 // The Toeplitz column pass for M = 1024 S (S = 2, 4) when at most M/2 rows
@@ -204,21 +246,22 @@ constexpr size_t cols_split_smem()
 // folded to 1024 points), so warp r of a column computes the outputs
 // k = r mod S; after the spectrum and the inverse 1024-point DFT u_r, the
 // column's rows are y[n] = sum_r w_M^(-r n) u_r[n mod 1024], summed in a fixed
-// order.  16 warps: 16 / S columns a group, staged from X as row pieces of
-// 16 / S neighbouring columns; CTAs loop over the groups.  tw[e] = w_M^e.
+// order.  8 / S columns a group, staged from X as row pieces of 8 / S
+// neighbouring columns; CTAs loop over the groups.  tw[e] = w_M^e.
 template <int S>
-__global__ void __launch_bounds__(kSplitThreads, 1)
+__global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
 k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, const float* __restrict__ Chat)
 {
-    constexpr int M = 1024 * S, C = 16 / S, H = M / 2, LDS = H + 4;
+    constexpr int M = 1024 * S, C = kSplitWarps / S, H = M / 2, LDS = cols_split_ld<S>();
     extern __shared__ float2 sm[];
     float2* stage = sm;
     float2* areas = stage + C * LDS;
-    float2* t2 = areas + 16 * kSplitArea;
+    float2* t2 = areas + kSplitWarps * kSplitArea;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cc = warp / S, r = warp - cc * S;
     for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
     for (int x0 = blockIdx.x * C; x0 < M; x0 += gridDim.x * C) {
+#pragma unroll 4
         for (int e = tid; e < C * H; e += kSplitThreads) {
             const int y = e / C, c = e - y * C;
             stage[c * LDS + y] = y < n_in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
@@ -230,16 +273,7 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
         {
             const float2* col = stage + cc * LDS;
 #pragma unroll 4
-            for (int m = lane; m < 1024; m += 32) {
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int t = 0; t < S / 2; ++t) {
-                    const int n = m + 1024 * t;
-                    const float2 v = col[n];
-                    acc = freg::add(acc, r == 0 ? v : cmul(v, __ldg(tw + ((r * n) & (M - 1)))));
-                }
-                area[m] = acc;
-            }
+            for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(col, m, r, tw);
         }
         __syncwarp();
         float2 x[32];
@@ -262,11 +296,7 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
         __syncthreads();
         for (int e = tid; e < C * n_out; e += kSplitThreads) {
             const int y = e / C, c = e - y * C;
-            const float2* u = areas + c * S * kSplitArea + (y & 1023);
-            float2 acc = u[0];
-#pragma unroll
-            for (int q = 1; q < S; ++q) acc = freg::add(acc, cmul(u[q * kSplitArea], conjf2(__ldg(tw + ((q * y) & (M - 1))))));
-            X[(int64_t)y * M + x0 + c] = acc;
+            X[(int64_t)y * M + x0 + c] = combine_output<S>(areas + c * S * kSplitArea + (y & 1023), kSplitArea, y, tw);
         }
         __syncthreads();  // the next group refills the stage and the areas
     }
@@ -285,7 +315,7 @@ __host__ __device__ constexpr int row_area() { return 1056 + (S == 4 ? 4 : 8); }
 template <int S, bool STAGE>
 constexpr size_t rows_split_smem()
 {
-    return ((STAGE ? (size_t)(16 / S) * (512 * S + 4) : 0) + 16 * row_area<S>() + 1024) * sizeof(float2);
+    return ((STAGE ? (size_t)(kSplitWarps / S) * (512 * S + 4) : 0) + kSplitWarps * row_area<S>() + 1024) * sizeof(float2);
 }
 
 // Row pass 1 for M = 1024 S (S = 2, 4) with at most M/2 nonzero inputs
@@ -294,17 +324,17 @@ constexpr size_t rows_split_smem()
 // rows_fwd_group) staged in shared memory, then warp r of a row computes the
 // outputs k = r mod S of its 1024-point DFT from the folded input
 // sum_t x[m + 1024 t] w_M^(r (m + 1024 t)), and the block writes whole rows
-// of X.  16 / S rows a group; CTAs loop over the groups.
+// of X.  8 / S rows a group; CTAs loop over the groups.
 template <int S, int MODE, int KIND>
-__global__ void __launch_bounds__(kSplitThreads, 1)
+__global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
 k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, const float2* __restrict__ tw,
                  CgPass c)
 {
-    constexpr int M = 1024 * S, R = 16 / S, H = M / 2, LDS = H + 4, A = row_area<S>();
+    constexpr int M = 1024 * S, R = kSplitWarps / S, H = M / 2, LDS = H + 4, A = row_area<S>();
     extern __shared__ float2 sm[];
     float2* stage = sm;
     float2* areas = stage + R * LDS;
-    float2* t2 = areas + 16 * A;
+    float2* t2 = areas + kSplitWarps * A;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp / S, r = warp - q * S;
     for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
@@ -319,6 +349,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
     float acc[3] = {0.f, 0.f, 0.f};
     for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
         const int nr = min(R, rows - r0);
+#pragma unroll 4
         for (int e = tid; e < R * H; e += kSplitThreads) {
             const int qq = e / H, m = e - qq * H;
             float2 v = make_float2(0.f, 0.f);
@@ -336,6 +367,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         __syncthreads();
         if (MODE == 1) {
             const Reg reg = c.reg;
+#pragma unroll 2
             for (int e = tid; e < nr * N; e += kSplitThreads) {
                 const int qq = e / N, m = e - qq * N;
                 const int n = r0 + qq;
@@ -378,16 +410,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
             float2* area = areas + warp * A;
             const float2* row = stage + q * LDS;
 #pragma unroll 4
-            for (int m = lane; m < 1024; m += 32) {
-                float2 z = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int t = 0; t < S / 2; ++t) {
-                    const int n = m + 1024 * t;
-                    const float2 v = row[n];
-                    z = freg::add(z, r == 0 ? v : cmul(v, __ldg(tw + ((r * n) & (M - 1)))));
-                }
-                area[m] = z;
-            }
+            for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(row, m, r, tw);
             __syncwarp();
             float2 x[32];
 #pragma unroll
@@ -426,20 +449,21 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
 // inverse 1024-point DFT u_r, and out[m] = sum_r w_M^(-r m) u_r[m mod 1024]
 // in a fixed order; with dotx the same grid sum and scalars as k_rows_inv.
 template <int S, int MODE>
-__global__ void __launch_bounds__(kSplitThreads, 1)
+__global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
 k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2* __restrict__ tw,
                  const float2* dotx, CgPass c, int dot_scalar)
 {
-    constexpr int M = 1024 * S, R = 16 / S, A = row_area<S>();
+    constexpr int M = 1024 * S, R = kSplitWarps / S, A = row_area<S>();
     extern __shared__ float2 sm[];
     float2* areas = sm;
-    float2* t2 = areas + 16 * A;
+    float2* t2 = areas + kSplitWarps * A;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp / S;
     for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
     float acc = 0.f;
     for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
         const int nr = min(R, rows - r0);
+#pragma unroll 4
         for (int e = tid; e < nr * M; e += kSplitThreads) {
             const int qq = e / M, kk = e - qq * M;
             areas[(qq * S + (kk & (S - 1))) * A + kk / S] = __ldcg(X + (int64_t)(r0 + qq) * M + kk);
@@ -458,10 +482,7 @@ k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2
         __syncthreads();
         for (int e = tid; e < nr * n_out; e += kSplitThreads) {
             const int qq = e / n_out, m = e - qq * n_out;
-            const float2* u = areas + qq * S * A + (m & 1023);
-            float2 y = u[0];
-#pragma unroll
-            for (int rr = 1; rr < S; ++rr) y = freg::add(y, cmul(u[rr * A], conjf2(__ldg(tw + ((rr * m) & (M - 1))))));
+            const float2 y = combine_output<S>(areas + qq * S * A + (m & 1023), A, m, tw);
             const int64_t o = (int64_t)(r0 + qq) * n_out + m;
             out[o] = y;
             if (dotx) acc += redot(__ldcg(dotx + o), y);
@@ -654,7 +675,7 @@ struct LaunchRowsFwd {
     int ld_in, n_in, rows, mode, blocks;
     Shape s;
     CgPass c;
-    int split_grid;  // CTAs of the split passes (M = 2048, 4096): the SM count
+    int split_grid;  // CTAs of the split passes (M = 2048, 4096): two an SM
     template <int S, int MODE, int KIND>
     void split(int grid)
     {
@@ -667,7 +688,7 @@ struct LaunchRowsFwd {
         if constexpr (MC == 2048 || MC == 4096) {
             constexpr int S = MC / 1024;
             if (2 * n_in <= MC) {
-                const int groups = (rows + 16 / S - 1) / (16 / S);
+                const int groups = (rows + kSplitWarps / S - 1) / (kSplitWarps / S);
                 const int grid = groups < split_grid ? groups : split_grid;
                 if (mode == 0) split<S, 0, -1>(grid);
                 else if (c.reg.kind == SPIREC_PHI_HUBER) split<S, 1, SPIREC_PHI_HUBER>(grid);
@@ -708,8 +729,9 @@ struct LaunchCols {
             if (2 * n_in <= MC && 2 * n_out <= MC) {
                 int sms = 0;
                 if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
-                const int groups = MC / (16 / S);
-                k_cols_split<S><<<groups < sms ? groups : sms, kSplitThreads, cols_split_smem<S>(), p->stream>>>(
+                const int groups = MC / (kSplitWarps / S);
+                const int cap = kSplitCtasPerSm * sms;
+                k_cols_split<S><<<groups < cap ? groups : cap, kSplitThreads, cols_split_smem<S>(), p->stream>>>(
                     p->X, n_in, n_out, p->twiddle, p->Chat);
                 SPIREC_CK(cudaGetLastError());
                 p->launches += 1;
@@ -739,7 +761,7 @@ struct LaunchRowsInv {
         if constexpr (MC == 2048 || MC == 4096) {
             constexpr int S = MC / 1024;
             if (2 * p->N <= MC) {
-                const int groups = (p->N + 16 / S - 1) / (16 / S);
+                const int groups = (p->N + kSplitWarps / S - 1) / (kSplitWarps / S);
                 const int grid = groups < split_grid ? groups : split_grid;
                 if (mode == 0)
                     k_rows_inv_split<S, 0><<<grid, kSplitThreads, rows_split_smem<S, false>(), p->stream>>>(
@@ -814,7 +836,7 @@ int launch_rows_fwd(spirec_plan p, const float2* in, int ld_in, int n_in, int ro
     const CgPass c = cg ? *cg : plain_pass(p, 0, nullptr);
     int sms = 0;
     if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
-    return with_size(M, LaunchRowsFwd{p, in, ld_in, n_in, rows, mode, blocks, s, c, sms});
+    return with_size(M, LaunchRowsFwd{p, in, ld_in, n_in, rows, mode, blocks, s, c, kSplitCtasPerSm * sms});
 }
 
 int launch_cols(spirec_plan p, int n_in, int n_out)
@@ -838,7 +860,7 @@ int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, co
     const CgPass c = cg ? *cg : plain_pass(p, P_MISC, p->counters + C_MISC);
     int sms = 0;
     if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
-    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c, sms});
+    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c, kSplitCtasPerSm * sms});
 }
 
 int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar)

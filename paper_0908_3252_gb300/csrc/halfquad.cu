@@ -57,7 +57,7 @@ __device__ __forceinline__ float2 penalty_normal_at(const float2* x, HqW W, int 
 }
 
 // Weights at f and J(f) = ||s||^2 - 2 Re<f, D> + Re<f, T f> + R(f).
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int N, Reg reg, HqW W, float2* parts,
            unsigned* counter, double* scal, double* Jout)
 {
@@ -110,7 +110,7 @@ k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int 
 }
 
 // r = D - T f - P f, p = r, rho = <r, r>.
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_hq_residual(const float2* f, const float2* Tf, const float2* __restrict__ D, HqW W, int N, float2* r,
               float2* pv, float2* parts, unsigned* counter, double* scal)
 {
@@ -138,7 +138,7 @@ k_hq_residual(const float2* f, const float2* Tf, const float2* __restrict__ D, H
 }
 
 // q = T p + P p; alpha = rho / Re<p, q> (0 unless Re<p, q> > 0).
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_hq_apply(const float2* pv, const float2* Tp, HqW W, int N, float2* q, float2* parts, unsigned* counter,
            double* scal)
 {
@@ -167,7 +167,7 @@ k_hq_apply(const float2* pv, const float2* Tp, HqW W, int N, float2* q, float2* 
 
 // f += alpha p, T f += alpha T p, r -= alpha q; beta = <r, r> / rho
 // (0 when rho = 0), rho = <r, r>.
-__global__ void __launch_bounds__(kVecThreads)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
 k_hq_step(float2* f, float2* Tf, float2* r, const float2* pv, const float2* Tp, const float2* q, int N,
           float2* parts, unsigned* counter, double* scal)
 {
@@ -197,7 +197,7 @@ k_hq_step(float2* f, float2* Tf, float2* r, const float2* pv, const float2* Tp, 
 }
 
 // p = r + beta p.
-__global__ void __launch_bounds__(kVecThreads) k_hq_dir(const float2* r, float2* pv, int N, const double* scal)
+__global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm) k_hq_dir(const float2* r, float2* pv, int N, const double* scal)
 {
     const float b = (float)scal[S_HQ_BETA];
     const int P = N * N;

@@ -250,5 +250,6 @@ int tc_ctas(spirec_plan p, int knob, int sms, int64_t* P);  // nudft_tc.cu
 
 int vec_blocks(int N);
 constexpr int kVecThreads = 256;
+constexpr int kVecBlocksPerSm = 5;  // resident blocks an SM the vector kernels are built for
 
 }  // namespace spirec

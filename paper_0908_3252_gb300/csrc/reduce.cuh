@@ -6,7 +6,7 @@
 // Each thread sums its few products in FP32 and each warp its 32 threads in
 // FP32 (a 5-level tree); warps, blocks and the grid combine in float-float.
 // The last block of a grid to finish (ticket from an atomic counter, no
-// waiting) sums the per-block pairs in index order, so the result never
+// waiting) sums the per-block pairs in a fixed order, so the result never
 // depends on which block ran first.  Only the final scalars are FP64.
 #pragma once
 
@@ -118,21 +118,50 @@ __device__ __forceinline__ FF warp_sum_parts(const float2* parts, int n)
     return warp_sum_ff(acc);
 }
 
-// Grid totals of K values from n block partials; warp k sums value k.
-// Valid in thread 0 only.  Needs K <= blockDim.x / 32.
+// Grid totals of K values from n block partials, valid in thread 0 only:
+// thread t adds the partials t, t + blockDim.x, ... of each value in index
+// order (the loads of a round, 4 / 2 / 1 a value for K = 1 / 2-3 / more,
+// issued before they are added), then a fixed float-float tree over the
+// lanes of each warp and over the warps.
+// Needs K <= blockDim.x / 32.
 template <int K>
 __device__ __forceinline__ void sum_parts_ff(const float2* parts, int stride, int n, FF (&tot)[K])
 {
-    __shared__ FF ws[K];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ FF ws[K][32];
+    __shared__ FF wt[K];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    constexpr int J = K == 1 ? 4 : (K <= 3 ? 2 : 1);
+    FF acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = FF{0.f, 0.f};
+    for (int base = 0; base < n; base += J * blockDim.x) {
+        float2 v[K][J];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int i = base + threadIdx.x + j * blockDim.x;
+                v[k][j] = i < n ? __ldcg(parts + k * stride + i) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int j = 0; j < J; ++j) acc[k] = ff_add(acc[k], FF{v[k][j].x, v[k][j].y});
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const FF a = warp_sum_ff(acc[k]);
+        if (lane == 0) ws[k][warp] = a;
+    }
+    __syncthreads();
     if (warp < K) {
-        const FF a = warp_sum_parts(parts + warp * stride, n);
-        if (lane == 0) ws[warp] = a;
+        const FF a = warp_sum_ff(lane < nw ? ws[warp][lane] : FF{0.f, 0.f});
+        if (lane == 0) wt[warp] = a;
     }
     __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) tot[k] = ws[k];
+        for (int k = 0; k < K; ++k) tot[k] = wt[k];
 }
 
 }  // namespace spirec
