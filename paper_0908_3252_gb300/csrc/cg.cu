@@ -81,6 +81,7 @@ k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2
     const float tf = (float)t;
     const int P = N * N;
     float v[2] = {0.f, 0.f};
+#pragma unroll 2
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
         cgd::ls_pixel<KIND>(p, N, f, d, reg, tf, v[0], v[1]);
     FF bt[2];

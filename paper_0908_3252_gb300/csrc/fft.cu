@@ -261,7 +261,7 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
     const int cc = warp / S, r = warp - cc * S;
     for (int e = tid; e < 1024; e += kSplitThreads) t2[e] = __ldg(tw + ((S * (e >> 5) * (e & 31)) & (M - 1)));
     for (int x0 = blockIdx.x * C; x0 < M; x0 += gridDim.x * C) {
-#pragma unroll 4
+#pragma unroll 8
         for (int e = tid; e < C * H; e += kSplitThreads) {
             const int y = e / C, c = e - y * C;
             stage[c * LDS + y] = y < n_in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
@@ -272,7 +272,7 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
         float2* area = areas + warp * kSplitArea;
         {
             const float2* col = stage + cc * LDS;
-#pragma unroll 4
+#pragma unroll 8
             for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(col, m, r, tw);
         }
         __syncwarp();
@@ -294,6 +294,7 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
 #pragma unroll
         for (int m2 = 0; m2 < 32; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
         __syncthreads();
+#pragma unroll 4
         for (int e = tid; e < C * n_out; e += kSplitThreads) {
             const int y = e / C, c = e - y * C;
             X[(int64_t)y * M + x0 + c] = combine_output<S>(areas + c * S * kSplitArea + (y & 1023), kSplitArea, y, tw);
@@ -349,7 +350,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
     float acc[3] = {0.f, 0.f, 0.f};
     for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
         const int nr = min(R, rows - r0);
-#pragma unroll 4
+#pragma unroll 8
         for (int e = tid; e < R * H; e += kSplitThreads) {
             const int qq = e / H, m = e - qq * H;
             float2 v = make_float2(0.f, 0.f);
@@ -367,7 +368,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         __syncthreads();
         if (MODE == 1) {
             const Reg reg = c.reg;
-#pragma unroll 2
+#pragma unroll 4
             for (int e = tid; e < nr * N; e += kSplitThreads) {
                 const int qq = e / N, m = e - qq * N;
                 const int n = r0 + qq;
@@ -409,7 +410,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         if (q < nr) {
             float2* area = areas + warp * A;
             const float2* row = stage + q * LDS;
-#pragma unroll 4
+#pragma unroll 8
             for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(row, m, r, tw);
             __syncwarp();
             float2 x[32];
@@ -463,7 +464,7 @@ k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2
     float acc = 0.f;
     for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
         const int nr = min(R, rows - r0);
-#pragma unroll 4
+#pragma unroll 8
         for (int e = tid; e < nr * M; e += kSplitThreads) {
             const int qq = e / M, kk = e - qq * M;
             areas[(qq * S + (kk & (S - 1))) * A + kk / S] = __ldcg(X + (int64_t)(r0 + qq) * M + kk);
@@ -480,6 +481,7 @@ k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2
             for (int m2 = 0; m2 < 32; ++m2) area[lane + 32 * m2] = x[freg::bitrev5(m2)];
         }
         __syncthreads();
+#pragma unroll 4
         for (int e = tid; e < nr * n_out; e += kSplitThreads) {
             const int qq = e / n_out, m = e - qq * n_out;
             const float2 y = combine_output<S>(areas + qq * S * A + (m & 1023), A, m, tw);
