@@ -190,7 +190,11 @@ __device__ __forceinline__ void unreverse32(float2 (&x)[32])
 constexpr int kSplitWarps = 8;
 constexpr int kSplitThreads = 32 * kSplitWarps;
 constexpr int kSplitCtasPerSm = 16 / kSplitWarps;
-constexpr int kSplitArea = 1056;  // 32 x 33
+// Warp area of the column pass: 32 x 33 for the four-step DFT plus 2, so that
+// the S areas of one column start 8 (S = 4) or 4 (S = 2) float2 banks after
+// those of the previous column, and the combine step, whose neighbouring
+// threads read neighbouring columns, hits distinct banks.
+constexpr int kSplitArea = 1058;
 
 // Input m (m < 1024) of the 1024-point DFT that gives the outputs k = r mod S
 // of an M = 1024 S point DFT of x (x zero from M/2 on):
@@ -350,7 +354,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
     float acc[3] = {0.f, 0.f, 0.f};
     for (int r0 = blockIdx.x * R; r0 < rows; r0 += gridDim.x * R) {
         const int nr = min(R, rows - r0);
-#pragma unroll 8
+#pragma unroll 4
         for (int e = tid; e < R * H; e += kSplitThreads) {
             const int qq = e / H, m = e - qq * H;
             float2 v = make_float2(0.f, 0.f);
@@ -368,7 +372,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         __syncthreads();
         if (MODE == 1) {
             const Reg reg = c.reg;
-#pragma unroll 4
+#pragma unroll 2
             for (int e = tid; e < nr * N; e += kSplitThreads) {
                 const int qq = e / N, m = e - qq * N;
                 const int n = r0 + qq;
