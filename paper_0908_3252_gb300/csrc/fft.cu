@@ -414,7 +414,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         if (q < nr) {
             float2* area = areas + warp * A;
             const float2* row = stage + q * LDS;
-#pragma unroll 8
+#pragma unroll 4
             for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(row, m, r, tw);
             __syncwarp();
             float2 x[32];

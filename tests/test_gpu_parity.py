@@ -123,6 +123,25 @@ def test_toeplitz_equals_normal_operator(sp, wname):
     assert rel(got, want) < 1e-5
 
 
+@pytest.mark.parametrize("N,M", [(259, 2048), (601, 4096)])
+def test_toeplitz_split_passes(sp, N, M):
+    """T x at M = 2048 and 4096, where the row and column passes split every
+    transform into 2 or 4 warp-sized 1024-point DFTs, on images whose row
+    count leaves a partial last row group (4 rows a group at M = 2048, 2 at
+    4096), against the oracle's H^H (H x)."""
+    g = synth.rng(N)
+    kx, ky = synth.spiral(N, 2, 300, "variable")
+    w = dict(N=N, kx=kx, ky=ky)
+    x = c64(synth.complex_normal((N, N), g))
+    with _plan(sp, w, 0, M=M) as p:
+        assert p.M == M
+        Tx = empty_c64((N, N))
+        sp.spirec_toeplitz_dev(p.h, to_dev(x), Tx)
+        got = from_dev(Tx)
+    want = O.adjoint(kx, ky, O.forward(kx, ky, x), N)
+    assert rel(got, want) < 1e-5
+
+
 def test_spectrum_is_the_embedded_gram(sp):
     """Chat = Re FFT2(c) / M^2 with c[v mod M][u mod M] = conj G_{u,v}."""
     w = workload_ragged(N=20, I=2, S=150)
@@ -305,9 +324,9 @@ def _large_case(N, I, S, seed):
 # (radix-4 passes, 4-row groups), and M = 2048 and 4096, whose row caches do
 # not fit a block: the solve falls back to the kernel graph, whose row and
 # column passes split each row and column into 2 or 4 warp-sized 1024-point
-# DFTs
+# DFTs (N = 259 and 601 leave a partial last row group of those passes)
 LARGE_CASES = [(260, 1024, 3, 700, 21), (200, 512, 3, 500, 31), (520, 2048, 2, 400, 41),
-               (600, 4096, 2, 300, 43)]
+               (600, 4096, 2, 300, 43), (259, 2048, 3, 300, 49), (601, 4096, 2, 300, 47)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
