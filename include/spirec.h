@@ -195,13 +195,22 @@ int spirec_set_mode(spirec_plan plan, int32_t mode);
  *     linear conjugate-gradient steps on its normal equations
  *     (T + sum_e W_e delta_e^H delta_e) f = D from the iterate (inner_iters T
  *     applies).  J never increases; J_hist[k] is J after k outer steps.
- * inner_iters: 1..1000 (ignored for SPIREC_MIN_PRCG).  Both minimisers work in
- * either mode; the half-quadratic one runs as a captured graph of kernels, not
- * in the persistent loop.  SPIREC_EINVAL for an unknown kind or inner_iters
- * out of range; SPIREC_ENOMEM if its 12 N^2-byte weight buffer cannot be
- * allocated. */
+ *   SPIREC_MIN_NEWTON: the Newton-like method section 5 names, as truncated
+ *     Newton: each outer step takes inner_iters linear conjugate-gradient
+ *     steps from 0 on the Newton system Hess J(f) s = -grad J(f) (the exact
+ *     Hessian: 2 T plus, per edge or pixel, lambda (b I + e z z^T) with
+ *     b = phi'(r) / r, e = (phi''(r) - b) / r^2, z the difference at the
+ *     iterate), then the three majorize-minimize line-search steps of
+ *     SPIREC_MIN_PRCG along s (inner_iters + 0 T applies per outer step: T s
+ *     is accumulated).  J never increases; J_hist[k] is J after k outer steps.
+ * inner_iters: 1..1000 (ignored for SPIREC_MIN_PRCG).  Every minimiser works
+ * in either mode; the half-quadratic and Newton ones run as a captured graph
+ * of kernels, not in the persistent loop.  SPIREC_EINVAL for an unknown kind
+ * or inner_iters out of range; SPIREC_ENOMEM if their 24 N^2-byte weight
+ * buffer cannot be allocated. */
 #define SPIREC_MIN_PRCG 0
 #define SPIREC_MIN_HALF_QUADRATIC 1
+#define SPIREC_MIN_NEWTON 2
 int spirec_set_minimiser(spirec_plan plan, int32_t kind, int32_t inner_iters);
 
 /* ---- operator access (device pointers, enqueued on the plan's stream) ---- */

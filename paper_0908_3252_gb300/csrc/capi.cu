@@ -317,10 +317,12 @@ int run_iterations(spirec_plan p, int iters)
         SPIREC_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t l0 = p->launches;
         int rc = SPIREC_OK;
-        const bool hq = p->minimiser == SPIREC_MIN_HALF_QUADRATIC;
+        const int mn = p->minimiser;
         for (int k = 0; k < iters && rc == SPIREC_OK; ++k)
-            rc = hq ? hq_outer_step(p, k, p->Jdev) : cg_iteration(p, k, p->Jdev);
-        if (hq && rc == SPIREC_OK) rc = launch_hq_objective(p, p->Jdev + iters);  // J of the last iterate
+            rc = mn == SPIREC_MIN_HALF_QUADRATIC ? hq_outer_step(p, k, p->Jdev)
+                 : mn == SPIREC_MIN_NEWTON       ? nt_outer_step(p, k, p->Jdev)
+                                                 : cg_iteration(p, k, p->Jdev);
+        if (mn != SPIREC_MIN_PRCG && rc == SPIREC_OK) rc = launch_hq_objective(p, p->Jdev + iters);  // last J
         cudaError_t e = cudaStreamEndCapture(p->stream, &g);
         p->graph_kernels = p->launches - l0;  // captured, not yet run
         p->launches = l0;
@@ -373,7 +375,7 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
         SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
-    if (p->minimiser == SPIREC_MIN_HALF_QUADRATIC) {
+    if (p->minimiser != SPIREC_MIN_PRCG) {
         // outer steps in a captured graph; the iterate stays in f[0]
         p->result_slot = 0;
         rc = iters == 0 ? launch_hq_objective(p, p->Jdev) : run_iterations(p, iters);
@@ -495,7 +497,7 @@ int tune_contraction(spirec_plan p, int knob, int objective, int sms, int* chose
 int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, double* best_ms)
 {
     *chosen = 0;
-    if (p->mode == SPIREC_MODE_DIRECT || p->minimiser == SPIREC_MIN_HALF_QUADRATIC || !loop_supported(p->M) ||
+    if (p->mode == SPIREC_MODE_DIRECT || p->minimiser != SPIREC_MIN_PRCG || !loop_supported(p->M) ||
         !p->Xd || getenv("SPIREC_NO_LOOP"))
         return SPIREC_OK;
     int rc;
@@ -966,18 +968,18 @@ int spirec_set_minimiser(spirec_plan p, int32_t kind, int32_t inner_iters)
 {
     int rc = check_plan(p);
     if (rc) return rc;
-    if (kind != SPIREC_MIN_PRCG && kind != SPIREC_MIN_HALF_QUADRATIC) {
-        set_error("minimiser must be SPIREC_MIN_PRCG or SPIREC_MIN_HALF_QUADRATIC, not %d", kind);
+    if (kind != SPIREC_MIN_PRCG && kind != SPIREC_MIN_HALF_QUADRATIC && kind != SPIREC_MIN_NEWTON) {
+        set_error("minimiser must be SPIREC_MIN_PRCG, SPIREC_MIN_HALF_QUADRATIC or SPIREC_MIN_NEWTON, not %d", kind);
         return SPIREC_EINVAL;
     }
-    if (kind == SPIREC_MIN_HALF_QUADRATIC && (inner_iters < 1 || inner_iters > 1000)) {
+    if (kind != SPIREC_MIN_PRCG && (inner_iters < 1 || inner_iters > 1000)) {
         set_error("inner_iters must be in [1, 1000], not %d", inner_iters);
         return SPIREC_EINVAL;
     }
-    if (kind == SPIREC_MIN_HALF_QUADRATIC && !p->hqw) {
-        if ((rc = dalloc(p, &p->hqw, (size_t)3 * p->N * p->N)) != SPIREC_OK) return rc;
+    if (kind != SPIREC_MIN_PRCG && !p->hqw) {
+        if ((rc = dalloc(p, &p->hqw, (size_t)6 * p->N * p->N)) != SPIREC_OK) return rc;
     }
-    const int inner = kind == SPIREC_MIN_HALF_QUADRATIC ? inner_iters : 0;
+    const int inner = kind != SPIREC_MIN_PRCG ? inner_iters : 0;
     if ((p->minimiser != kind || p->hq_inner != inner) && p->graph) {  // the captured loop is minimiser-specific
         cudaStreamSynchronize(p->stream);
         cudaGraphExecDestroy(p->graph);

@@ -21,6 +21,11 @@
 // one radix-4 butterfly per thread per stage (plus one radix-2 stage for odd
 // log2 M), values in registers between a read and a write phase.  Any other
 // M = 2^a 3^b 5^c runs the runtime mixed-radix path with a ping-pong buffer.
+// At M = 2048 and 4096, where every transform of the apply has at most M/2
+// nonzero inputs and keeps at most M/2 outputs, the three passes instead
+// split each transform into S = M / 1024 warp-sized 1024-point DFTs, one per
+// output class k = r mod S (k_rows_fwd_split, k_cols_split,
+// k_rows_inv_split).
 #include <stdint.h>
 
 #include "fft_device.cuh"

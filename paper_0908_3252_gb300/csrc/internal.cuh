@@ -162,9 +162,9 @@ struct spirec_plan_s {
     int graph_parity_out;
     int result_slot;  // the last solve left its iterate in f[result_slot]
     int mode;         // SPIREC_MODE_TOEPLITZ or SPIREC_MODE_DIRECT
-    int minimiser;    // SPIREC_MIN_PRCG or SPIREC_MIN_HALF_QUADRATIC
-    int hq_inner;     // linear CG steps per half-quadratic outer step
-    float* hqw;       // 3 x N x N half-quadratic weights (right edge, down edge, pixel)
+    int minimiser;    // SPIREC_MIN_PRCG, SPIREC_MIN_HALF_QUADRATIC or SPIREC_MIN_NEWTON
+    int hq_inner;     // linear CG steps per half-quadratic or Newton outer step
+    float* hqw;       // 6 x N x N weights W, then E (right edge, down edge, pixel each)
     float2* ydir;     // L (+32): H d of the direct mode
 
     // timing
@@ -212,6 +212,9 @@ int launch_normal_direct(spirec_plan p, const float2* x, float2* Tx, bool dot_q2
 // CG steps on the frozen quadratic), iterate in f[0].
 int launch_hq_objective(spirec_plan p, double* Jout);
 int hq_outer_step(spirec_plan p, int k, double* Jdev);
+// Truncated Newton minimiser (halfquad.cu): one outer step k (J(f^k) ->
+// Jdev[k], hq_inner CG steps on the Newton system, the line search, the step).
+int nt_outer_step(spirec_plan p, int k, double* Jdev);
 // The whole loop (first gradient + iters iterations) as one persistent
 // cooperative kernel (cg_loop.cu); power-of-two M in [64, 2048] only, and
 // SPIREC_EUNSUPPORTED (nothing enqueued) when the image does not fit its

@@ -16,6 +16,24 @@ __device__ __forceinline__ float phi_weight(int kind, float alpha, float r2)
     return 2.f;
 }
 
+// e(r) = (phi''(r) - b(r)) / r^2, the coefficient of the rank-one part of
+// the Hessian of phi(|z|) in (Re z, Im z): b(r) I + e(r) z z^T.  Closed forms,
+// finite at r = 0: Huber 0 for r <= alpha and -2 alpha / r^3 beyond;
+// hyperbolic -2 alpha / (alpha^2 + r^2)^(3/2); quadratic 0.
+__device__ __forceinline__ float phi_curv_e(int kind, float alpha, float r2)
+{
+    if (kind == SPIREC_PHI_HUBER) {
+        if (r2 <= alpha * alpha) return 0.f;
+        const float rs = rsqrtf(r2);
+        return -2.f * alpha * rs * rs * rs;
+    }
+    if (kind == SPIREC_PHI_HYPERBOLIC) {
+        const float rs = rsqrtf(fmaf(alpha, alpha, r2));
+        return -2.f * alpha * rs * rs * rs;
+    }
+    return 0.f;
+}
+
 // phi(r); the hyperbolic form uses sqrt(a^2+r^2) - a = r^2 / (sqrt(a^2+r^2) + a).
 __device__ __forceinline__ float phi_value(int kind, float alpha, float r2)
 {

@@ -41,6 +41,7 @@ SPIREC_MODE_DIRECT = 1
 
 SPIREC_MIN_PRCG = 0
 SPIREC_MIN_HALF_QUADRATIC = 1
+SPIREC_MIN_NEWTON = 2
 
 SPIREC_KNOB_GRAM_SPLIT = 0
 SPIREC_KNOB_ADJOINT_SPLIT = 1

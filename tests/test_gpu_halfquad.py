@@ -133,7 +133,7 @@ def test_zero_outer_steps_and_switching_back(sp):
 def test_bad_arguments(sp):
     w = workload_c1()
     with _plan(sp, w, 0) as p:
-        for kind, inner in [(2, 3), (-1, 3), (1, 0), (1, 1001)]:
+        for kind, inner in [(3, 3), (-1, 3), (1, 0), (1, 1001)]:
             with pytest.raises(sp.SpirecError) as e:
                 sp.spirec_set_minimiser(p.h, kind, inner)
             assert e.value.code == sp.SPIREC_EINVAL
