@@ -263,12 +263,13 @@ def run_direct_mode(spirec, prec, w, s_host):
 
 
 def run_half_quadratic(spirec, prec, w, s_host, budget=50, ref_iters=400):
-    """The half-quadratic minimiser (section 5's dual optimisation) against
+    """The two replacements for the conjugate gradient that section 5 names,
+    the half-quadratic (dual) minimiser and the truncated Newton one, against
     PR+ CG at an equal budget of T applies on the metric's 512^2 workload:
-    PR+ CG for `budget` iterations, the half-quadratic one for outer x inner
-    = budget.  Reports each run's final J, its gap to J* (PR+ CG after
-    ref_iters iterations, relative to J(0) - J*) and its time (events on the
-    plan's stream, second of two runs)."""
+    PR+ CG for `budget` iterations, the others for outer x inner = budget.
+    Reports each run's final J, its gap to J* (PR+ CG after ref_iters
+    iterations, relative to J(0) - J*) and its time (events on the plan's
+    stream, second of two runs)."""
     import torch
     N, M, L = w["N"], w["M"], w["kx"].shape[0]
     st = torch.cuda.Stream()
@@ -304,6 +305,9 @@ def run_half_quadratic(spirec, prec, w, s_host, budget=50, ref_iters=400):
     for inner in (2, 5, 10):
         J, ms = run(spirec.SPIREC_MIN_HALF_QUADRATIC, inner, budget // inner)
         out["runs"]["hq_%dx%d" % (budget // inner, inner)] = entry(J, ms)
+    for inner in (5, 10, 25):
+        J, ms = run(spirec.SPIREC_MIN_NEWTON, inner, budget // inner)
+        out["runs"]["newton_%dx%d" % (budget // inner, inner)] = entry(J, ms)
     p.close()
     return out
 
@@ -828,7 +832,7 @@ def run_ours(args):
     if not args.no_direct:
         extra["direct_mode"] = run_direct_mode(spirec, prec, w, s)
     if not args.no_half_quadratic:
-        extra["half_quadratic"] = run_half_quadratic(spirec, prec, w, s)
+        extra["section5_minimisers"] = run_half_quadratic(spirec, prec, w, s)
     if not args.no_graph_path:
         extra["graph_path_2048"] = run_graph_path(spirec, prec, hbm_gbs=(peaks() or {}).get("hbm_gbs"))
     if not args.no_serving:

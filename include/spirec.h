@@ -201,8 +201,9 @@ int spirec_set_mode(spirec_plan plan, int32_t mode);
  *     Hessian: 2 T plus, per edge or pixel, lambda (b I + e z z^T) with
  *     b = phi'(r) / r, e = (phi''(r) - b) / r^2, z the difference at the
  *     iterate), then the three majorize-minimize line-search steps of
- *     SPIREC_MIN_PRCG along s (inner_iters + 0 T applies per outer step: T s
- *     is accumulated).  J never increases; J_hist[k] is J after k outer steps.
+ *     SPIREC_MIN_PRCG along s (inner_iters T applies per outer step: T s is
+ *     accumulated with s, so the line search needs no apply of its own).
+ *     J never increases; J_hist[k] is J after k outer steps.
  * inner_iters: 1..1000 (ignored for SPIREC_MIN_PRCG).  Every minimiser works
  * in either mode; the half-quadratic and Newton ones run as a captured graph
  * of kernels, not in the persistent loop.  SPIREC_EINVAL for an unknown kind
