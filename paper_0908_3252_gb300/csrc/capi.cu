@@ -152,13 +152,17 @@ void free_plan(spirec_plan p)
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
-                    p->kx128, p->ky128};
+                    p->kx128, p->ky128, p->s_in};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     for (int i = 0; i < (int)(sizeof(p->tev) / sizeof(p->tev[0])); ++i)
         if (p->tev_made[i]) cudaEventDestroy(p->tev[i]);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_s_ready) cudaEventDestroy(p->ev_s_ready);
+    if (p->ev_sin_free) cudaEventDestroy(p->ev_sin_free);
+    if (p->ev_traj_in) cudaEventDestroy(p->ev_traj_in);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -234,9 +238,10 @@ int flags_status(int flags)
 }
 
 // Fixed-point trajectory, G and the kernel spectrum.  With check_now the host
-// waits and reports a bad trajectory at once; otherwise (the _dev entry
-// point, which must not block) the device error word is reported at the next
-// host synchronisation of the plan (spirec_solve, spirec_sync).
+// waits for the conversion (not for G) and reports a bad trajectory at once;
+// otherwise (the _dev entry point, which must not block) the device error
+// word is reported at the next host synchronisation of the plan
+// (spirec_solve, spirec_sync), as is a timeout of the contraction either way.
 int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, bool check_now)
 {
     p->have_traj = false;
@@ -247,10 +252,14 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, 
     k_traj_fixed<<<blocks, 256, 0, p->stream>>>(kx_dev, ky_dev, p->L, p->kxq, p->kyq, p->dflag);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
-    int rc0;
-    if ((rc0 = launch_step128(p)) != SPIREC_OK) return rc0;
-    cudaEvent_t e;
     int rc;
+    if (check_now) {
+        int flags = 0;
+        if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+        if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
+    }
+    if ((rc = launch_step128(p)) != SPIREC_OK) return rc;
+    cudaEvent_t e;
     if ((rc = tstart(p, 0, &e)) != SPIREC_OK) return rc;
     if ((rc = launch_gram(p)) != SPIREC_OK) return rc;
     if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
@@ -258,14 +267,6 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, 
     if ((rc = launch_spectrum(p)) != SPIREC_OK) return rc;
     if ((rc = tstop(p, e)) != SPIREC_OK) return rc;
     p->have_traj = true;
-    if (check_now) {
-        int flags = 0;
-        if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
-        if ((rc = flags_status(flags)) != SPIREC_OK) {
-            p->have_traj = false;
-            return rc;
-        }
-    }
     return SPIREC_OK;
 }
 
@@ -607,6 +608,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     } while (0)
     TRYCUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
     TRYCUDA(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+    TRYCUDA(cudaEventCreateWithFlags(&p->ev_traj_in, cudaEventDisableTiming));
     const size_t NN = (size_t)N * N;
     // sample arrays carry 32 elements of padding: the tensor-core kernel reads
     // whole 16-byte multiples of a 32-sample chunk by TMA bulk copy
@@ -861,7 +863,19 @@ int spirec_set_trajectory(spirec_plan p, const double* kx, const double* ky)
     Join j(p);
     SPIREC_CK(cudaMemcpyAsync(p->kstage, kx, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
     SPIREC_CK(cudaMemcpyAsync(p->kstage + p->L, ky, sizeof(double) * p->L, cudaMemcpyHostToDevice, p->stream));
-    return build_trajectory(p, p->kstage, p->kstage + p->L, true);
+    SPIREC_CK(cudaEventRecord(p->ev_traj_in, p->stream));
+    rc = build_trajectory(p, p->kstage, p->kstage + p->L, false);
+    // the device conversion's range test, on the host while the GPU builds G
+    bool bad = false;
+    for (int64_t l = 0; l < p->L; ++l) bad |= !(fabs(kx[l]) <= 0.5) | !(fabs(ky[l]) <= 0.5);
+    SPIREC_CK(cudaEventSynchronize(p->ev_traj_in));  // the caller's arrays are copied
+    if (rc != SPIREC_OK) return rc;
+    if (bad) {
+        p->have_traj = false;
+        set_error("trajectory has a value outside [-0.5, 0.5] or not finite");
+        return SPIREC_EINVAL;
+    }
+    return SPIREC_OK;
 }
 
 int spirec_set_trajectory_dev(spirec_plan p, const double* kx, const double* ky)
@@ -889,9 +903,24 @@ int spirec_set_data(spirec_plan p, const float* s)
         return SPIREC_ESTATE;
     }
     Join j(p);
-    SPIREC_CK(cudaMemcpyAsync(p->s, s, sizeof(float2) * p->L, cudaMemcpyHostToDevice, p->stream));
+    // The caller's buffer is copied on a side stream and the call returns
+    // once that copy is done, not after the trajectory work queued before it
+    // on the plan's stream; the plan's stream then moves it into place.
+    const size_t bytes = sizeof(float2) * p->L;
+    if (!p->s_in) {
+        if ((rc = dalloc(p, &p->s_in, (size_t)p->L + 32)) != SPIREC_OK) return rc;
+        SPIREC_CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        SPIREC_CK(cudaEventCreateWithFlags(&p->ev_s_ready, cudaEventDisableTiming));
+        SPIREC_CK(cudaEventCreateWithFlags(&p->ev_sin_free, cudaEventDisableTiming));
+    }
+    SPIREC_CK(cudaStreamWaitEvent(p->copy_stream, p->ev_sin_free, 0));  // no-op before its first record
+    SPIREC_CK(cudaMemcpyAsync(p->s_in, s, bytes, cudaMemcpyHostToDevice, p->copy_stream));
+    SPIREC_CK(cudaEventRecord(p->ev_s_ready, p->copy_stream));
+    SPIREC_CK(cudaStreamWaitEvent(p->stream, p->ev_s_ready, 0));
+    SPIREC_CK(cudaMemcpyAsync(p->s, p->s_in, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    SPIREC_CK(cudaEventRecord(p->ev_sin_free, p->stream));
     rc = build_data(p);
-    if (rc == SPIREC_OK) SPIREC_CK(cudaStreamSynchronize(p->stream));
+    if (rc == SPIREC_OK) SPIREC_CK(cudaEventSynchronize(p->ev_s_ready));
     return rc;
 }
 

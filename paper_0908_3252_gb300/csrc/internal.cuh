@@ -110,6 +110,14 @@ struct spirec_plan_s {
     cudaStream_t user_stream;
     cudaStream_t stream;  // own, non-blocking
     cudaEvent_t ev_join;
+    // host data upload beside the plan's stream (spirec_set_data): the
+    // caller's s goes to s_in on copy_stream, then the plan's stream moves it
+    // into s; made on first use
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_s_ready;   // s_in holds the caller's data
+    cudaEvent_t ev_sin_free;  // the plan's stream has moved s_in into s
+    cudaEvent_t ev_traj_in;   // a host trajectory is on the device (spirec_set_trajectory)
+    float2* s_in;             // L (+32)
 
     // trajectory, fixed point: k * 2^64 mod 2^64
     int64_t* kxq;
