@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <new>
 #include <vector>
@@ -121,6 +122,26 @@ struct Join {
     }
 };
 
+// Plan buffers come from the device's stream-ordered pool (cudaMallocAsync on
+// the plan's stream, cudaFreeAsync when the plan goes): a plan's creation and
+// destruction then neither synchronise the device nor stall the streams of
+// other plans, which matters to a server that re-plans per request shape.
+// The pool keeps freed memory for reuse instead of returning it to the driver
+// (a release threshold of the whole address range; a property of this
+// process's allocator, set once per device).
+void keep_pool(int dev)
+{
+    static std::atomic<bool> done[64];
+    if (dev < 0 || dev >= 64 || done[dev].load(std::memory_order_acquire)) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev].store(true, std::memory_order_release);
+}
+
 template <typename T>
 int dalloc(spirec_plan p, T** ptr, size_t count)
 {
@@ -135,11 +156,12 @@ int dalloc(spirec_plan p, T** ptr, size_t count)
             return SPIREC_ENOMEM;
         }
     }
-    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    keep_pool(p->device);
+    cudaError_t e = cudaMallocAsync((void**)ptr, bytes, p->stream);
     if (e != cudaSuccess) {
         *ptr = nullptr;
         cudaGetLastError();
-        set_error("cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        set_error("cudaMallocAsync of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
         return SPIREC_ENOMEM;
     }
     p->device_bytes += bytes;
@@ -154,7 +176,10 @@ void free_plan(spirec_plan p)
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
                     p->kx128, p->ky128, p->s_in};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) {
+            if (p->stream) cudaFreeAsync(b, p->stream);
+            else cudaFree(b);
+        }
     if (p->graph) cudaGraphExecDestroy(p->graph);
     for (int i = 0; i < (int)(sizeof(p->tev) / sizeof(p->tev[0])); ++i)
         if (p->tev_made[i]) cudaEventDestroy(p->tev[i]);
@@ -286,8 +311,7 @@ int ensure_J(spirec_plan p, int iters)
 {
     if (p->Jcap >= iters + 1) return SPIREC_OK;
     if (p->Jdev) {
-        cudaStreamSynchronize(p->stream);
-        cudaFree(p->Jdev);
+        cudaFreeAsync(p->Jdev, p->stream);  // after the stream's earlier users
         p->Jdev = nullptr;
     }
     int cap = iters + 1 < 64 ? 64 : iters + 1;
@@ -679,8 +703,17 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
         free(tw);
         TRYCUDA(e);
     }
-    TRY(fft_setup_attributes(M));
-    TRY(tc_setup_attributes());
+    {
+        // kernel attributes (shared-memory limits) are per device context:
+        // set once, not per plan
+        static std::atomic<bool> attrs_set[64];
+        const bool once = p->device >= 0 && p->device < 64;
+        if (!once || !attrs_set[p->device].load(std::memory_order_acquire)) {
+            TRY(fft_setup_attributes(M));
+            TRY(tc_setup_attributes());
+            if (once) attrs_set[p->device].store(true, std::memory_order_release);
+        }
+    }
     if (kx || ky) {
         if (!kx || !ky) {
             free_plan(p);
@@ -908,10 +941,11 @@ int spirec_set_data(spirec_plan p, const float* s)
     // on the plan's stream; the plan's stream then moves it into place.
     const size_t bytes = sizeof(float2) * p->L;
     if (!p->s_in) {
-        if ((rc = dalloc(p, &p->s_in, (size_t)p->L + 32)) != SPIREC_OK) return rc;
         SPIREC_CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
         SPIREC_CK(cudaEventCreateWithFlags(&p->ev_s_ready, cudaEventDisableTiming));
         SPIREC_CK(cudaEventCreateWithFlags(&p->ev_sin_free, cudaEventDisableTiming));
+        if ((rc = dalloc(p, &p->s_in, (size_t)p->L + 32)) != SPIREC_OK) return rc;
+        SPIREC_CK(cudaEventRecord(p->ev_sin_free, p->stream));  // the copy stream follows the allocation
     }
     SPIREC_CK(cudaStreamWaitEvent(p->copy_stream, p->ev_sin_free, 0));  // no-op before its first record
     SPIREC_CK(cudaMemcpyAsync(p->s_in, s, bytes, cudaMemcpyHostToDevice, p->copy_stream));
