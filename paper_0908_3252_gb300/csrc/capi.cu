@@ -171,7 +171,7 @@ int dalloc(spirec_plan p, T** ptr, size_t count)
 void free_plan(spirec_plan p)
 {
     if (!p) return;
-    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->Xd, p->D, p->s, p->fsplit, p->ydir,
+    void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
                     p->kx128, p->ky128, p->s_in};
@@ -523,7 +523,7 @@ int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, dou
 {
     *chosen = 0;
     if (p->mode == SPIREC_MODE_DIRECT || p->minimiser != SPIREC_MIN_PRCG || !loop_supported(p->M) ||
-        !p->Xd || getenv("SPIREC_NO_LOOP"))
+        getenv("SPIREC_NO_LOOP"))
         return SPIREC_OK;
     int rc;
     if ((rc = ensure_J(p, iters)) != SPIREC_OK) return rc;
@@ -648,7 +648,6 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->Chat, (size_t)M * M));
     TRY(dalloc(p, &p->cwork, (size_t)M * M));
     TRY(dalloc(p, &p->X, (size_t)N * M));
-    if (loop_supported(M)) TRY(dalloc(p, &p->Xd, (size_t)N * M));
     if ((p->fsplit_bytes = fsplit_bytes_tc(N, precision)) > 0) TRY(dalloc(p, &p->fsplit, p->fsplit_bytes));
     TRY(dalloc(p, &p->D, NN));
     TRY(dalloc(p, &p->s, (size_t)L + 32));

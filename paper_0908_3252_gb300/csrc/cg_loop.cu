@@ -7,16 +7,17 @@
 // and keeps in shared memory f and d of those rows plus one halo row on each
 // side, and T f, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
 // halo row of g per side pass through global memory (L2):
-//   X   the row FFTs of g, overwritten by the column-filtered rows Y,
-//   Xd  the row FFTs of the current direction d (kept across iterations).
+//   X   the row FFTs of g, overwritten by the column-filtered rows Y.
 //
 // One iteration, five grid synchronisations:
-//   B  columns  Xd = -X + beta Xd (the row FFTs of d = -g + beta d_old, by
-//               linearity of the DFT); column FFT * Chat * IFFT -> Y in X
+//   B  columns  column FFT * Chat * IFFT of X -> Y in X
 //               [synchronisation without a value]
-//   C  rows     row IFFTs of Y -> T d; d = -g + beta d_old on the cached
-//               rows; sums q1 = Re<d, 2(Tf - D)>, q2 = Re<d, T d> and the
-//               penalty terms of h'(0) and of the curvature at t = 0
+//   C  rows     row IFFTs of Y -> T g, and T d = -T g + beta T d_old (-T g on
+//               a restart: T is linear, so the apply of the new direction
+//               d = -g + beta d_old follows from the gradient's alone);
+//               d = -g + beta d_old on the cached rows; sums
+//               q1 = Re<d, 2(Tf - D)>, q2 = Re<d, T d> and the penalty terms
+//               of h'(0) and of the curvature at t = 0
 //               [reduce 4 -> t1]
 //   D, E        majorize-minimize steps of the line search at t1, t2, from
 //               shared memory            [reduce 2 -> t2]  [reduce 2 -> t3]
@@ -69,7 +70,6 @@ struct LoopArgs {
     float2* Tf;        // T x0 in, T f out
     const float2* D;
     float2* X;
-    float2* Xd;
     const float* Chat;
     const float* ChatS;  // M = 1024: Chat in the split order of the column pass
     const float2* tw;
@@ -301,42 +301,33 @@ __device__ __forceinline__ void inv512(float2 (&x)[16], float2* area, const floa
 
 // Columns [x0, x0 + 8) of the M = 1024 Toeplitz pass, two warps per column
 // (warp 2 cc + h: column cc, output parity h).  The block loads the 8
-// columns of X (row FFTs of g) and Xd (of the old direction) as 64-byte row
-// pieces, forms Xd = -X + beta Xd (-X on a restart), stores it, and parks
-// the columns in shared memory.  Warp (cc, h) takes x[n] w1024^(h n) of its
+// columns of X (row FFTs of g) as 64-byte row pieces and parks them in
+// shared memory.  Warp (cc, h) takes x[n] w1024^(h n) of its
 // column (n = lane + 32 j < 512; rows >= n_in are zero), runs fwd512 (the
 // column spectrum at ky = 2 k + h), multiplies by the spectrum, runs inv512,
 // and multiplies by w1024^(-h n); the two warps' results add up to the
 // filtered column, whose rows < n_in go back to X.  chs holds the spectrum in
 // this split order: chs[c * 1024 + h * 512 + k] = Chat[kx(c)][2 k + h].
 // wn[j * 32 + l] = w1024^(l + 32 j).
-__device__ __forceinline__ void cols_split(float2* X, float2* Xd, int n_in, int x0, const float* __restrict__ chs,
-                                           const float2* t16, const float2* wn, float2* fbuf, float beta,
-                                           bool restart)
+__device__ __forceinline__ void cols_split(float2* X, int n_in, int x0, const float* __restrict__ chs,
+                                           const float2* t16, const float2* wn, float2* fbuf)
 {
     constexpr int M = 1024, COLS = 8, LDF = 1090, WA = 544;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cc = warp >> 1, h = warp & 1;
     {
         // 8 columns x 512 rows (rows >= n_in are zero), 8 per thread
-        float2 v[8], o[8];
+        float2 v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int e = tid + i * kLoopThreads;
-            const int y = e >> 3, c = e & 7;
-            const bool in = y < n_in;
-            v[i] = in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
-            o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
+            const int y = e >> 3;
+            v[i] = y < n_in ? __ldcg(X + (int64_t)y * M + x0 + (e & 7)) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int e = tid + i * kLoopThreads;
-            const int y = e >> 3, c = e & 7;
-            if (y < n_in) {
-                v[i] = fftd::new_direction(v[i], o[i], beta, restart);
-                Xd[(int64_t)y * M + x0 + c] = v[i];
-            }
-            fbuf[c * LDF + y] = v[i];
+            fbuf[(e & 7) * LDF + (e >> 3)] = v[i];
         }
     }
     __syncthreads();
@@ -642,7 +633,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
     const int N = R.N;
     if constexpr (G::FOURSTEP) {
         // the split row IFFTs of Y, two warps a row (warp 2 q + h takes the
-        // elements 2 k + h), eight rows at a time: T d = u_0 + w1024^(-m) u_1
+        // elements 2 k + h), eight rows at a time: T g = u_0 + w1024^(-m) u_1
         // on the columns m < N
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int h = warp & 1;
@@ -669,7 +660,10 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 #pragma unroll
                 for (int n2 = 0; n2 < 16; ++n2) {
                     const int m = lane + 32 * n2;
-                    if (m < N) cTd[q * N + m] = freg::add(x[freg::bitrev4(n2)], other[m]);
+                    if (m < N) {
+                        float2& td = cTd[q * N + m];
+                        td = fftd::new_direction(freg::add(x[freg::bitrev4(n2)], other[m]), td, beta, restart);
+                    }
                 }
             }
             __syncthreads();
@@ -694,7 +688,8 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         fftd::fft_pow2<MC, true, RX, true>(fbuf, G::LDR, stw);
         for (int e = threadIdx.x; e < nr * N; e += kLoopThreads) {
             const int q = e / N, m = e - q * N;
-            cTd[(g0 + q) * N + m] = fbuf[q * G::LDR + fftd::sidx<MC>(m)];
+            float2& td = cTd[(g0 + q) * N + m];
+            td = fftd::new_direction(fbuf[q * G::LDR + fftd::sidx<MC>(m)], td, beta, restart);
         }
         __syncthreads();
     }
@@ -843,13 +838,11 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * cpc;
             if constexpr (G::FOURSTEP)
-                cols_split(A.X, A.Xd, N, x0, A.ChatS, stw, stw + 512, fbuf, beta, restart);
+                cols_split(A.X, N, x0, A.ChatS, stw, stw + 512, fbuf);
             else if (wide_cols)
-                fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
-                                                 beta, restart);
+                fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr);
             else
-                fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr, A.Xd,
-                                                beta, restart);
+                fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr);
             __syncthreads();  // the next group refills fbuf
         }
         mark(0);
@@ -1052,7 +1045,7 @@ struct LaunchLoop {
         } else {
             int RB = 0, grid = 0;
             size_t smem = 0;
-            if (!p->Xd || !loop_shape<MC>(p, &RB, &grid, &smem)) {
+            if (!loop_shape<MC>(p, &RB, &grid, &smem)) {
                 cudaGetLastError();
                 set_error("the persistent loop does not fit N=%d, M=%d", p->N, p->M);
                 return SPIREC_EUNSUPPORTED;
@@ -1066,7 +1059,6 @@ struct LaunchLoop {
             A.Tf = p->Tf;
             A.D = p->D;
             A.X = p->X;
-            A.Xd = p->Xd;
             A.Chat = p->Chat;
             if constexpr (Geo<MC>::FOURSTEP) {
                 // the split-order copy, in the spectrum build's scratch (M x M complex)

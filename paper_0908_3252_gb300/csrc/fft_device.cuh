@@ -430,16 +430,12 @@ __device__ __forceinline__ void rows_inv_group(const float2* X, int r0, int nr, 
 // Columns [x0, x0 + nc) of the buffer X (M columns): FFT of the n_in nonzero
 // rows, times Chat[x][ky], IFFT, rows < n_out back into X.  Sequences sit at
 // stride seq_len + 4 (spreads the banks of the transposed loads).
-// MODE 1 (CG, compile-time M only): the column input is the row FFT of the
-// new direction, formed from the row FFTs of g (in X) and of the old
-// direction (in Xd) as -X + beta Xd (-X on a restart) by linearity of the
-// DFT, and written back to Xd before the transform; the twiddle table is in
-// shared memory and Chat is read through L2 only.
+// MODE 1 (the persistent CG loop, compile-time M only): the twiddle table is
+// in shared memory and Chat is read through L2 only.
 template <int MC, int BPT = 1, int MODE = 0>
 __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x0, int nc, int cpc,
                                            const FftPlan& fp, const float2* __restrict__ tw,
-                                           const float* __restrict__ Chat, float2* a, float2* b,
-                                           float2* Xd = nullptr, float beta = 0.f, bool restart = true)
+                                           const float* __restrict__ Chat, float2* a, float2* b)
 {
     static_assert(MODE == 0 || MC > 0, "the CG column mode needs a compile-time size");
     const int M = fp.M;
@@ -450,7 +446,6 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
         // spectrum values are all requested before the first is used
         constexpr int E = 4 * BPT;
         float2 v[E];
-        float2 o[MODE == 1 ? E : 1];
         float h[E];
 #pragma unroll
         for (int i = 0; i < E; ++i) {
@@ -458,8 +453,6 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
             const int y = e / cpc, cc = e - y * cpc;
             const bool in = y < n_in && cc < nc;
             v[i] = in ? __ldcg(X + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
-            if constexpr (MODE == 1)
-                o[i] = in && !restart ? __ldcg(Xd + (int64_t)y * M + x0 + cc) : make_float2(0.f, 0.f);
             const int hc = e / M, hk = e - hc * M;
             h[i] = hc < nc ? (MODE == 1 ? __ldcg(&Chat[(int64_t)(x0 + hc) * M + hk])
                                         : __ldg(&Chat[(int64_t)(x0 + hc) * M + hk]))
@@ -469,12 +462,6 @@ __device__ __forceinline__ void cols_group(float2* X, int n_in, int n_out, int x
         for (int i = 0; i < E; ++i) {
             const int e = threadIdx.x + i * blockDim.x;
             const int y = e / cpc, cc = e - y * cpc;
-            if constexpr (MODE == 1) {
-                if (y < n_in && cc < nc) {
-                    v[i] = new_direction(v[i], o[i], beta, restart);
-                    Xd[(int64_t)y * M + x0 + cc] = v[i];
-                }
-            }
             a[cc * ld + sidx<MC>(y)] = v[i];
         }
         __syncthreads();

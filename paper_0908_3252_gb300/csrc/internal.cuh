@@ -133,7 +133,6 @@ struct spirec_plan_s {
     float* Chat;   // M x M real, transposed: Chat[kx*M + ky]
     float2* cwork; // M x M complex (spectrum build)
     float2* X;     // N x M complex (Toeplitz rows)
-    float2* Xd;    // N x M complex: row FFTs of the CG direction (persistent loop only)
     float2* D;     // N x N
     float2* s;     // L (+32 padding)
     float2* ystage;  // L (+32 padding): a caller's y staged for the tensor-core adjoint

@@ -77,7 +77,7 @@ size_t plan_bytes(int N, int64_t L, int M, int precision)
     b += 2 * (size_t)L * 8;                      // staging
     b += (size_t)N * (2 * N - 1) * 8;            // G
     b += (size_t)M * M * 4 + (size_t)M * M * 8;  // spectrum + work
-    b += (size_t)N * M * 8 * (loop_supported(M) ? 2 : 1);  // rows (and direction rows)
+    b += (size_t)N * M * 8;                      // rows
     b += 2 * ((size_t)L + 32) * 8;               // data + staging
     b += 10 * NN * 8;                            // iterates, directions, gradients, D, scratch
     b += (size_t)M * 8 + (size_t)P_NSLOTS * kMaxParts * 8 + 4096;
