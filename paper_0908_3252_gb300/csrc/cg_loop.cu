@@ -23,7 +23,9 @@
 //               shared memory            [reduce 2 -> t2]  [reduce 2 -> t3]
 //   A  update   f += t3 d, T f += t3 T d, g = 2 (T f - D) + grad R(f), the six
 //               sums of J and beta; row FFTs of g -> X
-//               [reduce 6 -> J, beta]
+//               [synchronisation; the six totals are formed during the next
+//               column pass, which does not need beta, and J and beta at its
+//               closing synchronisation]
 // At M = 1024 every sequence the FFTs see is half zero (N <= 512 inputs of a
 // 1024-point transform), so each 1024-point DFT splits exactly into two
 // 512-point ones, X[2k + h] = DFT512(x w1024^(h n))[k], and one warp per
@@ -126,7 +128,12 @@ struct Geo {
 template <int MC>
 size_t loop_smem(int N, int RB)
 {
-    return ((size_t)Geo<MC>::FBUF + Geo<MC>::TW + (size_t)(2 * (RB + 2) + 4 * RB) * N) * sizeof(float2);
+    const size_t grid = (size_t)((N + RB - 1) / RB);
+    // FFT buffer, twiddles, f and d of RB + 2 rows, T f, D, g, T d of RB rows,
+    // and the deferred update partials (kUpdVals x even (grid + 1), and one
+    // float2 to align them to 16 bytes)
+    return ((size_t)Geo<MC>::FBUF + Geo<MC>::TW + (size_t)(2 * (RB + 2) + 4 * RB) * N +
+            kUpdVals * ((grid + 2) & ~(size_t)1) + 2) * sizeof(float2);
 }
 
 __device__ __forceinline__ uint64_t gtimer()
@@ -167,17 +174,6 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
     }
 }
 
-// The synchronisation alone (no values).
-__device__ __forceinline__ bool grid_sync(unsigned& seq, LoopShared& S, unsigned* counter, unsigned* abort_word,
-                                          int* err)
-{
-    __syncthreads();
-    ++seq;
-    if (threadIdx.x == 0) S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
-    __syncthreads();
-    return S.ok != 0;
-}
-
 // Block partials of K values to slot `slot`, the synchronisation, then the
 // grid totals as FP64 in S.red, readable by every thread on return.  seq
 // counts the synchronisations of the launch (the same in every thread).
@@ -202,6 +198,76 @@ __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int sl
     }
     __syncthreads();
     return true;
+}
+
+// The first half of grid_reduce: the block partials to slot `slot` and the
+// synchronisation; the totals are formed later (deferred_parts_fetch /
+// deferred_parts_sum), off the critical path.
+template <int K>
+__device__ __forceinline__ bool grid_arrive_parts(float (&v)[K], float2* parts, int slot, unsigned& seq,
+                                                  LoopShared& S, unsigned* counter, unsigned* abort_word, int* err)
+{
+    FF bt[K];
+    block_partial<K>(v, bt);
+    ++seq;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
+        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
+    }
+    __syncthreads();
+    return S.ok != 0;
+}
+
+// Copies the K x gridDim.x partials of a past synchronisation into shared
+// memory by asynchronous 16-byte copies through L2 (cp.async.cg: no register
+// and no L1 line, so later rounds never see stale data); the block goes on
+// with other work and waits for them in deferred_parts_sum.
+template <int K>
+__device__ __forceinline__ void deferred_parts_fetch(const float2* parts, int slot, float2* pbuf)
+{
+    const int nch = (gridDim.x + 1) >> 1;  // 16-byte chunks of a value (two partials each)
+    for (int e = threadIdx.x; e < K * nch; e += blockDim.x) {
+        const int k = e / nch, c = e - k * nch;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(pbuf + k * 2 * nch + 2 * c);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                     "l"(parts + (slot + k) * kMaxParts + 2 * c)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Waits for deferred_parts_fetch's copies; warps 1..K sum value k = warp - 1
+// of the block partials in index order (as warp_sum_parts) into S.red.
+// Contains __syncthreads() and a named barrier over warps 1..K+1 (K + 1 <= 15).
+template <int K>
+__device__ __forceinline__ void deferred_parts_sum(const float2* pbuf, LoopShared& S)
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nch = (gridDim.x + 1) >> 1;
+    if (warp >= 1 && warp <= K) {
+        const float2* v = pbuf + (warp - 1) * 2 * nch;
+        FF acc{0.f, 0.f};
+        for (int i = lane; i < (int)gridDim.x; i += 32) acc = ff_add(acc, FF{v[i].x, v[i].y});
+        acc = warp_sum_ff(acc);
+        if (lane == 0) S.red[warp - 1] = ff_to_double(acc);
+    }
+}
+
+// J and beta from the update sums in S.red (one thread): J(f_k), the PR+
+// beta of the next direction (0: restart), J_hist[k] by block 0.
+__device__ __forceinline__ void finish_update(const LoopArgs& A, LoopShared& S, int k)
+{
+    double J, beta_n;
+    cgd::update_finish(S.red, S.ss, S.gg, false, &J, &beta_n);
+    S.gg = S.red[0];
+    S.J = J;
+    S.beta = beta_n;
+    S.beta_f = (float)beta_n;
+    S.restart = beta_n == 0.0;
+    if (blockIdx.x == 0) A.Jdev[k] = J;
 }
 
 // partial slots: consecutive synchronisations use different slots (a fast
@@ -764,6 +830,8 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     float2* cD = cTf + RB * N;
     float2* cg = cD + RB * N;
     float2* cTd = cg + RB * N;
+    float2* pbuf = cTd + RB * N;  // deferred update partials (kUpdVals x even (grid + 1))
+    pbuf += ((uintptr_t)pbuf & 15) ? 1 : 0;  // 16-byte copies
     // column groups: the wide ones when every block still gets one
     const bool wide_cols = G::CBPT2 > G::CBPT && MC / G::CPC2 >= (int)gridDim.x;
     const int cpc = G::FOURSTEP ? G::FS_COLS : wide_cols ? G::CPC2 : G::CPC;
@@ -832,8 +900,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     }
 
     for (int k = 0; k < A.iters; ++k) {
-        const float beta = S.beta_f;
-        const bool restart = S.restart != 0;
+        // the sums of the previous update (k > 0) arrive while the columns run
+        const bool deferred = k > 0;
+        if (deferred) deferred_parts_fetch<kUpdVals>(A.parts, L_A, pbuf);
         // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * cpc;
@@ -846,8 +915,22 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             __syncthreads();  // the next group refills fbuf
         }
         mark(0);
-        if (!grid_sync(seq, S, A.counter, A.abort_word, A.err)) return;
+        // the synchronisation; meanwhile warps 1..6 sum the previous update's
+        // partials and warp 7 forms J and beta from them (the column pass does
+        // not need beta: T d = -T g + beta T d_old is formed in the row pass)
+        if (deferred) deferred_parts_sum<kUpdVals>(pbuf, S);
+        else __syncthreads();
+        ++seq;
+        if (threadIdx.x == 0) S.ok = grid_arrive_wait(A.counter, seq * gridDim.x, A.abort_word, A.err) ? 1 : 0;
+        if (deferred && (threadIdx.x >> 5) >= 1 && (threadIdx.x >> 5) <= kUpdVals + 1) {
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * (kUpdVals + 1)) : "memory");
+            if (threadIdx.x == 32 * (kUpdVals + 1)) finish_update(A, S, k);
+        }
+        __syncthreads();
+        if (!S.ok) return;
         mark(1);
+        const float beta = S.beta_f;
+        const bool restart = S.restart != 0;
         // ---- C: rows, direction, first line-search sums
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -889,25 +972,25 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             else
                 phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
-            if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
-            if (threadIdx.x == 0) {
-                double J, beta_n;
-                cgd::update_finish(S.red, S.ss, S.gg, false, &J, &beta_n);
-                S.gg = S.red[0];
-                S.J = J;
-                S.beta = beta_n;
-                S.beta_f = (float)beta_n;
-                S.restart = beta_n == 0.0;
-                if (blockIdx.x == 0) {
-                    A.Jdev[k + 1] = J;
-                    A.scal[S_Q1] = S.q1;
-                    A.scal[S_Q2] = S.q2;
-                    A.scal[S_T3] = S.t;
-                }
+            if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
+            if (threadIdx.x == 0 && blockIdx.x == 0) {
+                A.scal[S_Q1] = S.q1;
+                A.scal[S_Q2] = S.q2;
+                A.scal[S_T3] = S.t;
             }
-            __syncthreads();
             mark(9);
         }
+    }
+    // ---- J and beta of the last update
+    if (A.iters > 0) {
+        const int warp = threadIdx.x >> 5;
+        if (warp < kUpdVals) {
+            const FF a = warp_sum_parts(A.parts + (L_A + warp) * kMaxParts, gridDim.x);
+            if ((threadIdx.x & 31) == 0) S.red[warp] = ff_to_double(a);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) finish_update(A, S, A.iters);
+        __syncthreads();
     }
     // ---- the iterate and T f back to global memory
     {
