@@ -375,8 +375,9 @@ __device__ __forceinline__ void inv512(float2 (&x)[16], float2* area, const floa
 // filtered column, whose rows < n_in go back to X.  chs holds the spectrum in
 // this split order: chs[c * 1024 + h * 512 + k] = Chat[kx(c)][2 k + h].
 // wn[j * 32 + l] = w1024^(l + 32 j).
+template <typename F>
 __device__ __forceinline__ void cols_split(float2* X, int n_in, int x0, const float* __restrict__ chs,
-                                           const float2* t16, const float2* wn, float2* fbuf)
+                                           const float2* t16, const float2* wn, float2* fbuf, F&& after_staging)
 {
     constexpr int M = 1024, COLS = 8, LDF = 1090, WA = 544;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -397,6 +398,7 @@ __device__ __forceinline__ void cols_split(float2* X, int n_in, int x0, const fl
         }
     }
     __syncthreads();
+    after_staging();  // work that should not compete with the staging loads
     // the spectrum values of this warp (used after the forward FFT)
     float hs[16];
     {
@@ -902,12 +904,17 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     for (int k = 0; k < A.iters; ++k) {
         // the sums of the previous update (k > 0) arrive while the columns run
         const bool deferred = k > 0;
-        if (deferred) deferred_parts_fetch<kUpdVals>(A.parts, L_A, pbuf);
+        bool fetch = deferred;  // issued once the first column group is staged
+        auto fetch_parts = [&] {
+            if (fetch) deferred_parts_fetch<kUpdVals>(A.parts, L_A, pbuf);
+            fetch = false;
+        };
+        if constexpr (!G::FOURSTEP) fetch_parts();
         // ---- B: columns
         for (int gi = blockIdx.x; gi < col_groups; gi += gridDim.x) {
             const int x0 = gi * cpc;
             if constexpr (G::FOURSTEP)
-                cols_split(A.X, N, x0, A.ChatS, stw, stw + 512, fbuf);
+                cols_split(A.X, N, x0, A.ChatS, stw, stw + 512, fbuf, fetch_parts);
             else if (wide_cols)
                 fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr);
             else
@@ -918,6 +925,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         // the synchronisation; meanwhile warps 1..6 sum the previous update's
         // partials and warp 7 forms J and beta from them (the column pass does
         // not need beta: T d = -T g + beta T d_old is formed in the row pass)
+        fetch_parts();  // a block without a column group
         if (deferred) deferred_parts_sum<kUpdVals>(pbuf, S);
         else __syncthreads();
         ++seq;
