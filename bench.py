@@ -41,7 +41,7 @@ ITERS = 50
 # DRAM bytes (read + write) per launch of the dominant kernels on the default
 # workload, from one ncu capture of the current kernels (the commands and
 # figures are in profiles/k_cg_loop_512.md and profiles/k_tc_phase_gemm_512.md).
-NCU_TRAFFIC = {"k_cg_loop": None, "k_tc_phase_gemm_G": 3_195_648, "k_tc_phase_gemm_D": 4_246_272}
+NCU_TRAFFIC = {"k_cg_loop": 10_805_248, "k_tc_phase_gemm_G": 3_234_304, "k_tc_phase_gemm_D": 4_245_760}
 
 
 def workload(seed=3, S=4096):
