@@ -38,7 +38,10 @@
 //
 // After each reduction one warp per value sums the per-block float-float
 // partials (same order in every block) and thread 0 derives the FP64
-// scalars; the other threads read FP32 copies from shared memory.
+// scalars; the other threads read FP32 copies from shared memory.  The
+// update's six sums are the exception: their partials are copied into shared
+// memory during the next column pass and summed, with J and beta formed, at
+// that pass's synchronisation (deferred_parts_fetch, deferred_parts_sum).
 //
 // Every grid synchronisation is a reduction over block partials behind an
 // arrival counter (see grid_reduce).  Its wait is bounded in time: on expiry the block raises an
