@@ -459,10 +459,13 @@ class _NvmlClocks:
 
 def clocks_start(device=0):
     """Starts the clock record of the timed region: the NVML sampler when the
-    library loads, else nvidia-smi at its 200 ms period."""
+    library loads, else nvidia-smi at its 200 ms period.  The raw samples go
+    to clocks_<pid>.csv in the directory named by BENCH_CLOCKS_DIR, when it is
+    set and exists; the JSON line carries their summary either way."""
+    out_dir = os.environ.get("BENCH_CLOCKS_DIR", "")
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else os.devnull, "w")
+        f = open(os.path.join(out_dir, f"clocks_{os.getpid()}.csv") if out_dir and os.path.isdir(out_dir)
+                 else os.devnull, "w")
     except OSError:
         f = open(os.devnull, "w")
     try:
