@@ -78,7 +78,7 @@ size_t plan_bytes(int N, int64_t L, int M, int precision)
     b += (size_t)N * (2 * N - 1) * 8;            // G
     b += (size_t)M * M * 4 + (size_t)M * M * 8;  // spectrum + work
     b += (size_t)N * M * 8;                      // rows
-    b += 2 * ((size_t)L + 32) * 8;               // data + staging
+    b += 3 * ((size_t)L + 32) * 8;               // data, its staging, the host upload buffer
     b += 10 * NN * 8;                            // iterates, directions, gradients, D, scratch
     b += (size_t)M * 8 + (size_t)P_NSLOTS * kMaxParts * 8 + 4096;
     b += fsplit_bytes_tc(N, precision);  // split image of the tensor-core forward
