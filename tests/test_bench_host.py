@@ -61,3 +61,24 @@ def test_nvidia_smi_parse_filters_the_gpu_and_reads_reasons():
 def test_job_throughput_single_rank():
     value, seconds = bench.job_throughput(2.0, 100)
     assert seconds == pytest.approx(2.0) and value == pytest.approx(50.0)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and
+    prints one JSON line with the contract's keys (no GPU needed)."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["higher_is_better"] is True
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
