@@ -111,16 +111,22 @@ int spirec_plan_destroy(spirec_plan plan);
  * Each k is reduced exactly: it is stored as a 64-bit fixed-point fraction of a
  * cycle, so k * index mod 1 is exact before the trig call.
  * SPIREC_EINVAL if any |k| > 0.5 or a value is not finite.  Invalidates D.
- * The host variant waits for the build and reports a bad trajectory at once;
- * the _dev variant does not block and reports it (SPIREC_EINVAL, or
- * SPIREC_ETIMEOUT for a tensor-core pipeline timeout) at the plan's next host
- * synchronisation: spirec_sync or spirec_solve. */
+ * The host variant checks the values on the host while the GPU builds G,
+ * returns once the arrays are copied (the caller may then reuse them) and
+ * reports a bad trajectory at once; the build itself completes in stream
+ * order.  The _dev variant does not block and reports a bad trajectory
+ * (SPIREC_EINVAL) at the plan's next host synchronisation: spirec_sync or
+ * spirec_solve.  Either variant reports a tensor-core pipeline timeout
+ * (SPIREC_ETIMEOUT) there too. */
 int spirec_set_trajectory(spirec_plan plan, const double* kx, const double* ky);
 int spirec_set_trajectory_dev(spirec_plan plan, const double* kx, const double* ky);
 
 /* Load data s (2L floats) and compute, once per data set,
  *   D[n][m] = (1/N) sum_l s_l exp(-i2pi(kx_l m + ky_l n))   (Eq. AnnMatGD)
- * and ||s||^2 in FP64.  SPIREC_ESTATE without a trajectory. */
+ * and ||s||^2 in FP64.  SPIREC_ESTATE without a trajectory.  The host variant
+ * copies s on a side stream and returns once that copy is done (the caller
+ * may then reuse s); D is computed in stream order after the trajectory's
+ * work. */
 int spirec_set_data(spirec_plan plan, const float* s);
 int spirec_set_data_dev(spirec_plan plan, const float* s);
 
