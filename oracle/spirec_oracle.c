@@ -16,7 +16,7 @@
  *            (Eq. ModDirect; the paper calls H the inverse Fourier matrix).
  * Complex arrays are interleaved (re, im) doubles.
  *
- * Readings of the paper taken here (each also listed in the design doc):
+ * Readings of the paper taken here:
  *  - phi acts on the complex modulus: phi(|z|) (section 3.3 states Huber for
  *    real x only).
  *  - the difference sums of Omega_1 have a free boundary: N(N-1) differences

@@ -7,9 +7,10 @@ with the normal operator T = H^H H applied as the Toeplitz convolution of
 Appendix B through zero-padded FFTs (scipy.fft on the host cores), and the
 same minimiser as oracle.solve: PR+ CG with a descent restart and three
 majorize-minimize line-search steps on h(t) = J(f + t d).  G and D come from
-the oracle's direct sums.  The pin in tests/test_oracle_pins.py checks this
-solve against oracle.solve (direct NUDFTs) to FP64 rounding, which checks the
-rewriting itself.
+the oracle's direct sums, or, for full-size problems (problem_fp64), from the
+same sums taken as matrix products (oracle/factored.py).  The pin in
+tests/test_oracle_pins.py checks this solve against oracle.solve (direct
+NUDFTs) to FP64 rounding, which checks the rewriting itself.
 """
 from __future__ import annotations
 
@@ -38,6 +39,15 @@ def toeplitz_apply(C_hat: np.ndarray, x: np.ndarray) -> np.ndarray:
     xp = np.zeros((M, M), np.complex128)
     xp[:N, :N] = x
     return sfft.ifft2(C_hat * sfft.fft2(xp, workers=WORKERS), workers=WORKERS)[:N, :N]
+
+
+def problem_fp64(kx, ky, s, N: int, M: int):
+    """The rewritten problem in FP64 for any size: (C_hat, D, ||s||^2) with
+    G (Eq. AnnMatG) and D (Eq. AnnMatGD) from oracle/factored.py."""
+    from oracle import factored as F
+    s = np.asarray(s, np.complex128)
+    C_hat = kernel_spectrum(F.gram(kx, ky, N), N, M)
+    return C_hat, F.adjoint(kx, ky, s, N), float(np.sum(np.abs(s) ** 2))
 
 
 def _weight(kind: int, alpha: float, r: np.ndarray) -> np.ndarray:
