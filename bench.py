@@ -39,8 +39,9 @@ METRIC = "CG iters/s at 512^2 (mixed-prec vs FP32 plain, <=1e-3 err); p50/p99 la
 UNIT = "iters/s"
 ITERS = 50
 # DRAM bytes (read + write) per launch of the dominant kernels on the default
-# workload, from one ncu capture of the current kernels (the commands and
-# figures are in profiles/k_cg_loop_512.md and profiles/k_tc_phase_gemm_512.md).
+# workload: dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of
+# the current kernels (the persistent CG loop over 50 iterations, and one G and
+# one D contraction), taken with --clock-control none on this workload.
 NCU_TRAFFIC = {"k_cg_loop": 10_805_248, "k_tc_phase_gemm_G": 3_234_304, "k_tc_phase_gemm_D": 4_245_760}
 
 

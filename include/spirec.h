@@ -240,6 +240,29 @@ int spirec_toeplitz_dev(spirec_plan plan, const float* x, float* Tx);
  * Needs set_data and set_reg. */
 int spirec_objective_grad_dev(spirec_plan plan, const float* x, double* J_host, float* g);
 
+/* ---- operator access (host pointers) ----
+ * The input is copied to a plan buffer, the operator runs on the plan's
+ * stream and the result is copied back; each call returns once the result is
+ * in the caller's array and reports device-side errors as spirec_solve does.
+ * The plan's scratch buffers are reused, so these calls do not overlap with
+ * other work of the same plan (a plan is used by one host thread at a time). */
+
+/* y = H x (Eq. ModDirect): x 2N^2 floats, y 2L floats.  SPIREC_ESTATE
+ * without a trajectory. */
+int spirec_forward(spirec_plan plan, const float* x, float* y);
+/* x = H^H y (Eq. AnnMatGD with s = y; Appendix A): y 2L floats, x 2N^2
+ * floats.  SPIREC_ESTATE without a trajectory. */
+int spirec_adjoint(spirec_plan plan, const float* y, float* x);
+/* Tx = H^H H x, the Toeplitz-block-Toeplitz Gram product by the M x M
+ * zero-padded FFT convolution with conj(G) (section 3.4, Appendix B): 2N^2
+ * floats each.  SPIREC_ESTATE without a trajectory. */
+int spirec_gram_apply(spirec_plan plan, const float* x, float* Tx);
+/* J(x) through the rewritten criterion (Eq. NewCritLS plus R, section 3.3)
+ * into *J (may be NULL) and g = grad J(x) = 2 (T x - D) + grad R(x) into g
+ * (2N^2 floats).  SPIREC_ESTATE before set_data and set_reg; SPIREC_ENUMERIC
+ * if J is not finite. */
+int spirec_objective_grad(spirec_plan plan, const float* x, double* J, float* g);
+
 /* T x for callers that cannot allocate device memory: the same three-pass
  * zero-padded FFT as spirec_toeplitz_dev, but with no plan and no allocation
  * of any kind (no cudaMalloc, no cudaFree, no allocating library routine).

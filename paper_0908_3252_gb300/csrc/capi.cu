@@ -172,7 +172,7 @@ void free_plan(spirec_plan p)
 {
     if (!p) return;
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s, p->fsplit, p->ydir,
-                    p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->Tf, p->Td, p->tmp, p->twiddle,
+                    p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->res, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
                     p->kx128, p->ky128, p->s_in};
     for (void* b : bufs)
@@ -393,13 +393,14 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
     if (x0) {
         SPIREC_CK(cudaMemcpyAsync(p->f[0], x0, img,
                                   x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
-        if ((rc = direct ? launch_normal_direct(p, p->f[0], p->Tf, false) : launch_toeplitz(p, p->f[0], p->Tf, -1)) !=
+        if ((rc = direct ? launch_normal_direct(p, p->f[0], p->res, false) : launch_toeplitz(p, p->f[0], p->res, -1)) !=
             SPIREC_OK)
             return rc;
     } else {
         SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
-        SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
     }
+    // the iteration carries res = T f - D (the data term's gradient is 2 res)
+    if ((rc = launch_res_init(p, p->res, x0 != nullptr)) != SPIREC_OK) return rc;
     if (p->minimiser != SPIREC_MIN_PRCG) {
         // outer steps in a captured graph; the iterate stays in f[0]
         p->result_slot = 0;
@@ -417,7 +418,7 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
     if (rc == SPIREC_EUNSUPPORTED) {
         p->result_slot = iters & 1;
         // gradient at x0, J(x0), beta = 0 (the first direction is -g)
-        if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->Tf, nullptr, p->g, 1, p->Jdev)) !=
+        if ((rc = launch_update(p, p->f[0], p->f[0], p->dbuf[1], p->res, nullptr, p->g, 1, p->Jdev)) !=
             SPIREC_OK)
             return rc;
         if ((rc = run_iterations(p, iters)) != SPIREC_OK) return rc;
@@ -540,7 +541,8 @@ int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, dou
             p,
             [&]() -> int {
                 SPIREC_CK(cudaMemsetAsync(p->f[0], 0, img, p->stream));
-                SPIREC_CK(cudaMemsetAsync(p->Tf, 0, img, p->stream));
+                const int rc1 = launch_res_init(p, p->res, false);
+                if (rc1 != SPIREC_OK) return rc1;
                 return launch_cg_loop(p, iters);
             },
             &ms);
@@ -657,7 +659,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->dbuf[0], NN));
     TRY(dalloc(p, &p->dbuf[1], NN));
     TRY(dalloc(p, &p->g, NN));
-    TRY(dalloc(p, &p->Tf, NN));
+    TRY(dalloc(p, &p->res, NN));
     TRY(dalloc(p, &p->Td, NN));
     TRY(dalloc(p, &p->tmp, NN));
     TRY(dalloc(p, &p->twiddle, (size_t)M));
@@ -1215,12 +1217,119 @@ int spirec_objective_grad_dev(spirec_plan p, const float* x, double* J_host, flo
     }
     Join j(p);
     if ((rc = launch_toeplitz(p, (const float2*)x, p->tmp, -1)) != SPIREC_OK) return rc;
+    if ((rc = launch_res_init(p, p->tmp, true)) != SPIREC_OK) return rc;  // T x - D
     if ((rc = launch_update(p, (const float2*)x, (float2*)x, p->dbuf[0], p->tmp, nullptr, (float2*)g, 1,
                             nullptr)) != SPIREC_OK)
         return rc;
     if (J_host) {
         SPIREC_CK(cudaMemcpyAsync(J_host, p->scal + S_J, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
         SPIREC_CK(cudaStreamSynchronize(p->stream));
+    }
+    return SPIREC_OK;
+}
+
+// ---- host-pointer operator calls: the input goes to a plan buffer, the
+// operator runs on the plan's stream, the result comes back; each returns
+// after its copy-out (and reports device-side errors like spirec_solve).
+
+namespace spirec {
+namespace {
+int finish_host_call(spirec_plan p)
+{
+    SPIREC_CK(cudaStreamSynchronize(p->stream));
+    int flags = 0, rc;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    return flags_status(flags);
+}
+}  // namespace
+}  // namespace spirec
+
+int spirec_forward(spirec_plan p, const float* x, float* y)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !y) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("forward needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    SPIREC_CK(cudaMemcpyAsync(p->tmp, x, sizeof(float2) * (size_t)p->N * p->N, cudaMemcpyHostToDevice, p->stream));
+    if ((rc = launch_forward(p, p->tmp, p->ystage)) != SPIREC_OK) return rc;
+    SPIREC_CK(cudaMemcpyAsync(y, p->ystage, sizeof(float2) * (size_t)p->L, cudaMemcpyDeviceToHost, p->stream));
+    return finish_host_call(p);
+}
+
+int spirec_adjoint(spirec_plan p, const float* y, float* x)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !y) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("adjoint needs a trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    // ystage is the plan's padded sample buffer the contractions read
+    SPIREC_CK(cudaMemcpyAsync(p->ystage, y, sizeof(float2) * (size_t)p->L, cudaMemcpyHostToDevice, p->stream));
+    if ((rc = launch_adjoint(p, p->ystage, p->tmp)) != SPIREC_OK) return rc;
+    SPIREC_CK(cudaMemcpyAsync(x, p->tmp, sizeof(float2) * (size_t)p->N * p->N, cudaMemcpyDeviceToHost, p->stream));
+    return finish_host_call(p);
+}
+
+int spirec_gram_apply(spirec_plan p, const float* x, float* Tx)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !Tx) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_traj) {
+        set_error("no trajectory");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    const size_t img = sizeof(float2) * (size_t)p->N * p->N;
+    SPIREC_CK(cudaMemcpyAsync(p->tmp, x, img, cudaMemcpyHostToDevice, p->stream));
+    if ((rc = launch_toeplitz(p, p->tmp, p->Td, -1)) != SPIREC_OK) return rc;
+    SPIREC_CK(cudaMemcpyAsync(Tx, p->Td, img, cudaMemcpyDeviceToHost, p->stream));
+    return finish_host_call(p);
+}
+
+int spirec_objective_grad(spirec_plan p, const float* x, double* J, float* g)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!x || !g) {
+        set_error("null pointer");
+        return SPIREC_EINVAL;
+    }
+    if (!p->have_data || !p->have_reg) {
+        set_error("objective needs data and a penalty");
+        return SPIREC_ESTATE;
+    }
+    Join j(p);
+    const size_t img = sizeof(float2) * (size_t)p->N * p->N;
+    SPIREC_CK(cudaMemcpyAsync(p->Td, x, img, cudaMemcpyHostToDevice, p->stream));
+    if ((rc = launch_toeplitz(p, p->Td, p->tmp, -1)) != SPIREC_OK) return rc;
+    if ((rc = launch_res_init(p, p->tmp, true)) != SPIREC_OK) return rc;  // T x - D
+    if ((rc = launch_update(p, p->Td, p->Td, p->dbuf[0], p->tmp, nullptr, p->g, 1, nullptr)) != SPIREC_OK)
+        return rc;
+    SPIREC_CK(cudaMemcpyAsync(g, p->g, img, cudaMemcpyDeviceToHost, p->stream));
+    double Jv = 0.0;
+    SPIREC_CK(cudaMemcpyAsync(&Jv, p->scal + S_J, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    if ((rc = finish_host_call(p)) != SPIREC_OK) return rc;
+    if (J) *J = Jv;
+    if (!isfinite(Jv)) {
+        set_error("criterion is not finite");
+        return SPIREC_ENUMERIC;
     }
     return SPIREC_OK;
 }

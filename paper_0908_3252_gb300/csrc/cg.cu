@@ -3,15 +3,17 @@
 //
 //   J(f)      = ||s||^2 - 2 Re<f, D> + Re<f, T f> + R(f)
 //   grad J(f) = 2 (T f - D) + grad R(f)       (dJ/dRe f + i dJ/dIm f)
+// The iteration carries res = T f - D, not T f: it starts as T x0 - D and
+// moves by t T d with every step.
 //   R(f)      = lambda1 sum_edges phi1(|f_q - f_p|) + lambda0 sum_p phi0(|f_p|)
 //
 // One iteration k is six kernels, all on the device, no host round trip:
-//   rows_fwd  d = -g + beta d_old; q1 = Re<d, 2 (Tf - D)>; line-search
+//   rows_fwd  d = -g + beta d_old; q1 = Re<d, 2 res>; line-search
 //             sums at t = 0; row FFTs of d                         (fft.cu)
 //   cols      column FFT * Chat * IFFT                             (fft.cu)
 //   rows_inv  row IFFTs -> T d; q2 = Re<d, T d>; t1                (fft.cu)
 //   2 x line-search step j -> t_{j+1} = t_j - h'(t_j) / curvature (here)
-//   update    f += t3 d, T f += t3 T d, g' = grad J(f), J, beta    (here)
+//   update    f += t3 d, res += t3 T d, g' = grad J(f), J, beta    (here)
 // h(t) = J(f + t d) = J_LS(f) + q1 t + q2 t^2 + R(f + t d); each step
 // minimises the half-quadratic majorant of h at t_j:
 //   h'(t)  = q1 + 2 q2 t + sum_e lambda b(|z_e + t w_e|) Re(conj(z_e + t w_e) w_e)
@@ -100,7 +102,7 @@ k_line_search(const float2* f, const float2* d, int N, Reg reg, int step, float2
 // Gradient and step (cgd::update_pixel); the last block forms J and beta.
 template <bool FIRST, int KIND>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const float2* Td,
+k_update(const float2* f_in, float2* f_out, const float2* d, float2* res, const float2* Td,
          const float2* __restrict__ D, float2* g, int N, Reg reg, float2* parts, unsigned* counter,
          double* scal, double* Jout)
 {
@@ -110,7 +112,7 @@ k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const f
 #pragma unroll
     for (int i = 0; i < kUpdVals; ++i) a[i] = 0.f;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-        cgd::update_pixel<FIRST, KIND>(p, N, f_in, f_out, d, Tf, Td, D, g, reg, t, a);
+        cgd::update_pixel<FIRST, KIND>(p, N, f_in, f_out, d, res, Td, D, g, reg, t, a);
     FF bt[kUpdVals];
     block_partial<kUpdVals>(a, bt);
     store_parts<kUpdVals>(bt, parts, kMaxParts);
@@ -134,7 +136,26 @@ k_update(const float2* f_in, float2* f_out, const float2* d, float2* Tf, const f
 
 float2* slot(spirec_plan p, int s) { return reinterpret_cast<float2*>(p->part) + (size_t)s * kMaxParts; }
 
+// res = res - D (res holds T x0) or res = -D (x0 = 0): the residual the
+// iteration starts from.
+__global__ void k_res_init(float2* res, const float2* __restrict__ D, int64_t n, int have_tx)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 dv = D[i];
+        const float2 t = have_tx ? res[i] : make_float2(0.f, 0.f);
+        res[i] = make_float2(t.x - dv.x, t.y - dv.y);
+    }
+}
+
 }  // namespace
+
+int launch_res_init(spirec_plan p, float2* res, bool have_tx)
+{
+    k_res_init<<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(res, p->D, (int64_t)p->N * p->N, have_tx ? 1 : 0);
+    SPIREC_CK(cudaGetLastError());
+    p->launches += 1;
+    return SPIREC_OK;
+}
 
 int launch_data_norm(spirec_plan p)
 {
@@ -155,15 +176,15 @@ void line_search_k(spirec_plan p, const float2* f, const float2* d, int step)
 }
 
 template <int KIND>
-void update_k(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf, const float2* Td,
+void update_k(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* res, const float2* Td,
               float2* g, int first, double* Jout)
 {
     if (first)
         k_update<true, KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+            f_in, f_out, d, res, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
     else
         k_update<false, KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            f_in, f_out, d, Tf, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+            f_in, f_out, d, res, Td, p->D, g, p->N, p->reg, slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
 }
 }  // namespace
 
@@ -180,13 +201,13 @@ int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step
     return SPIREC_OK;
 }
 
-int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf,
+int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* res,
                   const float2* Td, float2* g, int first, double* Jout)
 {
     switch (p->reg.kind) {
-    case SPIREC_PHI_HUBER: update_k<SPIREC_PHI_HUBER>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
-    case SPIREC_PHI_HYPERBOLIC: update_k<SPIREC_PHI_HYPERBOLIC>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
-    default: update_k<SPIREC_PHI_QUADRATIC>(p, f_in, f_out, d, Tf, Td, g, first, Jout); break;
+    case SPIREC_PHI_HUBER: update_k<SPIREC_PHI_HUBER>(p, f_in, f_out, d, res, Td, g, first, Jout); break;
+    case SPIREC_PHI_HYPERBOLIC: update_k<SPIREC_PHI_HYPERBOLIC>(p, f_in, f_out, d, res, Td, g, first, Jout); break;
+    default: update_k<SPIREC_PHI_QUADRATIC>(p, f_in, f_out, d, res, Td, g, first, Jout); break;
     }
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
@@ -250,7 +271,7 @@ int cg_iteration(spirec_plan p, int k, double* Jdev)
     a.d_old = p->dbuf[(k + 1) & 1];
     a.d_new = dk;
     a.f = fin;
-    a.Tf = p->Tf;
+    a.res = p->res;
     a.D = p->D;
     a.reg = p->reg;
     a.parts = slot(p, P_ROWA);
@@ -270,7 +291,7 @@ int cg_iteration(spirec_plan p, int k, double* Jdev)
     }
     for (int j = 1; j <= 2; ++j)
         if ((rc = launch_line_search(p, fin, dk, j)) != SPIREC_OK) return rc;
-    return launch_update(p, fin, fout, dk, p->Tf, p->Td, p->g, 0, Jdev ? Jdev + k + 1 : nullptr);
+    return launch_update(p, fin, fout, dk, p->res, p->Td, p->g, 0, Jdev ? Jdev + k + 1 : nullptr);
 }
 
 }  // namespace spirec

@@ -72,16 +72,16 @@ __device__ __forceinline__ double ls_next(double t, double q1, double q2, double
     return c > 0.0 ? t - h1 / c : t;
 }
 
-// Gradient at a pixel from its values: g = 2 (Tf - D) + grad R(f), and its
-// share rv of R (right and down edges, the pixel).  An edge from p to q with
-// z = f_q - f_p adds +psi(z) at q and -psi(z) at p, psi(z) = b(|z|) z.
-// Masked neighbours carry the centre value (z = 0).
+// Gradient at a pixel from its values: g = 2 res + grad R(f), res = T f - D
+// the data term's residual in the image domain, and its share rv of R (right
+// and down edges, the pixel).  An edge from p to q with z = f_q - f_p adds
+// +psi(z) at q and -psi(z) at p, psi(z) = b(|z|) z.  Masked neighbours carry
+// the centre value (z = 0).
 template <int KIND = -1>
-__device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float2 fdn, float2 fr, float2 tf,
-                                          float2 dv, bool has_u, bool has_l, bool has_d, bool has_r,
-                                          const Reg& reg, float& rv)
+__device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float2 fdn, float2 fr, float2 rs,
+                                          bool has_u, bool has_l, bool has_d, bool has_r, const Reg& reg, float& rv)
 {
-    float2 gp = make_float2(2.f * (tf.x - dv.x), 2.f * (tf.y - dv.y));
+    float2 gp = make_float2(2.f * rs.x, 2.f * rs.y);
     rv = 0.f;
     if (reg.lambda1 != 0.f) {
         const float l1 = reg.lambda1;
@@ -111,12 +111,15 @@ __device__ __forceinline__ float2 grad_at(float2 fc, float2 fu, float2 fl, float
 }
 
 // Gradient and step at pixel p.  Unless FIRST: f_out = f_in + t d,
-// Tf += t Td.  g = 2 (Tf - D) + grad R(f); per-thread sums
-//   a[0] <g,g>, a[1] Re<g, g_old>, a[2] Re<g, d>, a[3] R(f), a[4] Re<f, D>, a[5] Re<f, Tf>.
+// res += t Td (res = T f - D: T is linear and D fixed, so the residual moves
+// by t T d; carrying it, rather than T f, keeps its FP32 rounding relative to
+// the residual instead of to D, of which it is a small fraction near the
+// minimum).  g = 2 res + grad R(f); per-thread sums
+//   a[0] <g,g>, a[1] Re<g, g_old>, a[2] Re<g, d>, a[3] R(f), a[4] Re<f, D>, a[5] Re<f, res>.
 // All loads first (clamped neighbours, masked terms).
 template <bool FIRST, int KIND = -1>
 __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, float2* f_out,
-                                             const float2* d, float2* Tf, const float2* Td,
+                                             const float2* d, float2* res, const float2* Td,
                                              const float2* __restrict__ D, float2* g, const Reg& reg,
                                              float t, float (&a)[kUpdVals])
 {
@@ -126,7 +129,7 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
     const int pd = has_d ? p + N : p, pr = has_r ? p + 1 : p;
     float2 fc = __ldcg(f_in + p), fu = __ldcg(f_in + pu), fl = __ldcg(f_in + pl);
     float2 fdn = __ldcg(f_in + pd), fr = __ldcg(f_in + pr);
-    float2 tf = __ldcg(Tf + p);
+    float2 rs = __ldcg(res + p);
     const float2 dv = __ldg(D + p);
     float2 dc = make_float2(0.f, 0.f), gold = dc;
     if (!FIRST) {
@@ -139,12 +142,12 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
         fl = f2axpy(t, dl, fl);
         fdn = f2axpy(t, ddn, fdn);
         fr = f2axpy(t, dr, fr);
-        tf = f2axpy(t, tdv, tf);
-        Tf[p] = tf;
+        rs = f2axpy(t, tdv, rs);
+        res[p] = rs;
         f_out[p] = fc;
     }
     float rv;
-    const float2 gp = grad_at<KIND>(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+    const float2 gp = grad_at<KIND>(fc, fu, fl, fdn, fr, rs, has_u, has_l, has_d, has_r, reg, rv);
     a[0] += redot(gp, gp);
     if (!FIRST) {
         a[1] += redot(gp, gold);
@@ -152,17 +155,18 @@ __device__ __forceinline__ void update_pixel(int p, int N, const float2* f_in, f
     }
     a[3] += rv;
     a[4] += redot(fc, dv);
-    a[5] += redot(fc, tf);
+    a[5] += redot(fc, rs);
     g[p] = gp;
 }
 
-// Scalars after an update: J = ||s||^2 - 2 Re<f,D> + Re<f,Tf> + R and the
+// Scalars after an update: J = ||s||^2 - 2 Re<f,D> + Re<f,T f> + R
+// = ||s||^2 - Re<f,D> + Re<f,res> + R (T f = res + D) and the
 // Polak-Ribiere beta = max(0, (<g,g> - Re<g,g_old>) / <g_old,g_old>), set to
 // 0 when Re<g, -g + beta d> >= 0 (restart) or on the first gradient.
 __device__ __forceinline__ void update_finish(const double* s, double ss, double gg_old,
                                               bool first, double* J, double* beta)
 {
-    *J = ss - 2.0 * s[4] + s[5] + s[3];
+    *J = ss - s[4] + s[5] + s[3];
     double b = 0.0;
     if (!first) {
         b = gg_old > 0.0 ? (s[0] - s[1]) / gg_old : 0.0;

@@ -5,7 +5,7 @@
 // spills: with the row caches in shared memory little L1 is left for local
 // memory).  Block b owns the image rows [R0, R0 + RB) for the whole solve
 // and keeps in shared memory f and d of those rows plus one halo row on each
-// side, and T f, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
+// side, and T f - D, D, g and T d of its own rows.  Only the Toeplitz row buffers and one
 // halo row of g per side pass through global memory (L2):
 //   X   the row FFTs of g, overwritten by the column-filtered rows Y.
 //
@@ -16,12 +16,12 @@
 //               a restart: T is linear, so the apply of the new direction
 //               d = -g + beta d_old follows from the gradient's alone);
 //               d = -g + beta d_old on the cached rows; sums
-//               q1 = Re<d, 2(Tf - D)>, q2 = Re<d, T d> and the penalty terms
+//               q1 = Re<d, 2 res>, q2 = Re<d, T d> and the penalty terms
 //               of h'(0) and of the curvature at t = 0
 //               [reduce 4 -> t1]
 //   D, E        majorize-minimize steps of the line search at t1, t2, from
 //               shared memory            [reduce 2 -> t2]  [reduce 2 -> t3]
-//   A  update   f += t3 d, T f += t3 T d, g = 2 (T f - D) + grad R(f), the six
+//   A  update   f += t3 d, res += t3 T d, g = 2 res + grad R(f), the six
 //               sums of J and beta; row FFTs of g -> X
 //               [synchronisation; the six totals are formed during the next
 //               column pass, which does not need beta, and J and beta at its
@@ -72,7 +72,7 @@ struct LoopArgs {
     int N, iters, RB;  // RB: rows owned per block
     float2* f0;        // x0 in, the last iterate out
     float2* g;         // gradient rows (halo exchange)
-    float2* Tf;        // T x0 in, T f out
+    float2* res;       // T x0 - D in, T f - D out (the data term's residual)
     const float2* D;
     float2* X;
     const float* Chat;
@@ -132,7 +132,7 @@ template <int MC>
 size_t loop_smem(int N, int RB)
 {
     const size_t grid = (size_t)((N + RB - 1) / RB);
-    // FFT buffer, twiddles, f and d of RB + 2 rows, T f, D, g, T d of RB rows,
+    // FFT buffer, twiddles, f and d of RB + 2 rows, T f - D, D, g, T d of RB rows,
     // and the deferred update partials (kUpdVals x even (grid + 1), and one
     // float2 to align them to 16 bytes)
     return ((size_t)Geo<MC>::FBUF + Geo<MC>::TW + (size_t)(2 * (RB + 2) + 4 * RB) * N +
@@ -478,7 +478,7 @@ __device__ __forceinline__ void rows_fwd_split(const float2* src, int N, int nro
 // six update sums of cgd::update_pixel.
 template <int KIND, bool FIRST>
 __device__ __forceinline__ void grad_rows(const LoopArgs& A, const Rows& R, const float2* cf, const float2* cd,
-                                          const float2* cTf, const float2* cD, float2* cg, float (&a)[kUpdVals])
+                                          const float2* cRes, const float2* cD, float2* cg, float (&a)[kUpdVals])
 {
     const int N = R.N;
     const Reg reg = A.reg;
@@ -489,9 +489,9 @@ __device__ __forceinline__ void grad_rows(const LoopArgs& A, const Rows& R, cons
         const float2 fc = row[m];
         const float2 fu = has_u ? row[m - N] : fc, fdn = has_d ? row[m + N] : fc;
         const float2 fl = has_l ? row[m - 1] : fc, fr = has_r ? row[m + 1] : fc;
-        const float2 tf = cTf[e], dv = cD[e];
+        const float2 rs = cRes[e], dv = cD[e];
         float rv;
-        const float2 gp = cgd::grad_at<KIND>(fc, fu, fl, fdn, fr, tf, dv, has_u, has_l, has_d, has_r, reg, rv);
+        const float2 gp = cgd::grad_at<KIND>(fc, fu, fl, fdn, fr, rs, has_u, has_l, has_d, has_r, reg, rv);
         a[0] += cgd::redot(gp, gp);
         if (!FIRST) {
             a[1] += cgd::redot(gp, cg[e]);
@@ -499,7 +499,7 @@ __device__ __forceinline__ void grad_rows(const LoopArgs& A, const Rows& R, cons
         }
         a[3] += rv;
         a[4] += cgd::redot(fc, dv);
-        a[5] += cgd::redot(fc, tf);
+        a[5] += cgd::redot(fc, rs);
         cg[e] = gp;
         A.g[(int64_t)n * N + m] = gp;
     }
@@ -520,7 +520,7 @@ __device__ __forceinline__ void ls_edge(float lam, float alpha, int kind, float 
 }
 
 // Line-search sums of the own pixels at step t (phi fixed at compile time).
-// T0 (the first step, t = 0): also Re<d, 2(T f - D)> into acc[0] and
+// T0 (the first step, t = 0): also Re<d, 2 (T f - D)> into acc[0] and
 // Re<d, T d> into acc[3], the penalty terms into acc[1], acc[2]; with PRE it
 // stores each edge's |z|^2, Re(conj(z) w), |w|^2 (z of f, w of d) in the
 // planes E (plane k at E + k nown N: right edge 0-2, down edge 3-5, pixel
@@ -528,7 +528,7 @@ __device__ __forceinline__ void ls_edge(float lam, float alpha, int kind, float 
 // instead of f and d.
 template <int KIND, bool T0, bool PRE>
 __device__ __forceinline__ void ls_rows(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
-                                        const float2* cTf, const float2* cD, const float2* cTd, float t,
+                                        const float2* cRes, const float2* cD, const float2* cTd, float t,
                                         float* acc, float* E)
 {
     const int N = R.N, P = R.nown * N;
@@ -554,7 +554,7 @@ __device__ __forceinline__ void ls_rows(const Reg& reg, const Rows& R, const flo
             float* num = T0 ? &acc[1] : &acc[0];
             float* den = T0 ? &acc[2] : &acc[1];
             if constexpr (T0) {
-                acc[0] += 2.f * cgd::redot(dp, cgd::f2sub(cTf[e], cD[e]));
+                acc[0] += 2.f * cgd::redot(dp, cRes[e]);
                 acc[3] += cgd::redot(dp, cTd[e]);
             }
             if constexpr (PRE) {
@@ -598,38 +598,38 @@ __device__ __forceinline__ bool ls_planes_fit(const Reg& reg, int npix, int fbuf
 // The per-pixel loops above for the run-time phi.
 template <bool FIRST>
 __device__ __forceinline__ void grad_rows_any(const LoopArgs& A, const Rows& R, const float2* cf, const float2* cd,
-                                              const float2* cTf, const float2* cD, float2* cg, float (&a)[kUpdVals])
+                                              const float2* cRes, const float2* cD, float2* cg, float (&a)[kUpdVals])
 {
     switch (A.reg.kind) {
-    case SPIREC_PHI_HUBER: grad_rows<SPIREC_PHI_HUBER, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
-    case SPIREC_PHI_HYPERBOLIC: grad_rows<SPIREC_PHI_HYPERBOLIC, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
-    default: grad_rows<SPIREC_PHI_QUADRATIC, FIRST>(A, R, cf, cd, cTf, cD, cg, a); break;
+    case SPIREC_PHI_HUBER: grad_rows<SPIREC_PHI_HUBER, FIRST>(A, R, cf, cd, cRes, cD, cg, a); break;
+    case SPIREC_PHI_HYPERBOLIC: grad_rows<SPIREC_PHI_HYPERBOLIC, FIRST>(A, R, cf, cd, cRes, cD, cg, a); break;
+    default: grad_rows<SPIREC_PHI_QUADRATIC, FIRST>(A, R, cf, cd, cRes, cD, cg, a); break;
     }
 }
 
 template <bool T0, bool PRE>
 __device__ __forceinline__ void ls_rows_k(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
-                                          const float2* cTf, const float2* cD, const float2* cTd, float t, float* acc,
+                                          const float2* cRes, const float2* cD, const float2* cTd, float t, float* acc,
                                           float* E)
 {
     switch (reg.kind) {
-    case SPIREC_PHI_HUBER: ls_rows<SPIREC_PHI_HUBER, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E); break;
+    case SPIREC_PHI_HUBER: ls_rows<SPIREC_PHI_HUBER, T0, PRE>(reg, R, cf, cd, cRes, cD, cTd, t, acc, E); break;
     case SPIREC_PHI_HYPERBOLIC:
-        ls_rows<SPIREC_PHI_HYPERBOLIC, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
+        ls_rows<SPIREC_PHI_HYPERBOLIC, T0, PRE>(reg, R, cf, cd, cRes, cD, cTd, t, acc, E);
         break;
-    default: ls_rows<SPIREC_PHI_QUADRATIC, T0, PRE>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E); break;
+    default: ls_rows<SPIREC_PHI_QUADRATIC, T0, PRE>(reg, R, cf, cd, cRes, cD, cTd, t, acc, E); break;
     }
 }
 
 template <bool T0>
 __device__ __forceinline__ void ls_rows_any(const Reg& reg, const Rows& R, const float2* cf, const float2* cd,
-                                            const float2* cTf, const float2* cD, const float2* cTd, float t,
+                                            const float2* cRes, const float2* cD, const float2* cTd, float t,
                                             float* acc, float* E, bool pre)
 {
     if (pre)
-        ls_rows_k<T0, true>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
+        ls_rows_k<T0, true>(reg, R, cf, cd, cRes, cD, cTd, t, acc, E);
     else
-        ls_rows_k<T0, false>(reg, R, cf, cd, cTf, cD, cTd, t, acc, E);
+        ls_rows_k<T0, false>(reg, R, cf, cd, cRes, cD, cTd, t, acc, E);
 }
 
 // Step (unless FIRST), gradient and the six update sums over the own rows
@@ -638,7 +638,7 @@ __device__ __forceinline__ void ls_rows_any(const Reg& reg, const Rows& R, const
 template <int MC, bool FIRST, int RX>
 __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
                                              float2* cf,
-                                             const float2* cd, float2* cTf, const float2* cD, float2* cg,
+                                             const float2* cd, float2* cRes, const float2* cD, float2* cg,
                                              const float2* cTd, float t, bool do_fft, float (&a)[kUpdVals])
 {
     using G = Geo<MC>;
@@ -648,13 +648,13 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
         float2* fr0 = cf + R.cache(R.hlo);
         const float2* dr0 = cd + R.cache(R.hlo);
         for (int e = threadIdx.x; e < nc; e += kLoopThreads) fr0[e] = cgd::f2axpy(t, dr0[e], fr0[e]);
-        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) cTf[e] = cgd::f2axpy(t, cTd[e], cTf[e]);
+        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) cRes[e] = cgd::f2axpy(t, cTd[e], cRes[e]);
         __syncthreads();
     }
     if constexpr (G::FOURSTEP) {
         // gradient of every own pixel, then the split row FFTs of g, two
         // warps a row, eight rows at a time
-        grad_rows_any<FIRST>(A, R, cf, cd, cTf, cD, cg, a);
+        grad_rows_any<FIRST>(A, R, cf, cd, cRes, cD, cg, a);
         if (do_fft) {
             __syncthreads();  // g of every own row is in cg
             for (int g0 = 0; g0 < R.nown; g0 += 8)
@@ -664,7 +664,7 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
     } else {
         // gradient of every own pixel, then the row FFTs of g, RX * RPC rows
         // at a time
-        grad_rows_any<FIRST>(A, R, cf, cd, cTf, cD, cg, a);
+        grad_rows_any<FIRST>(A, R, cf, cd, cRes, cD, cg, a);
         if (do_fft) {
             __syncthreads();  // g of every own row is in cg
             for (int g0 = 0; g0 < R.nown; g0 += RX * G::RPC) {
@@ -697,7 +697,7 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
 template <int MC, int RX>
 __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
                                            const float2* cf,
-                                           float2* cd, const float2* cTf, const float2* cD, const float2* cg,
+                                           float2* cd, const float2* cRes, const float2* cD, const float2* cg,
                                            float2* cTd, float beta, bool restart, float (&acc)[4])
 {
     using G = Geo<MC>;
@@ -795,7 +795,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         }
     }
     __syncthreads();
-    ls_rows_any<true>(A.reg, R, cf, cd, cTf, cD, cTd, 0.f, acc, reinterpret_cast<float*>(fbuf),
+    ls_rows_any<true>(A.reg, R, cf, cd, cRes, cD, cTd, 0.f, acc, reinterpret_cast<float*>(fbuf),
                       ls_planes_fit(A.reg, R.nown * N, G::FBUF));
 }
 
@@ -831,8 +831,8 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     float2* stw = fbuf + G::FBUF;     // staged twiddles of exp(-2 pi i k / M)
     float2* cf = stw + G::TW;         // rows R0-1 .. R0+RB: f
     float2* cd = cf + (RB + 2) * N;   // the same rows: d
-    float2* cTf = cd + (RB + 2) * N;  // own rows: T f, D, g, T d
-    float2* cD = cTf + RB * N;
+    float2* cRes = cd + (RB + 2) * N;  // own rows: T f - D, D, g, T d
+    float2* cD = cRes + RB * N;
     float2* cg = cD + RB * N;
     float2* cTd = cg + RB * N;
     float2* pbuf = cTd + RB * N;  // deferred update partials (kUpdVals x even (grid + 1))
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         }
     };
 
-    // ---- caches: twiddles, f of the cached rows, T f and D of the own rows
+    // ---- caches: twiddles, f of the cached rows, T f - D and D of the own rows
     {
         if constexpr (G::FOURSTEP) {
             // T16[k2][l] = w512^(l k2) = w1024^(2 l k2); WN[j][l] = w1024^(l + 32 j)
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         for (int e = threadIdx.x; e < nc; e += kLoopThreads) dst[e] = __ldcg(src + e);
         const int64_t o = (int64_t)R.R0 * N;
         for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
-            cTf[e] = __ldcg(A.Tf + o + e);
+            cRes[e] = __ldcg(A.res + o + e);
             cD[e] = __ldg(A.D + o + e);
         }
     }
@@ -886,9 +886,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     {
         float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (rx2)
-            phase_update<MC, true, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+            phase_update<MC, true, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, 0.f, A.iters > 0, a);
         else
-            phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, 0.f, A.iters > 0, a);
+            phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, 0.f, A.iters > 0, a);
         if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
         if (threadIdx.x == 0) {
             double J, beta;
@@ -946,9 +946,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         {
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
             if (rx2)
-                phase_rows<MC, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+                phase_rows<MC, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, beta, restart, acc);
             else
-                phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, beta, restart, acc);
+                phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, beta, restart, acc);
             mark(2);
             if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0) {
@@ -979,9 +979,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         {
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (rx2)
-                phase_update<MC, false, RX2>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+                phase_update<MC, false, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             else
-                phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cTf, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+                phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
             if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
             if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1003,13 +1003,13 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         if (threadIdx.x == 0) finish_update(A, S, A.iters);
         __syncthreads();
     }
-    // ---- the iterate and T f back to global memory
+    // ---- the iterate and T f - D back to global memory
     {
         const int64_t o = (int64_t)R.R0 * N;
         const float2* fo = cf + R.cache(R.R0);
         for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads) {
             A.f0[o + e] = fo[e];
-            A.Tf[o + e] = cTf[e];
+            A.res[o + e] = cRes[e];
         }
     }
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1150,7 +1150,7 @@ struct LaunchLoop {
             A.RB = RB;
             A.f0 = p->f[0];
             A.g = p->g;
-            A.Tf = p->Tf;
+            A.res = p->res;
             A.D = p->D;
             A.X = p->X;
             A.Chat = p->Chat;

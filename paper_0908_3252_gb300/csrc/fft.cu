@@ -28,6 +28,9 @@
 // k_rows_inv_split).
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "fft_device.cuh"
 #include "fft_reg.cuh"
 #include "internal.cuh"
@@ -388,8 +391,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
                 const float2 dr = stage[qq * LDS + (has_r ? m + 1 : m)];
                 const float2 fp_ = __ldcg(c.f + o), fr = __ldcg(c.f + (has_r ? o + 1 : o)), fd = __ldcg(c.f + od);
                 const float2 gd = __ldcg(c.g + od), dold_d = __ldcg(c.d_old + od);
-                const float2 tfv = __ldcg(c.Tf + o), dv = __ldg(c.D + o);
-                acc[0] += 2.f * redot(dn, f2sub(tfv, dv));
+                acc[0] += 2.f * redot(dn, __ldcg(c.res + o));
                 if (reg.lambda1 != 0.f) {
                     {
                         const float2 w = f2sub(dr, dn);
@@ -919,8 +921,11 @@ constexpr size_t kNoAllocBytes = kNoAllocRowsBytes + kNoAllocSpecBytes + kNoAllo
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_base[kNoAllocMaxDevices];  // device address of the array, per device
-bool g_noalloc_ready[kNoAllocMaxDevices];
+// device address of the array per device, published once its set-up is done
+// (release store, acquire load); the mutex makes the first calls of several
+// host threads on one device run the set-up once
+std::atomic<void*> g_noalloc_base[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
 
 // tw[k] = exp(-2 pi i k / M)
 __global__ void k_noalloc_twiddles(float2* tw, int M)
@@ -1004,16 +1009,19 @@ extern "C" int spirec_toeplitz_noalloc(const float* x, const float* spectrum, fl
     }
     // first call on this device: the array's device address and the kernels'
     // shared-memory limits (no allocation; must happen outside stream capture)
-    if (!g_noalloc_ready[dev]) {
-        void* base = nullptr;
-        e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-        int rc = fft_setup_attributes(M);
-        if (rc != SPIREC_OK) return rc;
-        g_noalloc_base[dev] = base;
-        g_noalloc_ready[dev] = true;
+    void* addr = g_noalloc_base[dev].load(std::memory_order_acquire);
+    if (!addr) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        addr = g_noalloc_base[dev].load(std::memory_order_relaxed);
+        if (!addr) {
+            e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+            int rc = fft_setup_attributes(M);
+            if (rc != SPIREC_OK) return rc;
+            g_noalloc_base[dev].store(addr, std::memory_order_release);
+        }
     }
-    unsigned char* base = static_cast<unsigned char*>(g_noalloc_base[dev]);
+    unsigned char* base = static_cast<unsigned char*>(addr);
     float2* rows = reinterpret_cast<float2*>(base);
     float* chat = reinterpret_cast<float*>(base + kNoAllocRowsBytes);
     float2* tw = reinterpret_cast<float2*>(base + kNoAllocRowsBytes + kNoAllocSpecBytes);

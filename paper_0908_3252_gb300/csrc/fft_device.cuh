@@ -272,7 +272,7 @@ __device__ __forceinline__ float2 new_direction(float2 g, float2 dold, float bet
 // Rows [r0, r0 + rpc) (nr of them real).  MODE 0: the rows of `in` (n_in
 // nonzero entries, stride ld_in).  MODE 1 (CG): the rows of the new direction
 // d = -g + beta d_old, written to c.d_new, with the per-thread sums
-//   acc[0] += Re<d, 2 (Tf - D)>                       (q1)
+//   acc[0] += Re<d, 2 res>, res = T f - D             (q1)
 //   acc[1] += sum_e lambda b(|z_e|) Re(conj(z_e) w_e)  (h'(0) penalty part)
 //   acc[2] += sum_e lambda b(|z_e|) |w_e|^2            (curvature at t = 0)
 // over the right/down edges and pixels of these rows.  Then the FFTs and the
@@ -349,8 +349,7 @@ __device__ __forceinline__ void rows_fwd_group(const float2* in, int ld_in, int 
             const float2 dr = a[q * ld + sidx<MC>(has_r ? m + 1 : m)];
             const float2 fp_ = __ldcg(c.f + o), fr = __ldcg(c.f + (has_r ? o + 1 : o)), fd = __ldcg(c.f + od);
             const float2 gd = __ldcg(c.g + od), dold_d = __ldcg(c.d_old + od);
-            const float2 tfv = __ldcg(c.Tf + o), dv = __ldg(c.D + o);
-            acc[0] += 2.f * redot(dn, f2sub(tfv, dv));
+            acc[0] += 2.f * redot(dn, __ldcg(c.res + o));
             if (reg.lambda1 != 0.f) {
                 {
                     const float2 w = f2sub(dr, dn);

@@ -15,13 +15,14 @@
 //           r = D - T f - P f, p = r, rho = <r, r>          k_hq_residual
 //   inner   T p (zero-padded FFT, or H^H H p in direct mode)
 //           q = T p + P p; alpha = rho / Re<p, q>           k_hq_apply
-//           f += alpha p, T f += alpha T p, r -= alpha q;
+//           f += alpha p, res += alpha T p, r -= alpha q;
 //           beta = <r, r> / rho, rho = <r, r>               k_hq_step
 //           p = r + beta p                                  k_hq_dir
 // P x = sum_e W_e delta_e^H delta_e x (an edge p -> q with z = x_q - x_p adds
-// W_e z at q and -W_e z at p).  T f is carried along (T f += alpha T p), so J
-// needs no extra T apply.  alpha = 0 when Re<p, q> <= 0 and beta = 0 when
-// rho = 0, as in the oracle.  Vectors FP32, sums float-float, scalars FP64.
+// W_e z at q and -W_e z at p).  res = T f - D is carried along
+// (res += alpha T p), so J needs no extra T apply, and D - T f = -res.
+// alpha = 0 when Re<p, q> <= 0 and beta = 0 when rho = 0, as in the oracle.
+// Vectors FP32, sums float-float, scalars FP64.
 //
 // The same kernels run the truncated Newton minimiser (the Newton-like method
 // section 5 names): the direction s solves half the Newton system,
@@ -31,15 +32,15 @@
 // delta_e x)) with E_e = lambda_e e(r_e) / 2, z_e = delta_e f: together half
 // the penalty's Hessian b I + e z z^T (penalty.cuh, phi_curv_e).  Then the
 // three majorize-minimize line-search steps of the PR+ CG path along s, and
-// f += t3 s, T f += t3 T s:
+// f += t3 s, res += t3 T s:
 //   outer   W, E from f; J(f)                               k_hq_outer<true>
 //           r = D - T f - P_W f, p = r, s = T s = 0          k_hq_residual<true>
 //   inner   T p; q = T p + P_W p + P_E p; alpha             k_hq_apply<true>
 //           s += alpha p, T s += alpha T p, r -= alpha q     k_hq_step
 //           p = r + beta p                                  k_hq_dir
-//   search  q1 = Re<s, 2 (T f - D)>, q2 = Re<s, T s>, t1     k_nt_ls0
+//   search  q1 = Re<s, 2 res>, q2 = Re<s, T s>, t1           k_nt_ls0
 //           t2, t3 (the PR+ CG line-search kernel)          k_line_search
-//           f += t3 s, T f += t3 T s                        k_nt_update
+//           f += t3 s, res += t3 T s                        k_nt_update
 #include <stdint.h>
 
 #include "cg_device.cuh"
@@ -105,15 +106,16 @@ __device__ __forceinline__ float2 penalty_curv_at(const float2* f, const float2*
     return out;
 }
 
-// Weights at f and J(f) = ||s||^2 - 2 Re<f, D> + Re<f, T f> + R(f); with NT
+// Weights at f and J(f) = ||s||^2 - 2 Re<f, D> + Re<f, T f> + R(f)
+// = ||s||^2 - Re<f, D> + Re<f, res> + R(f); with NT
 // also the rank-one coefficients E = lambda e(r) / 2 of the Newton system.
 template <bool NT>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int N, Reg reg, HqW W, float2* parts,
+k_hq_outer(const float2* f, const float2* res, const float2* __restrict__ D, int N, Reg reg, HqW W, float2* parts,
            unsigned* counter, double* scal, double* Jout)
 {
     const int P = N * N;
-    float v[3] = {0.f, 0.f, 0.f};  // R, Re<f, D>, Re<f, T f>
+    float v[3] = {0.f, 0.f, 0.f};  // R, Re<f, D>, Re<f, res>
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const int n = p / N, m = p - n * N;
         const float2 fc = __ldcg(f + p);
@@ -149,7 +151,7 @@ k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int 
             W.eo[p] = eo;
         }
         v[1] += redot(fc, __ldg(D + p));
-        v[2] += redot(fc, __ldcg(Tf + p));
+        v[2] += redot(fc, __ldcg(res + p));
     }
     FF bt[3];
     block_partial<3>(v, bt);
@@ -159,7 +161,7 @@ k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int 
         sum_parts_ff<3>(parts, kMaxParts, gridDim.x, t);
         if (threadIdx.x == 0) {
             const double R = ff_to_double(t[0]);
-            const double J = scal[S_SS] - 2.0 * ff_to_double(t[1]) + ff_to_double(t[2]) + R;
+            const double J = scal[S_SS] - ff_to_double(t[1]) + ff_to_double(t[2]) + R;
             scal[S_J] = J;
             scal[S_R] = R;
             if (Jout) *Jout = J;
@@ -168,18 +170,18 @@ k_hq_outer(const float2* f, const float2* Tf, const float2* __restrict__ D, int 
     }
 }
 
-// r = D - T f - P f, p = r, rho = <r, r>; with NT also s = T s = 0.
+// r = D - T f - P f = -res - P f, p = r, rho = <r, r>; with NT also s = T s = 0.
 template <bool NT>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_hq_residual(const float2* f, const float2* Tf, const float2* __restrict__ D, HqW W, int N, float2* r,
+k_hq_residual(const float2* f, const float2* res, HqW W, int N, float2* r,
               float2* pv, float2* sv, float2* Ts, float2* parts, unsigned* counter, double* scal)
 {
     const int P = N * N;
     float v[1] = {0.f};
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const float2 pf = penalty_normal_at(f, W, p, N);
-        const float2 tf = __ldcg(Tf + p), dv = __ldg(D + p);
-        const float2 rv = make_float2(dv.x - tf.x - pf.x, dv.y - tf.y - pf.y);
+        const float2 rs = __ldcg(res + p);
+        const float2 rv = make_float2(-rs.x - pf.x, -rs.y - pf.y);
         r[p] = rv;
         pv[p] = rv;
         if (NT) {
@@ -235,10 +237,10 @@ k_hq_apply(const float2* pv, const float2* Tp, HqW W, const float2* f, int N, fl
     }
 }
 
-// f += alpha p, T f += alpha T p, r -= alpha q; beta = <r, r> / rho
+// f += alpha p, res += alpha T p, r -= alpha q; beta = <r, r> / rho
 // (0 when rho = 0), rho = <r, r>.
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_hq_step(float2* f, float2* Tf, float2* r, const float2* pv, const float2* Tp, const float2* q, int N,
+k_hq_step(float2* f, float2* res, float2* r, const float2* pv, const float2* Tp, const float2* q, int N,
           float2* parts, unsigned* counter, double* scal)
 {
     const float a = (float)scal[S_HQ_ALPHA];
@@ -246,7 +248,7 @@ k_hq_step(float2* f, float2* Tf, float2* r, const float2* pv, const float2* Tp, 
     float v[1] = {0.f};
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         f[p] = f2axpy(a, __ldcg(pv + p), __ldcg(f + p));
-        Tf[p] = f2axpy(a, __ldcg(Tp + p), __ldcg(Tf + p));
+        res[p] = f2axpy(a, __ldcg(Tp + p), __ldcg(res + p));
         const float2 rv = f2axpy(-a, __ldcg(q + p), __ldcg(r + p));
         r[p] = rv;
         v[0] += redot(rv, rv);
@@ -275,20 +277,20 @@ __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm) k_hq_dir(const f
         pv[p] = f2axpy(b, __ldcg(pv + p), __ldcg(r + p));
 }
 
-// The first line-search step along the Newton direction s: q1 = Re<s, 2 (T f
-// - D)>, q2 = Re<s, T s> and the penalty terms at t = 0 (KIND: phi fixed at
+// The first line-search step along the Newton direction s: q1 = Re<s, 2 res>
+// (res = T f - D), q2 = Re<s, T s> and the penalty terms at t = 0 (KIND: phi fixed at
 // compile time), then t1 = -(q1 + num0) / (2 q2 + den0) (0 when the
 // curvature is not > 0), the quantities the PR+ CG line-search steps use.
 template <int KIND>
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_nt_ls0(const float2* f, const float2* sv, const float2* Ts, const float2* Tf, const float2* __restrict__ D, int N,
+k_nt_ls0(const float2* f, const float2* sv, const float2* Ts, const float2* res, int N,
          Reg reg, float2* parts, unsigned* counter, double* scal)
 {
     const int P = N * N;
     float v[4] = {0.f, 0.f, 0.f, 0.f};  // q1, q2, num0, den0
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const float2 sp = __ldcg(sv + p);
-        v[0] += 2.f * redot(sp, f2sub(__ldcg(Tf + p), __ldg(D + p)));
+        v[0] += 2.f * redot(sp, __ldcg(res + p));
         v[1] += redot(sp, __ldcg(Ts + p));
         cgd::ls_pixel<KIND>(p, N, f, sv, reg, 0.f, v[2], v[3]);
     }
@@ -311,15 +313,15 @@ k_nt_ls0(const float2* f, const float2* sv, const float2* Ts, const float2* Tf, 
     }
 }
 
-// f += t3 s, T f += t3 T s.
+// f += t3 s, res += t3 T s.
 __global__ void __launch_bounds__(kVecThreads, kVecBlocksPerSm)
-k_nt_update(float2* f, float2* Tf, const float2* sv, const float2* Ts, int N, const double* scal)
+k_nt_update(float2* f, float2* res, const float2* sv, const float2* Ts, int N, const double* scal)
 {
     const float t = (float)scal[S_T3];
     const int P = N * N;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         f[p] = f2axpy(t, __ldcg(sv + p), __ldcg(f + p));
-        Tf[p] = f2axpy(t, __ldcg(Ts + p), __ldcg(Tf + p));
+        res[p] = f2axpy(t, __ldcg(Ts + p), __ldcg(res + p));
     }
 }
 
@@ -334,7 +336,7 @@ HqW weights_of(spirec_plan p)
 template <int KIND>
 void nt_ls0_k(spirec_plan p, const float2* sv, const float2* Ts)
 {
-    k_nt_ls0<KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(p->f[0], sv, Ts, p->Tf, p->D, p->N, p->reg,
+    k_nt_ls0<KIND><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(p->f[0], sv, Ts, p->res, p->N, p->reg,
                                                                     slot(p, P_UPD), p->counters + C_UPD, p->scal);
 }
 
@@ -348,16 +350,16 @@ int launch_hq_objective(spirec_plan p, double* Jout)
     }
     if (p->minimiser == SPIREC_MIN_NEWTON)
         k_hq_outer<true><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            p->f[0], p->Tf, p->D, p->N, p->reg, weights_of(p), slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+            p->f[0], p->res, p->D, p->N, p->reg, weights_of(p), slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
     else
         k_hq_outer<false><<<vec_blocks(p->N), kVecThreads, 0, p->stream>>>(
-            p->f[0], p->Tf, p->D, p->N, p->reg, weights_of(p), slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
+            p->f[0], p->res, p->D, p->N, p->reg, weights_of(p), slot(p, P_UPD), p->counters + C_UPD, p->scal, Jout);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     return SPIREC_OK;
 }
 
-// Outer step k: the iterate is f[0], T f in Tf; r in g, p in dbuf[0], T p in
+// Outer step k: the iterate is f[0], T f - D in res; r in g, p in dbuf[0], T p in
 // Td, q in tmp.  J(f^k) goes to Jdev[k].
 int hq_outer_step(spirec_plan p, int k, double* Jdev)
 {
@@ -366,7 +368,7 @@ int hq_outer_step(spirec_plan p, int k, double* Jdev)
     float2 *f = p->f[0], *pv = p->dbuf[0];
     int rc;
     if ((rc = launch_hq_objective(p, Jdev ? Jdev + k : nullptr)) != SPIREC_OK) return rc;
-    k_hq_residual<false><<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, p->D, W, N, p->g, pv, nullptr, nullptr,
+    k_hq_residual<false><<<blocks, kVecThreads, 0, p->stream>>>(f, p->res, W, N, p->g, pv, nullptr, nullptr,
                                                                 slot(p, P_UPD), p->counters + C_UPD, p->scal);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
@@ -377,7 +379,7 @@ int hq_outer_step(spirec_plan p, int k, double* Jdev)
         k_hq_apply<false><<<blocks, kVecThreads, 0, p->stream>>>(pv, p->Td, W, nullptr, N, p->tmp, slot(p, P_UPD),
                                                                  p->counters + C_UPD, p->scal);
         SPIREC_CK(cudaGetLastError());
-        k_hq_step<<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, p->g, pv, p->Td, p->tmp, N, slot(p, P_UPD),
+        k_hq_step<<<blocks, kVecThreads, 0, p->stream>>>(f, p->res, p->g, pv, p->Td, p->tmp, N, slot(p, P_UPD),
                                                          p->counters + C_UPD, p->scal);
         SPIREC_CK(cudaGetLastError());
         k_hq_dir<<<blocks, kVecThreads, 0, p->stream>>>(p->g, pv, N, p->scal);
@@ -387,7 +389,7 @@ int hq_outer_step(spirec_plan p, int k, double* Jdev)
     return SPIREC_OK;
 }
 
-// Newton outer step k: the iterate is f[0], T f in Tf; r in g, p in dbuf[0],
+// Newton outer step k: the iterate is f[0], T f - D in res; r in g, p in dbuf[0],
 // T p in Td, q in tmp, the direction s in dbuf[1] and T s in f[1].  J(f^k)
 // goes to Jdev[k].
 int nt_outer_step(spirec_plan p, int k, double* Jdev)
@@ -397,7 +399,7 @@ int nt_outer_step(spirec_plan p, int k, double* Jdev)
     float2 *f = p->f[0], *pv = p->dbuf[0], *sv = p->dbuf[1], *Ts = p->f[1];
     int rc;
     if ((rc = launch_hq_objective(p, Jdev ? Jdev + k : nullptr)) != SPIREC_OK) return rc;
-    k_hq_residual<true><<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, p->D, W, N, p->g, pv, sv, Ts,
+    k_hq_residual<true><<<blocks, kVecThreads, 0, p->stream>>>(f, p->res, W, N, p->g, pv, sv, Ts,
                                                                slot(p, P_UPD), p->counters + C_UPD, p->scal);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
@@ -424,7 +426,7 @@ int nt_outer_step(spirec_plan p, int k, double* Jdev)
     p->launches += 1;
     if ((rc = launch_line_search(p, f, sv, 1)) != SPIREC_OK) return rc;
     if ((rc = launch_line_search(p, f, sv, 2)) != SPIREC_OK) return rc;
-    k_nt_update<<<blocks, kVecThreads, 0, p->stream>>>(f, p->Tf, sv, Ts, N, p->scal);
+    k_nt_update<<<blocks, kVecThreads, 0, p->stream>>>(f, p->res, sv, Ts, N, p->scal);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     return SPIREC_OK;

@@ -89,7 +89,7 @@ struct CgPass {
     const float2* d_old;
     float2* d_new;
     const float2* f;
-    const float2* Tf;
+    const float2* res;  // T f - D, the data term's image-domain residual
     const float2* D;
     Reg reg;
     float2* parts;
@@ -139,7 +139,7 @@ struct spirec_plan_s {
     float2* f[2];
     float2* dbuf[2];  // direction of iteration k in dbuf[k & 1]
     float2* g;
-    float2* Tf;
+    float2* res;   // T f - D of the iterate (the data term's gradient is 2 res)
     float2* Td;
     float2* tmp;   // N x N scratch for operator calls
     float2* twiddle;  // M entries, exp(-2 pi i k / M)
@@ -206,8 +206,10 @@ int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, co
 
 // CG pieces (cg.cu).  Iteration k reads f[k & 1] and writes f[(k + 1) & 1].
 int launch_data_norm(spirec_plan p);
-// gradient at f (Tf given): g, J -> Jout, <g,g>; first = no step taken
-int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* Tf,
+// res = Tx - D where res holds T x (have_tx), else res = -D (x = 0)
+int launch_res_init(spirec_plan p, float2* res, bool have_tx);
+// gradient at f (res = T f - D given): g, J -> Jout, <g,g>; first = no step taken
+int launch_update(spirec_plan p, const float2* f_in, float2* f_out, const float2* d, float2* res,
                   const float2* Td, float2* g, int first, double* Jout);
 int launch_line_search(spirec_plan p, const float2* f, const float2* d, int step);
 int cg_iteration(spirec_plan p, int k, double* Jdev);

@@ -989,7 +989,7 @@ int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb,
     int64_t P = 0;
     if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
     unsigned* amax = nullptr;
-    if (w && w != p->s) {
+    if (w && w != p->s && w != p->ystage) {
         // the kernel reads padded, plan-owned sample arrays
         SPIREC_CK(cudaMemcpyAsync(p->ystage, w, sizeof(float2) * p->L, cudaMemcpyDeviceToDevice, p->stream));
         w = p->ystage;

@@ -80,6 +80,10 @@ SIGNATURES = {
     "spirec_data_adjoint_dev": (ctypes.c_int, [_P, _P]),
     "spirec_toeplitz_dev": (ctypes.c_int, [_P, _P, _P]),
     "spirec_objective_grad_dev": (ctypes.c_int, [_P, _P, _P, _P]),
+    "spirec_forward": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_adjoint": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_gram_apply": (ctypes.c_int, [_P, _P, _P]),
+    "spirec_objective_grad": (ctypes.c_int, [_P, _P, _P, _P]),
     "spirec_toeplitz_noalloc": (ctypes.c_int, [_P, _P, _P, _I32, _I32, _P]),
     "spirec_sync": (ctypes.c_int, [_P]),
     "spirec_plan_info": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -308,6 +312,49 @@ def spirec_objective_grad_dev(plan, x, g):
     J = ctypes.c_double(0.0)
     _check(load().spirec_objective_grad_dev(plan, _dev_ptr(x), ctypes.byref(J), _dev_ptr(g)))
     return J.value
+
+
+def _plan_sizes(plan):
+    N, L = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().spirec_plan_info(plan, ctypes.byref(N), ctypes.byref(L), None, None, None))
+    return N.value, L.value
+
+
+def spirec_forward(plan, x):
+    """y = H x through host memory: x (N, N) complex64 -> y (L,) complex64."""
+    N, L = _plan_sizes(plan)
+    x = _c64(x, N * N)
+    y = np.empty(L, np.complex64)
+    _check(load().spirec_forward(plan, _host_ptr(x), _host_ptr(y)))
+    return y
+
+
+def spirec_adjoint(plan, y):
+    """x = H^H y through host memory: y (L,) complex64 -> x (N, N) complex64."""
+    N, L = _plan_sizes(plan)
+    y = _c64(y, L)
+    x = np.empty((N, N), np.complex64)
+    _check(load().spirec_adjoint(plan, _host_ptr(y), _host_ptr(x)))
+    return x
+
+
+def spirec_gram_apply(plan, x):
+    """T x = H^H H x (zero-padded FFT convolution) through host memory."""
+    N, _ = _plan_sizes(plan)
+    x = _c64(x, N * N)
+    Tx = np.empty((N, N), np.complex64)
+    _check(load().spirec_gram_apply(plan, _host_ptr(x), _host_ptr(Tx)))
+    return Tx
+
+
+def spirec_objective_grad(plan, x):
+    """(J, g) at x through host memory."""
+    N, _ = _plan_sizes(plan)
+    x = _c64(x, N * N)
+    g = np.empty((N, N), np.complex64)
+    J = ctypes.c_double()
+    _check(load().spirec_objective_grad(plan, _host_ptr(x), ctypes.byref(J), _host_ptr(g)))
+    return J.value, g
 
 
 def spirec_toeplitz_noalloc(x, spectrum, Tx, N, M, stream=None):

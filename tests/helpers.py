@@ -62,3 +62,37 @@ def from_dev(t):
 def empty_c64(shape):
     import torch
     return torch.zeros(shape, dtype=torch.complex64, device=torch_dev())
+
+
+_SPREAD = {}
+
+
+def fp32_spread(w, x0=None, iters=None, noise=1e-7, seeds=range(8)):
+    """Distances from the FP64 oracle's iterate of the FP32 rounding model
+    (oracle/fp32_model.py) after `iters` iterations of the workload: FP32
+    storage of every vector, and per-evaluation relative perturbations of
+    `noise` (the FP32 path's operators sit about 1e-7 from the oracle's),
+    one run per seed.  Cached per workload."""
+    from oracle import fp32_model as FM
+    from oracle import toeplitz_cpu as TC
+    N = w["N"]
+    iters = w["iters"] if iters is None else iters
+    key = (N, w["kx"].shape[0], float(w["kx"][-1]), float(np.abs(w["s"]).sum()), iters, noise,
+           None if x0 is None else float(np.abs(x0).sum()))
+    if key not in _SPREAD:
+        x0c = np.zeros((N, N)) if x0 is None else c64(x0)
+        C = TC.kernel_spectrum(O.gram(w["kx"], w["ky"], N), N, 2 * N)
+        D = O.adjoint(w["kx"], w["ky"], w["s"], N)
+        ss = float(np.sum(np.abs(w["s"]) ** 2))
+        xo, _, _ = O.solve(w["kx"], w["ky"], w["s"], w["reg"], x0c, iters)
+        _SPREAD[key] = FM.spread(C, D, ss, w["reg"], x0c, iters, xo, noise=noise, seeds=seeds)
+    return _SPREAD[key]
+
+
+def iter_tol(w, prec, x0=None, iters=None):
+    """Tolerance of an iterate after many iterations: the path's target (1e-5
+    FP32, 1e-3 mixed) or 3 x the largest distance the FP32 rounding model
+    shows on the same problem, whichever is larger."""
+    target = 1e-5 if prec == 0 else 1e-3
+    return max(target, 3.0 * max(fp32_spread(w, x0, iters)))
+

@@ -10,22 +10,22 @@ iterations.  Two quantities are differences of much larger terms in the
 rewritten criterion (section 3.4), so the bar is stated against those terms:
   grad J = 2 (T x - D) + grad R   -> ||err|| <= tol * (2||T x|| + 2||D|| + ||grad R||)
   J = ||s||^2 - 2 Re<x,D> + Re<x,T x> + R -> |err| <= tol * (sum of |terms|)
-and the iterate after many nonlinear CG iterations inherits that cancellation
-floor (the PR+ trajectory amplifies it): ITER_TOL = 1e-3 after 30-50
-iterations, derived from the measured growth (1e-7 per evaluation, x10-1000
-over 50 iterations; J itself still agrees to < 1e-6).
+The iterate after 30-50 nonlinear CG iterations is held at the target or at
+3 x the distance the FP32 rounding model of the same minimiser shows from the
+oracle on the same problem, whichever is larger (tests.helpers.iter_tol,
+oracle/fp32_model.py): an FP32 implementation of the method cannot land
+closer than that model on these problems.
 """
 import numpy as np
 import pytest
 
 from oracle import oracle as O
 from paper_0908_3252_gb300 import synth
-from tests.helpers import c64, empty_c64, from_dev, rel, to_dev, workload_c1, workload_ragged
+from tests.helpers import c64, empty_c64, from_dev, iter_tol, rel, to_dev, workload_c1, workload_ragged
 
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1: 1e-3, 2: 1e-3}
-ITER_TOL = 1e-3
 PRECISIONS = [0, 1, 2]
 
 
@@ -200,7 +200,7 @@ def test_solve_c1(sp, prec):
     assert np.all(np.isfinite(J))
     assert np.all(np.diff(J) <= 1e-6 * J[0]), "J must not increase"
     assert rel(J, Jo) < TOL[prec]
-    assert rel(x, xo) < ITER_TOL
+    assert rel(x, xo) < iter_tol(w, prec), (rel(x, xo), iter_tol(w, prec))
     w3 = dict(w, iters=3)
     x3, _, xo3, _ = _solve_both(sp, w3, prec)
     assert rel(x3, xo3) < TOL[prec]
@@ -213,7 +213,7 @@ def test_solve_ragged_with_x0(sp):
     x, J, xo, Jo = _solve_both(sp, w, 0, x0)
     assert np.all(np.diff(J) <= 1e-6 * J[0])
     assert rel(J, Jo) < 1e-5
-    assert rel(x, xo) < ITER_TOL
+    assert rel(x, xo) < iter_tol(w, 0, x0), (rel(x, xo), iter_tol(w, 0, x0))
     x3, _, xo3, _ = _solve_both(sp, dict(w, iters=3), 0, x0)
     assert rel(x3, xo3) < 1e-5
 
@@ -297,7 +297,7 @@ def test_persistent_loop_matches_kernel_graph(sp, monkeypatch):
     for mode in res:
         x, J = res[mode]
         assert rel(J, Jo) < 1e-5, mode
-        assert rel(x, xo) < ITER_TOL, mode
+        assert rel(x, xo) < iter_tol(w, 0), (mode, rel(x, xo))
     assert rel(res["loop"][1], res["graph"][1]) < 1e-5
 
 
@@ -373,8 +373,8 @@ def test_direct_mode_matches_oracle_and_toeplitz_mode(sp, prec):
     x, J = res[sp.SPIREC_MODE_DIRECT]
     assert np.all(np.diff(J) <= 1e-6 * J[0])
     assert rel(J, Jo) < TOL[prec]
-    assert rel(x, xo) < ITER_TOL
-    assert rel(x, res[sp.SPIREC_MODE_TOEPLITZ][0]) < ITER_TOL
+    assert rel(x, xo) < iter_tol(w, prec), rel(x, xo)
+    assert rel(x, res[sp.SPIREC_MODE_TOEPLITZ][0]) < 2 * iter_tol(w, prec)
 
 
 def test_direct_mode_from_x0_and_errors(sp):
