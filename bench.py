@@ -595,54 +595,79 @@ def oracle_sample(w, budget_s=12.0):
                        f"{total:.3e} s per reconstruction")
 
 
-def cpu_toeplitz_sample(w, s_host, budget_s=6.0, sub=2048):
-    """The paper's method on the host cores (oracle/toeplitz_cpu.py: FP64, the
-    rewritten criterion, H^H H by zero-padded FFTs with scipy.fft on all
-    cores, the same minimiser).  The 50 iterations at 512^2 run in full, on
-    G and D of the first `sub` samples (the cost of an iteration does not
-    depend on L); G and D for all L samples are extrapolated from the time of
-    sampled entries of the oracle's direct sums."""
+def cpu_fp64_leg(spirec, w, dev, model_noise=3e-7):
+    """The CPU leg at full size, and every GPU path's error against it.
+
+    The workload's data are simulated by the FP64 forward model (the phantom,
+    trajectory and noise draw of the GPU leg); the paper's method then runs on
+    the host cores in FP64, timed in full: G (Eq. AnnMatG) and D (Eq.
+    AnnMatGD) as matrix products of phase matrices (oracle/factored.py), the
+    kernel spectrum, and the 50 iterations of the rewritten criterion with
+    zero-padded scipy FFTs (oracle/toeplitz_cpu.py).  On the same data each
+    precision's GPU solve is compared with that FP64 solve (iterate relative
+    L2, J history on the scale of ||s||^2, final J); beside them stand two
+    controls: the FP32 rounding model of the minimiser (oracle/fp32_model.py,
+    operator perturbations `model_noise`, the size of the FP32 path's measured
+    operator errors) and the FP64 solve with the trajectory moved by 1e-7
+    (relative, seeded)."""
+    import torch
+    from oracle import factored as F
+    from oracle import fp32_model as FM
     from oracle import oracle as O
     from oracle import toeplitz_cpu as TC
-    O.build()
-    N, M = w["N"], w["M"]
-    kx, ky = w["kx"], w["ky"]
+    from paper_0908_3252_gb300 import synth
+    w2 = workload(seed=3, S=w["kx"].shape[0] // 32)
+    N, M = w2["N"], w2["M"]
+    kx, ky = w2["kx"], w2["ky"]
     L = kx.shape[0]
-    s = np.asarray(s_host, np.complex128)
-    g = np.random.default_rng(0)
-
-    def per_entry(fn, make, total, budget):
-        k = 8
-        while True:
-            args = make(k)
-            t0 = time.perf_counter()
-            fn(*args)
-            dt = time.perf_counter() - t0
-            if dt > budget or k >= total:
-                return dt / k
-            k *= 4
-
-    tg = per_entry(lambda u, v: O.gram_at(kx, ky, N, u, v),
-                   lambda k: (g.integers(0, N, k).astype(np.int32), g.integers(-(N - 1), N, k).astype(np.int32)),
-                   N * (2 * N - 1), budget_s / 4) * N * (2 * N - 1)
-    td = per_entry(lambda n, m: O.adjoint_at(kx, ky, s, N, n, m),
-                   lambda k: (g.integers(0, N, k).astype(np.int32), g.integers(0, N, k).astype(np.int32)),
-                   N * N, budget_s / 4) * N * N
+    s64 = synth.add_noise(F.forward(kx, ky, w2["f_true"]), w2["snr"], w2["g"]).astype(np.complex64)
+    reg = O.Reg(w2["lambda1"], w2["alpha1"], w2["lambda0"], w2["alpha0"], w2["phi"])
+    x0 = np.zeros((N, N))
     t0 = time.perf_counter()
-    Ch = TC.kernel_spectrum(O.gram(kx[:sub], ky[:sub], N), N, M)
-    D = O.adjoint(kx[:sub], ky[:sub], s[:sub], N)
-    t_sub = time.perf_counter() - t0
-    reg = O.Reg(w["lambda1"], w["alpha1"], w["lambda0"], w["alpha0"], w["phi"])
+    G = F.gram(kx, ky, N)
+    t_g = time.perf_counter() - t0
     t0 = time.perf_counter()
-    TC.solve(Ch, D, float(np.sum(np.abs(s[:sub]) ** 2)), reg, np.zeros((N, N)), ITERS)
+    D = F.adjoint(kx, ky, s64, N)
+    t_d = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    C = TC.kernel_spectrum(G, N, M)
+    ss = float(np.sum(np.abs(s64.astype(np.complex128)) ** 2))
+    x64, J64 = TC.solve(C, D, ss, reg, x0, ITERS)
     t_it = time.perf_counter() - t0
-    total = tg + td + t_it
-    return dict(value=ITERS / total, unit=UNIT, cores=TC.WORKERS,
-                kind="the paper's method on the CPU (Toeplitz form, FP64, scipy.fft)",
-                seconds={"G_extrapolated": tg, "D_extrapolated": td, "iterations": t_it,
-                         "G_D_of_the_subset": t_sub},
-                sample=f"{ITERS} iterations at {N}^2 (M = {M}) timed in full on G and D of {sub} of {L} "
-                       f"samples; G and D for all samples extrapolated from sampled entries")
+    total = t_g + t_d + t_it
+    cpu = dict(value=ITERS / total, unit=UNIT, cores=TC.WORKERS,
+               kind="the paper's method on the CPU (rewritten criterion, FP64, scipy.fft; G and D as "
+                    "FP64 matrix products)",
+               seconds={"G": t_g, "D": t_d, "spectrum_and_iterations": t_it},
+               sample=f"the full workload ({N}^2, L = {L}, M = {M}, {ITERS} iterations), timed in full")
+
+    def gap(x):
+        return float(np.linalg.norm(x - x64) / np.linalg.norm(x64))
+
+    err = {"reference": "FP64 rewritten-criterion solve of the same data (G, D by FP64 matrix products)",
+           "data": "the workload's phantom, trajectory and noise draw, simulated by the FP64 forward model"}
+    stream = torch.cuda.Stream(device=dev)
+    names = {"fp32": spirec.SPIREC_FP32, "fp16x3": spirec.SPIREC_MIXED_FP16X3, "bf16x3": spirec.SPIREC_MIXED_BF16X3}
+    for name, prec in names.items():
+        p = spirec.Plan(N, L, M, prec, stream.cuda_stream, kx, ky)
+        spirec.spirec_set_data(p.h, s64)
+        spirec.spirec_set_reg(p.h, w2["lambda1"], w2["alpha1"], w2["lambda0"], w2["alpha0"], w2["phi"])
+        x, J = spirec.spirec_solve(p.h, None, ITERS, N)
+        p.close()
+        x = x.astype(np.complex128)
+        err[name] = {"iterate_rel_l2": gap(x), "J_history_max_over_s2": float(np.max(np.abs(J - J64)) / ss),
+                     "final_J_rel": float(abs(J[-1] - J64[-1]) / J64[-1]),
+                     "error_to_phantom": float(np.linalg.norm(x - w2["f_true"]) / np.linalg.norm(w2["f_true"]))}
+    xd, jd = FM.deviations(C, D, ss, reg, x0, ITERS, x64, J64, noise=model_noise, seeds=[0, 1])
+    err["fp32_rounding_model"] = {"iterate_rel_l2": xd, "J_history_max_over_s2": [v / ss for v in jd],
+                                  "runs": "unperturbed, then seeds 0 and 1", "operator_noise": model_noise}
+    pert = 1e-7 * np.random.default_rng(17).standard_normal(L)
+    kxp, kyp = kx * (1 + pert), ky * (1 - pert)
+    Cp = TC.kernel_spectrum(F.gram(kxp, kyp, N), N, M)
+    xp, _ = TC.solve(Cp, F.adjoint(kxp, kyp, s64, N), ss, reg, x0, ITERS)
+    err["fp64_k_perturbed_1e-7"] = {"iterate_rel_l2": gap(xp)}
+    err["fp64_error_to_phantom"] = float(np.linalg.norm(x64 - w2["f_true"]) / np.linalg.norm(w2["f_true"]))
+    return cpu, err
 
 
 def run_reference(args):
@@ -900,7 +925,7 @@ def run_ours(args):
         from oracle import oracle as O
         O.build()
         cpu = oracle_sample(w, budget_s=args.cpu_budget)
-        extra["cpu_baseline_toeplitz"] = cpu_toeplitz_sample(w, s)
+        extra["cpu_baseline_toeplitz"], extra["err_vs_fp64"] = cpu_fp64_leg(spirec, w, dev)
 
     dtype = {spirec.SPIREC_FP32: "f32", spirec.SPIREC_MIXED_FP16X3: "fp16x3+f32",
              spirec.SPIREC_MIXED_BF16X3: "bf16x3+f32"}[prec]

@@ -22,9 +22,10 @@ FP32 FFTs, stencils and contractions.
 
 With fp32=False and noise=0 nothing is rounded and the model is the FP64
 minimiser (pinned to oracle.solve in tests/test_oracle_fp32_model_pins.py).
-`spread` runs several perturbation seeds and returns each run's relative L2
-distance to a reference iterate: the spread an FP32 implementation of the
-method can show on that problem after that many iterations.
+`deviations` (and `spread`) run several perturbation seeds and return each
+run's relative L2 distance to a reference iterate (and the largest difference
+of the J histories): the spread an FP32 implementation of the method can show
+on that problem after that many iterations.
 """
 from __future__ import annotations
 
@@ -92,12 +93,22 @@ def solve(C_hat, D, ss, reg: O.Reg, x0, iters, fp32=True, noise=0.0, seed=None):
     return f, np.array(Js)
 
 
+def deviations(C_hat, D, ss, reg: O.Reg, x0, iters, x_ref, J_ref=None, noise=1e-7, seeds=range(8)):
+    """The FP32 model after `iters` iterations against a reference run: per
+    run (the unperturbed one first, then one per seed) the relative L2
+    distance of the iterate to x_ref and, with J_ref, the largest absolute
+    difference of the J histories.  Returns (x_distances, J_differences)."""
+    nref = max(np.linalg.norm(x_ref), 1e-300)
+    xd, jd = [], []
+    for sd in [None] + list(seeds):
+        x, J = solve(C_hat, D, ss, reg, x0, iters, fp32=True, noise=0.0 if sd is None else noise, seed=sd)
+        xd.append(float(np.linalg.norm(x - x_ref) / nref))
+        if J_ref is not None:
+            jd.append(float(np.max(np.abs(J - np.asarray(J_ref)))))
+    return xd, jd
+
+
 def spread(C_hat, D, ss, reg: O.Reg, x0, iters, x_ref, noise=1e-7, seeds=range(8)):
     """Relative L2 distance to x_ref of the FP32 model after `iters`
     iterations: the unperturbed run first, then one run per seed."""
-    nref = max(np.linalg.norm(x_ref), 1e-300)
-    out = []
-    for sd in [None] + list(seeds):
-        x, _ = solve(C_hat, D, ss, reg, x0, iters, fp32=True, noise=0.0 if sd is None else noise, seed=sd)
-        out.append(float(np.linalg.norm(x - x_ref) / nref))
-    return out
+    return deviations(C_hat, D, ss, reg, x0, iters, x_ref, None, noise, seeds)[0]

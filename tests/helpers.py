@@ -67,12 +67,17 @@ def empty_c64(shape):
 _SPREAD = {}
 
 
-def fp32_spread(w, x0=None, iters=None, noise=1e-7, seeds=range(8)):
+# relative error of the FP32 path's operators against the oracle, measured on
+# the 32^2 workload: G 2.8e-7, D 1.8e-7, T 2.7e-7
+OPERATOR_NOISE = 3e-7
+
+
+def fp32_spread(w, x0=None, iters=None, noise=OPERATOR_NOISE, seeds=range(8)):
     """Distances from the FP64 oracle's iterate of the FP32 rounding model
     (oracle/fp32_model.py) after `iters` iterations of the workload: FP32
-    storage of every vector, and per-evaluation relative perturbations of
-    `noise` (the FP32 path's operators sit about 1e-7 from the oracle's),
-    one run per seed.  Cached per workload."""
+    storage of every vector, and relative perturbations of `noise` of the
+    kernel spectrum, D, every T apply and every gradient (the size of the
+    FP32 path's operator errors), one run per seed.  Cached per workload."""
     from oracle import fp32_model as FM
     from oracle import toeplitz_cpu as TC
     N = w["N"]
