@@ -331,11 +331,22 @@ typedef struct spirec_server_s* spirec_server;
  * with its own stream and resident plan (reused while requests keep the same
  * N and L).  A queued request is admitted, first come first served, when a
  * slot is idle and its device footprint fits hbm_budget_bytes next to the
- * plans already resident; admitted requests run concurrently and their
- * kernels overlap.  Each result equals the result of the same request run
+ * plans already resident (idle workers release their plans when the head
+ * request needs the room); admitted requests run concurrently and their
+ * kernels overlap.  Solves on the persistent CG loop start only while the
+ * loops already running leave room for all of their blocks on the device
+ * (a cooperative launch needs every block resident at once); otherwise they
+ * wait for a running loop to end.  Each result equals the result of the same request run
  * alone (launch shapes and summation orders depend only on its own sizes).
  * precision: spirec_precision of every plan. */
 int spirec_server_create(spirec_server* out, size_t hbm_budget_bytes, int32_t max_slots, int32_t precision);
+/* The device footprint the request loop reserves for a request of this shape
+ * (its admission estimate: every buffer of the plan it creates, the host
+ * upload buffer included) and, in *M (may be NULL), the grid side it plans
+ * the request with.  Host-only.  The request loop is serving infrastructure;
+ * no passage of the paper defines it.  SPIREC_EINVAL for N outside
+ * [2, 2048], L < 1 or an unknown precision. */
+int spirec_server_plan_bytes(int32_t N, int64_t L, int32_t precision, size_t* bytes, int32_t* M);
 /* Queue a request; *ticket identifies it.  SPIREC_EBUSY if the request alone
  * exceeds the budget, SPIREC_EINVAL for bad fields (checked again on the GPU
  * path, e.g. |k| > 0.5, and then reported by spirec_server_wait). */
@@ -431,6 +442,37 @@ int spirec_plan_scalars(spirec_plan plan, double* out, int32_t n);
 /* Number of CUDA kernels the plan has launched so far (a CUDA-graph replay
  * counts each of its kernel nodes).  Memory copies and sets are not kernels. */
 int spirec_launch_count(spirec_plan plan, int64_t* count);
+
+/* ---- failure injection, for tests of the error paths ----
+ * No passage of the paper defines these: they let a test make each failure
+ * the library reports happen, without faulting the GPU. */
+
+/* Device allocations of plans succeed n more times, then fail with
+ * SPIREC_ENOMEM (a plan creation that meets one releases what it had
+ * allocated); n < 0, the default, injects nothing.  Process-wide. */
+int spirec_inject_alloc_failure(int64_t n);
+
+/* The kernels named by the bit mask (SPIREC_STALL_LOOP: the persistent CG
+ * loop; SPIREC_STALL_CONTRACTION: the tensor-core contractions of G, D, H^H y
+ * and H f) launched from now on first wait on a condition that nothing
+ * fulfils, so that their bounded wait runs out (see spirec_set_wait_limit_ns)
+ * and they end early as a real timeout would; 0 (the default) ends the
+ * injection.  SPIREC_EINVAL for other bits.  Process-wide. */
+#define SPIREC_STALL_LOOP 1
+#define SPIREC_STALL_CONTRACTION 2
+int spirec_inject_wait_stall(int32_t kernels);
+
+/* Limit, in nanoseconds, of every bounded device wait in the kernels launched
+ * from now on: the persistent CG loop's grid synchronisations and the
+ * tensor-core contractions' pipeline waits.  0 restores the default, 2 s.
+ * A wait that runs out ends its kernel early: the loop's blocks return at
+ * their next synchronisation, a contraction's CTA waits (with a fixed 2 s
+ * bound) for the copies and MMAs it issued, releases its tensor memory and
+ * returns.  The plan then reports SPIREC_ETIMEOUT at its next host
+ * synchronisation (spirec_solve, spirec_sync) until its trajectory is set
+ * again; the results of that work are invalid.  Graphs captured earlier keep
+ * the limit of their capture.  Process-wide. */
+int spirec_set_wait_limit_ns(uint64_t ns);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* spirec_last_error(void);

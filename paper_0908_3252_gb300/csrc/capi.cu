@@ -29,6 +29,17 @@ namespace spirec {
 
 static thread_local char g_err[512] = "";
 
+// 2 s: far beyond any wait of a working launch, short enough that a stuck
+// one gives its SMs back soon
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
+static std::atomic<int> g_stall{0};
+
+bool injected_stall(int kind) { return (g_stall.load(std::memory_order_relaxed) & kind) != 0; }
+
 void set_error(const char* fmt, ...)
 {
     va_list ap;
@@ -142,19 +153,30 @@ void keep_pool(int dev)
     done[dev].store(true, std::memory_order_release);
 }
 
+// Injected allocation failure (spirec_inject_alloc_failure): the number of
+// plan allocations that still succeed, or < 0 when nothing is injected.
+std::atomic<int64_t> g_allocs_left{-1};
+
+// One allocation against the injected budget: false once it is spent.
+bool alloc_allowed()
+{
+    int64_t cur = g_allocs_left.load(std::memory_order_relaxed);
+    while (cur >= 0) {
+        if (cur == 0) return false;
+        if (g_allocs_left.compare_exchange_weak(cur, cur - 1, std::memory_order_relaxed)) return true;
+    }
+    return true;
+}
+
 template <typename T>
 int dalloc(spirec_plan p, T** ptr, size_t count)
 {
     *ptr = nullptr;
     if (count == 0) count = 1;
     const size_t bytes = count * sizeof(T);
-    if (getenv("SPIREC_FAIL_ALLOC_AFTER")) {
-        static thread_local long budget = -2;
-        if (budget == -2) budget = atol(getenv("SPIREC_FAIL_ALLOC_AFTER"));
-        if (budget-- <= 0) {
-            set_error("injected allocation failure");
-            return SPIREC_ENOMEM;
-        }
+    if (!alloc_allowed()) {
+        set_error("injected allocation failure (spirec_inject_alloc_failure)");
+        return SPIREC_ENOMEM;
     }
     keep_pool(p->device);
     cudaError_t e = cudaMallocAsync((void**)ptr, bytes, p->stream);
@@ -370,6 +392,12 @@ int run_iterations(spirec_plan p, int iters)
     return SPIREC_OK;
 }
 
+bool solve_uses_loop(spirec_plan p)
+{
+    return p->mode != SPIREC_MODE_DIRECT && p->minimiser == SPIREC_MIN_PRCG && loop_supported(p->M) &&
+           !getenv("SPIREC_NO_LOOP");
+}
+
 int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
 {
     if (!p->have_traj || !p->have_data) {
@@ -409,7 +437,7 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
         return tstop(p, e);
     }
     rc = SPIREC_EUNSUPPORTED;
-    if (!direct && loop_supported(p->M) && !getenv("SPIREC_NO_LOOP")) {
+    if (solve_uses_loop(p)) {
         // first gradient and every iteration in one persistent kernel
         rc = launch_cg_loop(p, iters);
         if (rc != SPIREC_OK && rc != SPIREC_EUNSUPPORTED) return rc;
@@ -425,6 +453,18 @@ int solve_core(spirec_plan p, const float* x0, bool x0_dev, int iters)
     }
     return tstop(p, e);
 }
+
+}  // namespace
+
+int solve_loop_demand(spirec_plan p, int* blocks, int* capacity)
+{
+    *blocks = 0;
+    *capacity = 0;
+    if (!solve_uses_loop(p)) return 0;
+    return loop_demand(p, blocks, capacity);
+}
+
+namespace {
 
 // ------------------------------------------------------------ autotuning
 
@@ -1374,6 +1414,28 @@ int spirec_autotune(spirec_plan p, int32_t objective, int32_t loop_iters, int32_
         chosen[k] = got[k];
         if (best_ms) best_ms[k] = ms[k];
     }
+    return SPIREC_OK;
+}
+
+int spirec_inject_alloc_failure(int64_t n)
+{
+    g_allocs_left.store(n < 0 ? -1 : n, std::memory_order_relaxed);
+    return SPIREC_OK;
+}
+
+int spirec_inject_wait_stall(int32_t kernels)
+{
+    if (kernels & ~(kStallLoop | kStallContraction)) {
+        set_error("unknown kernel bits %d", kernels);
+        return SPIREC_EINVAL;
+    }
+    g_stall.store(kernels, std::memory_order_relaxed);
+    return SPIREC_OK;
+}
+
+int spirec_set_wait_limit_ns(uint64_t ns)
+{
+    g_wait_ns.store(ns == 0 ? kDefaultWaitNs : (unsigned long long)ns, std::memory_order_relaxed);
     return SPIREC_OK;
 }
 

@@ -44,11 +44,14 @@
 // that pass's synchronisation (deferred_parts_fetch, deferred_parts_sum).
 //
 // Every grid synchronisation is a reduction over block partials behind an
-// arrival counter (see grid_reduce).  Its wait is bounded in time: on expiry the block raises an
-// abort word and an error bit, every block returns at its next
-// synchronisation, and the host reports SPIREC_ETIMEOUT.  The cooperative
-// launch guarantees that all blocks are resident, so no wait depends on an
-// unscheduled block.
+// arrival counter (see grid_reduce).  Its wait is bounded in time (the
+// launch's wait limit, 2 s unless a test sets it): on expiry the block raises
+// an abort word and an error bit, every block returns at its next
+// synchronisation, and the host reports SPIREC_ETIMEOUT.  No asynchronous
+// copy is in flight at a synchronisation (the deferred partials are waited
+// for before it), so a block that returns there leaves nothing behind.  The
+// cooperative launch guarantees that all blocks are resident, so no wait
+// depends on an unscheduled block.
 #include <stdint.h>
 
 #include <mutex>
@@ -64,7 +67,6 @@ namespace spirec {
 namespace {
 
 constexpr int kLoopThreads = 512;
-constexpr unsigned long long kBarrierNs = 2000000000ull;  // 2 s
 constexpr int kMaxGroupsPerBlock = 8;
 constexpr int kProf = 10;
 
@@ -86,6 +88,8 @@ struct LoopArgs {
     unsigned* counter;  // arrivals, zero at the launch
     unsigned* abort_word;
     int* err;
+    unsigned long long wait_ns;  // limit of every grid wait (wait_limit_ns())
+    int stall;                   // a test's injected stall (injected_stall())
 };
 
 // Loop scalars, one copy per block.  Thread 0 writes them between two
@@ -156,7 +160,8 @@ __device__ __forceinline__ uint64_t gtimer()
 // waits for n * gridDim.x).  Then one warp per value sums the partials of
 // all blocks in index order.
 
-__device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned target, unsigned* abort_word, int* err)
+__device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned target, unsigned* abort_word, int* err,
+                                                 unsigned long long limit_ns)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(counter) : "memory");
     const uint64_t t0 = gtimer();
@@ -168,7 +173,7 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
             unsigned ab;
             asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(ab) : "l"(abort_word) : "memory");
             if (ab) return false;
-            if (gtimer() - t0 > kBarrierNs) {
+            if (gtimer() - t0 > limit_ns) {
                 atomicExch(abort_word, 1u);
                 atomicOr(err, E_TIMEOUT);
                 return false;
@@ -182,7 +187,8 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
 // counts the synchronisations of the launch (the same in every thread).
 template <int K>
 __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned& seq, LoopShared& S,
-                                            unsigned* counter, unsigned* abort_word, int* err)
+                                            unsigned* counter, unsigned* abort_word, int* err,
+                                            unsigned long long limit_ns)
 {
     FF bt[K];
     block_partial<K>(v, bt);  // ends with __syncthreads(): the block's writes precede thread 0
@@ -190,7 +196,7 @@ __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int sl
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
+        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err, limit_ns) ? 1 : 0;
     }
     __syncthreads();
     if (!S.ok) return false;
@@ -208,7 +214,8 @@ __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int sl
 // deferred_parts_sum), off the critical path.
 template <int K>
 __device__ __forceinline__ bool grid_arrive_parts(float (&v)[K], float2* parts, int slot, unsigned& seq,
-                                                  LoopShared& S, unsigned* counter, unsigned* abort_word, int* err)
+                                                  LoopShared& S, unsigned* counter, unsigned* abort_word, int* err,
+                                                  unsigned long long limit_ns)
 {
     FF bt[K];
     block_partial<K>(v, bt);
@@ -216,7 +223,7 @@ __device__ __forceinline__ bool grid_arrive_parts(float (&v)[K], float2* parts, 
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err) ? 1 : 0;
+        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err, limit_ns) ? 1 : 0;
     }
     __syncthreads();
     return S.ok != 0;
@@ -881,6 +888,14 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         }
     }
     __syncthreads();
+    if (A.stall) {
+        // a test's injected stall: wait for one arrival more than the grid
+        // makes, so that the bounded wait runs out in every block
+        if (threadIdx.x == 0)
+            S.ok = grid_arrive_wait(A.counter, gridDim.x + 1, A.abort_word, A.err, A.wait_ns) ? 1 : 0;
+        __syncthreads();
+        if (!S.ok) return;
+    }
 
     // ---- gradient at x0, J(x0); the first direction is -g (beta = 0)
     {
@@ -889,7 +904,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             phase_update<MC, true, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, 0.f, A.iters > 0, a);
         else
             phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, 0.f, A.iters > 0, a);
-        if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
+        if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
         if (threadIdx.x == 0) {
             double J, beta;
             cgd::update_finish(S.red, S.ss, 0.0, true, &J, &beta);
@@ -932,7 +947,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
         if (deferred) deferred_parts_sum<kUpdVals>(pbuf, S);
         else __syncthreads();
         ++seq;
-        if (threadIdx.x == 0) S.ok = grid_arrive_wait(A.counter, seq * gridDim.x, A.abort_word, A.err) ? 1 : 0;
+        if (threadIdx.x == 0) S.ok = grid_arrive_wait(A.counter, seq * gridDim.x, A.abort_word, A.err, A.wait_ns) ? 1 : 0;
         if (deferred && (threadIdx.x >> 5) >= 1 && (threadIdx.x >> 5) <= kUpdVals + 1) {
             asm volatile("bar.sync 1, %0;" ::"r"(32 * (kUpdVals + 1)) : "memory");
             if (threadIdx.x == 32 * (kUpdVals + 1)) finish_update(A, S, k);
@@ -950,7 +965,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             else
                 phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, beta, restart, acc);
             mark(2);
-            if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err)) return;
+            if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             if (threadIdx.x == 0) {
                 S.q1 = S.red[0];
                 S.q2 = S.red[3];
@@ -967,7 +982,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             float acc[2] = {0.f, 0.f};
             phase_ls<MC>(A.reg, R, cf, cd, fbuf, S.t_f, acc);
             mark(4 + 2 * j);
-            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err)) return;
+            if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             if (threadIdx.x == 0) {
                 S.t = cgd::ls_next(S.t, S.q1, S.q2, S.red[0], S.red[1]);
                 S.t_f = (float)S.t;
@@ -983,7 +998,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             else
                 phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
-            if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err)) return;
+            if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             if (threadIdx.x == 0 && blockIdx.x == 0) {
                 A.scal[S_Q1] = S.q1;
                 A.scal[S_Q2] = S.q2;
@@ -1171,6 +1186,8 @@ struct LaunchLoop {
             A.counter = p->counters + C_BAR;
             A.abort_word = p->counters + C_BAR + 2;
             A.err = p->dflag;
+            A.wait_ns = wait_limit_ns();
+            A.stall = injected_stall(kStallLoop) ? 1 : 0;
             // no arrivals, no abort
             SPIREC_CK(cudaMemsetAsync(A.counter, 0, 3 * sizeof(unsigned), p->stream));
             void* args[] = {&A};
@@ -1193,6 +1210,7 @@ struct Shapes {
     int* grid;
     int max;
     bool current;
+    int* capacity;  // with current: co-resident blocks the device holds of that shape
     template <int MC>
     int run()
     {
@@ -1201,16 +1219,27 @@ struct Shapes {
         } else {
             if (current) {
                 size_t smem = 0;
-                return loop_shape<MC>(p, RB, grid, &smem) ? 1 : 0;
+                if (!loop_shape<MC>(p, RB, grid, &smem)) return 0;
+                if (capacity) {
+                    int sms = 0, per_sm = 0;
+                    if (device_sms(&sms) != SPIREC_OK ||
+                        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_loop<MC>, kLoopThreads, smem) !=
+                            cudaSuccess) {
+                        cudaGetLastError();
+                        return 0;
+                    }
+                    *capacity = sms * per_sm;
+                }
+                return 1;
             }
             return loop_shapes<MC>(p->N, RB, grid, max);
         }
     }
 };
 
-int shapes_for(const spirec_plan_s* p, int* RB, int* grid, int max, bool current)
+int shapes_for(const spirec_plan_s* p, int* RB, int* grid, int max, bool current, int* capacity = nullptr)
 {
-    Shapes s{p, RB, grid, max, current};
+    Shapes s{p, RB, grid, max, current, capacity};
     switch (p->M) {
     case 64: return s.run<64>();
     case 128: return s.run<128>();
@@ -1226,6 +1255,15 @@ int shapes_for(const spirec_plan_s* p, int* RB, int* grid, int max, bool current
 int loop_candidates(spirec_plan p, int* RB, int* grid, int max) { return shapes_for(p, RB, grid, max, false); }
 
 int loop_current(spirec_plan p, int* RB, int* grid) { return shapes_for(p, RB, grid, 1, true); }
+
+int loop_demand(spirec_plan p, int* blocks, int* capacity)
+{
+    int RB = 0;
+    *blocks = 0;
+    *capacity = 0;
+    if (!loop_supported(p->M)) return 0;
+    return shapes_for(p, &RB, blocks, 1, true, capacity);
+}
 
 int launch_cg_loop(spirec_plan p, int iters)
 {

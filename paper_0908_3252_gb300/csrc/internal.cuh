@@ -258,7 +258,27 @@ int contraction_split(spirec_plan p, int knob, int* value, int* sms_used);
 // (cg_loop.cu); the shape a launch uses now.
 int loop_candidates(spirec_plan p, int* RB, int* grid, int max);
 int loop_current(spirec_plan p, int* RB, int* grid);
+// Blocks the persistent loop of the plan's current shape launches, and how
+// many blocks of that shape the device holds at once (1 when it has a shape;
+// 0 and nothing set otherwise).  A cooperative launch needs all its blocks
+// resident together, so concurrent loops must fit that capacity jointly.
+int loop_demand(spirec_plan p, int* blocks, int* capacity);
+// The same for the plan's next solve: 0 blocks when it will not run the
+// persistent loop (direct mode, another minimiser, M without a loop).
+int solve_loop_demand(spirec_plan p, int* blocks, int* capacity);
+// Device bytes the request loop reserves for a request of this shape, and the
+// grid side M it plans it with (server.cu).
+size_t server_plan_bytes(int N, int64_t L, int precision, int* M);
 int tc_ctas(spirec_plan p, int knob, int sms, int64_t* P);  // nudft_tc.cu
+
+// Limit of every bounded device wait of the kernels launched from now on
+// (2 s unless spirec_set_wait_limit_ns changed it).
+unsigned long long wait_limit_ns();
+// Kernels a test has asked to stall (spirec_inject_wait_stall): such a launch
+// waits once on a condition nothing fulfils, so its bounded wait runs out.
+constexpr int kStallLoop = 1;         // the persistent CG loop
+constexpr int kStallContraction = 2;  // the tensor-core contractions
+bool injected_stall(int kind);
 
 int vec_blocks(int N);
 constexpr int kVecThreads = 256;

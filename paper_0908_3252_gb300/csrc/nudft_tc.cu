@@ -77,10 +77,16 @@ constexpr uint32_t TRAJ_OFF = TC_STAGES * STAGE_BYTES;
 constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
 constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
-static_assert(8 * (2 * TC_STAGES + 2 + TRAJ_RING) + 8 <= 128, "barrier area");
+static_assert(8 * (2 * TC_STAGES + 3 + TRAJ_RING) + 8 <= 128, "barrier area");
 constexpr int kMaxCtas = 152;       // CTAs of one contraction (one per SM)
 
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
+// Every pipeline wait is bounded by the launch's wait limit (a kernel
+// argument, 2 s unless a test sets it); on expiry the CTA raises E_TIMEOUT and
+// winds down.  Before it releases its TMEM and exits it waits, with this
+// fixed bound, for the asynchronous work it issued (TMA copies into its shared
+// memory, MMAs reading it and writing TMEM), so that nothing of it is in
+// flight once the CTA is gone.
+constexpr unsigned long long kDrainNs = 2000000000ull;
 constexpr int kErrTimeout = E_TIMEOUT;
 
 // ------------------------------------------------------------ PTX helpers
@@ -120,15 +126,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: false after kWaitNs without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Bounded wait: false after limit_ns without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
 {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 
@@ -170,6 +176,23 @@ __device__ __forceinline__ void tc_fence_after()
 __device__ __forceinline__ void producers_sync()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory");
+}
+
+// producers_sync that also returns, to every producer alike, whether any of
+// them passed v = true (a barrier with an OR reduction): a decision every
+// producer takes the same way, as it must be before a named barrier.
+__device__ __forceinline__ bool producers_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(TC_PRODUCERS)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols)
@@ -403,7 +426,8 @@ template <bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ kbs,
                 const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L, int tilesC,
-                int oa, int ob, int sa, int sb, int64_t K, int64_t U, float* __restrict__ part, int* err)
+                int oa, int ob, int sa, int sb, int64_t K, int64_t U, float* __restrict__ part, int* err,
+                unsigned long long wait_ns, int stall)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -413,7 +437,8 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
     const uint32_t bar_acc_full = bar_empty + 8 * TC_STAGES;  // segment accumulated
     const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained
     const uint32_t bar_traj = bar_acc_empty + 8;              // TRAJ_RING: trajectory chunk landed
-    const uint32_t misc = BAR_OFF + 8 * (2 * TC_STAGES + 2 + TRAJ_RING);
+    const uint32_t bar_drain = bar_traj + 8 * TRAJ_RING;      // every MMA issued has completed
+    const uint32_t misc = BAR_OFF + 8 * (2 * TC_STAGES + 3 + TRAJ_RING);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
     const uint32_t traj_s = sbase + TRAJ_OFF;
@@ -432,6 +457,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
         mbar_init(bar_acc_full, 1);
         mbar_init(bar_acc_empty, TC_PRODUCERS);
         for (int r = 0; r < TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
+        mbar_init(bar_drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -447,7 +473,9 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
         // TMA feed of the trajectory (and data) chunk of stage `it` into ring
         // slot it % 4; stages are issued in order, kci is the chunk of the next
         int64_t kci = u0 % K;
+        int issued = 0;  // stages whose chunk thread 0 has requested
         auto issue_traj = [&](int it) {
+            ++issued;
             const int64_t l0 = kci * TC_KS;
             if (++kci == K) kci = 0;
             // the whole chunk, also past L: the plan's sample arrays have 32
@@ -477,14 +505,14 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             // warps drift apart by at most the ring depth: a warp past the
             // wait for stage it knows every producer has finished stage
             // it - 2, whose trajectory slot the TMA of stage it + 2 reuses.
-            if (lane == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+            if (lane == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
             __syncwarp();
-            if (*abort_flag) break;
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;  // the warp stops as one
             if (tid == 0 && it + 2 < n) issue_traj(it + 2);
-            if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1)) {
+            if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
@@ -578,10 +606,11 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
                 // drain the previous one
                 if (sw.seg > 0) {
                     const int j = sw.seg - 1;
-                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1, wait_ns)) {
                         atomicOr(err, kErrTimeout);
                         *abort_flag = 1;
                     }
+                    __syncwarp();  // the tensor-memory loads are warp-collective
                     tc_fence_after();
                     drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
                     tc_fence_before();
@@ -591,16 +620,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
                 dfirst = sw.first_of_tile;
             }
         }
-        // the last segment
-        if (sw.seg >= 0 && !*abort_flag) {
+        // the last segment (a warp drains it as one, or not at all)
+        if (sw.seg >= 0 && !__any_sync(0xffffffffu, *abort_flag != 0)) {
             const int j = sw.seg;
-            if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
-                atomicOr(err, kErrTimeout);
-            } else {
+            const bool landed = mbar_wait(bar_acc_full, (uint32_t)j & 1, wait_ns);
+            if (!landed) atomicOr(err, kErrTimeout);
+            if (__all_sync(0xffffffffu, landed)) {
                 tc_fence_after();
                 drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
             }
         }
+        // every requested chunk has landed before the CTA goes (at most one
+        // request per ring slot is open: the last TRAJ_RING stages)
+        if (tid == 0)
+            for (int j = issued > TRAJ_RING ? issued - TRAJ_RING : 0; j < issued; ++j)
+                if (!mbar_wait(bar_traj + 8 * (j % TRAJ_RING), (uint32_t)(j / TRAJ_RING) & 1, kDrainNs))
+                    atomicOr(err, kErrTimeout);
     } else if (lane == 0) {
         // ------------------------------------------------ MMA issuer
         // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and 10,
@@ -610,19 +645,24 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
         const uint32_t idesc_neg = idesc | (1u << 13);
         SegWalk sw{u0, K};
-        for (int it = 0; it < n; ++it) {
+        int issued = 0;  // stages whose MMAs were issued
+        // a test's injected stall: nothing completes bar_drain before this
+        // thread's own commit, so the bounded wait runs out and no MMA issues
+        if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
+        for (int it = 0; !stall && it < n; ++it) {
             const int s = it % TC_STAGES;
             const uint32_t use = (uint32_t)(it / TC_STAGES);
             sw.step(it);
             const uint32_t tre = tmem, tim = tmem + TC_COLS;
-            if (sw.pos == 0 && sw.seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(sw.seg - 1) & 1)) {
+            if (sw.pos == 0 && sw.seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(sw.seg - 1) & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
-            if (!mbar_wait(bar_full + 8 * s, use & 1)) {
+            if (!mbar_wait(bar_full + 8 * s, use & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
+            ++issued;
             tc_fence_after();
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
@@ -641,6 +681,11 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             }
             mma_commit(bar_empty + 8 * s);
             if (sw.closes(it, n)) mma_commit(bar_acc_full);
+        }
+        // no MMA may still read the stages or write TMEM once the CTA frees it
+        if (issued > 0) {
+            mma_commit(bar_drain);
+            if (!mbar_wait(bar_drain, 0, kDrainNs)) atomicOr(err, kErrTimeout);
         }
     }
 
@@ -758,7 +803,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, const uint8_t* __restrict__ FB,
              const unsigned* __restrict__ amax2, int64_t L, int N, int kchunks, float scale, float2* __restrict__ y,
-             int* err)
+             int* err, unsigned long long wait_ns, int stall)
 {
     scale /= weight_scale_inv(amax2);  // undoes k_split_image's 2^-e
     extern __shared__ uint8_t smem_raw[];
@@ -768,9 +813,9 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
     const uint32_t bar_empty = bar_full + 8 * TC_STAGES;  // TC_STAGES: stage consumed
     const uint32_t bar_acc_full = bar_empty + 8 * TC_STAGES;
     const uint32_t bar_acc_empty = bar_acc_full + 8;
-    const uint32_t misc = FW_BAR + 8 * (2 * TC_STAGES + 2);
+    const uint32_t bar_drain = bar_acc_empty + 8;  // every MMA issued has completed
+    const uint32_t misc = FW_BAR + 8 * (2 * TC_STAGES + 3);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
     float2* ypart = reinterpret_cast<float2*>(smem + FW_YPART);  // [4 column quarters][128 samples]
 
     const int tid = threadIdx.x;
@@ -788,7 +833,7 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
         }
         mbar_init(bar_acc_full, 1);
         mbar_init(bar_acc_empty, TC_PRODUCERS);
-        *abort_flag = 0;
+        mbar_init(bar_drain, 1);
         fence_mbar_init();
     }
     if (warp == TC_PRODUCERS / 32) tmem_alloc(smem_u32(tmem_slot), 512);
@@ -799,12 +844,18 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
 
     if (warp < TC_PRODUCERS / 32) {
         // ------------------------------------------------ producers
+        // A wait that runs out sets the thread's `late`; the producers decide
+        // to stop together, at the OR-barrier that starts each stage, so none
+        // is left alone at a named barrier of the epilogue.
         const int r = tid & 127, g = tid >> 7;  // A row (sample in the tile), group of 8 n
+        int issued = 0;                          // stages whose image block thread 0 requested
+        bool late = false, stopped = false;
         int64_t ka = 0;                          // ky of this thread's sample (fixed point)
         int64_t cur_tile = -1;
         float2 ysum = make_float2(0.f, 0.f);     // threads 0..127: y of sample tid over m-tiles
         // the epilogue of the segment (tile t, m-tile mt): this warp's 64 columns
         auto epilogue = [&](int64_t t, int mt) {
+            __syncwarp();  // the tensor-memory loads are warp-collective
             const int lq = warp & 3, cq = warp >> 2;
             const int rs = 32 * lq + lane;
             const int64_t l = t * TC_ROWS + rs;
@@ -844,15 +895,20 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
             const uint32_t use = (uint32_t)(it / TC_STAGES);
             const int64_t t = blockIdx.x + (int64_t)(it / per_tile) * gridDim.x;
             const int rem = it % per_tile, mt = rem / kchunks, kc = rem % kchunks;
-            if (tid == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
-                *abort_flag = 1;
+            if (tid == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
+                late = true;
                 atomicOr(err, kErrTimeout);
             }
-            producers_sync();  // stage s is free
-            if (*abort_flag) break;
+            if (producers_any(late)) {  // stage s is free, or every producer stops here
+                stopped = true;
+                break;
+            }
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES;
+            // from here to its arrival below every producer completes the
+            // stage, so the phase of bar_full[s] ends once the block lands
             if (tid == 0) {
+                ++issued;
                 fence_proxy_async();
                 mbar_expect_tx(bar_full + 8 * s, FW_BLOCK);
                 bulk_g2s(bH, FB + ((int64_t)mt * kchunks + kc) * FW_BLOCK, FW_BLOCK, bar_full + 8 * s);
@@ -885,9 +941,9 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
                     // the MMA has the first stage of a new segment queued: the
                     // epilogue of the previous one
                     const int j = it / kchunks - 1;
-                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+                    if (!mbar_wait(bar_acc_full, (uint32_t)j & 1, wait_ns)) {
                         atomicOr(err, kErrTimeout);
-                        *abort_flag = 1;
+                        late = true;  // every producer still runs the epilogue (it holds a named barrier)
                     }
                     tc_fence_after();
                     epilogue(seg_t, seg_mt);
@@ -898,34 +954,46 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
                 seg_mt = mt;
             }
         }
-        if (n > 0 && !*abort_flag) {
+        if (n > 0 && !stopped) {
             const int j = n / kchunks - 1;
-            if (!mbar_wait(bar_acc_full, (uint32_t)j & 1)) {
+            if (!mbar_wait(bar_acc_full, (uint32_t)j & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
-            } else {
+                late = true;
+            }
+            if (!producers_any(late)) {  // the last epilogue: all producers or none
                 tc_fence_after();
                 epilogue(seg_t, seg_mt);
             }
         }
+        // every requested image block has landed before the CTA goes (the
+        // open requests are among the last TC_STAGES stages)
+        if (tid == 0)
+            for (int j = issued > TC_STAGES ? issued - TC_STAGES : 0; j < issued; ++j)
+                if (!mbar_wait(bar_full + 8 * (j % TC_STAGES), (uint32_t)(j / TC_STAGES) & 1, kDrainNs))
+                    atomicOr(err, kErrTimeout);
     } else if (lane == 0) {
         // ------------------------------------------------ MMA issuer
         const uint32_t fmt = BF16 ? 1u : 0u;
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
         const uint32_t idesc_neg = idesc | (1u << 13);
         const uint32_t tre = tmem, tim = tmem + TC_COLS;
-        for (int it = 0; it < n; ++it) {
+        int issued = 0;  // stages whose MMAs were issued
+        // a test's injected stall (as in k_tc_phase_gemm)
+        if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
+        for (int it = 0; !stall && it < n; ++it) {
             const int s = it % TC_STAGES;
             const uint32_t use = (uint32_t)(it / TC_STAGES);
             const int kc = (it % per_tile) % kchunks;
             const int seg = it / kchunks;
-            if (kc == 0 && seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(seg - 1) & 1)) {
+            if (kc == 0 && seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(seg - 1) & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
-            if (!mbar_wait(bar_full + 8 * s, use & 1)) {
+            if (!mbar_wait(bar_full + 8 * s, use & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
                 break;
             }
+            ++issued;
             tc_fence_after();
             const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
             const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
@@ -944,6 +1012,11 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
             }
             mma_commit(bar_empty + 8 * s);
             if (kc == kchunks - 1) mma_commit(bar_acc_full);
+        }
+        // no MMA may still read the stages or write TMEM once the CTA frees it
+        if (issued > 0) {
+            mma_commit(bar_drain);
+            if (!mbar_wait(bar_drain, 0, kDrainNs)) atomicOr(err, kErrTimeout);
         }
     }
 
@@ -1011,18 +1084,20 @@ int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb,
         return SPIREC_ESTATE;
     }
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
+    const unsigned long long wait_ns = wait_limit_ns();
+    const int stall = injected_stall(kStallContraction) ? 1 : 0;
     if (bf16 && w)
         k_tc_phase_gemm<true, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
     else if (bf16)
         k_tc_phase_gemm<true, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
     else if (w)
         k_tc_phase_gemm<false, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
     else
         k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag);
+            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
     SPIREC_CK(cudaGetLastError());
     const dim3 rgrid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
     k_reduce_tc<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
@@ -1070,10 +1145,14 @@ int launch_forward_tc(spirec_plan p, const float2* x, float2* yout)
     const float scale = 1.0f / (float)N;
     if (bf16)
         k_tc_forward<true><<<(unsigned)P, TC_THREADS, FW_SMEM, p->stream>>>(p->kxq, p->kyq, p->fsplit, amax, p->L,
-                                                                           N, kchunks, scale, yout, p->dflag);
+                                                                           N, kchunks, scale, yout, p->dflag,
+                                                                           wait_limit_ns(),
+                                                                           injected_stall(kStallContraction) ? 1 : 0);
     else
         k_tc_forward<false><<<(unsigned)P, TC_THREADS, FW_SMEM, p->stream>>>(p->kxq, p->kyq, p->fsplit, amax,
-                                                                            p->L, N, kchunks, scale, yout, p->dflag);
+                                                                            p->L, N, kchunks, scale, yout, p->dflag,
+                                                                            wait_limit_ns(),
+                                                                            injected_stall(kStallContraction) ? 1 : 0);
     SPIREC_CK(cudaGetLastError());
     p->launches += 3;
     return SPIREC_OK;

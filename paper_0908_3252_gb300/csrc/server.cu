@@ -6,12 +6,25 @@
 // device) and reuses it while requests keep the same (N, L).  Requests wait
 // in a FIFO queue; the head is admitted when a worker is idle and its device
 // footprint fits the HBM budget next to the plans already resident (a worker
-// whose plan does not fit the next request releases it first).  Admitted
-// requests run concurrently on their workers' streams, so a request that
-// arrives while others are on the GPU starts as soon as a slot and memory
-// free up, and its kernels overlap theirs.  Results are identical alone and
-// in a mix: every kernel's launch shape and summation order depend only on
-// the request's own sizes.
+// whose plan does not fit the next request releases it first).  When the
+// head fits only once plans held by other idle workers go, the admitting
+// worker asks those workers to release them (they are idle, so their plans
+// are not in use), instead of waiting for a completion that may never come.
+// Admitted requests run concurrently on their workers' streams, so a request
+// that arrives while others are on the GPU starts as soon as a slot and
+// memory free up, and its kernels overlap theirs.
+//
+// Co-residency: a solve on the persistent CG loop is one cooperative launch
+// whose blocks wait on each other at every grid synchronisation, so all of
+// them must be resident at once.  Concurrent loops of several workers must
+// therefore fit the device together: before a solve, a worker reserves its
+// loop's blocks against the device's capacity for that loop (one block per
+// SM) and waits while the running loops hold too many; the reservation ends
+// when the solve returns.  Other kernels never wait on each other, so they
+// can only delay a loop's blocks, not hold them off for good.
+//
+// Results are identical alone and in a mix: every kernel's launch shape and
+// summation order depend only on the request's own sizes.
 #include <stdio.h>
 
 #include <algorithm>
@@ -48,11 +61,24 @@ struct Job {
 }  // namespace
 }  // namespace spirec
 
+namespace spirec {
+namespace {
+// A worker's state as the admission sees it (guarded by the server's mutex).
+struct Slot {
+    bool idle = false;   // waiting for work, its plan unused
+    bool evict = false;  // asked to release its plan
+    size_t bytes = 0;    // footprint of its resident plan
+};
+}  // namespace
+}  // namespace spirec
+
 struct spirec_server_s {
     int device;
     int precision;
     size_t budget;
     size_t in_use = 0;  // device bytes of resident plans
+    int loop_blocks = 0;  // persistent-loop blocks of the running solves
+    std::vector<spirec::Slot> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<spirec::Job>> queue;
@@ -103,7 +129,7 @@ int choose_M(int N)
     return (double)p2 <= 1.4 * m && loop_supported(p2) ? p2 : m;
 }
 
-void worker_main(spirec_server srv)
+void worker_main(spirec_server srv, int me)
 {
     cudaSetDevice(srv->device);
     // the worker's own stream: plans joined to the legacy default stream would
@@ -113,31 +139,73 @@ void worker_main(spirec_server srv)
     spirec_plan plan = nullptr;
     int pN = 0, pM = 0;
     int64_t pL = 0;
-    size_t pbytes = 0;
+    Slot& slot = srv->slots[me];
+    auto release_plan = [&](std::unique_lock<std::mutex>& lk) {
+        // the plan is idle: drop it outside the lock, then return its bytes
+        spirec_plan old = plan;
+        plan = nullptr;
+        pN = 0;
+        lk.unlock();
+        if (old) spirec_plan_destroy(old);
+        lk.lock();
+        srv->in_use -= slot.bytes;
+        slot.bytes = 0;
+        slot.evict = false;
+        srv->cv_work.notify_all();
+    };
     for (;;) {
         std::shared_ptr<Job> job;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
+            slot.idle = true;
             for (;;) {
                 if (srv->stop) break;
+                if (slot.evict) {
+                    release_plan(lk);
+                    continue;
+                }
                 if (!srv->queue.empty()) {
                     const spirec_request& r = srv->queue.front()->req;
                     const int M = choose_M(r.N);
                     const bool reuse = plan && pN == r.N && pL == r.L && pM == M;
                     const size_t need = reuse ? 0 : plan_bytes(r.N, r.L, M, srv->precision);
-                    const size_t freed = reuse ? 0 : pbytes;
-                    if (srv->in_use - freed + need <= srv->budget || srv->in_use == pbytes) {
+                    const size_t freed = reuse ? 0 : slot.bytes;
+                    if (srv->in_use - freed + need <= srv->budget || srv->in_use == slot.bytes) {
                         job = srv->queue.front();
                         srv->queue.pop_front();
                         if (!reuse) {
                             srv->in_use = srv->in_use - freed + need;
-                            pbytes = need;
+                            slot.bytes = need;
                         }
                         break;
+                    }
+                    // would the plans of the other idle workers, released,
+                    // make room?  Then ask them (largest first) to release
+                    std::vector<int> idle;
+                    size_t avail = srv->budget - std::min(srv->budget, srv->in_use - freed);
+                    for (int i = 0; i < (int)srv->slots.size(); ++i)
+                        if (i != me && srv->slots[i].idle && srv->slots[i].bytes > 0 && !srv->slots[i].evict)
+                            idle.push_back(i);
+                    std::sort(idle.begin(), idle.end(),
+                              [&](int a, int b) { return srv->slots[a].bytes > srv->slots[b].bytes; });
+                    size_t pending = 0;
+                    for (auto& o : srv->slots)
+                        if (o.evict) pending += o.bytes;
+                    size_t gain = pending;
+                    std::vector<int> pick;
+                    for (int i : idle) {
+                        if (avail + gain >= need) break;
+                        gain += srv->slots[i].bytes;
+                        pick.push_back(i);
+                    }
+                    if (avail + gain >= need && !pick.empty()) {
+                        for (int i : pick) srv->slots[i].evict = true;
+                        srv->cv_work.notify_all();
                     }
                 }
                 srv->cv_work.wait(lk);
             }
+            slot.idle = false;
             if (!job) break;
         }
         job->t_start = Clock::now();
@@ -161,17 +229,27 @@ void worker_main(spirec_server srv)
         if (rc == SPIREC_OK) rc = spirec_set_data(plan, r.s);
         if (rc == SPIREC_OK) rc = spirec_set_reg(plan, r.lambda1, r.alpha1, r.lambda0, r.alpha0, r.phi);
         std::vector<double> Jh((size_t)std::max(r.iters, 0) + 1);
+        int blocks = 0, capacity = 0;
+        if (rc == SPIREC_OK && r.iters > 0) solve_loop_demand(plan, &blocks, &capacity);
+        if (blocks > 0) {
+            // the loop's blocks must be resident together with those of
+            // the other running loops (a loop alone always fits)
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv_work.wait(lk, [&] { return srv->loop_blocks == 0 || srv->loop_blocks + blocks <= capacity; });
+            srv->loop_blocks += blocks;
+        }
         if (rc == SPIREC_OK) rc = spirec_solve(plan, nullptr, r.iters, job->x.data(), Jh.data());
         job->t_end = Clock::now();
         {
             std::lock_guard<std::mutex> lk(srv->mu);
+            srv->loop_blocks -= blocks;
             job->status = rc;
             if (rc != SPIREC_OK) {
                 snprintf(job->err, sizeof(job->err), "%s", spirec_last_error());
                 ++srv->failed;
                 if (!plan) {
-                    srv->in_use -= pbytes;
-                    pbytes = 0;
+                    srv->in_use -= slot.bytes;
+                    slot.bytes = 0;
                 }
             } else {
                 job->J = Jh[(size_t)r.iters];
@@ -186,8 +264,19 @@ void worker_main(spirec_server srv)
     if (plan) spirec_plan_destroy(plan);
     if (st) cudaStreamDestroy(st);
     std::lock_guard<std::mutex> lk(srv->mu);
-    srv->in_use -= pbytes;
+    srv->in_use -= slot.bytes;
+    slot.bytes = 0;
 }
+
+}  // namespace
+
+size_t server_plan_bytes(int N, int64_t L, int precision, int* M)
+{
+    *M = choose_M(N);
+    return plan_bytes(N, L, *M, precision);
+}
+
+namespace {
 
 double percentile(std::vector<double> v, double q)
 {
@@ -224,8 +313,21 @@ int spirec_server_create(spirec_server* out, size_t hbm_budget_bytes, int32_t ma
     }
     srv->precision = precision;
     srv->budget = hbm_budget_bytes;
-    for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back(worker_main, srv);
+    srv->slots.resize((size_t)max_slots);
+    for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back(worker_main, srv, i);
     *out = srv;
+    return SPIREC_OK;
+}
+
+int spirec_server_plan_bytes(int32_t N, int64_t L, int32_t precision, size_t* bytes, int32_t* M)
+{
+    if (!bytes || N < 2 || N > 2048 || L < 1 || precision < SPIREC_FP32 || precision > SPIREC_MIXED_BF16X3) {
+        set_error("bad arguments");
+        return SPIREC_EINVAL;
+    }
+    int m = 0;
+    *bytes = server_plan_bytes(N, L, precision, &m);
+    if (M) *M = m;
     return SPIREC_OK;
 }
 

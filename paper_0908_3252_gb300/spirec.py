@@ -93,6 +93,7 @@ SIGNATURES = {
     "spirec_timing_read": (ctypes.c_int, [_P, _P, _P]),
     "spirec_batch_solve": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P]),
     "spirec_server_create": (ctypes.c_int, [_P, ctypes.c_size_t, _I32, _I32]),
+    "spirec_server_plan_bytes": (ctypes.c_int, [_I32, _I64, _I32, _P, _P]),
     "spirec_server_submit": (ctypes.c_int, [_P, _P, _P]),
     "spirec_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _I32, _P, _P, _P]),
     "spirec_server_stats": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -104,6 +105,9 @@ SIGNATURES = {
     "spirec_tune_clear": (ctypes.c_int, []),
     "spirec_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "spirec_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "spirec_inject_alloc_failure": (ctypes.c_int, [_I64]),
+    "spirec_set_wait_limit_ns": (ctypes.c_int, [ctypes.c_uint64]),
+    "spirec_inject_wait_stall": (ctypes.c_int, [_I32]),
     "spirec_last_error": (ctypes.c_char_p, []),
     "spirec_version": (ctypes.c_char_p, []),
 }
@@ -168,6 +172,25 @@ def spirec_last_error() -> str:
 
 def spirec_version() -> str:
     return load().spirec_version().decode()
+
+
+def spirec_inject_alloc_failure(n):
+    """Plan allocations succeed n more times, then fail (n < 0: off)."""
+    return _check(load().spirec_inject_alloc_failure(int(n)))
+
+
+SPIREC_STALL_LOOP = 1
+SPIREC_STALL_CONTRACTION = 2
+
+
+def spirec_inject_wait_stall(kernels):
+    """Later launches of the kernels in the mask stall until their wait runs out (0: off)."""
+    return _check(load().spirec_inject_wait_stall(int(kernels)))
+
+
+def spirec_set_wait_limit_ns(ns):
+    """Limit of every bounded device wait of later launches (0: the 2 s default)."""
+    return _check(load().spirec_set_wait_limit_ns(int(ns)))
 
 
 def spirec_plan_create(N, L, M=0, precision=SPIREC_FP32, stream=None, kx=None, ky=None):
@@ -418,6 +441,13 @@ def spirec_server_create(hbm_budget_bytes, max_slots, precision):
     srv = ctypes.c_void_p()
     _check(load().spirec_server_create(ctypes.byref(srv), int(hbm_budget_bytes), int(max_slots), int(precision)))
     return srv
+
+
+def spirec_server_plan_bytes(N, L, precision):
+    """(bytes, M): the request loop's device footprint for a request of this shape."""
+    b, m = ctypes.c_size_t(), ctypes.c_int32()
+    _check(load().spirec_server_plan_bytes(int(N), int(L), int(precision), ctypes.byref(b), ctypes.byref(m)))
+    return b.value, m.value
 
 
 def spirec_server_submit(srv, N, kx, ky, s, lambda1, alpha1, lambda0, alpha0, phi, iters):

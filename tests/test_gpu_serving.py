@@ -151,3 +151,82 @@ def test_batch_solve_equals_single_solves(sp):
     finally:
         for p, _ in plans:
             p.close()
+
+
+def test_idle_plans_are_released_for_a_larger_request(sp):
+    """Two idle workers each keep the plan of their last request; the next
+    request fits the budget alone but not beside either plan.  The workers
+    must release their idle plans for it (before, no worker admitted it and
+    the queue stalled, as nothing was running to wake them)."""
+    g = synth.rng(21)
+
+    def req(N, I, S):
+        kx, ky = synth.spiral(N, I, S)
+        return dict(N=N, kx=kx, ky=ky, s=c64(synth.complex_normal(kx.shape[0], g)), lambda1=0.05, alpha1=0.05,
+                    lambda0=0.0, alpha0=0.05, phi=0, iters=5)
+
+    a, b, c = req(48, 2, 500), req(64, 2, 600), req(160, 8, 2048)
+    ba = sp.spirec_server_plan_bytes(a["N"], a["kx"].shape[0], 0)[0]
+    bb = sp.spirec_server_plan_bytes(b["N"], b["kx"].shape[0], 0)[0]
+    bc = sp.spirec_server_plan_bytes(c["N"], c["kx"].shape[0], 0)[0]
+    assert bc > ba + bb
+    budget = bc + (1 << 16)  # c fits alone, not beside a or b
+    srv = sp.spirec_server_create(budget, 2, 0)
+    try:
+        ta = _submit(sp, srv, a)
+        tb = _submit(sp, srv, b)
+        sp.spirec_server_wait(srv, ta, a["N"], timeout_ms=60000)
+        sp.spirec_server_wait(srv, tb, b["N"], timeout_ms=60000)
+        tc = _submit(sp, srv, c)
+        x, J, _ = sp.spirec_server_wait(srv, tc, c["N"], timeout_ms=60000)
+        assert np.isfinite(J)
+        st = sp.spirec_server_stats(srv)
+        assert st["completed"] == 3 and st["failed"] == 0
+    finally:
+        sp.spirec_server_destroy(srv)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_footprint_estimate_covers_the_plan(sp, prec):
+    """The request loop admits by spirec_server_plan_bytes: it must cover
+    every buffer a plan of that shape allocates through a served request's
+    calls (trajectory, data, penalty, solve)."""
+    g = synth.rng(22)
+    for N, L in [(2, 1), (24, 333), (64, 5000), (100, 20000), (192, 8192), (256, 70000), (384, 200000)]:
+        nbytes, M = sp.spirec_server_plan_bytes(N, L, prec)
+        kx, ky = synth.uniform_k(L, g)
+        with sp.Plan(N, L, M, prec, None, kx, ky) as p:
+            sp.spirec_set_data(p.h, c64(synth.complex_normal(L, g)))
+            sp.spirec_set_reg(p.h, 0.05, 0.05, 0.0, 0.05, 0)
+            sp.spirec_solve(p.h, None, 1, N)
+            used = sp.spirec_plan_info(p.h)["device_bytes"]
+        assert used <= nbytes, (N, L, used, nbytes)
+
+
+def test_concurrent_persistent_loops_all_complete(sp):
+    """Eight slots of the largest loop grids (N = 384 to 512: 96 to 128
+    one-SM blocks each, so no two fit the device together): every solve
+    must complete (no loop left waiting for blocks another loop holds) and
+    equal its result alone."""
+    g = synth.rng(23)
+    reqs = []
+    for i in range(8):
+        N = [384, 448, 512, 512][i % 4]
+        kx, ky = synth.spiral(N, 2, 700 + 50 * i)
+        reqs.append(dict(N=N, kx=kx, ky=ky, s=c64(synth.complex_normal(kx.shape[0], g)), lambda1=0.05,
+                         alpha1=0.05, lambda0=0.0, alpha0=0.05, phi=0, iters=10))
+    srv = sp.spirec_server_create(64 << 30, 8, 1)
+    try:
+        tickets = [_submit(sp, srv, r) for r in reqs]
+        mixed = [sp.spirec_server_wait(srv, t, r["N"], timeout_ms=120000) for t, r in zip(tickets, reqs)]
+        st = sp.spirec_server_stats(srv)
+    finally:
+        sp.spirec_server_destroy(srv)
+    assert st["completed"] == 8 and st["failed"] == 0
+    srv = sp.spirec_server_create(64 << 30, 1, 1)
+    try:
+        for r, (xm, Jm, _) in zip(reqs[:4], mixed[:4]):
+            xa, Ja, _ = sp.spirec_server_wait(srv, _submit(sp, srv, r), r["N"], timeout_ms=120000)
+            assert np.array_equal(xa, xm) and Ja == Jm
+    finally:
+        sp.spirec_server_destroy(srv)
