@@ -90,3 +90,84 @@ def test_cache_argument_errors(sp, series):
             assert e.value.code == sp.SPIREC_EINVAL
     finally:
         sp.spirec_kcache_destroy(cache)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_captured_series_matches_the_oracle(sp, prec):
+    """A dynamic series as the benchmark runs it, small: six frames of sizes
+    32, 48 and 64, each using 4 of 16 golden-angle interleaves from a kernel
+    cache, each with its own plan and stream; every frame's trajectory (from
+    the cache), data and 20 iterations are captured as ONE CUDA graph (fork
+    from a capture stream, join back) and replayed twice.  Every frame of
+    the replays is compared with the oracle's 20 iterations on the frame's
+    own samples, and the two replays with each other (bitwise)."""
+    import torch
+    from tests.helpers import iter_tol
+    g = synth.rng(71)
+    S16 = 256
+    kx16, ky16 = synth.spiral(64, 16, S16, "archimedean", "golden")
+    offsets = np.arange(0, 16 * S16 + 1, S16)
+    Ms = {32: 64, 48: 128, 64: 128}
+    caches = {n: sp.spirec_kcache_create(n, m, prec, offsets, kx16, ky16) for n, m in Ms.items()}
+    frames, keep = [], []
+    iters = 20
+    try:
+        for i, n in enumerate([32, 48, 64, 48, 32, 64]):
+            sub = np.sort(g.choice(16, 4, replace=False)).astype(np.int32)
+            idx = np.concatenate([np.arange(j * S16, (j + 1) * S16) for j in sub])
+            kx, ky = kx16[idx], ky16[idx]
+            f = synth.phantom(n, "ellipses_phase", synth.rng(80 + i))
+            s = c64(synth.add_noise(O.forward(kx, ky, f), 30.0, g))
+            st = torch.cuda.Stream()
+            p = sp.Plan(n, kx.shape[0], Ms[n], prec, st.cuda_stream)
+            s_d = torch.from_numpy(s.astype(np.complex64)).cuda()
+            x = torch.zeros((n, n), dtype=torch.complex64, device="cuda")
+            sp.spirec_set_reg(p.h, 0.05, 0.05, 0.0, 0.05, 0)
+            frames.append(dict(p=p, st=st, s_d=s_d, x=x, sub=sub, kx=kx, ky=ky, s=s, N=n, cache=caches[n]))
+        torch.cuda.synchronize()
+
+        def frame(fr):
+            sp.spirec_set_trajectory_cached(fr["p"].h, fr["cache"], fr["sub"])
+            sp.spirec_set_data_dev(fr["p"].h, fr["s_d"])
+            sp.spirec_solve_dev(fr["p"].h, None, iters, fr["x"], None)
+
+        for fr in frames:  # every plan's buffers and kernels in place before capture
+            frame(fr)
+        torch.cuda.synchronize()
+        cap = torch.cuda.Stream()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            fork = torch.cuda.Event()
+            fork.record(cap)
+            joins = []
+            for fr in frames:
+                fr["st"].wait_event(fork)
+                frame(fr)
+                e = torch.cuda.Event()
+                e.record(fr["st"])
+                joins.append(e)
+            for e in joins:
+                cap.wait_event(e)
+        results = []
+        for _ in range(2):
+            for fr in frames:
+                fr["x"].zero_()
+            torch.cuda.synchronize()
+            graph.replay()
+            torch.cuda.synchronize()
+            results.append([fr["x"].cpu().numpy() for fr in frames])
+        for fr in frames:
+            sp.spirec_sync(fr["p"].h)
+        del graph
+    finally:
+        for fr in frames:
+            fr["p"].close()
+        for c in caches.values():
+            sp.spirec_kcache_destroy(c)
+    reg = O.Reg(0.05, 0.05, 0.0, 0.05, O.PHI_HUBER)
+    for fr, x1, x2 in zip(frames, results[0], results[1]):
+        assert np.array_equal(x1, x2)
+        n = fr["N"]
+        xo, _, _ = O.solve(fr["kx"], fr["ky"], fr["s"], reg, np.zeros((n, n)), iters)
+        w = dict(N=n, kx=fr["kx"], ky=fr["ky"], s=fr["s"], reg=reg, iters=iters)
+        assert rel(x1, xo) < max(1e-3, iter_tol(w, prec)), (n, rel(x1, xo))
