@@ -196,7 +196,7 @@ void free_plan(spirec_plan p)
     void* bufs[] = {p->kxq, p->kyq, p->dflag, p->G, p->Chat, p->cwork, p->X, p->D, p->s, p->fsplit, p->ydir,
                     p->f[0], p->f[1], p->dbuf[0], p->dbuf[1], p->g, p->res, p->Td, p->tmp, p->twiddle,
                     p->part, p->scal, p->counters, p->Jdev, p->kpart, p->kstage, p->ystage, p->hqw,
-                    p->kx128, p->ky128, p->s_in};
+                    p->wpair, p->s_in};
     for (void* b : bufs)
         if (b) {
             if (p->stream) cudaFreeAsync(b, p->stream);
@@ -305,7 +305,6 @@ int build_trajectory(spirec_plan p, const double* kx_dev, const double* ky_dev, 
         if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
         if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
     }
-    if ((rc = launch_step128(p)) != SPIREC_OK) return rc;
     cudaEvent_t e;
     if ((rc = tstart(p, 0, &e)) != SPIREC_OK) return rc;
     if ((rc = launch_gram(p)) != SPIREC_OK) return rc;
@@ -681,8 +680,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     TRY(dalloc(p, &p->kxq, (size_t)L + 32));
     TRY(dalloc(p, &p->kyq, (size_t)L + 32));
     if (precision != SPIREC_FP32) {
-        TRY(dalloc(p, &p->kx128, (size_t)L + 32));
-        TRY(dalloc(p, &p->ky128, (size_t)L + 32));
+        TRY(dalloc(p, &p->wpair, (size_t)L + 32));
     }
     TRY(dalloc(p, &p->kstage, 2 * (size_t)L));
     TRY(dalloc(p, &p->dflag, 1));
@@ -720,10 +718,7 @@ int spirec_plan_create(spirec_plan* out, int32_t N, int64_t L, int32_t M, int32_
     // zero, so a contraction chunk that runs past L gets zero weights
     TRYCUDA(cudaMemsetAsync(p->s, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
     TRYCUDA(cudaMemsetAsync(p->ystage, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
-    if (p->kx128) {
-        TRYCUDA(cudaMemsetAsync(p->kx128, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
-        TRYCUDA(cudaMemsetAsync(p->ky128, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
-    }
+    if (p->wpair) TRYCUDA(cudaMemsetAsync(p->wpair, 0, sizeof(float2) * ((size_t)L + 32), p->stream));
     TRYCUDA(cudaMemsetAsync(p->scal, 0, S_NSCAL * sizeof(double), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[0], 0, NN * sizeof(float2), p->stream));
     TRYCUDA(cudaMemsetAsync(p->dbuf[1], 0, NN * sizeof(float2), p->stream));
@@ -906,10 +901,6 @@ int spirec_set_trajectory_cached(spirec_plan p, spirec_kcache c, const int32_t* 
         SPIREC_CK(cudaMemcpyAsync(p->kxq + pos, c->kxq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
         SPIREC_CK(cudaMemcpyAsync(p->kyq + pos, c->kyq + o, sizeof(int64_t) * Li, cudaMemcpyDeviceToDevice, p->stream));
         pos += Li;
-    }
-    {
-        const int rc1 = launch_step128(p);
-        if (rc1 != SPIREC_OK) return rc1;
     }
     const int64_t MM = (int64_t)p->M * p->M, NG2 = 2 * (int64_t)p->N * (2 * p->N - 1);
     int blocks = (int)((MM + 255) / 256);

@@ -122,10 +122,9 @@ struct spirec_plan_s {
     // trajectory, fixed point: k * 2^64 mod 2^64
     int64_t* kxq;
     int64_t* kyq;
-    // exp(+i 2 pi k 128) per sample (mixed precisions; 32 zero entries of
-    // padding): the factor between contraction columns 128 apart
-    float2* kx128;
-    float2* ky128;
+    // the weights of a paired tensor-core contraction (mixed precisions; 32
+    // zero entries of padding): w_l times the phase of the pairing's centre
+    float2* wpair;
     double* kstage;  // 2L: host trajectory staged on the device
     int* dflag;  // device error flag
 
@@ -233,7 +232,6 @@ int launch_cg_loop(spirec_plan p, int iters);
 
 // tensor-core contractions (FP16x3 / BF16x3)
 int launch_gram_tc(spirec_plan p);
-int launch_step128(spirec_plan p);  // kx128, ky128 from kxq, kyq
 int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x);
 int launch_forward_tc(spirec_plan p, const float2* x, float2* y);
 size_t fsplit_bytes_tc(int N, int precision);  // the forward's split-image buffer

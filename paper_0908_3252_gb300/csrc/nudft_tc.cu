@@ -1,14 +1,19 @@
 // nudft_tc.cu -- tensor-core (tcgen05, sm_103a) contractions of the exact
-// NUDFT: G (Eq. AnnMatG) and D = H^H s (Eq. AnnMatGD).
+// NUDFT: G (Eq. AnnMatG), D = H^H s (Eq. AnnMatGD) and the forward H f
+// (Eq. ModDirect).
 //
-// Both are complex GEMMs C[i][c] = sum_l A(l,i) B(l,c) of depth K = L whose
-// operands are phases generated on the fly (phase.cuh).  A tile is 128
-// complex rows x 256 complex columns; the accumulator (all 512 columns of
-// tensor memory, 128 lanes) holds Re C in columns 0..255 and Im C in
-// columns 256..511, built from four real MMAs (M = 128, N = 256) per K slice:
-//      Re C += Ar Br^T - Ai Bi^T      Im C += Ar Bi^T + Ai Br^T
-// (the minus by the instruction's negate-A bit), so each operand is stored
-// once, as [re | im] along K.
+// G and D are complex GEMMs C[i][c] = sum_l A(l,i) B(l,c) of depth K = L
+// whose operands are phases generated on the fly (phase.cuh).  The B
+// operand's phases come in conjugate pairs: exp(-i x) = conj(exp(i x)), so
+// output columns mirrored about a centre share one set of four real
+// products (PairGeom): per tile of 128 rows x 128 B columns, the four real
+// MMAs (M = 128, N = 128) per K slice
+//      P_ac = Ar Br^T   P_bd = Ai Bi^T   P_ad = Ar Bi^T   P_bc = Ai Br^T
+// fill four 128-column accumulators (all 512 columns of tensor memory), and
+// the drain forms both columns, (P_ac - P_bd, P_ad + P_bc) and (P_ac + P_bd,
+// P_bc - P_ad).  G needs its lags v and -v, D its columns on both sides of
+// the image centre: half the MMAs of forming every column on its own.  Each
+// operand is stored once, as [re | im] along K.
 //
 // Split precision: every operand value x is stored as x_hi = fp16(x) (or
 // bf16) and x_lo = fp16(x - x_hi); the products hi*hi + hi*lo + lo*hi feed
@@ -19,36 +24,36 @@
 // contiguous ranges, one per CTA and one CTA per SM, so every SM does the
 // same work whatever the tile count; a range may end in one tile and go on
 // in the next.  CTA c writes its partial of tile t to slot c + t (unique,
-// since both grow along the ranges) and k_reduce_tc adds the partials of
+// since both grow along the ranges) and k_reduce_pair adds the partials of
 // each tile in CTA order.
 //
 // Pipeline per CTA (544 threads):
 //   warps 0-15 producers: per stage of 32 samples, each thread forms the
-//              phasors of one A row and one B column (exact fixed-point phase,
-//              fast hardware sin/cos), splits them into the four operand tiles
-//              (A_hi, A_lo, B_hi, B_lo) in the 128-byte-swizzled K-major
-//              layout the MMA reads, then arrives on full[stage];
+//              phasors of one A row (times the weight, for D) and one B
+//              column (exact fixed-point phase, fast hardware sin/cos),
+//              splits them into the four operand tiles (A_hi, A_lo, B_hi,
+//              B_lo) in the 128-byte-swizzled K-major layout the MMA reads,
+//              then arrives on full[stage];
 //   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
-//              issues 24 tcgen05.mma (M = 128, N = 256, K = 16 each) and
+//              issues 24 tcgen05.mma (M = 128, N = 128, K = 16 each) and
 //              commits to empty[stage];
 //   warps 0-15 drain: at the end of every segment (at most SEG stages of one
-//              tile) the finished accumulator is read with tcgen05.ld and
-//              added to the CTA's partial tile in global memory by
-//              fire-and-forget vector reductions (red.global.add.v4.f32,
-//              round-to-nearest; the first segment of a tile stores), laid
-//              out so that a warp's 32 lanes cover 512 contiguous bytes.  The
-//              MMA waits for the drain (one accumulator).
+//              tile) the finished accumulators are read with tcgen05.ld and
+//              the paired outputs added to the CTA's partial tile in global
+//              memory by fire-and-forget vector reductions
+//              (red.global.add.v4.f32, round-to-nearest; the first segment
+//              of a tile stores), laid out so that a warp's 32 lanes cover
+//              512 contiguous bytes.  The MMA waits for the drain.
 // The tensor core's FP32 accumulation loses about one unit in the last place
 // per accumulation step (truncation-like, measured: 2.8e-4 relative after
 // 12k steps); draining every 32 stages (384 accumulation steps) bounds that
-// error: G and D at 512^2, L = 131072 come within 7.5e-6 of the FP64 sums
-// (4e-6 with 16-stage segments, at 8% more time: each drain stalls the MMA).  Two stages of
-// 96 KB buffer generation against the tensor core.  The
-// stage's 32 samples of the trajectory (and of the data, for D) arrive by TMA
-// bulk copy (cp.async.bulk) into a 4-deep shared-memory ring two stages
-// ahead, so the table builders never wait on global memory.
+// error.  Three stages of 64 KB buffer generation against the tensor core.
+// The stage's 32 samples of the trajectory (and of the weights, for D) arrive
+// by TMA bulk copy (cp.async.bulk) into an 8-deep shared-memory ring two
+// stages ahead, so the table builders never wait on global memory.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
-// error bit, lets the other roles run out, frees its TMEM and returns.
+// error bit, lets the other roles run out, waits for its own copies and
+// MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -71,13 +76,21 @@ constexpr int TC_TILE_FLOATS = 2 * TC_COLS * TC_ROWS;  // partial tile: 512 colu
 constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
-constexpr int TRAJ_RING = 4;
-constexpr uint32_t TRAJ_BUF = 4 * TC_KS * 8;  // ka, kb (int64), w and the kb step table (float2)
-constexpr uint32_t TRAJ_OFF = TC_STAGES * STAGE_BYTES;
-constexpr uint32_t BAR_OFF = TRAJ_OFF + TRAJ_RING * TRAJ_BUF;
-constexpr uint32_t SMEM_BYTES = BAR_OFF + 128 + 1024;  // + 1024 alignment slack
-static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
-static_assert(8 * (2 * TC_STAGES + 3 + TRAJ_RING) + 8 <= 128, "barrier area");
+// The paired contraction (G, D): tiles of 128 rows x 128 B columns, each B
+// column giving two output columns (see PairGeom), four accumulators of 128
+// TMEM columns; 64 KB stages, three deep; the trajectory (and weight) chunks
+// in an 8-deep ring, two stages ahead.
+constexpr int PG_COLS = 128;                                       // B columns per tile (MMA N)
+constexpr uint32_t PB_BYTES = PG_COLS * 128;                       // 128 rows x 64 halves
+constexpr uint32_t PG_STAGE_BYTES = 2 * A_BYTES + 2 * PB_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int PG_STAGES = 3;
+constexpr int PG_TRAJ_RING = 8;  // > PG_STAGES + 2: a slot is refilled only after every producer left it
+constexpr uint32_t PG_TRAJ_BUF = 3 * TC_KS * 8;  // ka, kb (int64), w' (float2)
+constexpr uint32_t PG_TRAJ_OFF = PG_STAGES * PG_STAGE_BYTES;
+constexpr uint32_t PG_BAR_OFF = PG_TRAJ_OFF + PG_TRAJ_RING * PG_TRAJ_BUF;
+constexpr uint32_t PG_SMEM = PG_BAR_OFF + 256 + 1024;  // + 1024 alignment slack
+static_assert(PG_SMEM <= 232448, "shared memory per CTA");
+static_assert(8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING) + 8 <= 256, "barrier area");
 constexpr int kMaxCtas = 152;       // CTAs of one contraction (one per SM)
 
 // Every pipeline wait is bounded by the launch's wait limit (a kernel
@@ -235,6 +248,19 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
+{
+    uint32_t r[8];
+    // load and wait in one statement: the registers are valid only after the wait
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
 {
     uint32_t r[16];
@@ -318,12 +344,6 @@ __device__ __forceinline__ float2 phasor_signed(int64_t kq, uint32_t a, float sc
     return make_float2(cs, sn);
 }
 
-// *p += v at the memory (round-to-nearest FP32 add, no reply).
-__device__ __forceinline__ void red_global(float* p, float v)
-{
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-
 __device__ __forceinline__ void st_global_v4(float* p, const float* v)
 {
     asm volatile("st.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3])
@@ -349,35 +369,79 @@ __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
     return ldexpf(1.f, -e);
 }
 
-// Adds (first: stores) the accumulator into the partial tile, laid out as
-// [column / 4][row][column % 4] (512 columns: real part at c, imaginary at
-// 256 + c; 128 rows): a thread's four consecutive columns are one 16-byte
-// vector, and the 32 lanes (consecutive rows) of a warp cover 512 contiguous
-// bytes.  Fire-and-forget vector reductions; a thread's adds to one address
-// come in program order, so the partial is the same sum on every run.
-__device__ __forceinline__ void drain_accumulator(uint32_t tacc, float* ptile, int warp, int lane,
-                                                  bool first)
+// Pairing of the output columns.  The B operand is a pure phase,
+// E(l, j) = exp(sb i2pi kb_l (j + half/2)), and its conjugate is the phase of
+// the mirrored column, so one set of four real products
+//      P_ac = Ar Br^T   P_bd = Ai Bi^T   P_ad = Ar Bi^T   P_bc = Ai Br^T
+// (A' = Ar + i Ai, E = Br + i Bi, summed over the samples) gives two output
+// columns:
+//      sum A' E       = (P_ac - P_bd) + i (P_ad + P_bc)   at column c+(j)
+//      sum A' conj(E) = (P_ac + P_bd) + i (P_bc - P_ad)   at column c-(j)
+// with c+-(j) = (C2 +- (2j + half)) / 2.  The weight of the original B operand
+// and the phase of the centre column move into A (A' = w' A,
+// w'_l = w_l exp(sb i2pi kb_l (C2 / 2 + ob)), k_pair_weights).
+//   G (Eq. AnnMatG): columns v + N - 1, centre v = 0 (C2 = 2N - 2, half 0),
+//     j = 0 .. N - 1: the lags v and -v, unweighted.
+//   D (Eq. AnnMatGD): columns m, centre (N - 1) / 2 (C2 = N - 1); for even N
+//     the offsets are half-integers (half 1, j = 0 .. N/2 - 1: m = N/2 + j
+//     and N/2 - 1 - j), for odd N integers (half 0, j = 0 .. (N - 1)/2).
+// A half-integer phase k (j + 1/2) is (k/2)(2j + 1): the fixed-point k
+// shifted right by one bit (an error of 2^-65 cycles times 2j + 1).
+struct PairGeom {
+    int R, C;   // output rows and columns
+    int C2;     // twice the centre column
+    int half;   // offsets j + 1/2
+    int J;      // B columns j = 0 .. J - 1
+};
+
+// Adds (first: stores) the four accumulators (P_ac, P_bd, P_ad, P_bc in TMEM
+// columns 0, 128, 256, 384) as the two paired outputs into the partial tile,
+// laid out as [column / 4][row][column % 4] (256 complex columns: c+(j) at
+// j, c-(j) at 128 + j; real parts in the first 256 float columns, imaginary
+// in the next 256; 128 rows): a thread's four consecutive columns are one
+// 16-byte vector, and a warp's 32 lanes (consecutive rows) cover 512
+// contiguous bytes.  Fire-and-forget vector reductions; a thread's adds to
+// one address come in program order, so the partial is the same sum on
+// every run.
+__device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int warp, int lane, bool first)
 {
     const int lbase = 32 * (warp & 3);
-    const int quarter = warp >> 2;
+    const int quarter = warp >> 2;  // columns j = 32 quarter .. + 31
     const int row = lbase + lane;
 #pragma unroll 1
-    for (int cc = 0; cc < 64; cc += 16) {
-        float re[16], im[16];
-        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(64 * quarter + cc);
-        tmem_ld16(ta, re);
-        tmem_ld16(ta + TC_COLS, im);
+    for (int cc = 0; cc < 32; cc += 8) {
+        float ac[8], bd[8], ad[8], bc[8];
+        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(32 * quarter + cc);
+        tmem_ld8(ta, ac);
+        tmem_ld8(ta + PG_COLS, bd);
+        tmem_ld8(ta + 2 * PG_COLS, ad);
+        tmem_ld8(ta + 3 * PG_COLS, bc);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int cg = (64 * quarter + cc) / 4 + v;  // column group of the real part
-            float* pr = ptile + ((size_t)cg * TC_ROWS + row) * 4;
-            float* pi = ptile + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4;
+        for (int h = 0; h < 2; ++h) {
+            float pre[4], pim[4], mre[4], mim[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = 4 * h + e;
+                pre[e] = ac[x] - bd[x];
+                pim[e] = ad[x] + bc[x];
+                mre[e] = ac[x] + bd[x];
+                mim[e] = bc[x] - ad[x];
+            }
+            const int cg = (32 * quarter + cc) / 4 + h;  // column group of c+; c- is 32 groups further
+            float* p_re = ptile + ((size_t)cg * TC_ROWS + row) * 4;
+            float* p_im = ptile + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4;
+            float* m_re = ptile + ((size_t)(PG_COLS / 4 + cg) * TC_ROWS + row) * 4;
+            float* m_im = ptile + ((size_t)(TC_COLS / 4 + PG_COLS / 4 + cg) * TC_ROWS + row) * 4;
             if (first) {
-                st_global_v4(pr, re + 4 * v);
-                st_global_v4(pi, im + 4 * v);
+                st_global_v4(p_re, pre);
+                st_global_v4(p_im, pim);
+                st_global_v4(m_re, mre);
+                st_global_v4(m_im, mim);
             } else {
-                red_global_v4(pr, re + 4 * v);
-                red_global_v4(pi, im + 4 * v);
+                red_global_v4(p_re, pre);
+                red_global_v4(p_im, pim);
+                red_global_v4(m_re, mre);
+                red_global_v4(m_im, mim);
             }
         }
     }
@@ -420,28 +484,29 @@ struct SegWalk {
 };
 
 // Partials of CTA blockIdx.x over its units [u0, u1) (unit = tile * K +
-// chunk of 32 samples; tile = row tile * tilesC + column tile):
-//   A(l,i) = exp(sa i2pi ka_l (i + oa)),  B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
+// chunk of 32 samples; tile = row tile * tilesC + column tile of 128 j):
+//   A'(l,i) = w'_l exp(sa i2pi ka_l (i + oa)) (w' = 1 unweighted),
+//   E(l,j)  = exp(sb i2pi kb_l (j + half/2)),
+// the four real products of each into the four accumulators.
 template <bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ kbs,
-                const float2* __restrict__ w, const unsigned* __restrict__ amax2, int64_t L, int tilesC,
-                int oa, int ob, int sa, int sb, int64_t K, int64_t U, float* __restrict__ part, int* err,
-                unsigned long long wait_ns, int stall)
+k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ w,
+               const unsigned* __restrict__ amax2, int64_t L, int tilesC, int oa, int sa, int sb, int half, int J,
+               int64_t K, int64_t U, float* __restrict__ part, int* err, unsigned long long wait_ns, int stall)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_full = sbase + BAR_OFF;                // stage filled
-    const uint32_t bar_empty = bar_full + 8 * TC_STAGES;      // stage consumed
-    const uint32_t bar_acc_full = bar_empty + 8 * TC_STAGES;  // segment accumulated
+    const uint32_t bar_full = sbase + PG_BAR_OFF;             // stage filled
+    const uint32_t bar_empty = bar_full + 8 * PG_STAGES;      // stage consumed
+    const uint32_t bar_acc_full = bar_empty + 8 * PG_STAGES;  // segment accumulated
     const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained
-    const uint32_t bar_traj = bar_acc_empty + 8;              // TRAJ_RING: trajectory chunk landed
-    const uint32_t bar_drain = bar_traj + 8 * TRAJ_RING;      // every MMA issued has completed
-    const uint32_t misc = BAR_OFF + 8 * (2 * TC_STAGES + 3 + TRAJ_RING);
+    const uint32_t bar_traj = bar_acc_empty + 8;              // PG_TRAJ_RING: trajectory chunk landed
+    const uint32_t bar_drain = bar_traj + 8 * PG_TRAJ_RING;      // every MMA issued has completed
+    const uint32_t misc = PG_BAR_OFF + 8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
-    const uint32_t traj_s = sbase + TRAJ_OFF;
+    const uint32_t traj_s = sbase + PG_TRAJ_OFF;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -450,13 +515,13 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
     const int n = (int)(unit_start(blockIdx.x + 1, U, P) - u0);
 
     if (tid == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < PG_STAGES; ++i) {
             mbar_init(bar_full + 8 * i, TC_PRODUCERS);
             mbar_init(bar_empty + 8 * i, 1);
         }
         mbar_init(bar_acc_full, 1);
         mbar_init(bar_acc_empty, TC_PRODUCERS);
-        for (int r = 0; r < TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
+        for (int r = 0; r < PG_TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
@@ -470,8 +535,8 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
     if (warp < TC_PRODUCERS / 32) {
         // ------------------------------------------------ producers
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
-        // TMA feed of the trajectory (and data) chunk of stage `it` into ring
-        // slot it % 4; stages are issued in order, kci is the chunk of the next
+        // TMA feed of the trajectory (and weight) chunk of stage `it` into
+        // ring slot it % 4; stages are issued in order, kci is the chunk of the next
         int64_t kci = u0 % K;
         int issued = 0;  // stages whose chunk thread 0 has requested
         auto issue_traj = [&](int it) {
@@ -481,14 +546,13 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             // the whole chunk, also past L: the plan's sample arrays have 32
             // entries of padding, the weights' padding is zero
             const uint32_t bytes = (uint32_t)TC_KS * 8;
-            const uint32_t buf = traj_s + (uint32_t)(it % TRAJ_RING) * TRAJ_BUF;
-            const uint32_t bar = bar_traj + 8 * (it % TRAJ_RING);
+            const uint32_t buf = traj_s + (uint32_t)(it % PG_TRAJ_RING) * PG_TRAJ_BUF;
+            const uint32_t bar = bar_traj + 8 * (it % PG_TRAJ_RING);
             fence_proxy_async();
-            mbar_expect_tx(bar, (WEIGHTED ? 4u : 3u) * bytes);
+            mbar_expect_tx(bar, (WEIGHTED ? 3u : 2u) * bytes);
             bulk_g2s(buf, ka + l0, bytes, bar);
             bulk_g2s(buf + TC_KS * 8, kb + l0, bytes, bar);
             if (WEIGHTED) bulk_g2s(buf + 2 * TC_KS * 8, w + l0, bytes, bar);
-            bulk_g2s(buf + 3 * TC_KS * 8, kbs + l0, bytes, bar);
         };
         if (tid == 0)
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
@@ -498,21 +562,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
         int64_t dtile = 0;  // tile of the segment being accumulated
         bool dfirst = true;
         for (int it = 0; it < n; ++it) {
-            const int s = it % TC_STAGES;
-            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            const int s = it % PG_STAGES;
+            const uint32_t use = (uint32_t)(it / PG_STAGES);
             // stage s is free once the MMA has consumed its previous use.
             // Each warp waits for that itself (no producer-wide barrier), so
             // warps drift apart by at most the ring depth: a warp past the
             // wait for stage it knows every producer has finished stage
-            // it - 2, whose trajectory slot the TMA of stage it + 2 reuses.
-            if (lane == 0 && it >= TC_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
+            // it - PG_STAGES, whose trajectory slot the TMA of stage it + 2
+            // reuses (it + 2 - PG_TRAJ_RING < it - PG_STAGES + 1).
+            if (lane == 0 && it >= PG_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
             __syncwarp();
             if (__any_sync(0xffffffffu, *abort_flag != 0)) break;  // the warp stops as one
             if (tid == 0 && it + 2 < n) issue_traj(it + 2);
-            if (!mbar_wait(bar_traj + 8 * (it % TRAJ_RING), (uint32_t)(it / TRAJ_RING) & 1, wait_ns)) {
+            if (!mbar_wait(bar_traj + 8 * (it % PG_TRAJ_RING), (uint32_t)(it / PG_TRAJ_RING) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
@@ -522,23 +587,26 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
                 ++trow;
             }
             const int64_t l0 = sw.kc * TC_KS;
-            const int i0 = trow * TC_ROWS, c0 = tcol * TC_COLS;
-            const uint8_t* tbuf = smem + TRAJ_OFF + (it % TRAJ_RING) * TRAJ_BUF;
+            const int i0 = trow * TC_ROWS, j0 = tcol * PG_COLS;
+            const uint8_t* tbuf = smem + PG_TRAJ_OFF + (it % PG_TRAJ_RING) * PG_TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
-            const float2* q_s = reinterpret_cast<const float2*>(tbuf + 3 * TC_KS * 8);
-            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
-            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
-            // the signed index s j = +-a of the row (column) and the angle
-            // scale carrying its sign
+            const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + PB_BYTES;
             constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
+            // A row r: the signed index sa (i + oa) = +-aa, its sign in the scale
             const int sja = sa * (i0 + r + oa);
             const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
             const float sca = sja < 0 ? -kRev : kRev;
-            // samples past L (only in a tile's last chunk): B is zero there,
-            // through the zero padding of the weights, or the mask below when
-            // unweighted; A then multiplies zeros and needs no mask
+            // B column r: j = j0 + r (zero past J), the count 2j + 1 on the
+            // halved k for half-integer offsets
+            const int jb = j0 + r;
+            const uint32_t ab = half ? (uint32_t)(2 * jb + 1) : (uint32_t)jb;
+            const float scb = sb < 0 ? -kRev : kRev;
+            // samples past L (only in a tile's last chunk): A is zero there
+            // through the zero padding of the weights, or B by the mask below
+            // when unweighted
             const int nvalid = l0 + TC_KS > L ? (int)(L - l0) : TC_KS;
             float re[8], im[8];
             uint4 rh, rl, ih, il;
@@ -546,7 +614,13 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int l = 8 * g + e;
-                const float2 v = phasor_signed(ka_s[l], aa, sca);
+                float2 v = phasor_signed(ka_s[l], aa, sca);
+                if (WEIGHTED) {
+                    float2 ww = w_s[l];
+                    ww.x *= wmul;
+                    ww.y *= wmul;
+                    v = cmul(v, ww);
+                }
                 re[e] = v.x;
                 im[e] = v.y;
             }
@@ -556,49 +630,22 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             st_shared_v4(aH + sw128(r, 4 + g), ih);
             st_shared_v4(aL + sw128(r, g), rl);
             st_shared_v4(aL + sw128(r, 4 + g), il);
-            // B columns r and 128 + r: [Br | Bi]; column 128 + r is column r
-            // times exp(i 2 pi kb (s 128)), the sample's step table (conjugated
-            // for s < 0), so it needs no phase of its own and no weight
-            {
-                const int sjb = sb * (c0 + r + ob);
-                const uint32_t ab = (uint32_t)(sjb < 0 ? -sjb : sjb);
-                const float scb = sjb < 0 ? -kRev : kRev;
-                float2 v[8];
+            // B column r: [Br | Bi]
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int l = 8 * g + e;
-                    v[e] = phasor_signed(kb_s[l], ab, scb);
-                    if (WEIGHTED) {
-                        float2 ww = w_s[l];
-                        ww.x *= wmul;
-                        ww.y *= wmul;
-                        v[e] = cmul(v[e], ww);
-                    }
-                    if (!WEIGHTED && l >= nvalid) v[e] = make_float2(0.f, 0.f);
-                    re[e] = v[e].x;
-                    im[e] = v[e].y;
-                }
-                split8<BF16>(re, rh, rl);
-                split8<BF16>(im, ih, il);
-                st_shared_v4(bH + sw128(r, g), rh);
-                st_shared_v4(bH + sw128(r, 4 + g), ih);
-                st_shared_v4(bL + sw128(r, g), rl);
-                st_shared_v4(bL + sw128(r, 4 + g), il);
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    float2 q = q_s[8 * g + e];
-                    if (sb < 0) q.y = -q.y;
-                    const float2 u = cmul(v[e], q);
-                    re[e] = u.x;
-                    im[e] = u.y;
-                }
-                split8<BF16>(re, rh, rl);
-                split8<BF16>(im, ih, il);
-                st_shared_v4(bH + sw128(r + 128, g), rh);
-                st_shared_v4(bH + sw128(r + 128, 4 + g), ih);
-                st_shared_v4(bL + sw128(r + 128, g), rl);
-                st_shared_v4(bL + sw128(r + 128, 4 + g), il);
+            for (int e = 0; e < 8; ++e) {
+                const int l = 8 * g + e;
+                const int64_t kq = half ? (kb_s[l] >> 1) : kb_s[l];
+                float2 v = phasor_signed(kq, ab, scb);
+                if ((!WEIGHTED && l >= nvalid) || jb >= J) v = make_float2(0.f, 0.f);
+                re[e] = v.x;
+                im[e] = v.y;
             }
+            split8<BF16>(re, rh, rl);
+            split8<BF16>(im, ih, il);
+            st_shared_v4(bH + sw128(r, g), rh);
+            st_shared_v4(bH + sw128(r, 4 + g), ih);
+            st_shared_v4(bL + sw128(r, g), rl);
+            st_shared_v4(bL + sw128(r, 4 + g), il);
             fence_proxy_async();
             mbar_arrive(bar_full + 8 * s);
             if (sw.pos == 0) {
@@ -612,7 +659,7 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
                     }
                     __syncwarp();  // the tensor-memory loads are warp-collective
                     tc_fence_after();
-                    drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
+                    drain_pairs(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
                     tc_fence_before();
                     mbar_arrive(bar_acc_empty);
                 }
@@ -627,33 +674,31 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             if (!landed) atomicOr(err, kErrTimeout);
             if (__all_sync(0xffffffffu, landed)) {
                 tc_fence_after();
-                drain_accumulator(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
+                drain_pairs(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
             }
         }
         // every requested chunk has landed before the CTA goes (at most one
-        // request per ring slot is open: the last TRAJ_RING stages)
+        // request per ring slot is open: the last PG_TRAJ_RING stages)
         if (tid == 0)
-            for (int j = issued > TRAJ_RING ? issued - TRAJ_RING : 0; j < issued; ++j)
-                if (!mbar_wait(bar_traj + 8 * (j % TRAJ_RING), (uint32_t)(j / TRAJ_RING) & 1, kDrainNs))
+            for (int j = issued > PG_TRAJ_RING ? issued - PG_TRAJ_RING : 0; j < issued; ++j)
+                if (!mbar_wait(bar_traj + 8 * (j % PG_TRAJ_RING), (uint32_t)(j / PG_TRAJ_RING) & 1, kDrainNs))
                     atomicOr(err, kErrTimeout);
     } else if (lane == 0) {
         // ------------------------------------------------ MMA issuer
-        // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and 10,
-        // negate A at bit 13, both K-major, N = 256 (N>>3 at bit 17), M = 128
-        // (M>>4 at bit 24).
+        // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and
+        // 10, both K-major, N = 128 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
         const uint32_t fmt = BF16 ? 1u : 0u;
-        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
-        const uint32_t idesc_neg = idesc | (1u << 13);
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
         SegWalk sw{u0, K};
         int issued = 0;  // stages whose MMAs were issued
         // a test's injected stall: nothing completes bar_drain before this
         // thread's own commit, so the bounded wait runs out and no MMA issues
         if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
+        const uint32_t t_ac = tmem, t_bd = tmem + PG_COLS, t_ad = tmem + 2 * PG_COLS, t_bc = tmem + 3 * PG_COLS;
         for (int it = 0; !stall && it < n; ++it) {
-            const int s = it % TC_STAGES;
-            const uint32_t use = (uint32_t)(it / TC_STAGES);
+            const int s = it % PG_STAGES;
+            const uint32_t use = (uint32_t)(it / PG_STAGES);
             sw.step(it);
-            const uint32_t tre = tmem, tim = tmem + TC_COLS;
             if (sw.pos == 0 && sw.seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(sw.seg - 1) & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
                 break;
@@ -664,8 +709,8 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
             }
             ++issued;
             tc_fence_after();
-            const uint32_t st = sbase + (uint32_t)s * STAGE_BYTES;
-            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + B_BYTES;
+            const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
+            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + PB_BYTES;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const uint32_t oR = 32u * kk, oI = 64u + 32u * kk;  // 16 samples of re, of im
@@ -673,10 +718,10 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
                 for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
                     const uint32_t A = q == 2 ? aL : aH, B = q == 1 ? bL : bH;
                     const uint32_t acc = (sw.pos > 0 || kk > 0 || q > 0) ? 1u : 0u;
-                    mma_f16(tre, sdesc(A + oR), sdesc(B + oR), idesc, acc);
-                    mma_f16(tre, sdesc(A + oI), sdesc(B + oI), idesc_neg, 1u);
-                    mma_f16(tim, sdesc(A + oR), sdesc(B + oI), idesc, acc);
-                    mma_f16(tim, sdesc(A + oI), sdesc(B + oR), idesc, 1u);
+                    mma_f16(t_ac, sdesc(A + oR), sdesc(B + oR), idesc, acc);
+                    mma_f16(t_bd, sdesc(A + oI), sdesc(B + oI), idesc, acc);
+                    mma_f16(t_ad, sdesc(A + oR), sdesc(B + oI), idesc, acc);
+                    mma_f16(t_bc, sdesc(A + oI), sdesc(B + oR), idesc, acc);
                 }
             }
             mma_commit(bar_empty + 8 * s);
@@ -698,28 +743,33 @@ k_tc_phase_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, 
     }
 }
 
-// out[i][c] = scale * 2^e * (sum of the partials of tile(i, c) in CTA order);
-// 2^e undoes the weight scaling.  The CTAs holding units of tile t are
-// c_lo..c_hi, the last CTAs whose ranges start at or before the tile's first
-// and last unit; CTA c keeps its partial of tile t in slot c + t.  A block
-// sums a 32 x 32 patch: each thread reads four columns of one row as a
-// vector, the patch turns in shared memory, writes run along the rows of out.
-__global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
-                                                   int R, int C, int tilesC, float scale,
-                                                   const unsigned* __restrict__ amax2, float2* __restrict__ out)
+// out[i][c] = scale * 2^e * (sum of the partials of the tile holding output
+// (i, c) in CTA order); 2^e undoes the weight scaling.  A block sums a patch
+// of 32 rows x 32 columns of a partial tile (column q < 128: j = 128 tcol + q
+// at c+(j); q >= 128: j = 128 tcol + q - 128 at c-(j)).  The CTAs holding
+// units of tile t are c_lo..c_hi, the last CTAs whose ranges start at or
+// before the tile's first and last unit; CTA c keeps its partial of tile t in
+// slot c + t.  Each thread reads four columns of one row as a vector, the
+// patch turns in shared memory, and writes run along the rows of out (the
+// mirrored half in descending columns).  c-(0) = c+(0) for integer offsets
+// and is written once.
+__global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
+                                                     PairGeom pg, int tilesC, float scale,
+                                                     const unsigned* __restrict__ amax2, float2* __restrict__ out)
 {
     __shared__ float2 patch[32][33];
     float sc = scale;
     if (amax2) sc = scale / weight_scale_inv(amax2);
-    const int i0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int i0 = blockIdx.y * 32;
+    const int tcol = blockIdx.x >> 3, q0 = (blockIdx.x & 7) * 32;  // tile column, first partial column
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int64_t t = (int64_t)(i0 / TC_ROWS) * tilesC + c0 / TC_COLS;
+    const int64_t t = (int64_t)(i0 / TC_ROWS) * tilesC + tcol;
     const int64_t c_lo = ((t * K + 1) * P - 1) / U;
     const int64_t c_hi = ((t + 1) * K * P - 1) / U;
     const int row = (i0 % TC_ROWS) + tx;
     {
-        // thread (tx, ty): row tx of the patch, columns 4 ty .. 4 ty + 3
-        const int cg = ((c0 % TC_COLS) >> 2) + ty;
+        // thread (tx, ty): row tx of the patch, partial columns q0 + 4 ty .. + 3
+        const int cg = (q0 >> 2) + ty;
         float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = ar;
         for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
             if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
@@ -735,10 +785,29 @@ __global__ void __launch_bounds__(256) k_reduce_tc(const float* __restrict__ par
         patch[4 * ty + 3][tx] = make_float2(ar.w * sc, ai.w * sc);
     }
     __syncthreads();
+    const int q = q0 + tx;
+    const bool mirrored = q >= PG_COLS;
+    const int j = tcol * PG_COLS + (mirrored ? q - PG_COLS : q);
+    const int off = 2 * j + pg.half;
+    const int c = mirrored ? (pg.C2 - off) / 2 : (pg.C2 + off) / 2;
+    const bool ok = j < pg.J && c >= 0 && c < pg.C && !(mirrored && off == 0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = i0 + ty + 8 * j, c = c0 + tx;
-        if (i < R && c < C) out[(int64_t)i * C + c] = patch[tx][ty + 8 * j];
+    for (int k = 0; k < 4; ++k) {
+        const int i = i0 + ty + 8 * k;
+        if (ok && i < pg.R) out[(int64_t)i * pg.C + c] = patch[tx][ty + 8 * k];
+    }
+}
+
+// w'_l = w_l exp(sb i2pi (kb_l / 2) shift2) for l < L (the weight of the
+// original B operand and the phase of the pairing's centre column, shift2 =
+// C2 + 2 ob); the plan's buffer keeps its zero padding past L.
+__global__ void k_pair_weights(const float2* __restrict__ w, const int64_t* __restrict__ kb, int64_t L, int sb,
+                               int shift2, float2* __restrict__ wp)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x) {
+        float2 e = phasor_q(kb[l] >> 1, shift2);
+        if (sb < 0) e.y = -e.y;
+        wp[l] = cmul(w[l], e);
     }
 }
 
@@ -978,7 +1047,7 @@ k_tc_forward(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, c
         const uint32_t idesc_neg = idesc | (1u << 13);
         const uint32_t tre = tmem, tim = tmem + TC_COLS;
         int issued = 0;  // stages whose MMAs were issued
-        // a test's injected stall (as in k_tc_phase_gemm)
+        // a test's injected stall (as in k_tc_pair_gemm)
         if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
         for (int it = 0; !stall && it < n; ++it) {
             const int s = it % TC_STAGES;
@@ -1043,18 +1112,35 @@ __global__ void k_absmax2(const float2* __restrict__ y, int64_t n, unsigned* ama
     if ((threadIdx.x & 31) == 0 && isfinite(m)) atomicMax(amax2, __float_as_uint(m));
 }
 
-// Output rows and columns of the two contractions: G is N x (2N - 1), D N x N.
-void tc_shape(const spirec_plan_s* p, int knob, int* R, int* C)
+// The pairing geometry of G (knob SPIREC_KNOB_GRAM_SPLIT) or of D and every
+// other H^H y (SPIREC_KNOB_ADJOINT_SPLIT): see PairGeom.
+PairGeom pair_geom(const spirec_plan_s* p, int knob)
 {
-    *R = p->N;
-    *C = knob == SPIREC_KNOB_GRAM_SPLIT ? 2 * p->N - 1 : p->N;
+    const int N = p->N;
+    PairGeom g{};
+    g.R = N;
+    if (knob == SPIREC_KNOB_GRAM_SPLIT) {
+        g.C = 2 * N - 1;
+        g.C2 = 2 * N - 2;
+        g.half = 0;
+        g.J = N;
+    } else {
+        g.C = N;
+        g.C2 = N - 1;
+        g.half = (N % 2 == 0) ? 1 : 0;
+        g.J = g.half ? N / 2 : (N + 1) / 2;
+    }
+    return g;
 }
 
-int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, const float2* w, int R,
-                  int C, int oa, int ob, int sa, int sb, float scale, float2* out)
+// The paired contraction out[i][c] = scale sum_l A(l,i) B(l,c) with
+// A(l,i) = exp(sa i2pi ka_l (i + oa)), B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
+int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, const float2* w, int oa, int ob,
+                 int sa, int sb, float scale, float2* out)
 {
+    const PairGeom pg = pair_geom(p, knob);
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int tilesR = (R + TC_ROWS - 1) / TC_ROWS, tilesC = (C + TC_COLS - 1) / TC_COLS;
+    const int tilesR = (pg.R + TC_ROWS - 1) / TC_ROWS, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
     const int64_t T = (int64_t)tilesR * tilesC;
     const int64_t U = T * K;
     int sms = 0, rc;
@@ -1062,45 +1148,45 @@ int tc_phase_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb,
     int64_t P = 0;
     if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
     unsigned* amax = nullptr;
-    if (w && w != p->s && w != p->ystage) {
-        // the kernel reads padded, plan-owned sample arrays
-        SPIREC_CK(cudaMemcpyAsync(p->ystage, w, sizeof(float2) * p->L, cudaMemcpyDeviceToDevice, p->stream));
-        w = p->ystage;
+    const int shift2 = pg.C2 + 2 * ob;  // twice the phase offset of the centre column
+    if (!w && shift2 != 0) {
+        set_error("an unweighted paired contraction needs its centre at phase zero");
+        return SPIREC_EUNSUPPORTED;
     }
     if (w) {
-        amax = p->counters + C_AMAX;
-        SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
+        // w' = w exp(sb i2pi kb shift2 / 2) into the plan's padded buffer
+        // (its padding past L stays zero), and max |w'|^2 for the scaling
         int blocks = (int)((p->L + 255) / 256);
         if (blocks > 4 * kMaxCtas) blocks = 4 * kMaxCtas;
+        k_pair_weights<<<blocks, 256, 0, p->stream>>>(w, kb, p->L, sb, shift2, p->wpair);
+        SPIREC_CK(cudaGetLastError());
+        w = p->wpair;
+        amax = p->counters + C_AMAX;
+        SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
         k_absmax2<<<blocks, 256, 0, p->stream>>>(w, p->L, amax);
         SPIREC_CK(cudaGetLastError());
-        p->launches += 1;
+        p->launches += 2;
     }
     const dim3 grid((unsigned)P);
     float* part = p->kpart;
-    const float2* kbs = kb == p->kxq ? p->kx128 : p->ky128;  // the B side's step table
-    if (!kbs) {
-        set_error("plan has no step tables for the tensor-core contraction");
-        return SPIREC_ESTATE;
-    }
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
     const unsigned long long wait_ns = wait_limit_ns();
     const int stall = injected_stall(kStallContraction) ? 1 : 0;
     if (bf16 && w)
-        k_tc_phase_gemm<true, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
+        k_tc_pair_gemm<true, true><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
+            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
     else if (bf16)
-        k_tc_phase_gemm<true, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
+        k_tc_pair_gemm<true, false><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
+            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
     else if (w)
-        k_tc_phase_gemm<false, true><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
+        k_tc_pair_gemm<false, true><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
+            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
     else
-        k_tc_phase_gemm<false, false><<<grid, TC_THREADS, SMEM_BYTES, p->stream>>>(
-            ka, kb, kbs, w, amax, p->L, tilesC, oa, ob, sa, sb, K, U, part, p->dflag, wait_ns, stall);
+        k_tc_pair_gemm<false, false><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
+            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
     SPIREC_CK(cudaGetLastError());
-    const dim3 rgrid((unsigned)((C + 31) / 32), (unsigned)((R + 31) / 32));
-    k_reduce_tc<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, R, C, tilesC, scale, amax, out);
+    const dim3 rgrid((unsigned)(tilesC * 8), (unsigned)((pg.R + 31) / 32));
+    k_reduce_pair<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, pg, tilesC, scale, amax, out);
     SPIREC_CK(cudaGetLastError());
     p->launches += 2;
     return SPIREC_OK;
@@ -1158,32 +1244,6 @@ int launch_forward_tc(spirec_plan p, const float2* x, float2* yout)
     return SPIREC_OK;
 }
 
-// exp(+i 2 pi k 128) for both trajectory coordinates: the top 32 bits of
-// kq * 128 mod 2^64 are bits 25..56 of kq.
-__global__ void k_step128(const int64_t* __restrict__ kxq, const int64_t* __restrict__ kyq, int64_t L,
-                          float2* __restrict__ kx128, float2* __restrict__ ky128)
-{
-    constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x) {
-        float sn, cs;
-        __sincosf((float)(int)(uint32_t)(((uint64_t)kxq[l] << 7) >> 32) * kRev, &sn, &cs);
-        kx128[l] = make_float2(cs, sn);
-        __sincosf((float)(int)(uint32_t)(((uint64_t)kyq[l] << 7) >> 32) * kRev, &sn, &cs);
-        ky128[l] = make_float2(cs, sn);
-    }
-}
-
-int launch_step128(spirec_plan p)
-{
-    if (!p->kx128) return SPIREC_OK;  // FP32 plans do not use them
-    int blocks = (int)((p->L + 255) / 256);
-    if (blocks > 8 * kMaxCtas) blocks = 8 * kMaxCtas;
-    k_step128<<<blocks, 256, 0, p->stream>>>(p->kxq, p->kyq, p->L, p->kx128, p->ky128);
-    SPIREC_CK(cudaGetLastError());
-    p->launches += 1;
-    return SPIREC_OK;
-}
-
 size_t fsplit_bytes_tc(int N, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
@@ -1194,17 +1254,17 @@ size_t fsplit_bytes_tc(int N, int precision)
 size_t kpart_floats_tc(int N, int64_t, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
-    // slots c + t < P + T; G (N x 2N-1) has the most tiles
-    const size_t T = (size_t)((N + TC_ROWS - 1) / TC_ROWS) * (size_t)((2 * N - 1 + TC_COLS - 1) / TC_COLS);
+    // slots c + t < P + T; G (N rows, N paired columns) has the most tiles
+    const size_t T = (size_t)((N + TC_ROWS - 1) / TC_ROWS) * (size_t)((N + PG_COLS - 1) / PG_COLS);
     return ((size_t)kMaxCtas + T) * TC_TILE_FLOATS;
 }
 
 int tc_setup_attributes()
 {
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_phase_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
     return SPIREC_OK;
@@ -1213,14 +1273,16 @@ int tc_setup_attributes()
 int launch_gram_tc(spirec_plan p)
 {
     const int N = p->N;
-    return tc_phase_gemm(p, SPIREC_KNOB_GRAM_SPLIT, p->kxq, p->kyq, nullptr, N, 2 * N - 1, 0, -(N - 1), +1, +1,
-                         1.0f / ((float)N * (float)N), p->G);
+    // G[u][v+N-1] = (1/N^2) sum_l exp(i2pi kx_l u) exp(i2pi ky_l v), v = +-j
+    return tc_pair_gemm(p, SPIREC_KNOB_GRAM_SPLIT, p->kxq, p->kyq, nullptr, 0, -(N - 1), +1, +1,
+                        1.0f / ((float)N * (float)N), p->G);
 }
 
 int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
 {
     const int N = p->N;
-    return tc_phase_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, N, N, 0, 0, -1, -1, 1.0f / (float)N, x);
+    // x[n][m] = (1/N) sum_l exp(-i2pi ky_l n) y_l exp(-i2pi kx_l m)
+    return tc_pair_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, 0, 0, -1, -1, 1.0f / (float)N, x);
 }
 
 // The stream-K CTA count: the tuned value of the shape, else one CTA per SM
@@ -1228,10 +1290,9 @@ int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
 // c + t < P + T must fit the split-K buffer.
 int tc_ctas(spirec_plan p, int knob, int sms, int64_t* out)
 {
-    int R = 0, C = 0;
-    tc_shape(p, knob, &R, &C);
+    const PairGeom pg = pair_geom(p, knob);
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int64_t T = (int64_t)((R + TC_ROWS - 1) / TC_ROWS) * ((C + TC_COLS - 1) / TC_COLS);
+    const int64_t T = (int64_t)((pg.R + TC_ROWS - 1) / TC_ROWS) * ((pg.J + PG_COLS - 1) / PG_COLS);
     const int64_t U = T * K;
     int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
     const int tuned = tune_lookup(knob, p, sms);

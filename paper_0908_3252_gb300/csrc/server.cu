@@ -99,7 +99,7 @@ size_t plan_bytes(int N, int64_t L, int M, int precision)
     const size_t NN = (size_t)N * N;
     size_t b = 0;
     b += 2 * ((size_t)L + 32) * 8;              // fixed-point trajectory
-    if (precision != SPIREC_FP32) b += 2 * ((size_t)L + 32) * 8;  // its step tables
+    if (precision != SPIREC_FP32) b += ((size_t)L + 32) * 8;  // the paired contractions' weights
     b += 2 * (size_t)L * 8;                      // staging
     b += (size_t)N * (2 * N - 1) * 8;            // G
     b += (size_t)M * M * 4 + (size_t)M * M * 8;  // spectrum + work
