@@ -6,14 +6,18 @@
 // whose operands are phases generated on the fly (phase.cuh).  The B
 // operand's phases come in conjugate pairs: exp(-i x) = conj(exp(i x)), so
 // output columns mirrored about a centre share one set of four real
-// products (PairGeom): per tile of 128 rows x 128 B columns, the four real
-// MMAs (M = 128, N = 128) per K slice
+// products (PairGeom)
 //      P_ac = Ar Br^T   P_bd = Ai Bi^T   P_ad = Ar Bi^T   P_bc = Ai Br^T
-// fill four 128-column accumulators (all 512 columns of tensor memory), and
-// the drain forms both columns, (P_ac - P_bd, P_ad + P_bc) and (P_ac + P_bd,
-// P_bc - P_ad).  G needs its lags v and -v, D its columns on both sides of
-// the image centre: half the MMAs of forming every column on its own.  Each
-// operand is stored once, as [re | im] along K.
+// and the drain forms both columns, (P_ac - P_bd, P_ad + P_bc) and (P_ac +
+// P_bd, P_bc - P_ad).  G needs its lags v and -v, D its columns on both sides
+// of the image centre: half the MMAs of forming every column on its own.
+// Per tile of 128 rows x 128 B columns, B is stored once as a stacked
+// operand of 256 rows [Br ; Bi], so two MMAs (M = 128, N = 256) per K slice,
+// Ar [Br ; Bi]^T = [P_ac | P_ad] and Ai [Br ; Bi]^T = [P_bc | P_bd], fill all
+// 512 columns of tensor memory.  N = 256 reads 12 KB of shared memory per
+// 128 x 256 x 16 product where two N = 128 MMAs read 16 KB: the tensor
+// core's operand reads and the producers' stores share the shared-memory
+// data path, which bounds this kernel.
 //
 // Split precision: every operand value x is stored as x_hi = fp16(x) (or
 // bf16) and x_lo = fp16(x - x_hi); the products hi*hi + hi*lo + lo*hi feed
@@ -28,14 +32,16 @@
 // each tile in CTA order.
 //
 // Pipeline per CTA (544 threads):
-//   warps 0-15 producers: per stage of 32 samples, each thread forms the
-//              phasors of one A row (times the weight, for D) and one B
-//              column (exact fixed-point phase, fast hardware sin/cos),
-//              splits them into the four operand tiles (A_hi, A_lo, B_hi,
-//              B_lo) in the 128-byte-swizzled K-major layout the MMA reads,
-//              then arrives on full[stage];
+//   warps 0-15 producers: per stage of 32 samples, each thread of warps 0-7
+//              forms the phasors of two A rows (times the weight, for D) and
+//              each thread of warps 8-15 those of two B columns, for 8
+//              samples (exact fixed-point phase, fast hardware sin/cos), so
+//              a warp's 32 lanes share the 8 trajectory values they read;
+//              splits them into hi and lo operand tiles in the
+//              64-byte-swizzled K-major layout the MMA reads (rows of 32
+//              samples), then each warp arrives once on full[stage];
 //   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
-//              issues 24 tcgen05.mma (M = 128, N = 128, K = 16 each) and
+//              issues 12 tcgen05.mma (M = 128, N = 256, K = 16 each) and
 //              commits to empty[stage];
 //   warps 0-15 drain: at the end of every segment (at most SEG stages of one
 //              tile) the finished accumulators are read with tcgen05.ld and
@@ -77,12 +83,17 @@ constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
 // The paired contraction (G, D): tiles of 128 rows x 128 B columns, each B
-// column giving two output columns (see PairGeom), four accumulators of 128
-// TMEM columns; 64 KB stages, three deep; the trajectory (and weight) chunks
-// in an 8-deep ring, two stages ahead.
-constexpr int PG_COLS = 128;                                       // B columns per tile (MMA N)
-constexpr uint32_t PB_BYTES = PG_COLS * 128;                       // 128 rows x 64 halves
-constexpr uint32_t PG_STAGE_BYTES = 2 * A_BYTES + 2 * PB_BYTES;    // A_hi, A_lo, B_hi, B_lo
+// column giving two output columns (see PairGeom).  The operands are stored
+// in 64-byte-swizzled K-major tiles of 32 samples per row: A's real and
+// imaginary parts as two tiles of 128 rows, B as one stacked tile of 256
+// rows [Br ; Bi], so one MMA of N = 256 forms [P_ac | P_ad] = Ar [Br ; Bi]^T
+// and another [P_bc | P_bd] = Ai [Br ; Bi]^T (two accumulators of 256 TMEM
+// columns); 64 KB stages, three deep; the trajectory (and weight) chunks in
+// an 8-deep ring, two stages ahead.
+constexpr int PG_COLS = 128;                                       // B columns per tile
+constexpr uint32_t PA_BYTES = TC_ROWS * 64;                        // 128 rows x 32 halves
+constexpr uint32_t PB_BYTES = 2 * PG_COLS * 64;                    // 256 rows x 32 halves
+constexpr uint32_t PG_STAGE_BYTES = 4 * PA_BYTES + 2 * PB_BYTES;   // Ar, Ai (hi, lo), B (hi, lo)
 constexpr int PG_STAGES = 3;
 constexpr int PG_TRAJ_RING = 8;  // > PG_STAGES + 2: a slot is refilled only after every producer left it
 constexpr uint32_t PG_TRAJ_BUF = 3 * TC_KS * 8;  // ka, kb (int64), w' (float2)
@@ -230,6 +241,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr)
            (2ull << 61);
 }
 
+// The same for a 64-byte swizzle (rows of 64 bytes, 8-row groups 512 bytes
+// apart; layout type 4).
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | (32ull << 32) | (1ull << 46) |
+           (4ull << 61);
+}
+
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                         uint32_t accumulate)
 {
@@ -289,6 +308,14 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v)
 __device__ __forceinline__ uint32_t sw128(int row, int chunk)
 {
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// Byte offset of 16-byte chunk `chunk` (0..3) of K-major row `row` in a
+// 64-byte-swizzled tile whose base is 1024-aligned: address bits 4-5 are
+// XORed with bits 7-8.
+__device__ __forceinline__ uint32_t sw64(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
 }
 
 // hi/lo split of 8 values into 4 packed words each.
@@ -394,7 +421,7 @@ struct PairGeom {
     int J;      // B columns j = 0 .. J - 1
 };
 
-// Adds (first: stores) the four accumulators (P_ac, P_bd, P_ad, P_bc in TMEM
+// Adds (first: stores) the four accumulators (P_ac, P_ad, P_bc, P_bd in TMEM
 // columns 0, 128, 256, 384) as the two paired outputs into the partial tile,
 // laid out as [column / 4][row][column % 4] (256 complex columns: c+(j) at
 // j, c-(j) at 128 + j; real parts in the first 256 float columns, imaginary
@@ -413,9 +440,9 @@ __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int war
         float ac[8], bd[8], ad[8], bc[8];
         const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(32 * quarter + cc);
         tmem_ld8(ta, ac);
-        tmem_ld8(ta + PG_COLS, bd);
-        tmem_ld8(ta + 2 * PG_COLS, ad);
-        tmem_ld8(ta + 3 * PG_COLS, bc);
+        tmem_ld8(ta + PG_COLS, ad);
+        tmem_ld8(ta + 2 * PG_COLS, bc);
+        tmem_ld8(ta + 3 * PG_COLS, bd);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float pre[4], pim[4], mre[4], mim[4];
@@ -516,11 +543,11 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
 
     if (tid == 0) {
         for (int i = 0; i < PG_STAGES; ++i) {
-            mbar_init(bar_full + 8 * i, TC_PRODUCERS);
+            mbar_init(bar_full + 8 * i, TC_PRODUCERS / 32);  // one arrival per producer warp
             mbar_init(bar_empty + 8 * i, 1);
         }
         mbar_init(bar_acc_full, 1);
-        mbar_init(bar_acc_empty, TC_PRODUCERS);
+        mbar_init(bar_acc_empty, TC_PRODUCERS / 32);
         for (int r = 0; r < PG_TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
@@ -556,7 +583,11 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         };
         if (tid == 0)
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
-        const int r = tid & 127, g = tid >> 7;  // operand row (A) / column (B), sample group
+        // warps 0-7 form A, warps 8-15 B; thread t: rows (A) or columns (B)
+        // r and r + 64 of the tile for the samples 8g .. 8g + 7, so a warp's
+        // lanes share the trajectory values they load
+        const bool is_b = warp >= TC_PRODUCERS / 64;
+        const int r = tid & 63, g = (tid >> 6) & 3;
         SegWalk sw{u0, K};
         int trow = (int)(sw.tile / tilesC), tcol = (int)(sw.tile % tilesC);  // stepped with the tile
         int64_t dtile = 0;  // tile of the segment being accumulated
@@ -593,61 +624,82 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
             const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
-            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + PB_BYTES;
+            const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
+            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + PB_BYTES;
             constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
-            // A row r: the signed index sa (i + oa) = +-aa, its sign in the scale
-            const int sja = sa * (i0 + r + oa);
-            const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
-            const float sca = sja < 0 ? -kRev : kRev;
-            // B column r: j = j0 + r (zero past J), the count 2j + 1 on the
-            // halved k for half-integer offsets
-            const int jb = j0 + r;
-            const uint32_t ab = half ? (uint32_t)(2 * jb + 1) : (uint32_t)jb;
-            const float scb = sb < 0 ? -kRev : kRev;
-            // samples past L (only in a tile's last chunk): A is zero there
-            // through the zero padding of the weights, or B by the mask below
-            // when unweighted
-            const int nvalid = l0 + TC_KS > L ? (int)(L - l0) : TC_KS;
             float re[8], im[8];
             uint4 rh, rl, ih, il;
-            // A row r: [Ar(8g..8g+7) at chunk g | Ai at chunk 4+g]
+            if (!is_b) {
+                // A rows i = i0 + r + 64 v: the signed index sa (i + oa) = +-aa,
+                // its sign in the scale; the row's 8 samples in 16-byte chunk g
+                // of the Ar and Ai tiles
+                int64_t kq[8];
+                float2 ww[8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int l = 8 * g + e;
-                float2 v = phasor_signed(ka_s[l], aa, sca);
-                if (WEIGHTED) {
-                    float2 ww = w_s[l];
-                    ww.x *= wmul;
-                    ww.y *= wmul;
-                    v = cmul(v, ww);
+                for (int e = 0; e < 8; ++e) {
+                    kq[e] = ka_s[8 * g + e];
+                    if (WEIGHTED) {
+                        ww[e] = w_s[8 * g + e];
+                        ww[e].x *= wmul;
+                        ww[e].y *= wmul;
+                    }
                 }
-                re[e] = v.x;
-                im[e] = v.y;
-            }
-            split8<BF16>(re, rh, rl);
-            split8<BF16>(im, ih, il);
-            st_shared_v4(aH + sw128(r, g), rh);
-            st_shared_v4(aH + sw128(r, 4 + g), ih);
-            st_shared_v4(aL + sw128(r, g), rl);
-            st_shared_v4(aL + sw128(r, 4 + g), il);
-            // B column r: [Br | Bi]
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int l = 8 * g + e;
-                const int64_t kq = half ? (kb_s[l] >> 1) : kb_s[l];
-                float2 v = phasor_signed(kq, ab, scb);
-                if ((!WEIGHTED && l >= nvalid) || jb >= J) v = make_float2(0.f, 0.f);
-                re[e] = v.x;
-                im[e] = v.y;
+                for (int v = 0; v < 2; ++v) {
+                    const int row = r + 64 * v;
+                    const int sja = sa * (i0 + row + oa);
+                    const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
+                    const float sca = sja < 0 ? -kRev : kRev;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float2 z = phasor_signed(kq[e], aa, sca);
+                        if (WEIGHTED) z = cmul(z, ww[e]);
+                        re[e] = z.x;
+                        im[e] = z.y;
+                    }
+                    split8<BF16>(re, rh, rl);
+                    split8<BF16>(im, ih, il);
+                    st_shared_v4(aRH + sw64(row, g), rh);
+                    st_shared_v4(aRL + sw64(row, g), rl);
+                    st_shared_v4(aIH + sw64(row, g), ih);
+                    st_shared_v4(aIL + sw64(row, g), il);
+                }
+            } else {
+                // B columns j = j0 + r + 64 v (zero past J), the count 2j + 1
+                // on the halved k for half-integer offsets; Br in row j of the
+                // stacked tile, Bi in row 128 + j.  Samples past L (only in a
+                // tile's last chunk): A is zero there through the zero padding
+                // of the weights, or B by this mask when unweighted.
+                const int nvalid = l0 + TC_KS > L ? (int)(L - l0) : TC_KS;
+                const float scb = sb < 0 ? -kRev : kRev;
+                int64_t kq[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) kq[e] = half ? (kb_s[8 * g + e] >> 1) : kb_s[8 * g + e];
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int col = r + 64 * v;
+                    const int jb = j0 + col;
+                    const uint32_t ab = half ? (uint32_t)(2 * jb + 1) : (uint32_t)jb;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float2 z = phasor_signed(kq[e], ab, scb);
+                        if ((!WEIGHTED && 8 * g + e >= nvalid) || jb >= J) z = make_float2(0.f, 0.f);
+                        re[e] = z.x;
+                        im[e] = z.y;
+                    }
+                    split8<BF16>(re, rh, rl);
+                    split8<BF16>(im, ih, il);
+                    st_shared_v4(bH + sw64(col, g), rh);
+                    st_shared_v4(bL + sw64(col, g), rl);
+                    st_shared_v4(bH + sw64(PG_COLS + col, g), ih);
+                    st_shared_v4(bL + sw64(PG_COLS + col, g), il);
+                }
             }
-            split8<BF16>(re, rh, rl);
-            split8<BF16>(im, ih, il);
-            st_shared_v4(bH + sw128(r, g), rh);
-            st_shared_v4(bH + sw128(r, 4 + g), ih);
-            st_shared_v4(bL + sw128(r, g), rl);
-            st_shared_v4(bL + sw128(r, 4 + g), il);
+            // every lane's stores are made visible to the tensor core's
+            // proxy before the warp's one arrival
             fence_proxy_async();
-            mbar_arrive(bar_full + 8 * s);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_full + 8 * s);
             if (sw.pos == 0) {
                 // the MMA now has the first stage of a new segment queued:
                 // drain the previous one
@@ -661,7 +713,8 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     tc_fence_after();
                     drain_pairs(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
                     tc_fence_before();
-                    mbar_arrive(bar_acc_empty);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_acc_empty);
                 }
                 dtile = sw.tile;
                 dfirst = sw.first_of_tile;
@@ -686,15 +739,16 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
     } else if (lane == 0) {
         // ------------------------------------------------ MMA issuer
         // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and
-        // 10, both K-major, N = 128 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
+        // 10, both K-major, N = 256 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
         const uint32_t fmt = BF16 ? 1u : 0u;
-        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
         SegWalk sw{u0, K};
         int issued = 0;  // stages whose MMAs were issued
         // a test's injected stall: nothing completes bar_drain before this
         // thread's own commit, so the bounded wait runs out and no MMA issues
         if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
-        const uint32_t t_ac = tmem, t_bd = tmem + PG_COLS, t_ad = tmem + 2 * PG_COLS, t_bc = tmem + 3 * PG_COLS;
+        // [P_ac | P_ad] in TMEM columns 0-255, [P_bc | P_bd] in 256-511
+        const uint32_t t_r = tmem, t_i = tmem + 2 * PG_COLS;
         for (int it = 0; !stall && it < n; ++it) {
             const int s = it % PG_STAGES;
             const uint32_t use = (uint32_t)(it / PG_STAGES);
@@ -710,18 +764,17 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             ++issued;
             tc_fence_after();
             const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
-            const uint32_t aH = st, aL = st + A_BYTES, bH = st + 2 * A_BYTES, bL = bH + PB_BYTES;
+            const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
+            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + PB_BYTES;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-                const uint32_t oR = 32u * kk, oI = 64u + 32u * kk;  // 16 samples of re, of im
+                const uint32_t o = 32u * kk;  // samples 16 kk .. 16 kk + 15 of each row
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
-                    const uint32_t A = q == 2 ? aL : aH, B = q == 1 ? bL : bH;
+                    const uint32_t Ar = q == 2 ? aRL : aRH, Ai = q == 2 ? aIL : aIH, B = q == 1 ? bL : bH;
                     const uint32_t acc = (sw.pos > 0 || kk > 0 || q > 0) ? 1u : 0u;
-                    mma_f16(t_ac, sdesc(A + oR), sdesc(B + oR), idesc, acc);
-                    mma_f16(t_bd, sdesc(A + oI), sdesc(B + oI), idesc, acc);
-                    mma_f16(t_ad, sdesc(A + oR), sdesc(B + oI), idesc, acc);
-                    mma_f16(t_bc, sdesc(A + oI), sdesc(B + oR), idesc, acc);
+                    mma_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
+                    mma_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
                 }
             }
             mma_commit(bar_empty + 8 * s);
