@@ -82,25 +82,29 @@ constexpr int TC_TILE_FLOATS = 2 * TC_COLS * TC_ROWS;  // partial tile: 512 colu
 constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
-// The paired contraction (G, D): tiles of 128 rows x 128 B columns, each B
-// column giving two output columns (see PairGeom).  The operands are stored
-// in 64-byte-swizzled K-major tiles of 32 samples per row: A's real and
-// imaginary parts as two tiles of 128 rows, B as one stacked tile of 256
-// rows [Br ; Bi], so one MMA of N = 256 forms [P_ac | P_ad] = Ar [Br ; Bi]^T
-// and another [P_bc | P_bd] = Ai [Br ; Bi]^T (two accumulators of 256 TMEM
-// columns); 64 KB stages, three deep; the trajectory (and weight) chunks in
-// an 8-deep ring, two stages ahead.
-constexpr int PG_COLS = 128;                                       // B columns per tile
+// The paired contraction (G, D) runs on CTA pairs (clusters of two, one CTA
+// per SM): a pair tile is 256 rows x 128 B columns, each B column giving two
+// output columns (see PairGeom).  CTA h of the pair holds A rows 128 h ..
+// 128 h + 127 and the stacked operand [Br ; Bi] of B columns 64 h .. 64 h +
+// 63, both 64-byte-swizzled K-major with rows of 32 samples; the leader's
+// tcgen05.mma.cta_group::2 (M = 256, N = 256) reads both CTAs' tiles and
+// writes each CTA's 128 rows x 256 columns of tensor memory.  Two
+// accumulators, [Ar ; Ai] x the pair's B; 48 KB stages, four deep; the
+// trajectory (and weight) chunks in an 8-deep ring, two stages ahead.
+constexpr int PG_COLS = 128;                                       // B columns per pair tile
+constexpr int PG_HCOLS = 64;                                       // B columns per CTA
+constexpr int PG_ROWS = 2 * TC_ROWS;                               // output rows per pair tile
 constexpr uint32_t PA_BYTES = TC_ROWS * 64;                        // 128 rows x 32 halves
-constexpr uint32_t PB_BYTES = 2 * PG_COLS * 64;                    // 256 rows x 32 halves
+constexpr uint32_t PB_BYTES = 2 * PG_HCOLS * 64;                   // 128 stacked rows x 32 halves
 constexpr uint32_t PG_STAGE_BYTES = 4 * PA_BYTES + 2 * PB_BYTES;   // Ar, Ai (hi, lo), B (hi, lo)
-constexpr int PG_STAGES = 3;
-constexpr int PG_TRAJ_RING = 8;  // > PG_STAGES + 2: a slot is refilled only after every producer left it
+constexpr int PG_STAGES = 4;
+constexpr int PG_TRAJ_RING = 8;  // >= PG_STAGES + 2: a slot is refilled only after every producer left it
 constexpr uint32_t PG_TRAJ_BUF = 3 * TC_KS * 8;  // ka, kb (int64), w' (float2)
 constexpr uint32_t PG_TRAJ_OFF = PG_STAGES * PG_STAGE_BYTES;
 constexpr uint32_t PG_BAR_OFF = PG_TRAJ_OFF + PG_TRAJ_RING * PG_TRAJ_BUF;
 constexpr uint32_t PG_SMEM = PG_BAR_OFF + 256 + 1024;  // + 1024 alignment slack
 static_assert(PG_SMEM <= 232448, "shared memory per CTA");
+static_assert(PG_TRAJ_RING >= PG_STAGES + 2, "trajectory ring depth");
 static_assert(8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING) + 8 <= 256, "barrier area");
 constexpr int kMaxCtas = 152;       // CTAs of one contraction (one per SM)
 
@@ -267,6 +271,70 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
+// ------------------------------------------------ CTA-pair (cluster) helpers
+
+// Arrives on the mbarrier at shared offset `bar` of CTA `rank` of the
+// cluster, with the arrive's default semantics (release at CTA scope).  What
+// the arrival publishes is shared memory for the pair's MMAs, made visible to
+// the tensor core's proxy by the arriving warp's fence.proxy.async, and TMEM
+// read by tcgen05.ld that has completed: no cluster-scope fence (which would
+// also wait for the warp's outstanding global reductions) is needed.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar, uint32_t rank)
+{
+    asm volatile(
+        "{\n\t.reg .b32 ra;\n\t"
+        "mapa.shared::cluster.u32 ra, %0, %1;\n\t"
+        "mbarrier.arrive.shared::cluster.b64 _, [ra];\n\t}" ::"r"(bar),
+        "r"(rank)
+        : "memory");
+}
+
+// Every thread of both CTAs of the pair (release / acquire at cluster scope;
+// the non-aligned form: a warp need not be converged).
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// TMEM of a CTA pair: one warp of each CTA allocates (and frees) together.
+__device__ __forceinline__ void tmem_alloc2(uint32_t slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc2(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// One MMA across the pair: A rows 0-127 and B rows 0 .. N/2 - 1 from this
+// CTA's shared memory, A rows 128-255 and B rows N/2 .. N - 1 from the same
+// offsets in the peer's; each CTA's TMEM receives its 128 rows.
+__device__ __forceinline__ void mma2_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrives on the mbarrier at shared offset `bar` of both CTAs of the pair once
+// the pair MMAs this thread issued have completed.
+__device__ __forceinline__ void mma2_commit_pair(uint32_t bar)
+{
+    asm volatile(
+        "{\n\t.reg .b16 m;\n\t"
+        "mov.b16 m, 3;\n\t"
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], m;\n\t}" ::"r"(
+            bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
 {
     uint32_t r[8];
@@ -357,15 +425,16 @@ __device__ __forceinline__ float2 phasor_fast(int64_t kq, int j)
     return make_float2(cs, sn);
 }
 
-// exp(+i 2 pi k s a) for the fixed-point k, a count a >= 0 and a sign s = +-1
-// folded into scale = s * 2 pi / 2^32: the top 32 bits of kq * a mod 2^64 are
-// hi(kq) a + umulhi(lo(kq), a) mod 2^32 (two integer multiply-adds), the
-// signed fraction of a cycle; negating the angle conjugates the phasor.  The
-// same phase as phasor_fast up to one unit of the 32-bit fraction.
-__device__ __forceinline__ float2 phasor_signed(int64_t kq, uint32_t a, float scale)
+// exp(+i 2 pi k s a) for the fixed-point k = hi 2^32 + lo, a count a >= 0
+// and a sign s = +-1 folded into scale = s * 2 pi / 2^32: the top 32 bits of
+// kq * a mod 2^64 are hi a + umulhi(lo, a) mod 2^32 (two integer
+// multiply-adds), the signed fraction of a cycle; negating the angle
+// conjugates the phasor.  `c` adds a constant to that fraction (a half-integer
+// offset's kq / 2, see the B operand of k_tc_pair_gemm).  The same phase as
+// phasor_fast up to one unit of the 32-bit fraction.
+__device__ __forceinline__ float2 phasor_top(uint32_t lo, uint32_t hi, uint32_t c, uint32_t a, float scale)
 {
-    const uint32_t lo = (uint32_t)(uint64_t)kq, hi = (uint32_t)((uint64_t)kq >> 32);
-    const uint32_t top = __umulhi(lo, a) + hi * a;
+    const uint32_t top = __umulhi(lo, a) + c + hi * a;
     float sn, cs;
     __sincosf((float)(int)top * scale, &sn, &cs);
     return make_float2(cs, sn);
@@ -412,8 +481,9 @@ __device__ __forceinline__ float weight_scale_inv(const unsigned* amax2_bits)
 //   D (Eq. AnnMatGD): columns m, centre (N - 1) / 2 (C2 = N - 1); for even N
 //     the offsets are half-integers (half 1, j = 0 .. N/2 - 1: m = N/2 + j
 //     and N/2 - 1 - j), for odd N integers (half 0, j = 0 .. (N - 1)/2).
-// A half-integer phase k (j + 1/2) is (k/2)(2j + 1): the fixed-point k
-// shifted right by one bit (an error of 2^-65 cycles times 2j + 1).
+// A half-integer phase k (j + 1/2) is k j + k/2: the fixed-point k times j
+// plus k shifted right by one bit (an error of 2^-65 cycles, and one unit of
+// 2^-32 cycle from adding the two top words without the low words' carry).
 struct PairGeom {
     int R, C;   // output rows and columns
     int C2;     // twice the centre column
@@ -421,15 +491,18 @@ struct PairGeom {
     int J;      // B columns j = 0 .. J - 1
 };
 
-// Adds (first: stores) the four accumulators (P_ac, P_ad, P_bc, P_bd in TMEM
-// columns 0, 128, 256, 384) as the two paired outputs into the partial tile,
-// laid out as [column / 4][row][column % 4] (256 complex columns: c+(j) at
-// j, c-(j) at 128 + j; real parts in the first 256 float columns, imaginary
-// in the next 256; 128 rows): a thread's four consecutive columns are one
-// 16-byte vector, and a warp's 32 lanes (consecutive rows) cover 512
+// Adds (first: stores) this CTA's 128 rows of the four products as the two
+// paired outputs into its partial tile.  B column j (0..127) of the pair tile
+// is row j % 64 (Br) and 64 + j % 64 (Bi) of CTA j / 64's stacked operand, so
+// with cb = 128 (j / 64) + j % 64 the accumulators hold P_ac at TMEM column
+// cb, P_ad at cb + 64, P_bc at 256 + cb and P_bd at 320 + cb.  The partial
+// tile is laid out as [column / 4][row][column % 4] (256 complex columns:
+// c+(j) at j, c-(j) at 128 + j; real parts in the first 256 float columns,
+// imaginary in the next 256; 128 rows): a thread's four consecutive columns
+// are one 16-byte vector, and a warp's 32 lanes (consecutive rows) cover 512
 // contiguous bytes.  Fire-and-forget vector reductions; a thread's adds to
-// one address come in program order, so the partial is the same sum on
-// every run.
+// one address come in program order, so the partial is the same sum on every
+// run.
 __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int warp, int lane, bool first)
 {
     const int lbase = 32 * (warp & 3);
@@ -438,11 +511,13 @@ __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int war
 #pragma unroll 1
     for (int cc = 0; cc < 32; cc += 8) {
         float ac[8], bd[8], ad[8], bc[8];
-        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + (uint32_t)(32 * quarter + cc);
+        const int j = 32 * quarter + cc;
+        const uint32_t cb = 128u * (uint32_t)(j >> 6) + (uint32_t)(j & 63);
+        const uint32_t ta = tacc + ((uint32_t)lbase << 16) + cb;
         tmem_ld8(ta, ac);
-        tmem_ld8(ta + PG_COLS, ad);
-        tmem_ld8(ta + 2 * PG_COLS, bc);
-        tmem_ld8(ta + 3 * PG_COLS, bd);
+        tmem_ld8(ta + 64, ad);
+        tmem_ld8(ta + 256, bc);
+        tmem_ld8(ta + 320, bd);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float pre[4], pim[4], mre[4], mim[4];
@@ -472,6 +547,32 @@ __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int war
             }
         }
     }
+}
+
+// B column j = j0 + c of a CTA's half of a pair tile for the samples 8g ..
+// 8g + 7 (fixed-point k = khi 2^32 + klo, phase constant kc): Br into row c
+// and Bi into row 64 + c of the stacked hi and lo tiles.  MASK zeroes samples
+// from nvalid on and columns from J on.
+template <bool BF16, bool MASK>
+__device__ __forceinline__ void pair_b_col(const uint32_t* klo, const uint32_t* khi, const uint32_t* kc, int j0,
+                                           int c, int g, int J, int nvalid, float scb, uint32_t bH, uint32_t bL)
+{
+    float re[8], im[8];
+    uint4 rh, rl, ih, il;
+    const int jb = j0 + c;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        float2 z = phasor_top(klo[e], khi[e], kc[e], (uint32_t)jb, scb);
+        if (MASK && (8 * g + e >= nvalid || jb >= J)) z = make_float2(0.f, 0.f);
+        re[e] = z.x;
+        im[e] = z.y;
+    }
+    split8<BF16>(re, rh, rl);
+    split8<BF16>(im, ih, il);
+    st_shared_v4(bH + sw64(c, g), rh);
+    st_shared_v4(bL + sw64(c, g), rl);
+    st_shared_v4(bH + sw64(PG_HCOLS + c, g), ih);
+    st_shared_v4(bL + sw64(PG_HCOLS + c, g), il);
 }
 
 // The unit range [u0, u1) of CTA c among P over U units (tiles x chunks).
@@ -510,11 +611,17 @@ struct SegWalk {
     }
 };
 
-// Partials of CTA blockIdx.x over its units [u0, u1) (unit = tile * K +
-// chunk of 32 samples; tile = row tile * tilesC + column tile of 128 j):
+// Partials of the CTA pair blockIdx.x / 2 over its units [u0, u1) (unit =
+// tile * K + chunk of 32 samples; tile = row tile of 256 * tilesC + column
+// tile of 128 j):
 //   A'(l,i) = w'_l exp(sa i2pi ka_l (i + oa)) (w' = 1 unweighted),
 //   E(l,j)  = exp(sb i2pi kb_l (j + half/2)),
-// the four real products of each into the four accumulators.
+// the four real products of each into the two accumulators of each CTA.
+// CTA h = blockIdx.x % 2 (its rank in the cluster) forms A rows 128 h .. +127
+// and B columns 64 h .. +63 of each tile and keeps its rows' partial of tile
+// t in slot 2 (pair + t) + h.  Rank 0 issues the pair's MMAs: it waits on its
+// own full[stage] barrier, on which the producer warps of both CTAs arrive,
+// and its commits arrive on the barrier at the same offset in both CTAs.
 template <bool BF16, bool WEIGHTED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ w,
@@ -524,12 +631,12 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_full = sbase + PG_BAR_OFF;             // stage filled
+    const uint32_t bar_full = sbase + PG_BAR_OFF;             // stage filled (rank 0)
     const uint32_t bar_empty = bar_full + 8 * PG_STAGES;      // stage consumed
     const uint32_t bar_acc_full = bar_empty + 8 * PG_STAGES;  // segment accumulated
-    const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained
+    const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained (rank 0)
     const uint32_t bar_traj = bar_acc_empty + 8;              // PG_TRAJ_RING: trajectory chunk landed
-    const uint32_t bar_drain = bar_traj + 8 * PG_TRAJ_RING;      // every MMA issued has completed
+    const uint32_t bar_drain = bar_traj + 8 * PG_TRAJ_RING;   // every MMA issued has completed
     const uint32_t misc = PG_BAR_OFF + 8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
@@ -537,25 +644,27 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int64_t P = gridDim.x;
-    const int64_t u0 = unit_start(blockIdx.x, U, P);
-    const int n = (int)(unit_start(blockIdx.x + 1, U, P) - u0);
+    const uint32_t rank = blockIdx.x & 1u;  // the launch's clusters are pairs of consecutive blocks
+    const int64_t pair = blockIdx.x >> 1, P2 = gridDim.x >> 1;
+    const int64_t u0 = unit_start(pair, U, P2);
+    const int n = (int)(unit_start(pair + 1, U, P2) - u0);
 
     if (tid == 0) {
         for (int i = 0; i < PG_STAGES; ++i) {
-            mbar_init(bar_full + 8 * i, TC_PRODUCERS / 32);  // one arrival per producer warp
+            mbar_init(bar_full + 8 * i, 2 * TC_PRODUCERS / 32);  // one arrival per producer warp of the pair
             mbar_init(bar_empty + 8 * i, 1);
         }
         mbar_init(bar_acc_full, 1);
-        mbar_init(bar_acc_empty, TC_PRODUCERS / 32);
+        mbar_init(bar_acc_empty, 2 * TC_PRODUCERS / 32);
         for (int r = 0; r < PG_TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == TC_PRODUCERS / 32) tmem_alloc(smem_u32(tmem_slot), 512);
+    if (warp == TC_PRODUCERS / 32) tmem_alloc2(smem_u32(tmem_slot), 512);
     tc_fence_before();
     __syncthreads();
+    cluster_sync();  // both CTAs' barriers are initialised before any arrival from the other
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -563,7 +672,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         // ------------------------------------------------ producers
         const float wmul = WEIGHTED ? weight_scale_inv(amax2) : 1.f;
         // TMA feed of the trajectory (and weight) chunk of stage `it` into
-        // ring slot it % 4; stages are issued in order, kci is the chunk of the next
+        // its ring slot; stages are issued in order, kci is the chunk of the next
         int64_t kci = u0 % K;
         int issued = 0;  // stages whose chunk thread 0 has requested
         auto issue_traj = [&](int it) {
@@ -583,9 +692,9 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         };
         if (tid == 0)
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
-        // warps 0-7 form A, warps 8-15 B; thread t: rows (A) or columns (B)
-        // r and r + 64 of the tile for the samples 8g .. 8g + 7, so a warp's
-        // lanes share the trajectory values they load
+        // warps 0-7: A rows r and r + 64 of this CTA's 128, warps 8-15: B
+        // column r of its 64, for the samples 8g .. 8g + 7, so a warp's lanes
+        // share the trajectory values they load
         const bool is_b = warp >= TC_PRODUCERS / 64;
         const int r = tid & 63, g = (tid >> 6) & 3;
         SegWalk sw{u0, K};
@@ -595,12 +704,12 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         for (int it = 0; it < n; ++it) {
             const int s = it % PG_STAGES;
             const uint32_t use = (uint32_t)(it / PG_STAGES);
-            // stage s is free once the MMA has consumed its previous use.
-            // Each warp waits for that itself (no producer-wide barrier), so
-            // warps drift apart by at most the ring depth: a warp past the
-            // wait for stage it knows every producer has finished stage
-            // it - PG_STAGES, whose trajectory slot the TMA of stage it + 2
-            // reuses (it + 2 - PG_TRAJ_RING < it - PG_STAGES + 1).
+            // stage s is free once the pair's MMAs have consumed its previous
+            // use.  Each warp waits for that itself (no producer-wide
+            // barrier), so warps drift apart by at most the ring depth: a warp
+            // past the wait for stage it knows every producer has finished
+            // stage it - PG_STAGES, whose trajectory slot the TMA of stage
+            // it + 2 reuses (it + 2 - PG_TRAJ_RING <= it - PG_STAGES).
             if (lane == 0 && it >= PG_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
@@ -618,7 +727,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 ++trow;
             }
             const int64_t l0 = sw.kc * TC_KS;
-            const int i0 = trow * TC_ROWS, j0 = tcol * PG_COLS;
+            const int i0 = trow * PG_ROWS + (int)rank * TC_ROWS, j0 = tcol * PG_COLS + (int)rank * PG_HCOLS;
             const uint8_t* tbuf = smem + PG_TRAJ_OFF + (it % PG_TRAJ_RING) * PG_TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
@@ -627,23 +736,25 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
             const uint32_t bH = st + 4 * PA_BYTES, bL = bH + PB_BYTES;
             constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
-            float re[8], im[8];
-            uint4 rh, rl, ih, il;
             if (!is_b) {
                 // A rows i = i0 + r + 64 v: the signed index sa (i + oa) = +-aa,
                 // its sign in the scale; the row's 8 samples in 16-byte chunk g
                 // of the Ar and Ai tiles
-                int64_t kq[8];
+                uint32_t klo[8], khi[8];
                 float2 ww[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    kq[e] = ka_s[8 * g + e];
+                    const uint64_t k = (uint64_t)ka_s[8 * g + e];
+                    klo[e] = (uint32_t)k;
+                    khi[e] = (uint32_t)(k >> 32);
                     if (WEIGHTED) {
                         ww[e] = w_s[8 * g + e];
                         ww[e].x *= wmul;
                         ww[e].y *= wmul;
                     }
                 }
+                float re[8], im[8];
+                uint4 rh, rl, ih, il;
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     const int row = r + 64 * v;
@@ -652,7 +763,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     const float sca = sja < 0 ? -kRev : kRev;
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        float2 z = phasor_signed(kq[e], aa, sca);
+                        float2 z = phasor_top(klo[e], khi[e], 0u, aa, sca);
                         if (WEIGHTED) z = cmul(z, ww[e]);
                         re[e] = z.x;
                         im[e] = z.y;
@@ -665,41 +776,33 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     st_shared_v4(aIL + sw64(row, g), il);
                 }
             } else {
-                // B columns j = j0 + r + 64 v (zero past J), the count 2j + 1
-                // on the halved k for half-integer offsets; Br in row j of the
-                // stacked tile, Bi in row 128 + j.  Samples past L (only in a
+                // B column j = j0 + r: the phase k (j + half / 2) has the top
+                // 32 bits umulhi(lo, j) + hi j + half (hi >> 1), those of
+                // kq j + half (kq >> 1) mod 2^64 up to the carry out of the low
+                // words (one unit of 2^-32 cycle).  Samples past L (only in a
                 // tile's last chunk): A is zero there through the zero padding
-                // of the weights, or B by this mask when unweighted.
-                const int nvalid = l0 + TC_KS > L ? (int)(L - l0) : TC_KS;
+                // of the weights, or B by the mask when unweighted; columns
+                // past J are zero.
+                const int nvalid = (!WEIGHTED && l0 + TC_KS > L) ? (int)(L - l0) : TC_KS;
                 const float scb = sb < 0 ? -kRev : kRev;
-                int64_t kq[8];
+                uint32_t klo[8], khi[8], kc[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) kq[e] = half ? (kb_s[8 * g + e] >> 1) : kb_s[8 * g + e];
-#pragma unroll
-                for (int v = 0; v < 2; ++v) {
-                    const int col = r + 64 * v;
-                    const int jb = j0 + col;
-                    const uint32_t ab = half ? (uint32_t)(2 * jb + 1) : (uint32_t)jb;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        float2 z = phasor_signed(kq[e], ab, scb);
-                        if ((!WEIGHTED && 8 * g + e >= nvalid) || jb >= J) z = make_float2(0.f, 0.f);
-                        re[e] = z.x;
-                        im[e] = z.y;
-                    }
-                    split8<BF16>(re, rh, rl);
-                    split8<BF16>(im, ih, il);
-                    st_shared_v4(bH + sw64(col, g), rh);
-                    st_shared_v4(bL + sw64(col, g), rl);
-                    st_shared_v4(bH + sw64(PG_COLS + col, g), ih);
-                    st_shared_v4(bL + sw64(PG_COLS + col, g), il);
+                for (int e = 0; e < 8; ++e) {
+                    const uint64_t k = (uint64_t)kb_s[8 * g + e];
+                    klo[e] = (uint32_t)k;
+                    khi[e] = (uint32_t)(k >> 32);
+                    kc[e] = half ? (uint32_t)((int32_t)khi[e] >> 1) : 0u;
                 }
+                if (nvalid == TC_KS && j0 + PG_HCOLS <= J)
+                    pair_b_col<BF16, false>(klo, khi, kc, j0, r, g, J, nvalid, scb, bH, bL);
+                else
+                    pair_b_col<BF16, true>(klo, khi, kc, j0, r, g, J, nvalid, scb, bH, bL);
             }
             // every lane's stores are made visible to the tensor core's
-            // proxy before the warp's one arrival
+            // proxy before the warp's one arrival at the leader
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive(bar_full + 8 * s);
+            if (lane == 0) mbar_arrive_cluster(bar_full + 8 * s, 0);
             if (sw.pos == 0) {
                 // the MMA now has the first stage of a new segment queued:
                 // drain the previous one
@@ -711,10 +814,10 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     }
                     __syncwarp();  // the tensor-memory loads are warp-collective
                     tc_fence_after();
-                    drain_pairs(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
+                    drain_pairs(tmem, part + (2 * (pair + dtile) + rank) * TC_TILE_FLOATS, warp, lane, dfirst);
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(bar_acc_empty);
+                    if (lane == 0) mbar_arrive_cluster(bar_acc_empty, 0);
                 }
                 dtile = sw.tile;
                 dfirst = sw.first_of_tile;
@@ -727,7 +830,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             if (!landed) atomicOr(err, kErrTimeout);
             if (__all_sync(0xffffffffu, landed)) {
                 tc_fence_after();
-                drain_pairs(tmem, part + (blockIdx.x + dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
+                drain_pairs(tmem, part + (2 * (pair + dtile) + rank) * TC_TILE_FLOATS, warp, lane, dfirst);
             }
         }
         // every requested chunk has landed before the CTA goes (at most one
@@ -736,19 +839,19 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             for (int j = issued > PG_TRAJ_RING ? issued - PG_TRAJ_RING : 0; j < issued; ++j)
                 if (!mbar_wait(bar_traj + 8 * (j % PG_TRAJ_RING), (uint32_t)(j / PG_TRAJ_RING) & 1, kDrainNs))
                     atomicOr(err, kErrTimeout);
-    } else if (lane == 0) {
-        // ------------------------------------------------ MMA issuer
+    } else if (rank == 0 && lane == 0) {
+        // ------------------------------------------------ MMA issuer (the pair's)
         // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and
-        // 10, both K-major, N = 256 (N>>3 at bit 17), M = 128 (M>>4 at bit 24).
+        // 10, both K-major, N = 256 (N>>3 at bit 17), M = 256 (M>>4 at bit 24).
         const uint32_t fmt = BF16 ? 1u : 0u;
-        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
         SegWalk sw{u0, K};
         int issued = 0;  // stages whose MMAs were issued
         // a test's injected stall: nothing completes bar_drain before this
         // thread's own commit, so the bounded wait runs out and no MMA issues
         if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
-        // [P_ac | P_ad] in TMEM columns 0-255, [P_bc | P_bd] in 256-511
-        const uint32_t t_r = tmem, t_i = tmem + 2 * PG_COLS;
+        // [P_ac | P_ad] per B half in TMEM columns 0-255, [P_bc | P_bd] in 256-511
+        const uint32_t t_r = tmem, t_i = tmem + 256;
         for (int it = 0; !stall && it < n; ++it) {
             const int s = it % PG_STAGES;
             const uint32_t use = (uint32_t)(it / PG_STAGES);
@@ -773,39 +876,43 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
                     const uint32_t Ar = q == 2 ? aRL : aRH, Ai = q == 2 ? aIL : aIH, B = q == 1 ? bL : bH;
                     const uint32_t acc = (sw.pos > 0 || kk > 0 || q > 0) ? 1u : 0u;
-                    mma_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
-                    mma_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
+                    mma2_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
+                    mma2_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
                 }
             }
-            mma_commit(bar_empty + 8 * s);
-            if (sw.closes(it, n)) mma_commit(bar_acc_full);
+            mma2_commit_pair(bar_empty + 8 * s);
+            if (sw.closes(it, n)) mma2_commit_pair(bar_acc_full);
         }
-        // no MMA may still read the stages or write TMEM once the CTA frees it
+        // no MMA may still read either CTA's stages or write its TMEM once
+        // the pair frees it
         if (issued > 0) {
-            mma_commit(bar_drain);
+            mma2_commit_pair(bar_drain);
             if (!mbar_wait(bar_drain, 0, kDrainNs)) atomicOr(err, kErrTimeout);
         }
     }
 
     tc_fence_before();
     __syncthreads();
+    // the leader has seen its MMAs complete (they read this CTA's shared
+    // memory and write its TMEM) and no arrival on the other CTA is pending
+    cluster_sync();
     if (warp == TC_PRODUCERS / 32) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc2(tmem, 512);
     }
 }
 
 // out[i][c] = scale * 2^e * (sum of the partials of the tile holding output
-// (i, c) in CTA order); 2^e undoes the weight scaling.  A block sums a patch
+// (i, c) in pair order); 2^e undoes the weight scaling.  A block sums a patch
 // of 32 rows x 32 columns of a partial tile (column q < 128: j = 128 tcol + q
-// at c+(j); q >= 128: j = 128 tcol + q - 128 at c-(j)).  The CTAs holding
-// units of tile t are c_lo..c_hi, the last CTAs whose ranges start at or
-// before the tile's first and last unit; CTA c keeps its partial of tile t in
-// slot c + t.  Each thread reads four columns of one row as a vector, the
-// patch turns in shared memory, and writes run along the rows of out (the
-// mirrored half in descending columns).  c-(0) = c+(0) for integer offsets
-// and is written once.
+// at c+(j); q >= 128: j = 128 tcol + q - 128 at c-(j)).  The pairs holding
+// units of pair tile t are c_lo..c_hi (of P), the last pairs whose ranges
+// start at or before the tile's first and last unit; CTA h of pair c keeps its
+// 128 rows' partial of tile t in slot 2 (c + t) + h.  Each thread reads four
+// columns of one row as a vector, the patch turns in shared memory, and
+// writes run along the rows of out (the mirrored half in descending columns).
+// c-(0) = c+(0) for integer offsets and is written once.
 __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
                                                      PairGeom pg, int tilesC, float scale,
                                                      const unsigned* __restrict__ amax2, float2* __restrict__ out)
@@ -816,7 +923,9 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
     const int i0 = blockIdx.y * 32;
     const int tcol = blockIdx.x >> 3, q0 = (blockIdx.x & 7) * 32;  // tile column, first partial column
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int64_t t = (int64_t)(i0 / TC_ROWS) * tilesC + tcol;
+    const int tr = i0 / TC_ROWS;                   // 128-row half tile: pair tile row tr / 2, CTA tr % 2
+    const int64_t t = (int64_t)(tr >> 1) * tilesC + tcol;
+    const int h = tr & 1;
     const int64_t c_lo = ((t * K + 1) * P - 1) / U;
     const int64_t c_hi = ((t + 1) * K * P - 1) / U;
     const int row = (i0 % TC_ROWS) + tx;
@@ -826,7 +935,7 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
         float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = ar;
         for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
             if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
-            const float* pt = part + (cc + t) * TC_TILE_FLOATS;
+            const float* pt = part + (2 * (cc + t) + h) * TC_TILE_FLOATS;
             const float4 r = *reinterpret_cast<const float4*>(pt + ((size_t)cg * TC_ROWS + row) * 4);
             const float4 m = *reinterpret_cast<const float4*>(pt + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4);
             ar.x += r.x; ar.y += r.y; ar.z += r.z; ar.w += r.w;
@@ -1186,6 +1295,59 @@ PairGeom pair_geom(const spirec_plan_s* p, int knob)
     return g;
 }
 
+// Clusters of two k_tc_pair_gemm CTAs the device runs at once (cached per
+// device): the pairs a launch may spread its work over.
+int pair_clusters(int* out)
+{
+    static int cached[64];
+    int dev = 0;
+    SPIREC_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) dev = 63;
+    if (cached[dev] <= 0) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (kMaxCtas / 2));
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = PG_SMEM;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        SPIREC_CK(cudaOccupancyMaxActiveClusters(&n, (void*)k_tc_pair_gemm<false, false>, &cfg));
+        if (n < 1) {
+            set_error("the device runs no cluster of two contraction CTAs");
+            return SPIREC_EUNSUPPORTED;
+        }
+        cached[dev] = n;
+    }
+    *out = cached[dev];
+    return SPIREC_OK;
+}
+
+template <bool BF16, bool WEIGHTED>
+cudaError_t launch_pair_kernel(int64_t P, cudaStream_t stream, const int64_t* ka, const int64_t* kb, const float2* w,
+                               const unsigned* amax, int64_t L, int tilesC, int oa, int sa, int sb, int half, int J,
+                               int64_t K, int64_t U, float* part, int* err, unsigned long long wait_ns, int stall)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)P);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = PG_SMEM;
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tc_pair_gemm<BF16, WEIGHTED>, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J,
+                              K, U, part, err, wait_ns, stall);
+}
+
 // The paired contraction out[i][c] = scale sum_l A(l,i) B(l,c) with
 // A(l,i) = exp(sa i2pi ka_l (i + oa)), B(l,c) = w_l exp(sb i2pi kb_l (c + ob)).
 int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, const float2* w, int oa, int ob,
@@ -1193,7 +1355,7 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
 {
     const PairGeom pg = pair_geom(p, knob);
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int tilesR = (pg.R + TC_ROWS - 1) / TC_ROWS, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
+    const int tilesR = (pg.R + PG_ROWS - 1) / PG_ROWS, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
     const int64_t T = (int64_t)tilesR * tilesC;
     const int64_t U = T * K;
     int sms = 0, rc;
@@ -1220,26 +1382,26 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
         SPIREC_CK(cudaGetLastError());
         p->launches += 2;
     }
-    const dim3 grid((unsigned)P);
     float* part = p->kpart;
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
     const unsigned long long wait_ns = wait_limit_ns();
     const int stall = injected_stall(kStallContraction) ? 1 : 0;
+    cudaError_t le;
     if (bf16 && w)
-        k_tc_pair_gemm<true, true><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
+        le = launch_pair_kernel<true, true>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
+                                            U, part, p->dflag, wait_ns, stall);
     else if (bf16)
-        k_tc_pair_gemm<true, false><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
+        le = launch_pair_kernel<true, false>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
+                                             U, part, p->dflag, wait_ns, stall);
     else if (w)
-        k_tc_pair_gemm<false, true><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
+        le = launch_pair_kernel<false, true>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
+                                             U, part, p->dflag, wait_ns, stall);
     else
-        k_tc_pair_gemm<false, false><<<grid, TC_THREADS, PG_SMEM, p->stream>>>(
-            ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K, U, part, p->dflag, wait_ns, stall);
-    SPIREC_CK(cudaGetLastError());
+        le = launch_pair_kernel<false, false>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J,
+                                              K, U, part, p->dflag, wait_ns, stall);
+    SPIREC_CK(le);
     const dim3 rgrid((unsigned)(tilesC * 8), (unsigned)((pg.R + 31) / 32));
-    k_reduce_pair<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P, pg, tilesC, scale, amax, out);
+    k_reduce_pair<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P / 2, pg, tilesC, scale, amax, out);
     SPIREC_CK(cudaGetLastError());
     p->launches += 2;
     return SPIREC_OK;
@@ -1307,9 +1469,10 @@ size_t fsplit_bytes_tc(int N, int precision)
 size_t kpart_floats_tc(int N, int64_t, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
-    // slots c + t < P + T; G (N rows, N paired columns) has the most tiles
-    const size_t T = (size_t)((N + TC_ROWS - 1) / TC_ROWS) * (size_t)((N + PG_COLS - 1) / PG_COLS);
-    return ((size_t)kMaxCtas + T) * TC_TILE_FLOATS;
+    // slots 2 (c + t) + h < 2 (P + T) for P pairs and T pair tiles; G (N
+    // rows, N paired columns) has the most tiles
+    const size_t T = (size_t)((N + PG_ROWS - 1) / PG_ROWS) * (size_t)((N + PG_COLS - 1) / PG_COLS);
+    return ((size_t)kMaxCtas + 2 * T) * TC_TILE_FLOATS;
 }
 
 int tc_setup_attributes()
@@ -1338,26 +1501,31 @@ int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
     return tc_pair_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, 0, 0, -1, -1, 1.0f / (float)N, x);
 }
 
-// The stream-K CTA count: the tuned value of the shape, else one CTA per SM
-// (at most kMaxCtas); never more than the work units, and the partial slots
-// c + t < P + T must fit the split-K buffer.
+// The stream-K CTA count, always even (the contraction runs on pairs): the
+// tuned value of the shape rounded down to even (at least 2), else one CTA
+// per SM (at most kMaxCtas); never more pairs than the device runs at once or
+// than there are work units, and the partial slots 2 (c + t) + h < 2 (P / 2 +
+// T) must fit the split-K buffer.
 int tc_ctas(spirec_plan p, int knob, int sms, int64_t* out)
 {
     const PairGeom pg = pair_geom(p, knob);
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int64_t T = (int64_t)((pg.R + TC_ROWS - 1) / TC_ROWS) * ((pg.J + PG_COLS - 1) / PG_COLS);
+    const int64_t T = (int64_t)((pg.R + PG_ROWS - 1) / PG_ROWS) * ((pg.J + PG_COLS - 1) / PG_COLS);
     const int64_t U = T * K;
-    int64_t P = sms < kMaxCtas ? sms : kMaxCtas;
+    int clusters = 0, rc;
+    if ((rc = pair_clusters(&clusters)) != SPIREC_OK) return rc;
+    int64_t P2 = (sms < kMaxCtas ? sms : kMaxCtas) / 2;
     const int tuned = tune_lookup(knob, p, sms);
-    if (tuned > 0 && tuned < P) P = tuned;
-    if (P > U) P = U;
-    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float)));
-    if (P + T > cap) P = cap - T;
-    if (P < 1) {
+    if (tuned > 0 && tuned / 2 < P2) P2 = tuned / 2 > 0 ? tuned / 2 : 1;
+    if (P2 > clusters) P2 = clusters;
+    if (P2 > U) P2 = U;
+    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float))) / 2;
+    if (P2 + T > cap) P2 = cap - T;
+    if (P2 < 1) {
         set_error("partial buffer too small for %lld tiles", (long long)T);
         return SPIREC_EUNSUPPORTED;
     }
-    *out = P;
+    *out = 2 * P2;
     return SPIREC_OK;
 }
 
