@@ -386,28 +386,43 @@ __device__ __forceinline__ uint32_t sw64(int row, int chunk)
     return (uint32_t)((row >> 3) * 512 + (row & 7) * 64 + ((chunk ^ ((row >> 1) & 3)) << 4));
 }
 
+// hi/lo split of a pair: hi = the pair rounded to FP16 (BF16), packed (a in
+// the low half); lo = (x - hi) rounded the same way, where x - hi is formed
+// exactly in FP32 by one mixed-precision FMA per value (hi * -1 + x).
+template <bool BF16>
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo)
+{
+    float la, lb;
+    if (BF16) {
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+        asm("{\n\t.reg .b16 h0, h1, m;\n\t"
+            "mov.b32 {h0, h1}, %2;\n\t"
+            "mov.b16 m, 0xBF80;\n\t"  // -1
+            "fma.rn.f32.bf16 %0, h0, m, %3;\n\t"
+            "fma.rn.f32.bf16 %1, h1, m, %4;\n\t}"
+            : "=f"(la), "=f"(lb)
+            : "r"(hi), "f"(a), "f"(b));
+        asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(lb), "f"(la));
+    } else {
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(hi) : "f"(b), "f"(a));
+        asm("{\n\t.reg .f16 h0, h1, m;\n\t"
+            "mov.b32 {h0, h1}, %2;\n\t"
+            "mov.b16 m, 0xBC00;\n\t"  // -1
+            "fma.rn.f32.f16 %0, h0, m, %3;\n\t"
+            "fma.rn.f32.f16 %1, h1, m, %4;\n\t}"
+            : "=f"(la), "=f"(lb)
+            : "r"(hi), "f"(a), "f"(b));
+        asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(lo) : "f"(lb), "f"(la));
+    }
+}
+
 // hi/lo split of 8 values into 4 packed words each.
 template <bool BF16>
 __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo)
 {
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float a = x[2 * q], b = x[2 * q + 1];
-        if (BF16) {
-            const __nv_bfloat162 hv = __floats2bfloat162_rn(a, b);
-            const float2 back = __bfloat1622float2(hv);
-            const __nv_bfloat162 lv = __floats2bfloat162_rn(a - back.x, b - back.y);
-            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-        } else {
-            const __half2 hv = __floats2half2_rn(a, b);
-            const float2 back = __half22float2(hv);
-            const __half2 lv = __floats2half2_rn(a - back.x, b - back.y);
-            h[q] = *reinterpret_cast<const uint32_t*>(&hv);
-            l[q] = *reinterpret_cast<const uint32_t*>(&lv);
-        }
-    }
+    for (int q = 0; q < 4; ++q) split2<BF16>(x[2 * q], x[2 * q + 1], h[q], l[q]);
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
