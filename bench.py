@@ -45,8 +45,8 @@ ITERS = 50
 # is built from at the time of the capture.  A figure whose sources have
 # changed since is reported as null: the counters no longer describe the
 # kernel that runs.
-NCU_TRAFFIC = {"k_cg_loop": (10_694_656, "eb648684949b15af"), "k_tc_pair_gemm_G": (2_162_432, "53d41a8213fa5e72"),
-               "k_tc_pair_gemm_D": (3_204_864, "53d41a8213fa5e72")}
+NCU_TRAFFIC = {"k_cg_loop": (10_694_656, "eb648684949b15af"), "k_tc_pair_gemm_G": (2_174_976, "f223d2551dcf488b"),
+               "k_tc_pair_gemm_D": (3_207_936, "f223d2551dcf488b")}
 KERNEL_SOURCES = {
     "k_cg_loop": ["cg_loop.cu", "cg_device.cuh", "fft_device.cuh", "fft_reg.cuh", "reduce.cuh", "penalty.cuh",
                   "internal.cuh"],
@@ -933,14 +933,15 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": None, "kernel": dom}
     roof["stage_ms_per_step"] = {k: v[0] / max(args.steps, 1) for k, v in stages.items()}
     # the contraction beside it: G on the tensor cores, algorithmic flops (the
-    # dense count 8 N (2N-1) L of Eq. AnnMatG) and issued MMA flops (tiles of
-    # 128 rows x 128 paired columns, four real products and the three split
-    # products hi*hi + hi*lo + lo*hi each) against the measured bf16 rate
+    # dense count 8 N (2N-1) L of Eq. AnnMatG) and issued MMA flops (pair tiles
+    # of 256 rows x 128 paired columns: two accumulators of 256 rows x 256
+    # stacked B rows [Br ; Bi], three split products hi*hi + hi*lo + lo*hi
+    # each) against the measured bf16 rate
     if prec != spirec.SPIREC_FP32 and stages["gram"][1] > 0:
         g_ms = stages["gram"][0] / stages["gram"][1]
         flops = 8.0 * N * (2 * N - 1) * L
-        tiles = ((N + 127) // 128) * ((N + 127) // 128)
-        issued = 2.0 * 4 * 3 * 128 * 128 * (32 * ((L + 31) // 32)) * tiles
+        tiles = ((N + 255) // 256) * ((N + 127) // 128)
+        issued = 2.0 * 2 * 3 * 256 * 256 * (32 * ((L + 31) // 32)) * tiles
         peak = (pk or {}).get("bf16_tflops", 1900.0)
         extra["roofline_contraction"] = {
             "bound": "tensor", "kernel": "k_tc_pair_gemm (G) + its split-K sum (k_reduce_pair)", "unit": "TFLOP/s",

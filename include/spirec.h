@@ -382,8 +382,9 @@ int spirec_server_destroy(spirec_server srv);
  * heuristic.  Knobs and their values:
  *   SPIREC_KNOB_GRAM_SPLIT     G: tensor-core paths, the number of CTAs the
  *                              stream-K schedule spreads the work over
- *                              (1..152); FP32 path, the number of slices the
- *                              samples are cut into (>= 1).
+ *                              (2..152, rounded down to even: the contraction
+ *                              runs on CTA pairs); FP32 path, the number of
+ *                              slices the samples are cut into (>= 1).
  *   SPIREC_KNOB_ADJOINT_SPLIT  the same for D and every other H^H y.
  *   SPIREC_KNOB_LOOP_ROWS      persistent CG loop: image rows per block.
  * A value that does not fit the device or the plan at launch time (too many

@@ -11,55 +11,61 @@
 // and the drain forms both columns, (P_ac - P_bd, P_ad + P_bc) and (P_ac +
 // P_bd, P_bc - P_ad).  G needs its lags v and -v, D its columns on both sides
 // of the image centre: half the MMAs of forming every column on its own.
-// Per tile of 128 rows x 128 B columns, B is stored once as a stacked
-// operand of 256 rows [Br ; Bi], so two MMAs (M = 128, N = 256) per K slice,
-// Ar [Br ; Bi]^T = [P_ac | P_ad] and Ai [Br ; Bi]^T = [P_bc | P_bd], fill all
-// 512 columns of tensor memory.  N = 256 reads 12 KB of shared memory per
-// 128 x 256 x 16 product where two N = 128 MMAs read 16 KB: the tensor
-// core's operand reads and the producers' stores share the shared-memory
-// data path, which bounds this kernel.
+// The kernel runs on CTA pairs (clusters of two, one CTA per SM).  A pair
+// tile is 256 rows x 128 B columns; CTA h holds A rows 128 h .. 128 h + 127
+// (real and imaginary parts as two operand tiles) and, for B columns 64 h ..
+// 64 h + 63, B stored once as a stacked operand of 128 rows [Br ; Bi].  Two
+// pair MMAs (tcgen05.mma.cta_group::2, M = 256, N = 256) per K slice, A_re
+// [B]^T = [P_ac | P_ad] and A_im [B]^T = [P_bc | P_bd] per B half, read both
+// CTAs' tiles and fill all 512 columns of each CTA's tensor memory for its
+// 128 rows.  N = 256 reads 12 KB of shared memory per 128 x 256 x 16 product
+// where two N = 128 MMAs read 16 KB (the tensor core's operand reads and the
+// producers' stores share the shared-memory data path), and the pair halves
+// the B columns each SM generates.
 //
 // Split precision: every operand value x is stored as x_hi = fp16(x) (or
 // bf16) and x_lo = fp16(x - x_hi); the products hi*hi + hi*lo + lo*hi feed
 // the same FP32 accumulator (the dropped lo*lo term is 2^-22 relative for
 // FP16).
 //
-// Work split (stream-K): the tiles x sample-chunks units are cut into equal
-// contiguous ranges, one per CTA and one CTA per SM, so every SM does the
-// same work whatever the tile count; a range may end in one tile and go on
-// in the next.  CTA c writes its partial of tile t to slot c + t (unique,
-// since both grow along the ranges) and k_reduce_pair adds the partials of
-// each tile in CTA order.
+// Work split (stream-K): the pair tiles x sample-chunks units are cut into
+// equal contiguous ranges, one per pair and one pair per two SMs, so every
+// SM does the same work whatever the tile count; a range may end in one tile
+// and go on in the next.  CTA h of pair c writes its rows' partial of tile t
+// to slot 2 (c + t) + h (unique, since c and t grow along the ranges) and
+// k_reduce_pair adds the partials of each tile in pair order.
 //
 // Pipeline per CTA (544 threads):
 //   warps 0-15 producers: per stage of 32 samples, each thread of warps 0-7
 //              forms the phasors of two A rows (times the weight, for D) and
-//              each thread of warps 8-15 those of two B columns, for 8
+//              each thread of warps 8-15 those of one B column, for 8
 //              samples (exact fixed-point phase, fast hardware sin/cos), so
 //              a warp's 32 lanes share the 8 trajectory values they read;
 //              splits them into hi and lo operand tiles in the
 //              64-byte-swizzled K-major layout the MMA reads (rows of 32
-//              samples), then each warp arrives once on full[stage];
-//   warp 16    allocates 512 TMEM columns; one lane waits on full[stage],
-//              issues 12 tcgen05.mma (M = 128, N = 256, K = 16 each) and
-//              commits to empty[stage];
+//              samples), then each warp arrives once on the pair leader's
+//              full[stage];
+//   warp 16    allocates 512 TMEM columns (with the other CTA's warp 16); in
+//              the leader, one lane waits on full[stage], issues 12 pair
+//              MMAs (K = 16 each) and commits to empty[stage] of both CTAs;
 //   warps 0-15 drain: at the end of every segment (at most SEG stages of one
 //              tile) the finished accumulators are read with tcgen05.ld and
 //              the paired outputs added to the CTA's partial tile in global
 //              memory by fire-and-forget vector reductions
 //              (red.global.add.v4.f32, round-to-nearest; the first segment
 //              of a tile stores), laid out so that a warp's 32 lanes cover
-//              512 contiguous bytes.  The MMA waits for the drain.
+//              512 contiguous bytes.  The leader's MMA waits for the drains
+//              of both CTAs.
 // The tensor core's FP32 accumulation loses about one unit in the last place
 // per accumulation step (truncation-like, measured: 2.8e-4 relative after
 // 12k steps); draining every 32 stages (384 accumulation steps) bounds that
-// error.  Three stages of 64 KB buffer generation against the tensor core.
+// error.  Four stages of 48 KB buffer generation against the tensor core.
 // The stage's 32 samples of the trajectory (and of the weights, for D) arrive
 // by TMA bulk copy (cp.async.bulk) into an 8-deep shared-memory ring two
 // stages ahead, so the table builders never wait on global memory.
 // Every mbarrier wait is bounded in time; on expiry the kernel records an
 // error bit, lets the other roles run out, waits for its own copies and
-// MMAs, frees its TMEM and returns.
+// MMAs, meets the other CTA of its pair, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
