@@ -380,7 +380,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
         __syncthreads();
         if (MODE == 1) {
             const Reg reg = c.reg;
-#pragma unroll 2
+#pragma unroll 4
             for (int e = tid; e < nr * N; e += kSplitThreads) {
                 const int qq = e / N, m = e - qq * N;
                 const int n = r0 + qq;
