@@ -5,6 +5,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace spirec {
 namespace cgd {
@@ -70,6 +71,16 @@ __device__ __forceinline__ double ls_next(double t, double q1, double q2, double
     const double h1 = q1 + 2.0 * q2 * t + num;
     const double c = 2.0 * q2 + den;
     return c > 0.0 ? t - h1 / c : t;
+}
+
+// ls_next in float-float arithmetic (the persistent loop, where the step sits
+// between a grid synchronisation and the next phase of every block).
+__device__ __forceinline__ FF ls_next_ff(FF t, FF q1, FF q2, FF num, FF den)
+{
+    const FF q2x2 = ff_twice(q2);
+    const FF h1 = ff_add(ff_add(q1, ff_mul(q2x2, t)), num);
+    const FF c = ff_add(q2x2, den);
+    return c.hi > 0.f ? ff_add(t, ff_neg(ff_div_pos(h1, c))) : t;
 }
 
 // Gradient at a pixel from its values: g = 2 res + grad R(f), res = T f - D

@@ -95,8 +95,10 @@ struct LoopArgs {
 // Loop scalars, one copy per block.  Thread 0 writes them between two
 // __syncthreads(); the FP64 values are used by thread 0 only.
 struct LoopShared {
-    double red[8];  // grid sums of the last reduction
-    double ss, gg, J, beta, q1, q2, t;
+    double red[8];  // grid sums of the deferred update reduction (and the first)
+    FF redf[8];     // grid sums of the last grid_reduce
+    double ss, gg, J, beta;
+    FF q1, q2, t;   // line-search scalars, float-float: they sit on the critical path
     float beta_f, t_f;
     int restart, ok;
     unsigned long long prof[kProf], tmark;
@@ -183,7 +185,8 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
 }
 
 // Block partials of K values to slot `slot`, the synchronisation, then the
-// grid totals as FP64 in S.red, readable by every thread on return.  seq
+// grid totals as float-float pairs in S.redf, readable by every thread on
+// return.  seq
 // counts the synchronisations of the launch (the same in every thread).
 template <int K>
 __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned& seq, LoopShared& S,
@@ -203,7 +206,7 @@ __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int sl
     const int warp = threadIdx.x >> 5;
     if (warp < K) {
         const FF a = warp_sum_parts(parts + (slot + warp) * kMaxParts, gridDim.x);
-        if ((threadIdx.x & 31) == 0) S.red[warp] = ff_to_double(a);
+        if ((threadIdx.x & 31) == 0) S.redf[warp] = a;
     }
     __syncthreads();
     return true;
@@ -906,6 +909,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             phase_update<MC, true, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, 0.f, A.iters > 0, a);
         if (!grid_reduce<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
         if (threadIdx.x == 0) {
+            for (int v = 0; v < kUpdVals; ++v) S.red[v] = ff_to_double(S.redf[v]);
             double J, beta;
             cgd::update_finish(S.red, S.ss, 0.0, true, &J, &beta);
             S.gg = S.red[0];
@@ -967,11 +971,10 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             mark(2);
             if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             if (threadIdx.x == 0) {
-                S.q1 = S.red[0];
-                S.q2 = S.red[3];
-                const double curv = 2.0 * S.q2 + S.red[2];
-                S.t = curv > 0.0 ? -(S.q1 + S.red[1]) / curv : 0.0;
-                S.t_f = (float)S.t;
+                S.q1 = S.redf[0];
+                S.q2 = S.redf[3];
+                S.t = cgd::ls_next_ff(FF{0.f, 0.f}, S.q1, S.q2, S.redf[1], S.redf[2]);
+                S.t_f = S.t.hi + S.t.lo;
             }
             __syncthreads();
             mark(3);
@@ -984,8 +987,8 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             mark(4 + 2 * j);
             if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             if (threadIdx.x == 0) {
-                S.t = cgd::ls_next(S.t, S.q1, S.q2, S.red[0], S.red[1]);
-                S.t_f = (float)S.t;
+                S.t = cgd::ls_next_ff(S.t, S.q1, S.q2, S.redf[0], S.redf[1]);
+                S.t_f = S.t.hi + S.t.lo;
             }
             __syncthreads();
             mark(5 + 2 * j);
@@ -999,11 +1002,6 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
                 phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
             mark(8);
             if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
-            if (threadIdx.x == 0 && blockIdx.x == 0) {
-                A.scal[S_Q1] = S.q1;
-                A.scal[S_Q2] = S.q2;
-                A.scal[S_T3] = S.t;
-            }
             mark(9);
         }
     }
@@ -1015,7 +1013,14 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             if ((threadIdx.x & 31) == 0) S.red[warp] = ff_to_double(a);
         }
         __syncthreads();
-        if (threadIdx.x == 0) finish_update(A, S, A.iters);
+        if (threadIdx.x == 0) {
+            finish_update(A, S, A.iters);
+            if (blockIdx.x == 0) {  // the last iteration's line-search scalars
+                A.scal[S_Q1] = ff_to_double(S.q1);
+                A.scal[S_Q2] = ff_to_double(S.q2);
+                A.scal[S_T3] = ff_to_double(S.t);
+            }
+        }
         __syncthreads();
     }
     // ---- the iterate and T f - D back to global memory

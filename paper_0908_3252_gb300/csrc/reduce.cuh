@@ -28,6 +28,41 @@ __device__ __forceinline__ FF ff_add(FF a, FF b)
 
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
+// Float-float products and quotients for scalar work on the critical path of
+// a grid synchronisation (FP64 operations have long latencies on GB300; these
+// are FP32 operations).  hi + lo of the result is within a few 2^-46 of the
+// exact value.
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ FF ff_twice(FF a) { return FF{2.f * a.hi, 2.f * a.lo}; }
+
+// a * b: the product of the high parts and its exact rounding error from one
+// FMA (Ogita, Rump and Oishi's TwoProduct), the cross terms added to the
+// error, then Dekker's Fast2Sum.  __fmul_rn / __fadd_rn / __fsub_rn are never
+// contracted into FMAs.
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = __fadd_rn(p, e);
+    return FF{hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
+// a / b for b > 0 (Dekker's double-length division): q0 = a.hi / b.hi in
+// FP32, the remainder a - b q0 in float-float, and its quotient as the
+// correction.
+__device__ __forceinline__ FF ff_div_pos(FF a, FF b)
+{
+    const float rb = __frcp_rn(b.hi);
+    const float q0 = __fmul_rn(a.hi, rb);
+    const FF r = ff_add(a, ff_neg(ff_mul(b, FF{q0, 0.f})));
+    const float q1 = __fmul_rn(r.hi, rb);
+    const float hi = __fadd_rn(q0, q1);
+    return FF{hi, __fsub_rn(q1, __fsub_rn(hi, q0))};
+}
+
 // Warp-level float-float sum (valid in lane 0).
 __device__ __forceinline__ FF warp_sum_ff(FF a)
 {
