@@ -954,13 +954,28 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
         // thread (tx, ty): row tx of the patch, partial columns q0 + 4 ty .. + 3
         const int cg = (q0 >> 2) + ty;
         float4 ar = make_float4(0.f, 0.f, 0.f, 0.f), ai = ar;
-        for (int64_t cc = c_lo; cc <= c_hi; ++cc) {
-            if (unit_start(cc + 1, U, P) == unit_start(cc, U, P)) continue;  // an empty range
-            const float* pt = part + (2 * (cc + t) + h) * TC_TILE_FLOATS;
-            const float4 r = *reinterpret_cast<const float4*>(pt + ((size_t)cg * TC_ROWS + row) * 4);
-            const float4 m = *reinterpret_cast<const float4*>(pt + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4);
-            ar.x += r.x; ar.y += r.y; ar.z += r.z; ar.w += r.w;
-            ai.x += m.x; ai.y += m.y; ai.z += m.z; ai.w += m.w;
+        // four partials' loads in flight at a time, added in pair order; an
+        // empty range (or one past c_hi) adds zeros, which change no sum.
+        // Ranges can be empty only when there are fewer units than pairs.
+        constexpr int B = 4;
+        const bool any_empty = U < P;
+        for (int64_t c0 = c_lo; c0 <= c_hi; c0 += B) {
+            float4 r[B], m[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int64_t cc = c0 + b;
+                const bool use =
+                    cc <= c_hi && (!any_empty || unit_start(cc + 1, U, P) != unit_start(cc, U, P));
+                const float* pt = part + (2 * ((use ? cc : c_lo) + t) + h) * TC_TILE_FLOATS;
+                r[b] = *reinterpret_cast<const float4*>(pt + ((size_t)cg * TC_ROWS + row) * 4);
+                m[b] = *reinterpret_cast<const float4*>(pt + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4);
+                if (!use) r[b] = m[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                ar.x += r[b].x; ar.y += r[b].y; ar.z += r[b].z; ar.w += r[b].w;
+                ai.x += m[b].x; ai.y += m[b].y; ai.z += m[b].z; ai.w += m[b].w;
+            }
         }
         patch[4 * ty + 0][tx] = make_float2(ar.x * sc, ai.x * sc);
         patch[4 * ty + 1][tx] = make_float2(ar.y * sc, ai.y * sc);
@@ -983,15 +998,22 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
 
 // w'_l = w_l exp(sb i2pi (kb_l / 2) shift2) for l < L (the weight of the
 // original B operand and the phase of the pairing's centre column, shift2 =
-// C2 + 2 ob); the plan's buffer keeps its zero padding past L.
+// C2 + 2 ob); the plan's buffer keeps its zero padding past L.  amax2 (zeroed
+// before the launch) receives max_l |w'_l|^2 as float bits, as k_absmax2.
 __global__ void k_pair_weights(const float2* __restrict__ w, const int64_t* __restrict__ kb, int64_t L, int sb,
-                               int shift2, float2* __restrict__ wp)
+                               int shift2, float2* __restrict__ wp, unsigned* amax2)
 {
+    float mx = 0.f;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < L; l += (int64_t)gridDim.x * blockDim.x) {
         float2 e = phasor_q(kb[l] >> 1, shift2);
         if (sb < 0) e.y = -e.y;
-        wp[l] = cmul(w[l], e);
+        const float2 v = cmul(w[l], e);
+        wp[l] = v;
+        mx = fmaxf(mx, fmaf(v.x, v.x, v.y * v.y));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && isfinite(mx)) atomicMax(amax2, __float_as_uint(mx));
 }
 
 // ------------------------------------------------------------ forward H f
@@ -1394,14 +1416,12 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
         // (its padding past L stays zero), and max |w'|^2 for the scaling
         int blocks = (int)((p->L + 255) / 256);
         if (blocks > 4 * kMaxCtas) blocks = 4 * kMaxCtas;
-        k_pair_weights<<<blocks, 256, 0, p->stream>>>(w, kb, p->L, sb, shift2, p->wpair);
-        SPIREC_CK(cudaGetLastError());
-        w = p->wpair;
         amax = p->counters + C_AMAX;
         SPIREC_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), p->stream));
-        k_absmax2<<<blocks, 256, 0, p->stream>>>(w, p->L, amax);
+        k_pair_weights<<<blocks, 256, 0, p->stream>>>(w, kb, p->L, sb, shift2, p->wpair, amax);
         SPIREC_CK(cudaGetLastError());
-        p->launches += 2;
+        w = p->wpair;
+        p->launches += 1;
     }
     float* part = p->kpart;
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
