@@ -554,25 +554,37 @@ __global__ void __launch_bounds__(1024) k_cols_spectrum(const float2* cwork, Fft
 // c[y][x] = K[v][u] = conj G_{u,v} with v = y (y < N) or y - M (y > M - N),
 // u likewise from x; zero where |u| or |v| >= N.  G holds u >= 0; the rest is
 // G_{u,v} = conj G_{-u,-v}.
-__global__ void k_embed(const float2* __restrict__ G, int N, int M, float2* cwork)
+__global__ void __launch_bounds__(256) k_embed(const float2* __restrict__ G, int N, int M, float2* cwork)
 {
-    const int64_t MM = (int64_t)M * M;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MM;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int y = (int)(e / M), x = (int)(e % M);
-        const int v = y < N ? y : (y > M - N ? y - M : INT32_MIN);
-        const int u = x < N ? x : (x > M - N ? x - M : INT32_MIN);
+    // one 32 x 32 tile of cwork through shared memory: G is read along its
+    // rows (the lags v of one u) and cwork written along its rows (x)
+    __shared__ float2 tile[32][33];  // [x - x0][y - y0]
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int W = 2 * N - 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = x0 + ty + 8 * k, y = y0 + tx;
         float2 c = make_float2(0.f, 0.f);
-        if (v != INT32_MIN && u != INT32_MIN) {
-            const int W = 2 * N - 1;
-            if (u >= 0) {
-                const float2 g = G[(int64_t)u * W + (v + N - 1)];
-                c = make_float2(g.x, -g.y);
-            } else {
-                c = G[(int64_t)(-u) * W + (-v + N - 1)];
+        if (x < M && y < M) {
+            const int v = y < N ? y : (y > M - N ? y - M : INT32_MIN);
+            const int u = x < N ? x : (x > M - N ? x - M : INT32_MIN);
+            if (v != INT32_MIN && u != INT32_MIN) {
+                if (u >= 0) {
+                    const float2 g = G[(int64_t)u * W + (v + N - 1)];
+                    c = make_float2(g.x, -g.y);
+                } else {
+                    c = G[(int64_t)(-u) * W + (-v + N - 1)];
+                }
             }
         }
-        cwork[e] = c;
+        tile[ty + 8 * k][tx] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = x0 + tx, y = y0 + ty + 8 * k;
+        if (x < M && y < M) cwork[(int64_t)y * M + x] = tile[tx][ty + 8 * k];
     }
 }
 
@@ -888,7 +900,8 @@ int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar)
 int launch_spectrum(spirec_plan p)
 {
     const int N = p->N, M = p->M;
-    k_embed<<<4 * 152, 256, 0, p->stream>>>(p->G, N, M, p->cwork);
+    k_embed<<<dim3((unsigned)((M + 31) / 32), (unsigned)((M + 31) / 32)), dim3(32, 8), 0, p->stream>>>(p->G, N, M,
+                                                                                                   p->cwork);
     SPIREC_CK(cudaGetLastError());
     p->launches += 1;
     const bool pow2 = is_pow2_specialised(M);
