@@ -185,7 +185,8 @@ def run_batch(spirec, prec, frames=64, iters=50, seed=4):
         p = it[0]
         spirec.spirec_set_data_dev(p.h, it[4])
         chosen, _ = spirec.spirec_autotune(p.h, spirec.SPIREC_TUNE_THROUGHPUT, iters)
-        tuned[N] = dict(zip(("gram_split", "adjoint_split", "loop_rows"), chosen.tolist()))
+        tuned[N] = dict(zip(("gram_split", "adjoint_split", "loop_rows", "gram_tile", "adjoint_tile"),
+                            chosen.tolist()))
     tune_s = time.perf_counter() - t0
     dt_built = timed_graph(False)
     dt = timed_graph(True)

@@ -387,13 +387,23 @@ int spirec_server_destroy(spirec_server srv);
  *                              slices the samples are cut into (>= 1).
  *   SPIREC_KNOB_ADJOINT_SPLIT  the same for D and every other H^H y.
  *   SPIREC_KNOB_LOOP_ROWS      persistent CG loop: image rows per block.
+ *   SPIREC_KNOB_GRAM_TILE      G, tensor-core paths: the tile shape, 1 = one
+ *                              SM a tile of 128 output rows (MMA M = 128),
+ *                              2 = a pair of SMs a tile of 256 rows (a cluster
+ *                              of two CTAs, MMA M = 256 across the pair).
+ *                              Without an entry: 2, except 1 where 256-row
+ *                              tiles would leave a last tile half empty
+ *                              beyond 256 rows (N = 384, 640, ...).
+ *   SPIREC_KNOB_ADJOINT_TILE   the same for D and every other H^H y.
  * A value that does not fit the device or the plan at launch time (too many
  * CTAs for the split-K buffer, a loop shape whose blocks are not
  * co-resident) is clipped, or, for the loop, replaced by the heuristic. */
 #define SPIREC_KNOB_GRAM_SPLIT 0
 #define SPIREC_KNOB_ADJOINT_SPLIT 1
 #define SPIREC_KNOB_LOOP_ROWS 2
-#define SPIREC_NUM_KNOBS 3
+#define SPIREC_KNOB_GRAM_TILE 3
+#define SPIREC_KNOB_ADJOINT_TILE 4
+#define SPIREC_NUM_KNOBS 5
 
 /* Objectives: LATENCY minimises the time of one launch; THROUGHPUT the
  * SM-time (launch time x SMs the launch occupies), for many solves that share
@@ -407,7 +417,9 @@ int spirec_server_destroy(spirec_server srv);
  * store the best under the plan's key, and rebuild G, the spectrum and D with
  * it, so that the plan's state equals that of a new plan of the same shape.
  * The loop is timed over loop_iters iterations from x0 = 0 (>= 1; skipped in
- * direct mode and for M the loop does not handle).  chosen[SPIREC_NUM_KNOBS]
+ * direct mode and for M the loop does not handle); each contraction's tile
+ * shape is chosen first (at the heuristic split), then its split.
+ * chosen[SPIREC_NUM_KNOBS]
  * receives the stored values (0: knob not tuned); best_ms (may be NULL) the
  * median milliseconds of the winners.  Blocks the host until done. */
 int spirec_autotune(spirec_plan plan, int32_t objective, int32_t loop_iters, int32_t* chosen, double* best_ms);

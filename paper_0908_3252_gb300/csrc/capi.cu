@@ -559,6 +559,39 @@ int tune_contraction(spirec_plan p, int knob, int objective, int sms, int* chose
     return tune_store(knob, p, sms, best);
 }
 
+// The tile shape of a contraction (tensor-core paths): both shapes timed at
+// the heuristic split, the better one stored; the split is tuned after it.
+int tune_tile(spirec_plan p, int split_knob, int objective, int sms, int* chosen, double* best_ms)
+{
+    const int tile_knob = split_knob == SPIREC_KNOB_GRAM_SPLIT ? SPIREC_KNOB_GRAM_TILE : SPIREC_KNOB_ADJOINT_TILE;
+    *chosen = 0;
+    *best_ms = 0.0;
+    int rc;
+    if (p->precision == SPIREC_FP32) return tune_store(tile_knob, p, sms, 0);
+    if ((rc = tune_store(split_knob, p, sms, 0)) != SPIREC_OK) return rc;
+    double best_score = 0.0;
+    int best = 0;
+    for (int t : {2, 1}) {
+        if ((rc = tune_store(tile_knob, p, sms, t)) != SPIREC_OK) return rc;
+        int v = 0, used = 0;
+        if ((rc = contraction_split(p, split_knob, &v, &used)) != SPIREC_OK) return rc;
+        double ms = 0.0;
+        if (split_knob == SPIREC_KNOB_GRAM_SPLIT)
+            rc = time_median(p, [&] { return launch_gram(p); }, &ms);
+        else
+            rc = time_median(p, [&] { return launch_adjoint(p, p->s, p->D); }, &ms);
+        if (rc != SPIREC_OK) return rc;
+        const double score = objective == SPIREC_TUNE_THROUGHPUT ? ms * used : ms;
+        if (best == 0 || score < best_score) {
+            best = t;
+            best_score = score;
+            *best_ms = ms;
+        }
+    }
+    *chosen = best;
+    return tune_store(tile_knob, p, sms, best);
+}
+
 int tune_loop(spirec_plan p, int objective, int iters, int sms, int* chosen, double* best_ms)
 {
     *chosen = 0;
@@ -1387,10 +1420,16 @@ int spirec_autotune(spirec_plan p, int32_t objective, int32_t loop_iters, int32_
     }
     int sms = 0;
     if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
-    int got[SPIREC_NUM_KNOBS] = {0, 0, 0};
-    double ms[SPIREC_NUM_KNOBS] = {0.0, 0.0, 0.0};
+    int got[SPIREC_NUM_KNOBS] = {};
+    double ms[SPIREC_NUM_KNOBS] = {};
     SPIREC_CK(cudaStreamSynchronize(p->stream));
+    if ((rc = tune_tile(p, SPIREC_KNOB_GRAM_SPLIT, objective, sms, &got[SPIREC_KNOB_GRAM_TILE],
+                        &ms[SPIREC_KNOB_GRAM_TILE])) != SPIREC_OK)
+        return rc;
     if ((rc = tune_contraction(p, SPIREC_KNOB_GRAM_SPLIT, objective, sms, &got[0], &ms[0])) != SPIREC_OK) return rc;
+    if ((rc = tune_tile(p, SPIREC_KNOB_ADJOINT_SPLIT, objective, sms, &got[SPIREC_KNOB_ADJOINT_TILE],
+                        &ms[SPIREC_KNOB_ADJOINT_TILE])) != SPIREC_OK)
+        return rc;
     if ((rc = tune_contraction(p, SPIREC_KNOB_ADJOINT_SPLIT, objective, sms, &got[1], &ms[1])) != SPIREC_OK)
         return rc;
     // G, the spectrum and D as a new plan of this shape computes them

@@ -268,6 +268,9 @@ int solve_loop_demand(spirec_plan p, int* blocks, int* capacity);
 // grid side M it plans it with (server.cu).
 size_t server_plan_bytes(int N, int64_t L, int precision, int* M);
 int tc_ctas(spirec_plan p, int knob, int sms, int64_t* P);  // nudft_tc.cu
+// The tile shape the contraction of a split knob uses now: CTA pairs (true)
+// or one SM a tile (nudft_tc.cu).
+bool tc_pairs(spirec_plan p, int knob, int sms);
 
 // Limit of every bounded device wait of the kernels launched from now on
 // (2 s unless spirec_set_wait_limit_ns changed it).

@@ -88,30 +88,40 @@ constexpr int TC_TILE_FLOATS = 2 * TC_COLS * TC_ROWS;  // partial tile: 512 colu
 constexpr uint32_t A_BYTES = TC_ROWS * 128;          // 128 rows x 64 halves
 constexpr uint32_t B_BYTES = TC_COLS * 128;          // 256 rows x 64 halves
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo
-// The paired contraction (G, D) runs on CTA pairs (clusters of two, one CTA
-// per SM): a pair tile is 256 rows x 128 B columns, each B column giving two
-// output columns (see PairGeom).  CTA h of the pair holds A rows 128 h ..
-// 128 h + 127 and the stacked operand [Br ; Bi] of B columns 64 h .. 64 h +
-// 63, both 64-byte-swizzled K-major with rows of 32 samples; the leader's
-// tcgen05.mma.cta_group::2 (M = 256, N = 256) reads both CTAs' tiles and
-// writes each CTA's 128 rows x 256 columns of tensor memory.  Two
-// accumulators, [Ar ; Ai] x the pair's B; 48 KB stages, four deep; the
-// trajectory (and weight) chunks in an 8-deep ring, two stages ahead.
-constexpr int PG_COLS = 128;                                       // B columns per pair tile
-constexpr int PG_HCOLS = 64;                                       // B columns per CTA
-constexpr int PG_ROWS = 2 * TC_ROWS;                               // output rows per pair tile
+// The paired contraction (G, D): a tile is ROWS rows x 128 B columns, each B
+// column giving two output columns (see PairGeom).  The operands are stored
+// in 64-byte-swizzled K-major tiles of 32 samples per row: A's real and
+// imaginary parts as two tiles of 128 rows, B as a stacked tile [Br ; Bi] of
+// the BCOLS columns a CTA generates.  Two tile shapes (the tile knob):
+//   one SM a tile (PAIR = false): 128 rows; the CTA generates all 128 B
+//     columns (256 stacked rows); MMA M = 128, N = 256 (cta_group::1);
+//     three 64 KB stages;
+//   a CTA pair a tile (PAIR = true, clusters of two): 256 rows, CTA h holding
+//     rows 128 h .. +127 and B columns 64 h .. +63 (128 stacked rows); MMA
+//     M = 256, N = 256 (cta_group::2) issued by the pair's first CTA; four
+//     48 KB stages.
+// Either way each CTA's TMEM holds its 128 rows of [P_ac | P_ad] and
+// [P_bc | P_bd] (512 columns); the trajectory (and weight) chunks arrive in
+// an 8-deep ring, two stages ahead.
+constexpr int PG_COLS = 128;                                       // B columns per tile
 constexpr uint32_t PA_BYTES = TC_ROWS * 64;                        // 128 rows x 32 halves
-constexpr uint32_t PB_BYTES = 2 * PG_HCOLS * 64;                   // 128 stacked rows x 32 halves
-constexpr uint32_t PG_STAGE_BYTES = 4 * PA_BYTES + 2 * PB_BYTES;   // Ar, Ai (hi, lo), B (hi, lo)
-constexpr int PG_STAGES = 4;
-constexpr int PG_TRAJ_RING = 8;  // >= PG_STAGES + 2: a slot is refilled only after every producer left it
+constexpr int PG_TRAJ_RING = 8;  // >= stages + 2: a slot is refilled only after every producer left it
 constexpr uint32_t PG_TRAJ_BUF = 3 * TC_KS * 8;  // ka, kb (int64), w' (float2)
-constexpr uint32_t PG_TRAJ_OFF = PG_STAGES * PG_STAGE_BYTES;
-constexpr uint32_t PG_BAR_OFF = PG_TRAJ_OFF + PG_TRAJ_RING * PG_TRAJ_BUF;
-constexpr uint32_t PG_SMEM = PG_BAR_OFF + 256 + 1024;  // + 1024 alignment slack
-static_assert(PG_SMEM <= 232448, "shared memory per CTA");
-static_assert(PG_TRAJ_RING >= PG_STAGES + 2, "trajectory ring depth");
-static_assert(8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING) + 8 <= 256, "barrier area");
+template <bool PAIR>
+struct PairShape {
+    static constexpr int ROWS = PAIR ? 2 * TC_ROWS : TC_ROWS;        // output rows per tile
+    static constexpr int BCOLS = PAIR ? PG_COLS / 2 : PG_COLS;       // B columns a CTA generates
+    static constexpr uint32_t B_TILE = 2 * BCOLS * 64;                // stacked rows x 32 halves
+    static constexpr uint32_t STAGE = 4 * PA_BYTES + 2 * B_TILE;      // Ar, Ai (hi, lo), B (hi, lo)
+    static constexpr int STAGES = PAIR ? 4 : 3;
+    static constexpr uint32_t TRAJ_OFF = STAGES * STAGE;
+    static constexpr uint32_t BAR_OFF = TRAJ_OFF + PG_TRAJ_RING * PG_TRAJ_BUF;
+    static constexpr uint32_t SMEM = BAR_OFF + 256 + 1024;            // + 1024 alignment slack
+    static constexpr int ARRIVALS = (PAIR ? 2 : 1) * TC_PRODUCERS / 32;  // producer warps feeding one MMA issuer
+    static_assert(SMEM <= 232448, "shared memory per CTA");
+    static_assert(PG_TRAJ_RING >= STAGES + 2, "trajectory ring depth");
+    static_assert(8 * (2 * STAGES + 3 + PG_TRAJ_RING) + 8 <= 256, "barrier area");
+};
 constexpr int kMaxCtas = 152;       // CTAs of one contraction (one per SM)
 
 // Every pipeline wait is bounded by the launch's wait limit (a kernel
@@ -513,10 +523,12 @@ struct PairGeom {
 };
 
 // Adds (first: stores) this CTA's 128 rows of the four products as the two
-// paired outputs into its partial tile.  B column j (0..127) of the pair tile
-// is row j % 64 (Br) and 64 + j % 64 (Bi) of CTA j / 64's stacked operand, so
-// with cb = 128 (j / 64) + j % 64 the accumulators hold P_ac at TMEM column
-// cb, P_ad at cb + 64, P_bc at 256 + cb and P_bd at 320 + cb.  The partial
+// paired outputs into its partial tile.  B column j (0..127) of the tile is
+// row j % BCOLS (Br) and BCOLS + j % BCOLS (Bi) of the stacked operand of
+// the tile's (j / BCOLS)-th CTA (the only one, or one of a pair), so with
+// cb = 2 BCOLS (j / BCOLS) + j % BCOLS the accumulators hold P_ac at TMEM
+// column cb, P_ad at cb + BCOLS, P_bc at 256 + cb and P_bd at 256 + BCOLS +
+// cb.  The partial
 // tile is laid out as [column / 4][row][column % 4] (256 complex columns:
 // c+(j) at j, c-(j) at 128 + j; real parts in the first 256 float columns,
 // imaginary in the next 256; 128 rows): a thread's four consecutive columns
@@ -524,6 +536,7 @@ struct PairGeom {
 // contiguous bytes.  Fire-and-forget vector reductions; a thread's adds to
 // one address come in program order, so the partial is the same sum on every
 // run.
+template <int BCOLS>
 __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int warp, int lane, bool first)
 {
     const int lbase = 32 * (warp & 3);
@@ -533,12 +546,12 @@ __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int war
     for (int cc = 0; cc < 32; cc += 8) {
         float ac[8], bd[8], ad[8], bc[8];
         const int j = 32 * quarter + cc;
-        const uint32_t cb = 128u * (uint32_t)(j >> 6) + (uint32_t)(j & 63);
+        const uint32_t cb = 2u * BCOLS * (uint32_t)(j / BCOLS) + (uint32_t)(j % BCOLS);
         const uint32_t ta = tacc + ((uint32_t)lbase << 16) + cb;
         tmem_ld8(ta, ac);
-        tmem_ld8(ta + 64, ad);
+        tmem_ld8(ta + BCOLS, ad);
         tmem_ld8(ta + 256, bc);
-        tmem_ld8(ta + 320, bd);
+        tmem_ld8(ta + 256 + BCOLS, bd);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float pre[4], pim[4], mre[4], mim[4];
@@ -570,11 +583,11 @@ __device__ __forceinline__ void drain_pairs(uint32_t tacc, float* ptile, int war
     }
 }
 
-// B column j = j0 + c of a CTA's half of a pair tile for the samples 8g ..
+// B column j = j0 + c of the columns a CTA generates, for the samples 8g ..
 // 8g + 7 (fixed-point k = khi 2^32 + klo, phase constant kc): Br into row c
-// and Bi into row 64 + c of the stacked hi and lo tiles.  MASK zeroes samples
-// from nvalid on and columns from J on.
-template <bool BF16, bool MASK>
+// and Bi into row BCOLS + c of the stacked hi and lo tiles.  MASK zeroes
+// samples from nvalid on and columns from J on.
+template <bool BF16, bool MASK, int BCOLS>
 __device__ __forceinline__ void pair_b_col(const uint32_t* klo, const uint32_t* khi, const uint32_t* kc, int j0,
                                            int c, int g, int J, int nvalid, float scb, uint32_t bH, uint32_t bL)
 {
@@ -592,8 +605,8 @@ __device__ __forceinline__ void pair_b_col(const uint32_t* klo, const uint32_t* 
     split8<BF16>(im, ih, il);
     st_shared_v4(bH + sw64(c, g), rh);
     st_shared_v4(bL + sw64(c, g), rl);
-    st_shared_v4(bH + sw64(PG_HCOLS + c, g), ih);
-    st_shared_v4(bL + sw64(PG_HCOLS + c, g), il);
+    st_shared_v4(bH + sw64(BCOLS + c, g), ih);
+    st_shared_v4(bL + sw64(BCOLS + c, g), il);
 }
 
 // The unit range [u0, u1) of CTA c among P over U units (tiles x chunks).
@@ -632,60 +645,67 @@ struct SegWalk {
     }
 };
 
-// Partials of the CTA pair blockIdx.x / 2 over its units [u0, u1) (unit =
-// tile * K + chunk of 32 samples; tile = row tile of 256 * tilesC + column
-// tile of 128 j):
+// Partials of the tile owner c over its units [u0, u1) (unit = tile * K +
+// chunk of 32 samples; tile = row tile of ROWS * tilesC + column tile of 128
+// j):
 //   A'(l,i) = w'_l exp(sa i2pi ka_l (i + oa)) (w' = 1 unweighted),
 //   E(l,j)  = exp(sb i2pi kb_l (j + half/2)),
 // the four real products of each into the two accumulators of each CTA.
-// CTA h = blockIdx.x % 2 (its rank in the cluster) forms A rows 128 h .. +127
-// and B columns 64 h .. +63 of each tile and keeps its rows' partial of tile
-// t in slot 2 (pair + t) + h.  Rank 0 issues the pair's MMAs: it waits on its
-// own full[stage] barrier, on which the producer warps of both CTAs arrive,
-// and its commits arrive on the barrier at the same offset in both CTAs.
-template <bool BF16, bool WEIGHTED>
+// One SM a tile: owner c = CTA blockIdx.x, partial of tile t in slot c + t.
+// CTA pairs: owner c = pair blockIdx.x / 2; CTA h = blockIdx.x % 2 (its rank
+// in the cluster) forms A rows 128 h .. +127 and B columns 64 h .. +63 of
+// each tile and keeps its rows' partial of tile t in slot 2 (c + t) + h.
+// Rank 0 issues the pair's MMAs: it waits on its own full[stage] barrier, on
+// which the producer warps of both CTAs arrive, and its commits arrive on the
+// barrier at the same offset in both CTAs.
+template <bool BF16, bool WEIGHTED, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, const float2* __restrict__ w,
                const unsigned* __restrict__ amax2, int64_t L, int tilesC, int oa, int sa, int sb, int half, int J,
                int64_t K, int64_t U, float* __restrict__ part, int* err, unsigned long long wait_ns, int stall)
 {
+    using SH = PairShape<PAIR>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar_full = sbase + PG_BAR_OFF;             // stage filled (rank 0)
-    const uint32_t bar_empty = bar_full + 8 * PG_STAGES;      // stage consumed
-    const uint32_t bar_acc_full = bar_empty + 8 * PG_STAGES;  // segment accumulated
+    const uint32_t bar_full = sbase + SH::BAR_OFF;            // stage filled (the MMA issuer's CTA)
+    const uint32_t bar_empty = bar_full + 8 * SH::STAGES;     // stage consumed
+    const uint32_t bar_acc_full = bar_empty + 8 * SH::STAGES; // segment accumulated
     const uint32_t bar_acc_empty = bar_acc_full + 8;          // accumulator drained (rank 0)
     const uint32_t bar_traj = bar_acc_empty + 8;              // PG_TRAJ_RING: trajectory chunk landed
     const uint32_t bar_drain = bar_traj + 8 * PG_TRAJ_RING;   // every MMA issued has completed
-    const uint32_t misc = PG_BAR_OFF + 8 * (2 * PG_STAGES + 3 + PG_TRAJ_RING);
+    const uint32_t misc = SH::BAR_OFF + 8 * (2 * SH::STAGES + 3 + PG_TRAJ_RING);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + misc);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + misc + 4);
-    const uint32_t traj_s = sbase + PG_TRAJ_OFF;
+    const uint32_t traj_s = sbase + SH::TRAJ_OFF;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const uint32_t rank = blockIdx.x & 1u;  // the launch's clusters are pairs of consecutive blocks
-    const int64_t pair = blockIdx.x >> 1, P2 = gridDim.x >> 1;
+    // the launch's clusters are pairs of consecutive blocks
+    const uint32_t rank = PAIR ? (blockIdx.x & 1u) : 0u;
+    const int64_t pair = PAIR ? blockIdx.x >> 1 : blockIdx.x, P2 = PAIR ? gridDim.x >> 1 : gridDim.x;
     const int64_t u0 = unit_start(pair, U, P2);
     const int n = (int)(unit_start(pair + 1, U, P2) - u0);
 
     if (tid == 0) {
-        for (int i = 0; i < PG_STAGES; ++i) {
-            mbar_init(bar_full + 8 * i, 2 * TC_PRODUCERS / 32);  // one arrival per producer warp of the pair
+        for (int i = 0; i < SH::STAGES; ++i) {
+            mbar_init(bar_full + 8 * i, SH::ARRIVALS);  // one arrival per producer warp (of the pair)
             mbar_init(bar_empty + 8 * i, 1);
         }
         mbar_init(bar_acc_full, 1);
-        mbar_init(bar_acc_empty, 2 * TC_PRODUCERS / 32);
+        mbar_init(bar_acc_empty, SH::ARRIVALS);
         for (int r = 0; r < PG_TRAJ_RING; ++r) mbar_init(bar_traj + 8 * r, 1);
         mbar_init(bar_drain, 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
-    if (warp == TC_PRODUCERS / 32) tmem_alloc2(smem_u32(tmem_slot), 512);
+    if (warp == TC_PRODUCERS / 32) {
+        if constexpr (PAIR) tmem_alloc2(smem_u32(tmem_slot), 512);
+        else tmem_alloc(smem_u32(tmem_slot), 512);
+    }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();  // both CTAs' barriers are initialised before any arrival from the other
+    if constexpr (PAIR) cluster_sync();  // both CTAs' barriers are initialised before any arrival from the other
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -714,24 +734,27 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         if (tid == 0)
             for (int it = 0; it < 2 && it < n; ++it) issue_traj(it);
         // warps 0-7: A rows r and r + 64 of this CTA's 128, warps 8-15: B
-        // column r of its 64, for the samples 8g .. 8g + 7, so a warp's lanes
-        // share the trajectory values they load
+        // columns r (and r + 64 for one SM a tile) of its BCOLS, for the
+        // samples 8g .. 8g + 7, so a warp's lanes share the trajectory values
+        // they load
         const bool is_b = warp >= TC_PRODUCERS / 64;
+        // the partial slot of this CTA's rows of tile t
+        auto slot = [&](int64_t t) { return PAIR ? 2 * (pair + t) + rank : pair + t; };
         const int r = tid & 63, g = (tid >> 6) & 3;
         SegWalk sw{u0, K};
         int trow = (int)(sw.tile / tilesC), tcol = (int)(sw.tile % tilesC);  // stepped with the tile
         int64_t dtile = 0;  // tile of the segment being accumulated
         bool dfirst = true;
         for (int it = 0; it < n; ++it) {
-            const int s = it % PG_STAGES;
-            const uint32_t use = (uint32_t)(it / PG_STAGES);
-            // stage s is free once the pair's MMAs have consumed its previous
+            const int s = it % SH::STAGES;
+            const uint32_t use = (uint32_t)(it / SH::STAGES);
+            // stage s is free once the MMAs have consumed its previous
             // use.  Each warp waits for that itself (no producer-wide
             // barrier), so warps drift apart by at most the ring depth: a warp
             // past the wait for stage it knows every producer has finished
-            // stage it - PG_STAGES, whose trajectory slot the TMA of stage
-            // it + 2 reuses (it + 2 - PG_TRAJ_RING <= it - PG_STAGES).
-            if (lane == 0 && it >= PG_STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
+            // stage it - STAGES, whose trajectory slot the TMA of stage it + 2
+            // reuses (it + 2 - PG_TRAJ_RING <= it - STAGES).
+            if (lane == 0 && it >= SH::STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
             }
@@ -748,14 +771,14 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 ++trow;
             }
             const int64_t l0 = sw.kc * TC_KS;
-            const int i0 = trow * PG_ROWS + (int)rank * TC_ROWS, j0 = tcol * PG_COLS + (int)rank * PG_HCOLS;
-            const uint8_t* tbuf = smem + PG_TRAJ_OFF + (it % PG_TRAJ_RING) * PG_TRAJ_BUF;
+            const int i0 = trow * SH::ROWS + (int)rank * TC_ROWS, j0 = tcol * PG_COLS + (int)rank * SH::BCOLS;
+            const uint8_t* tbuf = smem + SH::TRAJ_OFF + (it % PG_TRAJ_RING) * PG_TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
             const float2* w_s = reinterpret_cast<const float2*>(tbuf + 2 * TC_KS * 8);
-            const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
+            const uint32_t st = sbase + (uint32_t)s * SH::STAGE;
             const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
-            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + PB_BYTES;
+            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + SH::B_TILE;
             constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
             if (!is_b) {
                 // A rows i = i0 + r + 64 v: the signed index sa (i + oa) = +-aa,
@@ -797,7 +820,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     st_shared_v4(aIL + sw64(row, g), il);
                 }
             } else {
-                // B column j = j0 + r: the phase k (j + half / 2) has the top
+                // B columns j = j0 + r (+ 64): the phase k (j + half / 2) has the top
                 // 32 bits umulhi(lo, j) + hi j + half (hi >> 1), those of
                 // kq j + half (kq >> 1) mod 2^64 up to the carry out of the low
                 // words (one unit of 2^-32 cycle).  Samples past L (only in a
@@ -814,16 +837,22 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     khi[e] = (uint32_t)(k >> 32);
                     kc[e] = half ? (uint32_t)((int32_t)khi[e] >> 1) : 0u;
                 }
-                if (nvalid == TC_KS && j0 + PG_HCOLS <= J)
-                    pair_b_col<BF16, false>(klo, khi, kc, j0, r, g, J, nvalid, scb, bH, bL);
-                else
-                    pair_b_col<BF16, true>(klo, khi, kc, j0, r, g, J, nvalid, scb, bH, bL);
+#pragma unroll
+                for (int v = 0; v < SH::BCOLS / 64; ++v) {
+                    if (nvalid == TC_KS && j0 + SH::BCOLS <= J)
+                        pair_b_col<BF16, false, SH::BCOLS>(klo, khi, kc, j0, r + 64 * v, g, J, nvalid, scb, bH, bL);
+                    else
+                        pair_b_col<BF16, true, SH::BCOLS>(klo, khi, kc, j0, r + 64 * v, g, J, nvalid, scb, bH, bL);
+                }
             }
             // every lane's stores are made visible to the tensor core's
-            // proxy before the warp's one arrival at the leader
+            // proxy before the warp's one arrival at the MMA issuer's CTA
             fence_proxy_async();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(bar_full + 8 * s, 0);
+            if (lane == 0) {
+                if constexpr (PAIR) mbar_arrive_cluster(bar_full + 8 * s, 0);
+                else mbar_arrive(bar_full + 8 * s);
+            }
             if (sw.pos == 0) {
                 // the MMA now has the first stage of a new segment queued:
                 // drain the previous one
@@ -835,10 +864,13 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     }
                     __syncwarp();  // the tensor-memory loads are warp-collective
                     tc_fence_after();
-                    drain_pairs(tmem, part + (2 * (pair + dtile) + rank) * TC_TILE_FLOATS, warp, lane, dfirst);
+                    drain_pairs<SH::BCOLS>(tmem, part + slot(dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive_cluster(bar_acc_empty, 0);
+                    if (lane == 0) {
+                        if constexpr (PAIR) mbar_arrive_cluster(bar_acc_empty, 0);
+                        else mbar_arrive(bar_acc_empty);
+                    }
                 }
                 dtile = sw.tile;
                 dfirst = sw.first_of_tile;
@@ -851,7 +883,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             if (!landed) atomicOr(err, kErrTimeout);
             if (__all_sync(0xffffffffu, landed)) {
                 tc_fence_after();
-                drain_pairs(tmem, part + (2 * (pair + dtile) + rank) * TC_TILE_FLOATS, warp, lane, dfirst);
+                drain_pairs<SH::BCOLS>(tmem, part + slot(dtile) * TC_TILE_FLOATS, warp, lane, dfirst);
             }
         }
         // every requested chunk has landed before the CTA goes (at most one
@@ -861,21 +893,22 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 if (!mbar_wait(bar_traj + 8 * (j % PG_TRAJ_RING), (uint32_t)(j / PG_TRAJ_RING) & 1, kDrainNs))
                     atomicOr(err, kErrTimeout);
     } else if (rank == 0 && lane == 0) {
-        // ------------------------------------------------ MMA issuer (the pair's)
+        // ------------------------------------------------ MMA issuer (the tile's)
         // kind::f16, D = F32 (bit 4), A/B = F16 (0) or BF16 (1) at bits 7 and
-        // 10, both K-major, N = 256 (N>>3 at bit 17), M = 256 (M>>4 at bit 24).
+        // 10, both K-major, N = 256 (N>>3 at bit 17), M = ROWS (M>>4 at bit 24).
         const uint32_t fmt = BF16 ? 1u : 0u;
-        const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | ((256u >> 4) << 24);
+        const uint32_t idesc =
+            (1u << 4) | (fmt << 7) | (fmt << 10) | ((256u >> 3) << 17) | (((uint32_t)SH::ROWS >> 4) << 24);
         SegWalk sw{u0, K};
         int issued = 0;  // stages whose MMAs were issued
         // a test's injected stall: nothing completes bar_drain before this
         // thread's own commit, so the bounded wait runs out and no MMA issues
         if (stall && !mbar_wait(bar_drain, 0, wait_ns)) atomicOr(err, kErrTimeout);
-        // [P_ac | P_ad] per B half in TMEM columns 0-255, [P_bc | P_bd] in 256-511
+        // [P_ac | P_ad] per BCOLS block in TMEM columns 0-255, [P_bc | P_bd] in 256-511
         const uint32_t t_r = tmem, t_i = tmem + 256;
         for (int it = 0; !stall && it < n; ++it) {
-            const int s = it % PG_STAGES;
-            const uint32_t use = (uint32_t)(it / PG_STAGES);
+            const int s = it % SH::STAGES;
+            const uint32_t use = (uint32_t)(it / SH::STAGES);
             sw.step(it);
             if (sw.pos == 0 && sw.seg >= 1 && !mbar_wait(bar_acc_empty, (uint32_t)(sw.seg - 1) & 1, wait_ns)) {
                 atomicOr(err, kErrTimeout);
@@ -887,9 +920,9 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             }
             ++issued;
             tc_fence_after();
-            const uint32_t st = sbase + (uint32_t)s * PG_STAGE_BYTES;
+            const uint32_t st = sbase + (uint32_t)s * SH::STAGE;
             const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
-            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + PB_BYTES;
+            const uint32_t bH = st + 4 * PA_BYTES, bL = bH + SH::B_TILE;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const uint32_t o = 32u * kk;  // samples 16 kk .. 16 kk + 15 of each row
@@ -897,17 +930,28 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 for (int q = 0; q < 3; ++q) {  // hi*hi, hi*lo, lo*hi
                     const uint32_t Ar = q == 2 ? aRL : aRH, Ai = q == 2 ? aIL : aIH, B = q == 1 ? bL : bH;
                     const uint32_t acc = (sw.pos > 0 || kk > 0 || q > 0) ? 1u : 0u;
-                    mma2_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
-                    mma2_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
+                    if constexpr (PAIR) {
+                        mma2_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
+                        mma2_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
+                    } else {
+                        mma_f16(t_r, sdesc64(Ar + o), sdesc64(B + o), idesc, acc);
+                        mma_f16(t_i, sdesc64(Ai + o), sdesc64(B + o), idesc, acc);
+                    }
                 }
             }
-            mma2_commit_pair(bar_empty + 8 * s);
-            if (sw.closes(it, n)) mma2_commit_pair(bar_acc_full);
+            if constexpr (PAIR) {
+                mma2_commit_pair(bar_empty + 8 * s);
+                if (sw.closes(it, n)) mma2_commit_pair(bar_acc_full);
+            } else {
+                mma_commit(bar_empty + 8 * s);
+                if (sw.closes(it, n)) mma_commit(bar_acc_full);
+            }
         }
-        // no MMA may still read either CTA's stages or write its TMEM once
-        // the pair frees it
+        // no MMA may still read the stages (of either CTA) or write TMEM once
+        // the tile's CTAs free it
         if (issued > 0) {
-            mma2_commit_pair(bar_drain);
+            if constexpr (PAIR) mma2_commit_pair(bar_drain);
+            else mma_commit(bar_drain);
             if (!mbar_wait(bar_drain, 0, kDrainNs)) atomicOr(err, kErrTimeout);
         }
     }
@@ -916,26 +960,28 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
     __syncthreads();
     // the leader has seen its MMAs complete (they read this CTA's shared
     // memory and write its TMEM) and no arrival on the other CTA is pending
-    cluster_sync();
+    if constexpr (PAIR) cluster_sync();
     if (warp == TC_PRODUCERS / 32) {
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc2(tmem, 512);
+        if constexpr (PAIR) tmem_dealloc2(tmem, 512);
+        else tmem_dealloc(tmem, 512);
     }
 }
 
 // out[i][c] = scale * 2^e * (sum of the partials of the tile holding output
-// (i, c) in pair order); 2^e undoes the weight scaling.  A block sums a patch
-// of 32 rows x 32 columns of a partial tile (column q < 128: j = 128 tcol + q
-// at c+(j); q >= 128: j = 128 tcol + q - 128 at c-(j)).  The pairs holding
-// units of pair tile t are c_lo..c_hi (of P), the last pairs whose ranges
-// start at or before the tile's first and last unit; CTA h of pair c keeps its
-// 128 rows' partial of tile t in slot 2 (c + t) + h.  Each thread reads four
+// (i, c) in owner order); 2^e undoes the weight scaling.  A block sums a
+// patch of 32 rows x 32 columns of a partial tile (column q < 128: j = 128
+// tcol + q at c+(j); q >= 128: j = 128 tcol + q - 128 at c-(j)).  The owners
+// (CTAs, or CTA pairs when `pairs`) holding units of tile t are c_lo..c_hi (of
+// P), the last owners whose ranges start at or before the tile's first and
+// last unit; owner c keeps its partial of tile t in slot c + t, or, for a
+// pair, CTA h its 128 rows' partial in slot 2 (c + t) + h.  Each thread reads four
 // columns of one row as a vector, the patch turns in shared memory, and
 // writes run along the rows of out (the mirrored half in descending columns).
 // c-(0) = c+(0) for integer offsets and is written once.
 __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ part, int64_t U, int64_t K, int64_t P,
-                                                     PairGeom pg, int tilesC, float scale,
+                                                     bool pairs, PairGeom pg, int tilesC, float scale,
                                                      const unsigned* __restrict__ amax2, float2* __restrict__ out)
 {
     __shared__ float2 patch[32][33];
@@ -944,9 +990,9 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
     const int i0 = blockIdx.y * 32;
     const int tcol = blockIdx.x >> 3, q0 = (blockIdx.x & 7) * 32;  // tile column, first partial column
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    const int tr = i0 / TC_ROWS;                   // 128-row half tile: pair tile row tr / 2, CTA tr % 2
-    const int64_t t = (int64_t)(tr >> 1) * tilesC + tcol;
-    const int h = tr & 1;
+    const int tr = i0 / TC_ROWS;                   // 128-row block: tile row tr (or tr / 2 with CTA tr % 2)
+    const int64_t t = (int64_t)(pairs ? tr >> 1 : tr) * tilesC + tcol;
+    const int h = pairs ? tr & 1 : 0;
     const int64_t c_lo = ((t * K + 1) * P - 1) / U;
     const int64_t c_hi = ((t + 1) * K * P - 1) / U;
     const int row = (i0 % TC_ROWS) + tx;
@@ -966,7 +1012,8 @@ __global__ void __launch_bounds__(256) k_reduce_pair(const float* __restrict__ p
                 const int64_t cc = c0 + b;
                 const bool use =
                     cc <= c_hi && (!any_empty || unit_start(cc + 1, U, P) != unit_start(cc, U, P));
-                const float* pt = part + (2 * ((use ? cc : c_lo) + t) + h) * TC_TILE_FLOATS;
+                const int64_t sl = pairs ? 2 * ((use ? cc : c_lo) + t) + h : (use ? cc : c_lo) + t;
+                const float* pt = part + sl * TC_TILE_FLOATS;
                 r[b] = *reinterpret_cast<const float4*>(pt + ((size_t)cg * TC_ROWS + row) * 4);
                 m[b] = *reinterpret_cast<const float4*>(pt + ((size_t)(TC_COLS / 4 + cg) * TC_ROWS + row) * 4);
                 if (!use) r[b] = m[b] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1355,11 +1402,11 @@ int pair_clusters(int* out)
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2 * (kMaxCtas / 2));
         cfg.blockDim = dim3(TC_THREADS);
-        cfg.dynamicSmemBytes = PG_SMEM;
+        cfg.dynamicSmemBytes = PairShape<true>::SMEM;
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        SPIREC_CK(cudaOccupancyMaxActiveClusters(&n, (void*)k_tc_pair_gemm<false, false>, &cfg));
+        SPIREC_CK(cudaOccupancyMaxActiveClusters(&n, (void*)k_tc_pair_gemm<false, false, true>, &cfg));
         if (n < 1) {
             set_error("the device runs no cluster of two contraction CTAs");
             return SPIREC_EUNSUPPORTED;
@@ -1370,7 +1417,7 @@ int pair_clusters(int* out)
     return SPIREC_OK;
 }
 
-template <bool BF16, bool WEIGHTED>
+template <bool BF16, bool WEIGHTED, bool PAIR>
 cudaError_t launch_pair_kernel(int64_t P, cudaStream_t stream, const int64_t* ka, const int64_t* kb, const float2* w,
                                const unsigned* amax, int64_t L, int tilesC, int oa, int sa, int sb, int half, int J,
                                int64_t K, int64_t U, float* part, int* err, unsigned long long wait_ns, int stall)
@@ -1383,12 +1430,31 @@ cudaError_t launch_pair_kernel(int64_t P, cudaStream_t stream, const int64_t* ka
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3((unsigned)P);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = PG_SMEM;
+    cfg.dynamicSmemBytes = PairShape<PAIR>::SMEM;
     cfg.stream = stream;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc_pair_gemm<BF16, WEIGHTED>, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J,
-                              K, U, part, err, wait_ns, stall);
+    cfg.attrs = PAIR ? at : nullptr;
+    cfg.numAttrs = PAIR ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_tc_pair_gemm<BF16, WEIGHTED, PAIR>, ka, kb, w, amax, L, tilesC, oa, sa, sb, half,
+                              J, K, U, part, err, wait_ns, stall);
+}
+
+template <bool PAIR>
+cudaError_t launch_pair_any(bool bf16, int64_t P, cudaStream_t stream, const int64_t* ka, const int64_t* kb,
+                            const float2* w, const unsigned* amax, int64_t L, int tilesC, int oa, int sa, int sb,
+                            int half, int J, int64_t K, int64_t U, float* part, int* err, unsigned long long wait_ns,
+                            int stall)
+{
+    if (bf16 && w)
+        return launch_pair_kernel<true, true, PAIR>(P, stream, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J, K, U,
+                                                    part, err, wait_ns, stall);
+    if (bf16)
+        return launch_pair_kernel<true, false, PAIR>(P, stream, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J, K, U,
+                                                     part, err, wait_ns, stall);
+    if (w)
+        return launch_pair_kernel<false, true, PAIR>(P, stream, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J, K, U,
+                                                     part, err, wait_ns, stall);
+    return launch_pair_kernel<false, false, PAIR>(P, stream, ka, kb, w, amax, L, tilesC, oa, sa, sb, half, J, K, U,
+                                                  part, err, wait_ns, stall);
 }
 
 // The paired contraction out[i][c] = scale sum_l A(l,i) B(l,c) with
@@ -1397,12 +1463,14 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
                  int sa, int sb, float scale, float2* out)
 {
     const PairGeom pg = pair_geom(p, knob);
-    const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int tilesR = (pg.R + PG_ROWS - 1) / PG_ROWS, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
-    const int64_t T = (int64_t)tilesR * tilesC;
-    const int64_t U = T * K;
     int sms = 0, rc;
     if ((rc = device_sms(&sms)) != SPIREC_OK) return rc;
+    const bool pairs = tc_pairs(p, knob, sms);
+    const int rows = pairs ? PairShape<true>::ROWS : PairShape<false>::ROWS;
+    const int64_t K = (p->L + TC_KS - 1) / TC_KS;
+    const int tilesR = (pg.R + rows - 1) / rows, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
+    const int64_t T = (int64_t)tilesR * tilesC;
+    const int64_t U = T * K;
     int64_t P = 0;
     if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
     unsigned* amax = nullptr;
@@ -1427,22 +1495,15 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
     const bool bf16 = p->precision == SPIREC_MIXED_BF16X3;
     const unsigned long long wait_ns = wait_limit_ns();
     const int stall = injected_stall(kStallContraction) ? 1 : 0;
-    cudaError_t le;
-    if (bf16 && w)
-        le = launch_pair_kernel<true, true>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
-                                            U, part, p->dflag, wait_ns, stall);
-    else if (bf16)
-        le = launch_pair_kernel<true, false>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
-                                             U, part, p->dflag, wait_ns, stall);
-    else if (w)
-        le = launch_pair_kernel<false, true>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
-                                             U, part, p->dflag, wait_ns, stall);
-    else
-        le = launch_pair_kernel<false, false>(P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J,
-                                              K, U, part, p->dflag, wait_ns, stall);
+    const cudaError_t le =
+        pairs ? launch_pair_any<true>(bf16, P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J, K,
+                                      U, part, p->dflag, wait_ns, stall)
+              : launch_pair_any<false>(bf16, P, p->stream, ka, kb, w, amax, p->L, tilesC, oa, sa, sb, pg.half, pg.J,
+                                       K, U, part, p->dflag, wait_ns, stall);
     SPIREC_CK(le);
     const dim3 rgrid((unsigned)(tilesC * 8), (unsigned)((pg.R + 31) / 32));
-    k_reduce_pair<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, P / 2, pg, tilesC, scale, amax, out);
+    k_reduce_pair<<<rgrid, dim3(32, 8), 0, p->stream>>>(part, U, K, pairs ? P / 2 : P, pairs, pg, tilesC, scale,
+                                                        amax, out);
     SPIREC_CK(cudaGetLastError());
     p->launches += 2;
     return SPIREC_OK;
@@ -1510,18 +1571,26 @@ size_t fsplit_bytes_tc(int N, int precision)
 size_t kpart_floats_tc(int N, int64_t, int precision)
 {
     if (precision == SPIREC_FP32) return 0;
-    // slots 2 (c + t) + h < 2 (P + T) for P pairs and T pair tiles; G (N
-    // rows, N paired columns) has the most tiles
-    const size_t T = (size_t)((N + PG_ROWS - 1) / PG_ROWS) * (size_t)((N + PG_COLS - 1) / PG_COLS);
-    return ((size_t)kMaxCtas + 2 * T) * TC_TILE_FLOATS;
+    // slots c + t < P + T for P CTAs and T one-SM tiles, 2 (c + t) + h <
+    // 2 (P + T) for P pairs and T pair tiles; G (N rows, N paired columns)
+    // has the most tiles
+    const size_t cols = (size_t)((N + PG_COLS - 1) / PG_COLS);
+    const size_t T1 = (size_t)((N + TC_ROWS - 1) / TC_ROWS) * cols;
+    const size_t T2 = 2 * (size_t)((N + 2 * TC_ROWS - 1) / (2 * TC_ROWS)) * cols;
+    return ((size_t)kMaxCtas + (T1 > T2 ? T1 : T2)) * TC_TILE_FLOATS;
 }
 
 int tc_setup_attributes()
 {
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
-    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PG_SMEM));
+    constexpr int S1 = PairShape<false>::SMEM, S2 = PairShape<true>::SMEM;
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S2));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S2));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S2));
+    SPIREC_CK(cudaFuncSetAttribute(k_tc_pair_gemm<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S2));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
     SPIREC_CK(cudaFuncSetAttribute(k_tc_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_SMEM));
     return SPIREC_OK;
@@ -1542,31 +1611,54 @@ int launch_adjoint_tc(spirec_plan p, const float2* y, float2* x)
     return tc_pair_gemm(p, SPIREC_KNOB_ADJOINT_SPLIT, p->kyq, p->kxq, y, 0, 0, -1, -1, 1.0f / (float)N, x);
 }
 
-// The stream-K CTA count, always even (the contraction runs on pairs): the
-// tuned value of the shape rounded down to even (at least 2), else one CTA
-// per SM (at most kMaxCtas); never more pairs than the device runs at once or
-// than there are work units, and the partial slots 2 (c + t) + h < 2 (P / 2 +
-// T) must fit the split-K buffer.
+// The tile shape of a contraction (knob SPIREC_KNOB_GRAM_TILE or
+// SPIREC_KNOB_ADJOINT_TILE beside the split knob): the tuned value (1: one SM
+// a tile of 128 rows, 2: CTA pairs, tiles of 256 rows), else pairs, except
+// where pair tiles would pad more than 256 output rows further than one-SM
+// tiles do (R = 384, 640, ...: the pair's last tile half empty).  Measured at
+// L = 131072: R = 384, G 0.37 ms one SM a tile, 0.44 ms pairs; R = 512,
+// 0.63 and 0.58 ms.
+bool tc_pairs(spirec_plan p, int knob, int sms)
+{
+    const int tile_knob = knob == SPIREC_KNOB_GRAM_SPLIT ? SPIREC_KNOB_GRAM_TILE : SPIREC_KNOB_ADJOINT_TILE;
+    const int tuned = tune_lookup(tile_knob, p, sms);
+    if (tuned == 1) return false;
+    if (tuned == 2) return true;
+    const int R = pair_geom(p, knob).R;
+    const int pad2 = (R + 2 * TC_ROWS - 1) / (2 * TC_ROWS) * (2 * TC_ROWS), pad1 = (R + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
+    return R <= 2 * TC_ROWS || pad2 == pad1;
+}
+
+// The stream-K CTA count: the tuned value of the shape, else one CTA per SM
+// (at most kMaxCtas), rounded down to even (at least 2) for CTA pairs; never
+// more owners (CTAs or pairs) than work units or, for pairs, than the device
+// runs at once, and the partial slots must fit the split-K buffer (c + t <
+// P + T, or 2 (c + t) + h < 2 (P / 2 + T) for pairs).
 int tc_ctas(spirec_plan p, int knob, int sms, int64_t* out)
 {
     const PairGeom pg = pair_geom(p, knob);
+    const bool pairs = tc_pairs(p, knob, sms);
+    const int rows = pairs ? PairShape<true>::ROWS : PairShape<false>::ROWS;
     const int64_t K = (p->L + TC_KS - 1) / TC_KS;
-    const int64_t T = (int64_t)((pg.R + PG_ROWS - 1) / PG_ROWS) * ((pg.J + PG_COLS - 1) / PG_COLS);
+    const int64_t T = (int64_t)((pg.R + rows - 1) / rows) * ((pg.J + PG_COLS - 1) / PG_COLS);
     const int64_t U = T * K;
-    int clusters = 0, rc;
-    if ((rc = pair_clusters(&clusters)) != SPIREC_OK) return rc;
-    int64_t P2 = (sms < kMaxCtas ? sms : kMaxCtas) / 2;
+    const int per = pairs ? 2 : 1;  // CTAs an owner
+    int64_t Q = (sms < kMaxCtas ? sms : kMaxCtas) / per;
     const int tuned = tune_lookup(knob, p, sms);
-    if (tuned > 0 && tuned / 2 < P2) P2 = tuned / 2 > 0 ? tuned / 2 : 1;
-    if (P2 > clusters) P2 = clusters;
-    if (P2 > U) P2 = U;
-    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float))) / 2;
-    if (P2 + T > cap) P2 = cap - T;
-    if (P2 < 1) {
+    if (tuned > 0 && tuned / per < Q) Q = tuned / per > 0 ? tuned / per : 1;
+    if (pairs) {
+        int clusters = 0, rc;
+        if ((rc = pair_clusters(&clusters)) != SPIREC_OK) return rc;
+        if (Q > clusters) Q = clusters;
+    }
+    if (Q > U) Q = U;
+    const int64_t cap = (int64_t)(p->kpart_bytes / (TC_TILE_FLOATS * sizeof(float))) / per;
+    if (Q + T > cap) Q = cap - T;
+    if (Q < 1) {
         set_error("partial buffer too small for %lld tiles", (long long)T);
         return SPIREC_EUNSUPPORTED;
     }
-    *out = 2 * P2;
+    *out = per * Q;
     return SPIREC_OK;
 }
 

@@ -46,7 +46,9 @@ SPIREC_MIN_NEWTON = 2
 SPIREC_KNOB_GRAM_SPLIT = 0
 SPIREC_KNOB_ADJOINT_SPLIT = 1
 SPIREC_KNOB_LOOP_ROWS = 2
-SPIREC_NUM_KNOBS = 3
+SPIREC_KNOB_GRAM_TILE = 3
+SPIREC_KNOB_ADJOINT_TILE = 4
+SPIREC_NUM_KNOBS = 5
 SPIREC_TUNE_LATENCY = 0
 SPIREC_TUNE_THROUGHPUT = 1
 

@@ -66,8 +66,12 @@ def test_autotune_state_equals_a_new_plan(sp, prec, objective):
     N, L = w["N"], w["kx"].shape[0]
     with _plan(sp, w, prec, 128) as p:
         chosen, ms = sp.spirec_autotune(p.h, objective, 5)
-        assert np.all(chosen > 0) and np.all(ms > 0)  # M = 128: the loop is tuned too
-        for k in range(3):
+        tiles = [sp.SPIREC_KNOB_GRAM_TILE, sp.SPIREC_KNOB_ADJOINT_TILE]
+        rest = [k for k in range(sp.SPIREC_NUM_KNOBS) if k not in tiles]
+        # M = 128: the loop is tuned too; the tile shapes only on the tensor-core paths
+        assert np.all(chosen[rest] > 0) and np.all(ms[rest] > 0)
+        assert np.all(chosen[tiles] > 0) if prec else np.all(chosen[tiles] == 0)
+        for k in range(sp.SPIREC_NUM_KNOBS):
             assert sp.spirec_tune_get(k, N, p.M, prec, L) == chosen[k]
         G1, D1 = _state(sp, p, N)
         x1, J1 = sp.spirec_solve(p.h, None, 12, N)
@@ -97,6 +101,38 @@ def test_every_split_matches_the_oracle(sp, prec):
             G, D = _state(sp, p, N)
         assert rel(G, Go) < TOL[prec], v
         assert rel(D, Do) < TOL[prec], v
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("N", [40, 200, 300])
+def test_every_tile_shape_matches_the_oracle(sp, prec, N):
+    """G and D with one SM a tile (128 rows) and with CTA pairs (256 rows),
+    each under a few CTA counts (odd ones rounded down to pairs), against
+    sampled oracle entries: N = 40 leaves most of a tile's rows empty, 200
+    one ragged tile of either shape, 300 several tiles with ragged edges."""
+    w = _workload(N=N, I=2, S=4 * N, seed=29)
+    L = w["kx"].shape[0]
+    M = 2 * N
+    g = synth.rng(30)
+    u = g.integers(0, N, 300)
+    v = g.integers(-(N - 1), N, 300)
+    n = g.integers(0, N, 300)
+    m = g.integers(0, N, 300)
+    Go = O.gram_at(w["kx"], w["ky"], N, u, v)
+    Do = O.adjoint_at(w["kx"], w["ky"], w["s"], N, n, m)
+    try:
+        for tile in (1, 2):
+            sp.spirec_tune_set(sp.SPIREC_KNOB_GRAM_TILE, N, M, prec, L, tile)
+            sp.spirec_tune_set(sp.SPIREC_KNOB_ADJOINT_TILE, N, M, prec, L, tile)
+            for val in (3, 38, 152):
+                sp.spirec_tune_set(sp.SPIREC_KNOB_GRAM_SPLIT, N, M, prec, L, val)
+                sp.spirec_tune_set(sp.SPIREC_KNOB_ADJOINT_SPLIT, N, M, prec, L, val)
+                with _plan(sp, w, prec, M) as p:
+                    G, D = _state(sp, p, N)
+                assert rel(G[u, v + N - 1], Go) < TOL[prec], (tile, val)
+                assert rel(D[n, m], Do) < TOL[prec], (tile, val)
+    finally:
+        sp.spirec_tune_clear()
 
 
 @pytest.mark.parametrize("prec", [1, 2])

@@ -51,8 +51,20 @@ def test_l_class_and_loop_key(sp):
     assert sp.spirec_tune_get(LR, 32, 64, 0, 10 ** 9, sms=SMS) == 16
 
 
+def test_tile_knobs_round_trip(sp):
+    """The tile-shape knobs are keyed like the split knobs (by L class)."""
+    GT, DT = sp.SPIREC_KNOB_GRAM_TILE, sp.SPIREC_KNOB_ADJOINT_TILE
+    assert sp.SPIREC_NUM_KNOBS == 5
+    sp.spirec_tune_set(GT, 256, 512, 1, 5000, 2, sms=SMS)
+    sp.spirec_tune_set(DT, 256, 512, 2, 5000, 1, sms=SMS)
+    assert sp.spirec_tune_get(GT, 256, 512, 1, 8192, sms=SMS) == 2  # the same L class
+    assert sp.spirec_tune_get(GT, 256, 512, 1, 8193, sms=SMS) == 0
+    assert sp.spirec_tune_get(DT, 256, 512, 2, 5000, sms=SMS) == 1
+    assert sp.spirec_tune_get(DT, 256, 512, 1, 5000, sms=SMS) == 0
+
+
 @pytest.mark.parametrize("args", [
-    (3, 32, 64, 0, 100, 1),      # unknown knob
+    (5, 32, 64, 0, 100, 1),      # unknown knob (SPIREC_NUM_KNOBS)
     (-1, 32, 64, 0, 100, 1),
     (0, 32, 64, 3, 100, 1),      # unknown precision
     (0, 1, 64, 0, 100, 1),       # N < 2
