@@ -615,12 +615,15 @@ __host__ __device__ __forceinline__ int64_t unit_start(int64_t c, int64_t U, int
 // Segment bookkeeping along a CTA's stages: a segment is at most TC_SEG
 // stages of one tile.  Producers and the MMA issuer step it identically.
 struct SegWalk {
-    int64_t K;
-    int64_t tile, kc;  // tile and chunk of the current stage's unit
+    int K;
+    int tile, kc;  // tile and chunk of the current stage's unit (units < 2^31)
     int seg = -1, pos = 0;
     bool first_of_tile = false;
     // the first unit u0 (one division; every later stage steps the chunk)
-    __device__ __forceinline__ SegWalk(int64_t u0, int64_t K_) : K(K_), tile(u0 / K_), kc(u0 % K_) {}
+    __device__ __forceinline__ SegWalk(int64_t u0, int64_t K_)
+        : K((int)K_), tile((int)(u0 / K_)), kc((int)(u0 % K_))
+    {
+    }
     // advance to stage it (called for it = 0, 1, 2, ...)
     __device__ __forceinline__ void step(int it)
     {
@@ -742,9 +745,27 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
         auto slot = [&](int64_t t) { return PAIR ? 2 * (pair + t) + rank : pair + t; };
         const int r = tid & 63, g = (tid >> 6) & 3;
         SegWalk sw{u0, K};
-        int trow = (int)(sw.tile / tilesC), tcol = (int)(sw.tile % tilesC);  // stepped with the tile
-        int64_t dtile = 0;  // tile of the segment being accumulated
+        int trow = sw.tile / tilesC, tcol = sw.tile % tilesC;  // stepped with the tile
+        int dtile = 0;  // tile of the segment being accumulated
         bool dfirst = true;
+        bool failed = false;  // this thread's last wait ran out
+        const int L32 = L < (int64_t)INT32_MAX ? (int)L : INT32_MAX;
+        // A rows: the signed indices sa (i + oa) = +-aa of rows r and r + 64,
+        // their signs in the scale: kept across stages and set at every tile
+        // change for G; formed per stage for D, whose weights already hold
+        // the registers (keeping them there was slower, measured)
+        uint32_t aa[2];
+        float sca[2];
+        constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
+        auto set_rows = [&](int i0) {
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const int sja = sa * (i0 + r + 64 * v + oa);
+                aa[v] = (uint32_t)(sja < 0 ? -sja : sja);
+                sca[v] = sja < 0 ? -kRev : kRev;
+            }
+        };
+        if (!WEIGHTED) set_rows(trow * SH::ROWS + (int)rank * TC_ROWS);
         for (int it = 0; it < n; ++it) {
             const int s = it % SH::STAGES;
             const uint32_t use = (uint32_t)(it / SH::STAGES);
@@ -757,21 +778,27 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             if (lane == 0 && it >= SH::STAGES && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
+                failed = true;
             }
-            __syncwarp();
-            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;  // the warp stops as one
+            // the warp stops as one: at once on a wait of its own that ran
+            // out, on another warp's (the shared flag) within four stages
+            if (__any_sync(0xffffffffu, failed || ((it & 3) == 0 && *abort_flag != 0))) break;
             if (tid == 0 && it + 2 < n) issue_traj(it + 2);
             if (!mbar_wait(bar_traj + 8 * (it % PG_TRAJ_RING), (uint32_t)(it / PG_TRAJ_RING) & 1, wait_ns)) {
                 *abort_flag = 1;
                 atomicOr(err, kErrTimeout);
+                failed = true;
             }
             sw.step(it);
-            if (it > 0 && sw.kc == 0 && ++tcol == tilesC) {
-                tcol = 0;
-                ++trow;
+            if (it > 0 && sw.kc == 0) {
+                if (++tcol == tilesC) {
+                    tcol = 0;
+                    ++trow;
+                }
+                if (!WEIGHTED) set_rows(trow * SH::ROWS + (int)rank * TC_ROWS);
             }
-            const int64_t l0 = sw.kc * TC_KS;
-            const int i0 = trow * SH::ROWS + (int)rank * TC_ROWS, j0 = tcol * PG_COLS + (int)rank * SH::BCOLS;
+            const int l0 = sw.kc * TC_KS;
+            const int j0 = tcol * PG_COLS + (int)rank * SH::BCOLS;
             const uint8_t* tbuf = smem + SH::TRAJ_OFF + (it % PG_TRAJ_RING) * PG_TRAJ_BUF;
             const int64_t* ka_s = reinterpret_cast<const int64_t*>(tbuf);
             const int64_t* kb_s = reinterpret_cast<const int64_t*>(tbuf + TC_KS * 8);
@@ -779,7 +806,6 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
             const uint32_t st = sbase + (uint32_t)s * SH::STAGE;
             const uint32_t aRH = st, aRL = st + PA_BYTES, aIH = st + 2 * PA_BYTES, aIL = st + 3 * PA_BYTES;
             const uint32_t bH = st + 4 * PA_BYTES, bL = bH + SH::B_TILE;
-            constexpr float kRev = 1.4629180792671596e-09f;  // 2 pi / 2^32
             if (!is_b) {
                 // A rows i = i0 + r + 64 v: the signed index sa (i + oa) = +-aa,
                 // its sign in the scale; the row's 8 samples in 16-byte chunk g
@@ -802,12 +828,16 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     const int row = r + 64 * v;
-                    const int sja = sa * (i0 + row + oa);
-                    const uint32_t aa = (uint32_t)(sja < 0 ? -sja : sja);
-                    const float sca = sja < 0 ? -kRev : kRev;
+                    uint32_t av = aa[v];
+                    float sv = sca[v];
+                    if (WEIGHTED) {
+                        const int sja = sa * (trow * SH::ROWS + (int)rank * TC_ROWS + row + oa);
+                        av = (uint32_t)(sja < 0 ? -sja : sja);
+                        sv = sja < 0 ? -kRev : kRev;
+                    }
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        float2 z = phasor_top(klo[e], khi[e], 0u, aa, sca);
+                        float2 z = phasor_top(klo[e], khi[e], 0u, av, sv);
                         if (WEIGHTED) z = cmul(z, ww[e]);
                         re[e] = z.x;
                         im[e] = z.y;
@@ -827,7 +857,7 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                 // tile's last chunk): A is zero there through the zero padding
                 // of the weights, or B by the mask when unweighted; columns
                 // past J are zero.
-                const int nvalid = (!WEIGHTED && l0 + TC_KS > L) ? (int)(L - l0) : TC_KS;
+                const int nvalid = (!WEIGHTED && l0 + TC_KS > L32) ? L32 - l0 : TC_KS;
                 const float scb = sb < 0 ? -kRev : kRev;
                 uint32_t klo[8], khi[8], kc[8];
 #pragma unroll
@@ -835,7 +865,8 @@ k_tc_pair_gemm(const int64_t* __restrict__ ka, const int64_t* __restrict__ kb, c
                     const uint64_t k = (uint64_t)kb_s[8 * g + e];
                     klo[e] = (uint32_t)k;
                     khi[e] = (uint32_t)(k >> 32);
-                    kc[e] = half ? (uint32_t)((int32_t)khi[e] >> 1) : 0u;
+                    // half-integer offsets only for D (weighted); G's are integers
+                    kc[e] = (WEIGHTED && half) ? (uint32_t)((int32_t)khi[e] >> 1) : 0u;
                 }
 #pragma unroll
                 for (int v = 0; v < SH::BCOLS / 64; ++v) {
@@ -1471,6 +1502,14 @@ int tc_pair_gemm(spirec_plan p, int knob, const int64_t* ka, const int64_t* kb, 
     const int tilesR = (pg.R + rows - 1) / rows, tilesC = (pg.J + PG_COLS - 1) / PG_COLS;
     const int64_t T = (int64_t)tilesR * tilesC;
     const int64_t U = T * K;
+    if (U > (int64_t)INT32_MAX) {
+        set_error("%lld contraction units exceed the kernel's 32-bit unit counters", (long long)U);
+        return SPIREC_EUNSUPPORTED;
+    }
+    if (!w && pg.half) {
+        set_error("an unweighted paired contraction takes integer offsets");
+        return SPIREC_EUNSUPPORTED;
+    }
     int64_t P = 0;
     if ((rc = tc_ctas(p, knob, sms, &P)) != SPIREC_OK) return rc;
     unsigned* amax = nullptr;
