@@ -351,20 +351,7 @@ __device__ __forceinline__ void mma2_commit_pair(uint32_t bar)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
-{
-    uint32_t r[8];
-    // load and wait in one statement: the registers are valid only after the wait
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Four tmem_ld8 loads (columns t0.., t1.., t2.., t3.. of the warp's lanes)
+// Four loads of 8 TMEM columns (t0.., t1.., t2.., t3.., the warp's 32 lanes)
 // behind one wait: one round trip to tensor memory instead of four.
 __device__ __forceinline__ void tmem_ld8x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, float* a, float* b,
                                            float* c, float* d)
