@@ -97,9 +97,10 @@ struct LoopArgs {
 struct LoopShared {
     double red[8];  // grid sums of the deferred update reduction (and the first)
     FF redf[8];     // grid sums of the last grid_reduce
+    float ws[32][8];  // warp sums of the block reduction in grid_reduce / grid_arrive_parts
     double ss, gg, J, beta;
-    FF q1, q2, t;   // line-search scalars, float-float: they sit on the critical path
-    float beta_f, t_f;
+    FF q1, q2, tb[2];  // line-search scalars, float-float: they sit on the critical path
+    float beta_f;
     int restart, ok;
     unsigned long long prof[kProf], tmark;
 };
@@ -184,24 +185,47 @@ __device__ __forceinline__ bool grid_arrive_wait(unsigned* counter, unsigned tar
     }
 }
 
+// The block's partials of K values to slot `slot` and the arrival: each
+// warp sums its lanes in FP32, then warp k sums value k over the warps in
+// float-float (the trees of block_partial) and stores it; thread 0 arrives
+// after a named barrier of those warps (its release covers their stores) and
+// waits.  S.ws is read only between this call's first and last barriers.
+template <int K>
+__device__ __forceinline__ void block_publish(float (&v)[K], float2* parts, int slot, unsigned seq, LoopShared& S,
+                                              unsigned* counter, unsigned* abort_word, int* err,
+                                              unsigned long long limit_ns)
+{
+    static_assert(K >= 1 && K <= 8, "one warp per value");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) S.ws[warp][k] = v[k];
+    __syncthreads();
+    if (warp < K) {
+        const int nw = (blockDim.x + 31) >> 5;
+        const FF bt = warp_sum_ff(FF{lane < nw ? S.ws[lane][warp] : 0.f, 0.f});
+        if (lane == 0) parts[(slot + warp) * kMaxParts + blockIdx.x] = make_float2(bt.hi, bt.lo);
+        if constexpr (K > 1) asm volatile("bar.sync 2, %0;" ::"r"(32 * K) : "memory");
+        if (threadIdx.x == 0) S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err, limit_ns) ? 1 : 0;
+    }
+    __syncthreads();
+}
+
 // Block partials of K values to slot `slot`, the synchronisation, then the
 // grid totals as float-float pairs in S.redf, readable by every thread on
-// return.  seq
-// counts the synchronisations of the launch (the same in every thread).
+// return.  seq counts the synchronisations of the launch (the same in every
+// thread).
 template <int K>
 __device__ __forceinline__ bool grid_reduce(float (&v)[K], float2* parts, int slot, unsigned& seq, LoopShared& S,
                                             unsigned* counter, unsigned* abort_word, int* err,
                                             unsigned long long limit_ns)
 {
-    FF bt[K];
-    block_partial<K>(v, bt);  // ends with __syncthreads(): the block's writes precede thread 0
     ++seq;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err, limit_ns) ? 1 : 0;
-    }
-    __syncthreads();
+    block_publish<K>(v, parts, slot, seq, S, counter, abort_word, err, limit_ns);
     if (!S.ok) return false;
     const int warp = threadIdx.x >> 5;
     if (warp < K) {
@@ -220,15 +244,8 @@ __device__ __forceinline__ bool grid_arrive_parts(float (&v)[K], float2* parts, 
                                                   LoopShared& S, unsigned* counter, unsigned* abort_word, int* err,
                                                   unsigned long long limit_ns)
 {
-    FF bt[K];
-    block_partial<K>(v, bt);
     ++seq;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) parts[(slot + k) * kMaxParts + blockIdx.x] = make_float2(bt[k].hi, bt[k].lo);
-        S.ok = grid_arrive_wait(counter, seq * gridDim.x, abort_word, err, limit_ns) ? 1 : 0;
-    }
-    __syncthreads();
+    block_publish<K>(v, parts, slot, seq, S, counter, abort_word, err, limit_ns);
     return S.ok != 0;
 }
 
@@ -856,6 +873,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
     constexpr int RX2 = G::FOURSTEP ? 1 : 2;
     const bool prof = blockIdx.x == 0;
     unsigned seq = 0;
+    float t_f = 0.f;  // the current line-search step, the same in every thread
     if (threadIdx.x == 0) {
         S.ss = A.scal[S_SS];
         for (int i = 0; i < kProf; ++i) S.prof[i] = 0;
@@ -970,36 +988,39 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
                 phase_rows<MC, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, beta, restart, acc);
             mark(2);
             if (!grid_reduce<4>(acc, A.parts, L_C, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
+            // every thread forms t1 from the totals (no broadcast, no barrier);
+            // thread 0 keeps q1, q2 and t1 for the next steps
+            const FF t1 = cgd::ls_next_ff(FF{0.f, 0.f}, S.redf[0], S.redf[3], S.redf[1], S.redf[2]);
+            t_f = t1.hi + t1.lo;
             if (threadIdx.x == 0) {
                 S.q1 = S.redf[0];
                 S.q2 = S.redf[3];
-                S.t = cgd::ls_next_ff(FF{0.f, 0.f}, S.q1, S.q2, S.redf[1], S.redf[2]);
-                S.t_f = S.t.hi + S.t.lo;
+                S.tb[0] = t1;
             }
-            __syncthreads();
             mark(3);
         }
         // ---- D, E: majorize-minimize steps at t1 and t2
 #pragma unroll 1
         for (int j = 0; j < 2; ++j) {
             float acc[2] = {0.f, 0.f};
-            phase_ls<MC>(A.reg, R, cf, cd, fbuf, S.t_f, acc);
+            phase_ls<MC>(A.reg, R, cf, cd, fbuf, t_f, acc);
             mark(4 + 2 * j);
             if (!grid_reduce<2>(acc, A.parts, j == 0 ? L_D : L_E, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
-            if (threadIdx.x == 0) {
-                S.t = cgd::ls_next_ff(S.t, S.q1, S.q2, S.redf[0], S.redf[1]);
-                S.t_f = S.t.hi + S.t.lo;
-            }
-            __syncthreads();
+            // t2 from t1 (tb[0] -> tb[1]), then t3 from t2 (tb[1] -> tb[0]),
+            // in every thread; the step read and the step written never share
+            // a slot
+            const FF tn = cgd::ls_next_ff(S.tb[j], S.q1, S.q2, S.redf[0], S.redf[1]);
+            t_f = tn.hi + tn.lo;
+            if (threadIdx.x == 0) S.tb[1 - j] = tn;
             mark(5 + 2 * j);
         }
         // ---- A: step, gradient, row FFTs of g for the next iteration
         {
             float a[kUpdVals] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (rx2)
-                phase_update<MC, false, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+                phase_update<MC, false, RX2>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, t_f, k + 1 < A.iters, a);
             else
-                phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, S.t_f, k + 1 < A.iters, a);
+                phase_update<MC, false, 1>(A, R, fbuf, stw, cf, cd, cRes, cD, cg, cTd, t_f, k + 1 < A.iters, a);
             mark(8);
             if (!grid_arrive_parts<kUpdVals>(a, A.parts, L_A, seq, S, A.counter, A.abort_word, A.err, A.wait_ns)) return;
             mark(9);
@@ -1018,7 +1039,7 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
             if (blockIdx.x == 0) {  // the last iteration's line-search scalars
                 A.scal[S_Q1] = ff_to_double(S.q1);
                 A.scal[S_Q2] = ff_to_double(S.q2);
-                A.scal[S_T3] = ff_to_double(S.t);
+                A.scal[S_T3] = ff_to_double(S.tb[0]);
             }
         }
         __syncthreads();
