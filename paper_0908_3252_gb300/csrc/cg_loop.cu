@@ -718,9 +718,45 @@ __device__ __forceinline__ void phase_update(const LoopArgs& A, const Rows& R, f
 
 // ---------------------------------------------------------------- phase C
 
+// d = -g + beta d_old on the cached rows, by the nthr threads tid = 0 ..
+// nthr - 1 (N <= 2 nthr: 256 threads at M = 1024, where N <= 512, and 512
+// threads up to N = 1024).  The halo rows' g comes from their owners via L2:
+// those loads go first, so their latency overlaps the own rows.
+__device__ __forceinline__ void direction_rows(const float2* gglob, const Rows& R, float2* cd, const float2* cg,
+                                               float beta, bool restart, int tid, int nthr)
+{
+    const int N = R.N;
+    const bool up = R.hlo < R.R0, dn = R.hhi >= R.R0 + R.nown;
+    constexpr int KH = 2;
+    float2 hu[KH], hd[KH];
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+        const int m = tid + k * nthr;
+        hu[k] = up && m < N ? __ldcg(gglob + (int64_t)R.hlo * N + m) : make_float2(0.f, 0.f);
+        hd[k] = dn && m < N ? __ldcg(gglob + (int64_t)R.hhi * N + m) : make_float2(0.f, 0.f);
+    }
+    float2* own = cd + R.cache(R.R0);
+    for (int e = tid; e < R.nown * N; e += nthr) own[e] = fftd::new_direction(cg[e], own[e], beta, restart);
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+        const int m = tid + k * nthr;
+        if (m < N) {
+            if (up) {
+                float2& v = cd[R.cache(R.hlo) + m];
+                v = fftd::new_direction(hu[k], v, beta, restart);
+            }
+            if (dn) {
+                float2& v = cd[R.cache(R.hhi) + m];
+                v = fftd::new_direction(hd[k], v, beta, restart);
+            }
+        }
+    }
+}
+
 // Row IFFTs of Y (in X) -> T d of the own rows, RX * RPC rows at a time; the
-// new direction on every cached row; the four sums of the first line-search
-// step.
+// new direction on every cached row (at M = 1024 with at most four own rows,
+// by the eight warps the row IFFTs leave idle, meanwhile); the four sums of
+// the first line-search step.
 template <int MC, int RX>
 __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, float2* fbuf, const float2* stw,
                                            const float2* cf,
@@ -729,6 +765,7 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 {
     using G = Geo<MC>;
     const int N = R.N;
+    const bool dir_aside = G::FOURSTEP && R.nown <= 4;  // warps 8 .. 15 have no row to transform
     if constexpr (G::FOURSTEP) {
         // the split row IFFTs of Y, two warps a row (warp 2 q + h takes the
         // elements 2 k + h), eight rows at a time: T g = u_0 + w1024^(-m) u_1
@@ -751,6 +788,8 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
                     for (int n2 = 0; n2 < 16; ++n2)
                         area[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
                 }
+            } else if (dir_aside && warp >= 8) {
+                direction_rows(A.g, R, cd, cg, beta, restart, (int)threadIdx.x - 256, kLoopThreads - 256);
             }
             __syncthreads();
             if (active && !h) {
@@ -791,37 +830,10 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
         }
         __syncthreads();
     }
-    // d = -g + beta d_old on the cached rows.  The halo rows' g comes from
-    // their owners via L2: those loads go first (columns tid and tid + 512;
-    // N <= 1024), so their latency overlaps the own rows.
-    {
-        const bool up = R.hlo < R.R0, dn = R.hhi >= R.R0 + R.nown;
-        float2 hu[2], hd[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int m = threadIdx.x + k * kLoopThreads;
-            hu[k] = up && m < N ? __ldcg(A.g + (int64_t)R.hlo * N + m) : make_float2(0.f, 0.f);
-            hd[k] = dn && m < N ? __ldcg(A.g + (int64_t)R.hhi * N + m) : make_float2(0.f, 0.f);
-        }
-        float2* own = cd + R.cache(R.R0);
-        for (int e = threadIdx.x; e < R.nown * N; e += kLoopThreads)
-            own[e] = fftd::new_direction(cg[e], own[e], beta, restart);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int m = threadIdx.x + k * kLoopThreads;
-            if (m < N) {
-                if (up) {
-                    float2& v = cd[R.cache(R.hlo) + m];
-                    v = fftd::new_direction(hu[k], v, beta, restart);
-                }
-                if (dn) {
-                    float2& v = cd[R.cache(R.hhi) + m];
-                    v = fftd::new_direction(hd[k], v, beta, restart);
-                }
-            }
-        }
+    if (!dir_aside) {
+        direction_rows(A.g, R, cd, cg, beta, restart, threadIdx.x, kLoopThreads);
+        __syncthreads();
     }
-    __syncthreads();
     ls_rows_any<true>(A.reg, R, cf, cd, cRes, cD, cTd, 0.f, acc, reinterpret_cast<float*>(fbuf),
                       ls_planes_fit(A.reg, R.nown * N, G::FBUF));
 }
