@@ -451,17 +451,30 @@ __device__ __forceinline__ void cols_split(float2* X, int n_in, int x0, const fl
         r = make_float2(r.x * hs[q], r.y * hs[q]);
     }
     inv512(x, area, t16, lane);
+    // y[n] = u_0[n] + w1024^(-n) u_1[n] (n = lane + 32 n2), the two warps of
+    // the column a half each: warp 0 the rows n < 256, warp 1 the rest.  Each
+    // first hands the other its half of the operands (warp 1 through its
+    // area, warp 0 through the column's upper half), then a barrier of the
+    // pair (named barrier 8 + cc)
+    float2* col = fbuf + cc * LDF;
+    float2* a1 = fbuf + cc * LDF + WA;
     if (h) {
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2)
-            area[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
-    }
-    __syncthreads();
-    if (!h) {
-        const float2* other = fbuf + cc * LDF + WA;
-        float2* col = fbuf + cc * LDF;
+        for (int n2 = 0; n2 < 8; ++n2) a1[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
+    } else {
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) col[lane + 32 * n2] = freg::add(x[freg::bitrev4(n2)], other[lane + 32 * n2]);
+        for (int n2 = 8; n2 < 16; ++n2) col[lane + 32 * n2] = x[freg::bitrev4(n2)];
+    }
+    asm volatile("bar.sync %0, 64;" ::"r"(8 + cc) : "memory");
+    if (h) {
+#pragma unroll
+        for (int n2 = 8; n2 < 16; ++n2) {
+            const int n = lane + 32 * n2;
+            col[n] = freg::add(col[n], cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane])));
+        }
+    } else {
+#pragma unroll
+        for (int n2 = 0; n2 < 8; ++n2) col[lane + 32 * n2] = freg::add(x[freg::bitrev4(n2)], a1[lane + 32 * n2]);
     }
     __syncthreads();
 #pragma unroll
@@ -782,26 +795,34 @@ __device__ __forceinline__ void phase_rows(const LoopArgs& A, const Rows& R, flo
 #pragma unroll
                 for (int q2 = 0; q2 < 16; ++q2) x[freg::bitrev4(q2)] = __ldcg(yr + 32 * q2);
                 inv512(x, area, stw, lane);
+                // T g[m] = u_0[m] + w1024^(-m) u_1[m], the row's two warps a
+                // half each (warp 0 the columns m < 256), after handing each
+                // other their halves of the operands and a barrier of the pair
+                const float2* wn = stw + 512;
+                float2* a0 = fbuf + (warp & ~1) * G::WA;
+                float2* a1 = a0 + G::WA;
                 if (h) {
-                    const float2* wn = stw + 512;
 #pragma unroll
-                    for (int n2 = 0; n2 < 16; ++n2)
-                        area[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
+                    for (int n2 = 0; n2 < 8; ++n2)
+                        a1[lane + 32 * n2] = cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane]));
+                } else {
+#pragma unroll
+                    for (int n2 = 8; n2 < 16; ++n2) a0[lane + 32 * n2] = x[freg::bitrev4(n2)];
+                }
+                asm volatile("bar.sync %0, 64;" ::"r"(8 + (warp >> 1)) : "memory");
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int n2 = h ? 8 + i : i;
+                    const int m = lane + 32 * n2;
+                    if (m < N) {
+                        const float2 tg = h ? freg::add(a0[m], cmul(x[freg::bitrev4(n2)], conjf2(wn[n2 * 32 + lane])))
+                                            : freg::add(x[freg::bitrev4(n2)], a1[m]);
+                        float2& td = cTd[q * N + m];
+                        td = fftd::new_direction(tg, td, beta, restart);
+                    }
                 }
             } else if (dir_aside && warp >= 8) {
                 direction_rows(A.g, R, cd, cg, beta, restart, (int)threadIdx.x - 256, kLoopThreads - 256);
-            }
-            __syncthreads();
-            if (active && !h) {
-                const float2* other = area + G::WA;
-#pragma unroll
-                for (int n2 = 0; n2 < 16; ++n2) {
-                    const int m = lane + 32 * n2;
-                    if (m < N) {
-                        float2& td = cTd[q * N + m];
-                        td = fftd::new_direction(freg::add(x[freg::bitrev4(n2)], other[m]), td, beta, restart);
-                    }
-                }
             }
             __syncthreads();
         }
