@@ -442,7 +442,10 @@ __device__ __forceinline__ void cols_split(float2* X, int n_in, int x0, const fl
 #pragma unroll
         for (int j = 0; j < 16; ++j) x[j] = h ? cmul(col[32 * j], wn[j * 32 + lane]) : col[32 * j];
     }
-    __syncthreads();  // the columns are in registers: their areas become the exchange areas
+    // the column is in both warps' registers: warp 0's exchange area, which
+    // overlaps the staged column (warp 1's lies past it), may be overwritten
+    // once the pair has passed (named barrier 8 + cc)
+    asm volatile("bar.sync %0, 64;" ::"r"(8 + cc) : "memory");
     float2* area = fbuf + cc * LDF + h * WA;
     fwd512(x, area, t16, lane);
 #pragma unroll
@@ -992,7 +995,9 @@ __global__ void __launch_bounds__(kLoopThreads, 1) k_cg_loop(LoopArgs A)
                 fftd::cols_group<MC, G::CBPT2, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr);
             else
                 fftd::cols_group<MC, G::CBPT, 1>(A.X, N, N, x0, cpc, cpc, A.fp, stw, A.Chat, fbuf, nullptr);
-            __syncthreads();  // the next group refills fbuf
+            // the next group refills fbuf (after the last one, the
+            // synchronisation below starts with a block barrier)
+            if (gi + (int)gridDim.x < col_groups) __syncthreads();
         }
         mark(0);
         // the synchronisation; meanwhile warps 1..6 sum the previous update's
