@@ -37,9 +37,9 @@
 // operands as its owner uses, so all copies of a pixel are bitwise equal.
 //
 // After each reduction one warp per value sums the per-block float-float
-// partials (same order in every block) and thread 0 derives the FP64
-// scalars; the other threads read FP32 copies from shared memory.  The
-// update's six sums are the exception: their partials are copied into shared
+// partials (same order in every block) and every thread forms the line-search
+// step from those totals in float-float arithmetic, so all blocks and threads
+// hold the same step bit for bit.  The update's six sums are the exception: their partials are copied into shared
 // memory during the next column pass and summed, with J and beta formed, at
 // that pass's synchronisation (deferred_parts_fetch, deferred_parts_sum).
 //
@@ -92,8 +92,10 @@ struct LoopArgs {
     int stall;                   // a test's injected stall (injected_stall())
 };
 
-// Loop scalars, one copy per block.  Thread 0 writes them between two
-// __syncthreads(); the FP64 values are used by thread 0 only.
+// Loop scalars, one copy per block.  Thread 0 writes them (the reductions'
+// totals: the warps that form them); every write is separated by a barrier
+// from the reads of the same slot, and the line-search steps alternate
+// between the two slots of tb.  The FP64 values are used by one thread only.
 struct LoopShared {
     double red[8];  // grid sums of the deferred update reduction (and the first)
     FF redf[8];     // grid sums of the last grid_reduce
@@ -155,9 +157,10 @@ __device__ __forceinline__ uint64_t gtimer()
 
 // ------------------------------------------------ grid-wide reductions
 //
-// A grid synchronisation is a reduction: thread 0 of every block writes the
-// block's K float-float partials, adds one to an arrival counter with a
-// release reduction (no return value awaited) and polls the counter with
+// A grid synchronisation is a reduction: warp k of every block writes the
+// block's float-float partial of value k, and thread 0, after a named barrier
+// of those warps, adds one to an arrival counter with a release reduction
+// (no return value awaited) and polls the counter with
 // acquire loads until all blocks of this synchronisation have arrived (the
 // counter grows monotonically during a launch: the n-th synchronisation
 // waits for n * gridDim.x).  Then one warp per value sums the partials of
