@@ -319,13 +319,17 @@ def _large_case(N, I, S, seed):
     return _LARGE[key]
 
 
-# (N, M, interleaves, samples): the M = 1024 loop (split 512-point column
-# and row FFTs, 4-row blocks, a last block with fewer rows), the M = 512 loop
-# (radix-4 passes, 4-row groups), and M = 2048 and 4096, whose row caches do
-# not fit a block: the solve falls back to the kernel graph, whose row and
-# column passes split each row and column into 2 or 4 warp-sized 1024-point
-# DFTs (N = 259 and 601 leave a partial last row group of those passes)
-LARGE_CASES = [(260, 1024, 3, 700, 21), (200, 512, 3, 500, 31), (520, 2048, 2, 400, 41),
+# (N, M, interleaves, samples, seed): the M = 1024 loop (split 512-point
+# column and row FFTs; N = 260 in 2-row blocks; N = 259 in 2-row blocks with
+# a last block of one row and two blocks without a column group; N = 511 in
+# 4-row blocks with a last block of three rows, so that some warp pairs of
+# the row passes have no row), the M = 512 loop (radix-4 passes, 4-row
+# groups), and M = 2048 and 4096, whose row caches do not fit a block: the
+# solve falls back to the kernel graph, whose row and column passes split
+# each row and column into 2 or 4 warp-sized 1024-point DFTs (N = 259 and 601
+# leave a partial last row group of those passes)
+LARGE_CASES = [(260, 1024, 3, 700, 21), (259, 1024, 3, 300, 53), (511, 1024, 2, 300, 57),
+               (200, 512, 3, 500, 31), (520, 2048, 2, 400, 41),
                (600, 4096, 2, 300, 43), (259, 2048, 3, 300, 49), (601, 4096, 2, 300, 47)]
 
 
