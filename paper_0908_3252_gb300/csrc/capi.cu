@@ -209,6 +209,7 @@ void free_plan(spirec_plan p)
     if (p->ev_s_ready) cudaEventDestroy(p->ev_s_ready);
     if (p->ev_sin_free) cudaEventDestroy(p->ev_sin_free);
     if (p->ev_traj_in) cudaEventDestroy(p->ev_traj_in);
+    if (p->hpin) cudaFreeHost(p->hpin);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -264,10 +265,25 @@ int tstop(spirec_plan p, cudaEvent_t e)
     return SPIREC_OK;
 }
 
+// The plan's pinned host words (made on first use) and the copy of the device
+// error word into the second, enqueued on the plan's stream; read with
+// pinned_flags after a synchronisation.
+int enqueue_flags(spirec_plan p)
+{
+    if (!p->hpin) SPIREC_CK(cudaMallocHost(reinterpret_cast<void**>(&p->hpin), 2 * sizeof(double)));
+    SPIREC_CK(cudaMemcpyAsync(reinterpret_cast<int*>(p->hpin + 1), p->dflag, sizeof(int), cudaMemcpyDeviceToHost,
+                              p->stream));
+    return SPIREC_OK;
+}
+
+int pinned_flags(spirec_plan p) { return *reinterpret_cast<const int*>(p->hpin + 1); }
+
 int read_device_flags(spirec_plan p, int* flags)
 {
-    SPIREC_CK(cudaMemcpyAsync(flags, p->dflag, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    int rc = enqueue_flags(p);
+    if (rc != SPIREC_OK) return rc;
     SPIREC_CK(cudaStreamSynchronize(p->stream));
+    *flags = pinned_flags(p);
     return SPIREC_OK;
 }
 
@@ -1128,17 +1144,18 @@ int spirec_solve(spirec_plan p, const float* x0, int32_t iters, float* x_out, do
     }
     Join j(p);
     if ((rc = solve_core(p, x0, false, iters)) != SPIREC_OK) return rc;
+    // every copy enqueued (the last J and the error word into the pinned
+    // words), then one synchronisation
     const size_t img = (size_t)p->N * p->N * sizeof(float2);
     SPIREC_CK(cudaMemcpyAsync(x_out, p->f[p->result_slot], img, cudaMemcpyDeviceToHost, p->stream));
-    double Jlast = 0.0;
-    SPIREC_CK(cudaMemcpyAsync(&Jlast, p->Jdev + iters, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     if (J_hist)
         SPIREC_CK(cudaMemcpyAsync(J_hist, p->Jdev, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost,
                                   p->stream));
+    if ((rc = enqueue_flags(p)) != SPIREC_OK) return rc;
+    SPIREC_CK(cudaMemcpyAsync(p->hpin, p->Jdev + iters, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     SPIREC_CK(cudaStreamSynchronize(p->stream));
-    int flags = 0;
-    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
-    if ((rc = flags_status(flags)) != SPIREC_OK) return rc;
+    if ((rc = flags_status(pinned_flags(p))) != SPIREC_OK) return rc;
+    const double Jlast = p->hpin[0];
     if (!isfinite(Jlast)) {
         set_error("criterion is not finite after %d iterations", iters);
         return SPIREC_ENUMERIC;
@@ -1300,9 +1317,8 @@ namespace spirec {
 namespace {
 int finish_host_call(spirec_plan p)
 {
-    SPIREC_CK(cudaStreamSynchronize(p->stream));
     int flags = 0, rc;
-    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;
+    if ((rc = read_device_flags(p, &flags)) != SPIREC_OK) return rc;  // one synchronisation
     return flags_status(flags);
 }
 }  // namespace

@@ -127,6 +127,10 @@ struct spirec_plan_s {
     float2* wpair;
     double* kstage;  // 2L: host trajectory staged on the device
     int* dflag;  // device error flag
+    // two pinned host words, made on first use: the last J of a host solve
+    // and (as an int) a copy of dflag, so that a host call's copies all go
+    // asynchronously and it synchronises once
+    double* hpin;
 
     float2* G;     // N x (2N-1)
     float* Chat;   // M x M real, transposed: Chat[kx*M + ky]
