@@ -150,3 +150,30 @@ def test_stall_mask_is_checked(sp):
     with pytest.raises(sp.SpirecError) as e:
         sp.spirec_inject_wait_stall(8)
     assert e.value.code == sp.SPIREC_EINVAL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("M", [0, 64])
+def test_non_finite_criterion_is_reported(sp, prec, M):
+    """Data with a NaN sample makes D, and so J, NaN; the host solve reads the
+    last J back with its other copies and reports SPIREC_ENUMERIC (NaN only
+    flows through arithmetic: no index or loop bound depends on data).  The
+    same plan then solves finite data to the oracle's result.  M = 0 takes
+    the plan's default size (the stand-alone kernels), M = 64 the persistent
+    loop."""
+    w = workload_ragged(N=24, I=2, S=150)
+    reg = w["reg"]
+    L = w["kx"].shape[0]
+    bad = w["s"].copy()
+    bad[L // 2] = np.complex64(complex(np.nan, 0.0))
+    with sp.Plan(w["N"], L, M, prec, None, w["kx"], w["ky"]) as p:
+        sp.spirec_set_reg(p.h, reg.lambda1, reg.alpha1, reg.lambda0, reg.alpha0, reg.kind)
+        sp.spirec_set_data(p.h, bad)
+        with pytest.raises(sp.SpirecError) as e:
+            sp.spirec_solve(p.h, None, 3, w["N"])
+        assert e.value.code == sp.SPIREC_ENUMERIC
+        sp.spirec_set_data(p.h, w["s"])
+        x, J = sp.spirec_solve(p.h, None, 3, w["N"])
+    xo, Jo, _ = O.solve(w["kx"], w["ky"], w["s"], reg, np.zeros((w["N"], w["N"])), 3)
+    tol = 1e-5 if prec == 0 else 1e-3
+    assert rel(x, xo) < tol and rel(J, Jo) < tol
