@@ -198,6 +198,9 @@ __device__ __forceinline__ void unreverse32(float2 (&x)[32])
 constexpr int kSplitWarps = 8;
 constexpr int kSplitThreads = 32 * kSplitWarps;
 constexpr int kSplitCtasPerSm = 16 / kSplitWarps;
+// The inverse row pass has no staging buffer (76 KB of shared memory a CTA),
+// so three CTAs fit an SM; its DFTs fit 85 registers a thread without spills.
+constexpr int kSplitInvCtasPerSm = 3;
 // Warp area of the column pass: 32 x 33 for the four-step DFT plus 2, so that
 // the S areas of one column start 8 (S = 4) or 4 (S = 2) float2 banks after
 // those of the previous column, and the combine step, whose neighbouring
@@ -461,7 +464,7 @@ k_rows_fwd_split(const float2* in, int ld_in, int n_in, int rows, float2* X, con
 // inverse 1024-point DFT u_r, and out[m] = sum_r w_M^(-r m) u_r[m mod 1024]
 // in a fixed order; with dotx the same grid sum and scalars as k_rows_inv.
 template <int S, int MODE>
-__global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
+__global__ void __launch_bounds__(kSplitThreads, kSplitInvCtasPerSm)
 k_rows_inv_split(const float2* X, int rows, float2* out, int n_out, const float2* __restrict__ tw,
                  const float2* dotx, CgPass c, int dot_scalar)
 {
@@ -885,7 +888,7 @@ int launch_rows_inv(spirec_plan p, float2* out, int mode, const float2* dotx, co
     const CgPass c = cg ? *cg : plain_pass(p, P_MISC, p->counters + C_MISC);
     int sms = 0;
     if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
-    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c, kSplitCtasPerSm * sms});
+    return with_size(M, LaunchRowsInv{p, out, mode, dotx, dot_scalar, blocks, s, c, kSplitInvCtasPerSm * sms});
 }
 
 int launch_toeplitz(spirec_plan p, const float2* x, float2* Tx, int dot_scalar)
