@@ -245,13 +245,16 @@ __device__ __forceinline__ float2 combine_output(const float2* u, int stride, in
 template <int S>
 __host__ __device__ constexpr int cols_split_ld() { return 512 * S + (S == 4 ? 8 : 4); }
 
-// Shared memory of k_cols_split<S>: the staged columns, the warps' areas,
-// the 32 x 32 twiddles.
+// Shared memory of k_cols_split<S>: the warps' areas, whose start the staged
+// columns share (they are dead once every warp has folded its column into
+// registers), then the 32 x 32 twiddles: 76 KB, three CTAs an SM.
 template <int S>
 constexpr size_t cols_split_smem()
 {
-    return ((size_t)(kSplitWarps / S) * cols_split_ld<S>() + kSplitWarps * kSplitArea + 1024) * sizeof(float2);
+    const size_t stage = (size_t)(kSplitWarps / S) * cols_split_ld<S>(), areas = (size_t)kSplitWarps * kSplitArea;
+    return ((stage > areas ? stage : areas) + 1024) * sizeof(float2);
 }
+constexpr int kSplitColCtasPerSm = 3;
 
 // The Toeplitz column pass for M = 1024 S (S = 2, 4) when at most M/2 rows
 // are nonzero and at most M/2 are kept (n_in, n_out <= M/2, always the case
@@ -264,13 +267,14 @@ constexpr size_t cols_split_smem()
 // order.  8 / S columns a group, staged from X as row pieces of 8 / S
 // neighbouring columns; CTAs loop over the groups.  tw[e] = w_M^e.
 template <int S>
-__global__ void __launch_bounds__(kSplitThreads, kSplitCtasPerSm)
+__global__ void __launch_bounds__(kSplitThreads, kSplitColCtasPerSm)
 k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, const float* __restrict__ Chat)
 {
     constexpr int M = 1024 * S, C = kSplitWarps / S, H = M / 2, LDS = cols_split_ld<S>();
+    static_assert(C * LDS <= kSplitWarps * kSplitArea, "the staged columns fit in the areas");
     extern __shared__ float2 sm[];
-    float2* stage = sm;
-    float2* areas = stage + C * LDS;
+    float2* areas = sm;
+    float2* stage = sm;  // shares the areas' start
     float2* t2 = areas + kSplitWarps * kSplitArea;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cc = warp / S, r = warp - cc * S;
@@ -282,19 +286,16 @@ k_cols_split(float2* X, int n_in, int n_out, const float2* __restrict__ tw, cons
             stage[c * LDS + y] = y < n_in ? __ldcg(X + (int64_t)y * M + x0 + c) : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // the warp's folded, twiddled input, through its area (no register
-        // array holds the S/2 loads of each element)
-        float2* area = areas + warp * kSplitArea;
+        // the warp's folded, twiddled input into registers; then every warp
+        // has read the stage, and the areas may overwrite it
+        float2 x[32];
         {
             const float2* col = stage + cc * LDS;
-#pragma unroll 8
-            for (int m = lane; m < 1024; m += 32) area[m] = fold_input<S>(col, m, r, tw);
-        }
-        __syncwarp();
-        float2 x[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = area[lane + 32 * j];
-        __syncwarp();
+            for (int j = 0; j < 32; ++j) x[j] = fold_input<S>(col, lane + 32 * j, r, tw);
+        }
+        __syncthreads();
+        float2* area = areas + warp * kSplitArea;
         dft1024_warp<false>(x, area, t2, lane);  // X[S (lane + 32 k2) + r] in x[bitrev5(k2)]
         unreverse32(x);
         {
@@ -758,7 +759,7 @@ struct LaunchCols {
                 int sms = 0;
                 if (device_sms(&sms) != SPIREC_OK) return SPIREC_ECUDA;
                 const int groups = MC / (kSplitWarps / S);
-                const int cap = kSplitCtasPerSm * sms;
+                const int cap = kSplitColCtasPerSm * sms;
                 k_cols_split<S><<<groups < cap ? groups : cap, kSplitThreads, cols_split_smem<S>(), p->stream>>>(
                     p->X, n_in, n_out, p->twiddle, p->Chat);
                 SPIREC_CK(cudaGetLastError());
